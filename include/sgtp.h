@@ -1,0 +1,255 @@
+/*
+ * sgtp.h -- C ABI of the B300 (sm_103a) SGTP best-response engine.
+ *
+ * SGTP (Li et al., "SGTP: Sampling-based Game-Theoretic Planning for
+ * Real-Time Multi-Vehicle Autonomous Racing") plans by iterative best
+ * response (Alg. 1).  Each best response samples K control sequences
+ * around a nominal one (Sec. II, Algorithm Formulation), rolls them through
+ * a kinematic bicycle model, scores them with the tracking cost (Eq. ctrack)
+ * plus the game-aware cost (Eqs. game_cost, c_contest, c_long, c_block,
+ * c_safety, allc), checks track boundaries and collisions (Eqs.
+ * selection-boundary, selection-vehicle) and selects the lowest-cost
+ * feasible sample (Eq. selection), falling back to the least violation.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All numeric arrays are float32, row-major and contiguous.  Arrays
+ *    passed to the compute calls are DEVICE pointers owned by the caller;
+ *    only sgtp_track_create* take HOST arrays.
+ *  - States are [x, y, psi, v] (m, m, rad, m/s); controls are [a, delta]
+ *    (m/s^2, rad) (Sec. II, Preliminaries).  Trajectories include tau = 0,
+ *    so a trajectory of horizon T has T+1 states.
+ *  - Lateral offset d > 0 is left of the raceline's direction of travel.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Compute calls only enqueue work: they return after launch-time
+ *    validation, and device-side faults (a wait that timed out) are written
+ *    to the caller's `status_dev` word, never by aborting the process.
+ *  - A return of SGTP_E_INVALID means nothing was launched.  The text of the
+ *    last error of the calling thread is returned by sgtp_last_error().
+ *  - "No feasible sample" is not an error: it is reported per best response
+ *    (any_feasible = 0) and the least-violation sample is returned
+ *    (Sec. III-B, fallback).
+ *  - Noise: sample k of a best response draws, at step tau, the Philox4x32-10
+ *    block with key (seed lo32, seed hi32) and counter
+ *    (k, (tau >> 1) | stream << 31, agent | round << 16, race); words 0,1
+ *    serve even tau and words 2,3 odd tau.  A word w becomes the uniform
+ *    u = ((w >> 9) + 0.5) * 2^-23 and a pair (u1, u2) the normals
+ *    z_a = sqrt(-2 ln u1) cos(2 pi u2), z_delta = sqrt(-2 ln u1) sin(2 pi u2)
+ *    (Box-Muller).  eps = (sigma_a z_a, sigma_delta z_delta).  stream is 0
+ *    for the plain Gaussian sampler.
+ *  - Workspace: calls that need device scratch take (workspace, bytes); the
+ *    caller allocates it (any device allocation, 256-byte aligned) and may
+ *    reuse it across calls on the same stream.  The library never allocates
+ *    inside a compute call.
+ */
+#ifndef SGTP_H
+#define SGTP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t sgtp_status;
+enum {
+    SGTP_OK = 0,
+    SGTP_E_INVALID = 1,   /* bad argument; nothing launched                         */
+    SGTP_E_CUDA = 2,      /* a CUDA runtime call failed (text in sgtp_last_error)   */
+    SGTP_E_NOMEM = 3,     /* setup-time allocation failed                           */
+    SGTP_E_TIMEOUT = 4,   /* a device-side wait ran past its limit and gave up      */
+    SGTP_E_DEVICE = 5,    /* a device-side check failed (bad index, bad state)      */
+    SGTP_E_UNSUPPORTED = 6
+};
+
+/* Limits of this build. */
+#define SGTP_MAX_AGENTS 16        /* vehicles per race (so <= 15 opponents)         */
+#define SGTP_MAX_T 128            /* horizon steps                                  */
+#define SGTP_MAX_K (1 << 30)      /* samples per best response                      */
+
+/* Planner parameters (Sec. IV-B names).  Passed by host pointer, copied at
+ * call time. */
+typedef struct sgtp_params {
+    float dt;                     /* step [s]                                        */
+    float wheelbase;              /* bicycle wheelbase [m]                           */
+    float a_min, a_max;           /* acceleration limits of Pi_U [m/s^2]             */
+    float delta_max;              /* |delta| <= delta_max of Pi_U [rad]              */
+    float v_min, v_max;           /* speed clamp of the model [m/s]                  */
+    float sigma_a, sigma_delta;   /* std-dev of the Gaussian perturbation (Sec. II)  */
+    float Q[4];                   /* state weights over (x, y, psi, v) (Eq. ctrack)  */
+    float R[2];                   /* control weights over (a, delta)                 */
+    float S[2];                   /* control-rate weights over (a, delta)            */
+    float w_game;                 /* weight of the game-aware cost (Eq. allc)        */
+    float w_contest, w_long, w_block, w_safety;  /* Eqs. c_contest .. c_safety      */
+    float s_contest;              /* contest range [m]                               */
+    float s_role;                 /* blocking role gap [m]                           */
+    float mu_tail;                /* tail share of the horizon for blocking          */
+    float g_safe;                 /* desired separation [m]                          */
+    float eps_alpha;              /* epsilon of the adaptive weight alpha            */
+    float m_bd;                   /* required boundary clearance [m]                 */
+    float d_col;                  /* collision distance [m]                          */
+} sgtp_params;
+
+/* ------------------------------------------------------------------ */
+/* Raceline G (Sec. II, Preliminaries)                                  */
+/* ------------------------------------------------------------------ */
+typedef struct sgtp_track sgtp_track;   /* opaque, device resident, library owned */
+
+/* Build a device raceline from HOST arrays.  xr: N x 4 waypoint states
+ * (x, y, psi, v^r) of a CLOSED loop (waypoint N-1 joins waypoint 0); wl, wr:
+ * N left/right widths (> 0).  3 <= N <= 1,048,576.  The library copies the
+ * arrays, then a device kernel computes, per segment j, the chord to the
+ * next waypoint, its squared-length inverse, the cumulative arc length s_j
+ * and the width/heading/speed increments used by the linear reference maps
+ * x^r(s), w^L(s), w^R(s).  Blocks until the track is ready.  On success
+ * *out owns device memory released by sgtp_track_destroy. */
+sgtp_status sgtp_track_create(const float *xr, const float *wl, const float *wr, int32_t N, void *stream,
+                              sgtp_track **out);
+
+/* Several racelines in one object (independent races of a batch): track t
+ * holds waypoints offsets[t] .. offsets[t+1]-1 of the concatenated arrays.
+ * offsets has n_tracks+1 HOST entries, offsets[0] = 0. */
+sgtp_status sgtp_track_create_many(const float *xr, const float *wl, const float *wr, const int32_t *offsets,
+                                   int32_t n_tracks, void *stream, sgtp_track **out);
+
+void sgtp_track_destroy(sgtp_track *trk);
+
+/* Host query: number of tracks, waypoints of track t, and its length (m). */
+sgtp_status sgtp_track_info(const sgtp_track *trk, int32_t track_id, int32_t *n_tracks, int32_t *N, float *length);
+
+/* ------------------------------------------------------------------ */
+/* One best response (Alg. 1, one pass of the vehicle loop)             */
+/* ------------------------------------------------------------------ */
+
+/* Device scratch needed by sgtp_rollout_costs / sgtp_best_response. */
+size_t sgtp_br_workspace_bytes(int32_t n_opp, int32_t T);
+
+/* Per-sample cost, feasibility and violation of the K candidates of one
+ * best response (Alg. 1: sampling, cost, feasibility indicator steps).
+ *   x0        [4]                current state x_{i,t}
+ *   u_nom     [T x 2]            nominal controls U-bar (Sec. II)
+ *   vref_scale                   scale of the agent's reference speed (1 = raceline)
+ *   opp       [n_opp x (T+1) x 4] fixed opponent predictions (may be NULL if n_opp = 0)
+ *   game_on   0: cost = c_track only (the initial round of Alg. 1)
+ *   cost, feasible, violation [K]  c (Eq. allc), h = b*o (Eq. selection), nu
+ * Optional outputs (NULL to skip): states [K x (T+1) x 4], frenet
+ * [K x (T+1) x 2] = (unwrapped progress s, lateral offset d) and controls
+ * [K x T x 2] (the clipped samples).  0 <= n_opp <= SGTP_MAX_AGENTS-1,
+ * 1 <= T <= SGTP_MAX_T, 1 <= K <= SGTP_MAX_K. */
+sgtp_status sgtp_rollout_costs(const sgtp_track *trk, int32_t track_id, const sgtp_params *p, const float *x0,
+                               const float *u_nom, float vref_scale, const float *opp, int32_t n_opp, int32_t T,
+                               int32_t K, uint64_t seed, uint32_t race, uint32_t agent, uint32_t round,
+                               int32_t game_on, float *cost, uint8_t *feasible, float *violation, float *states,
+                               float *frenet, float *controls, void *workspace, size_t workspace_bytes,
+                               void *stream);
+
+/* The full best response: the same K candidates, then the selection of
+ * Eq. selection with the least-violation fallback (ties to the lowest k),
+ * and the re-rolled winner.
+ *   k_star [1] (int32), u_star [T x 2], xi_star [(T+1) x 4], any_feasible [1]
+ * All outputs are device pointers written on `stream`. */
+sgtp_status sgtp_best_response(const sgtp_track *trk, int32_t track_id, const sgtp_params *p, const float *x0,
+                               const float *u_nom, float vref_scale, const float *opp, int32_t n_opp, int32_t T,
+                               int32_t K, uint64_t seed, uint32_t race, uint32_t agent, uint32_t round,
+                               int32_t game_on, int32_t *k_star, float *u_star, float *xi_star,
+                               int32_t *any_feasible, void *workspace, size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* The planning call (Alg. 1) and batches of independent races          */
+/* ------------------------------------------------------------------ */
+
+/* Launch shape of the persistent kernel.  Any zero field takes the
+ * library's choice.  Every shape gives bit-identical results. */
+typedef struct sgtp_launch_opts {
+    int32_t block;                /* threads per CTA: 64, 128, 256 or 512            */
+    int32_t samples_per_thread;   /* 1, 2 or 4                                       */
+    int32_t ctas_per_sm;          /* resident CTAs per SM (<= occupancy limit)       */
+    int32_t window;               /* track segments staged in shared memory per CTA  */
+    int64_t wait_timeout_ns;      /* limit of each device-side wait (default 1 s)    */
+    int32_t debug_flags;          /* SGTP_DEBUG_*; 0 in production                   */
+} sgtp_launch_opts;
+
+/* Fault injection for tests: CTA 0 never arrives at the grid barrier, so
+ * every other CTA's wait runs out and the call reports SGTP_E_TIMEOUT in
+ * status_dev.  No wait in the library is unbounded. */
+#define SGTP_DEBUG_SKIP_BARRIER_ARRIVAL 1
+
+/* Description of one race of a batch (HOST array given to
+ * sgtp_batch_create).  Arrays of a batch concatenate the races' agents:
+ * race r owns agents agent_offset .. agent_offset + n_v - 1. */
+typedef struct sgtp_race {
+    int32_t track_id;             /* track of the sgtp_track object                  */
+    int32_t n_v;                  /* vehicles, 1 .. SGTP_MAX_AGENTS                  */
+    int32_t T;                    /* horizon, 1 .. SGTP_MAX_T                        */
+    int32_t ego;                  /* ego vehicle index within the race               */
+    uint32_t race_tag;            /* the `race` word of the noise counter            */
+} sgtp_race;
+
+typedef struct sgtp_batch sgtp_batch;   /* opaque, device resident, library owned */
+
+/* Prepare a batch: validates the races, lays out the ragged arrays and
+ * uploads the race table.  K samples per best response and L IBR rounds
+ * are common to the batch.  Array sizes of sgtp_batch_plan follow from
+ * sgtp_batch_sizes.  Blocks until the table is on the device. */
+sgtp_status sgtp_batch_create(const sgtp_track *trk, const sgtp_race *races, int32_t n_races, int32_t K,
+                              int32_t L, sgtp_batch **out);
+void sgtp_batch_destroy(sgtp_batch *b);
+
+/* Element counts of the batch arrays (any pointer may be NULL):
+ *   agents  = sum n_v                     (X0 rows, vref_scale entries)
+ *   u_elems = sum n_v * T * 2             (U_io)
+ *   xi_elems= sum n_v * (T+1) * 4         (xi_out)
+ *   ks      = sum ((L+1) * n_v + 1)       (k_star_out, round-major per race)
+ *   workspace_bytes                       (device scratch of sgtp_batch_plan)
+ * Race r's slices start at the prefix sums of these counts in race order. */
+sgtp_status sgtp_batch_sizes(const sgtp_batch *b, int64_t *agents, int64_t *u_elems, int64_t *xi_elems,
+                             int64_t *ks, size_t *workspace_bytes);
+
+/* Plan every race of the batch in ONE persistent cooperative launch
+ * (Alg. 1 per race):
+ *   round 0: every vehicle answers the others' nominal rollouts (controls
+ *            U_io, clipped) with w_game off -- the initialisation of Alg. 1
+ *            with distance-based (collision-check) avoidance only;
+ *   rounds 1..L: Jacobi best responses to the previous round;
+ *   then one extra ego best response (round tag L+1).
+ * After every best response the vehicle's nominal controls become the
+ * selected ones.  Outputs: U_io (warm start for the next call), xi_out
+ * (round-L trajectories; the ego's is its extra response), k_star_out.
+ * Optional xi_hist / u_hist (NULL to skip) have (L+2) slots of xi_out /
+ * U_io layout: slot r after round r, slot L+1 after the extra ego response.
+ *   X0 [agents x 4], U_io [u_elems], vref_scale [agents], xi_out [xi_elems],
+ *   k_star_out [ks] (int32), status_dev [1] (int32, written 0 or SGTP_E_*).
+ * Workspace: workspace_bytes from sgtp_batch_sizes. */
+sgtp_status sgtp_batch_plan(const sgtp_batch *b, const sgtp_params *p, const float *X0, float *U_io,
+                            const float *vref_scale, uint64_t seed, float *xi_out, int32_t *k_star_out,
+                            float *xi_hist, float *u_hist, int32_t *status_dev, const sgtp_launch_opts *opts,
+                            void *workspace, size_t workspace_bytes, void *stream);
+
+/* Workspace of sgtp_ibr_plan. */
+size_t sgtp_plan_workspace_bytes(int32_t n_v, int32_t T, int32_t L);
+
+/* One race, the paper's planning call (Alg. 1; CT of Sec. IV-C covers all
+ * of it).  Same semantics as sgtp_batch_plan with a single race whose
+ * descriptor is passed by value, so no setup call is needed.
+ *   X0 [n_v x 4], U_io [n_v x T x 2], vref_scale [n_v], xi_out
+ *   [n_v x (T+1) x 4], k_star_out [(L+1)*n_v + 1], xi_hist/u_hist optional. */
+sgtp_status sgtp_ibr_plan(const sgtp_track *trk, int32_t track_id, const sgtp_params *p, int32_t n_v,
+                          const float *X0, float *U_io, const float *vref_scale, int32_t T, int32_t K, int32_t L,
+                          int32_t ego, uint64_t seed, uint32_t race, float *xi_out, int32_t *k_star_out,
+                          float *xi_hist, float *u_hist, int32_t *status_dev, const sgtp_launch_opts *opts,
+                          void *workspace, size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Misc                                                                 */
+/* ------------------------------------------------------------------ */
+const char *sgtp_last_error(void);     /* thread-local text of the last failure */
+const char *sgtp_version(void);
+/* Number of kernel launches this library has enqueued since load (all
+ * entry points); used to count launches inside a timed region. */
+int64_t sgtp_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGTP_H */
