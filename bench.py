@@ -1,0 +1,276 @@
+#!/usr/bin/env python
+"""Benchmark of the SGTP planning call on B300.
+
+A step is one SGTP planning call (Alg. 1) of the ten-car workload: 10
+vehicles on a seeded Fourier track (R = 500 m, 8 modes, 2000 waypoints),
+K = 16384 samples per best response, T = 60 steps of 0.05 s, L = 5 IBR
+rounds plus the extra ego response: 61 best responses, 59,965,440
+rollout-steps per plan, all in one persistent launch.
+
+Metric: rollout-steps/s (whole job), with the plan's milliseconds alongside.
+Inputs are resident in HBM when the timed region starts; between timed
+steps a 256 MiB buffer (larger than the 126 MB L2) is overwritten, outside
+the timed events.  `e2e` repeats the measurement through the public API with
+pinned host buffers: host->device copy of the state and warm start,
+the plan, device->host copy of the trajectories and selections.
+
+--impl reference times the FP64 CPU oracle (the reference of this build) on
+the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_V, K, T, L = 10, 16384, 60, 5
+WORKLOAD = "ten-car IBR plan: n_v=10, K=16384, T=60, dt=0.05, L=5 (+ extra ego), Fourier track seed 200+rank"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(gpu_index)], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(", ") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip() == "Active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_rate(seconds: float, seed: int = 200):
+    """FP64 oracle on all host cores: round-0 best responses of the ten-car
+    workload at K = 256 samples each, repeated until `seconds` have passed."""
+    import numpy as np
+    import oracle as O
+    from paper_2607_25388_b300 import scenario as S
+    sc = S.ten_car_race(seed)
+    p = S.params_fullscale()
+    ot = O.Track(sc.track.xr, sc.track.wl, sc.track.wr)
+    lo = np.float32([p["a_min"], -p["delta_max"]]); hi = np.float32([p["a_max"], p["delta_max"]])
+    nominal = np.stack([O.rollout(p, sc.X0[i], np.clip(sc.U0[i], lo, hi), T) for i in range(N_V)])
+    cores = os.cpu_count() or 1
+    ks = 256
+    steps = 0
+    t0 = time.perf_counter()
+    i = 0
+    while True:
+        a = i % N_V
+        opp = np.stack([nominal[j] for j in range(N_V) if j != a])
+        O.best_response(p, ot, sc.X0[a], sc.U0[a], sc.vref_scale[a], opp, T, ks, seed=seed, agent=a, rnd=0,
+                        game_on=False, nthreads=cores)
+        steps += ks * T
+        i += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": steps / el, "unit": "rollout-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{i} round-0 best responses of the ten-car workload at K={ks} (T={T}, 9 opponents, "
+                      f"N=2000 brute-force Frenet), {el:.1f} s on {cores} threads"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = max(1.0, min(10.0, 60.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_rate(per_step / 4)
+    vals = [oracle_rate(per_step) for _ in range(args.steps)]
+    v = statistics.mean(x["value"] for x in vals)
+    line = {"metric": "rollout-steps/s", "value": v, "unit": "rollout-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_v": N_V, "K": K, "T": T, "L": L}, "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": "rollout-steps/s", "cores": vals[0]["cores"], "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": "rollout-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2607_25388_b300 import _lib, planner as P, roofline as R, scenario as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    sc = S.ten_car_race(200 + rank)
+    p = S.params_fullscale()
+    trk = P.Track.from_data(sc.track)
+    X0 = torch.as_tensor(sc.X0).to(dev)
+    vref = torch.as_tensor(sc.vref_scale).to(dev)
+    U0 = torch.as_tensor(sc.U0).to(dev)
+    U = U0.clone()
+    ws = torch.empty(P.plan_workspace_bytes(N_V, T, L), dtype=torch.uint8, device=dev)
+    out = dict(xi=torch.empty((N_V, T + 1, 4), device=dev), k_star=torch.empty((L + 1) * N_V + 1, dtype=torch.int32,
+                                                                                 device=dev),
+               status=torch.zeros(1, dtype=torch.int32, device=dev))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def plan(seed):
+        U.copy_(U0)      # same warm start every step: identical work per step
+        return P.ibr_plan(trk, p, X0, U, vref, T, K, L, ego=0, seed=seed, workspace=ws, out=out)
+
+    for w in range(args.warmup):
+        plan(1000 + w)
+    torch.cuda.synchronize()
+    assert out["status"].item() == 0, f"plan status {out['status'].item()}"
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    n0 = _lib.lib().sgtp_launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        U.copy_(U0)
+        ev[s][0].record(stream)
+        P.ibr_plan(trk, p, X0, U, vref, T, K, L, ego=0, seed=s, workspace=ws, out=out)
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    launches = _lib.lib().sgtp_launch_count() - n0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    times = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(times)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = t.item()
+    status = out["status"].item()
+
+    steps_per_plan = R.rollout_steps_plan(N_V, K, T, L)
+    value = steps_per_plan * args.steps * world / (total_ms / 1e3)
+    ms_per_step = total_ms / args.steps
+    flops = R.flops_plan(N_V, K, T, L)
+    achieved = flops / (statistics.mean(times) / 1e3) / 1e12
+    peak = R.fp32_peak_tflops()
+
+    # ---- end to end through the public API with pinned host buffers
+    hX = torch.as_tensor(sc.X0).pin_memory()
+    hU = torch.as_tensor(sc.U0).pin_memory()
+    hV = torch.as_tensor(sc.vref_scale).pin_memory()
+    oxi = torch.empty((N_V, T + 1, 4), dtype=torch.float32).pin_memory()
+    oks = torch.empty((L + 1) * N_V + 1, dtype=torch.int32).pin_memory()
+    ost = torch.empty(1, dtype=torch.int32).pin_memory()
+    dX = torch.empty_like(X0); dV = torch.empty_like(vref)
+    e2e_ev = []
+    for s in range(max(3, args.steps)):
+        flush.fill_(float(s))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dX.copy_(hX, non_blocking=True); U.copy_(hU, non_blocking=True); dV.copy_(hV, non_blocking=True)
+        P.ibr_plan(trk, p, dX, U, dV, T, K, L, ego=0, seed=s, workspace=ws, out=out)
+        oxi.copy_(out["xi"], non_blocking=True); oks.copy_(out["k_star"], non_blocking=True)
+        ost.copy_(out["status"], non_blocking=True)
+        b.record(stream)
+        e2e_ev.append((a, b))
+    torch.cuda.synchronize()
+    e2e_ms = statistics.mean(a.elapsed_time(b) for a, b in e2e_ev)
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_ms = te.item()
+    h2d = hX.numel() * 4 + hU.numel() * 4 + hV.numel() * 4
+    d2h = oxi.numel() * 4 + oks.numel() * 4 + ost.numel() * 4
+
+    if rank == 0:
+        line = {
+            "metric": "rollout-steps/s", "value": value, "unit": "rollout-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_v": N_V, "K": K, "T": T, "L": L,
+                       "plan_ms_median": statistics.median(times), "plan_ms_p99": sorted(times)[
+                           min(len(times) - 1, int(0.99 * len(times)))],
+                       "rollout_steps_per_plan": steps_per_plan, "l2": "256 MiB buffer rewritten between steps",
+                       "parallelism": f"replicas x{world} (independent races)", "plan_status": status},
+            "clocks": clk,
+            "e2e": {"value": steps_per_plan / (e2e_ms / 1e3) * world, "unit": "rollout-steps/s",
+                    "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "plan_kernel (persistent cooperative, 1 launch per plan)",
+                         "peak_basis": "148 SMs x 128 FP32 lanes x 2 x 2032 MHz (unit counts, max clock)",
+                         "flops_per_plan": flops},
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = oracle_rate(args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -82,7 +82,7 @@ def lib():
         L.orc_rollout_costs.argtypes = [
             C.POINTER(OrcParams), dp, dp, dp, C.c_int, dp, dp, C.c_double, dp, C.c_int, C.c_int,
             C.POINTER(C.c_int32), C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int,
-            C.c_int, dp, C.POINTER(C.c_ubyte), dp, dp, dp, dp, dp, dp, C.c_int]
+            C.c_int, dp, C.POINTER(C.c_ubyte), dp, dp, dp, dp, dp, dp, dp, C.c_int]
         L.orc_eval_controls.argtypes = [
             C.POINTER(OrcParams), dp, dp, dp, C.c_int, dp, dp, C.c_int, C.c_double, dp, C.c_int, C.c_int,
             C.c_int, dp, C.POINTER(C.c_ubyte), dp, dp, dp]
@@ -211,7 +211,7 @@ def rollout_costs(params, track: Track, x0, u_nom, vref_scale, opp, T, K=None, k
         n = int(K)
         klp = None
     cost = np.zeros(n); viol = np.zeros(n); feas = np.zeros(n, dtype=np.uint8)
-    ctr = np.zeros(n); cg = np.zeros(n)
+    ctr = np.zeros(n); cg = np.zeros(n); mg = np.zeros((n, 3))
     states = np.zeros((n, T + 1, 4)) if want_states else None
     fr = np.zeros((n, T + 1, 2)) if want_frenet else None
     ctl = np.zeros((n, T, 2)) if want_controls else None
@@ -219,9 +219,9 @@ def rollout_costs(params, track: Track, x0, u_nom, vref_scale, opp, T, K=None, k
         C.byref(make_params(params)), *track.args(), _p(_d(x0)), _p(_d(u_nom)), float(np.float32(vref_scale)),
         _p(opp) if n_opp else None, n_opp, T, klp, n, seed, race, agent, rnd, stream, int(bool(game_on)),
         int(bool(zero_noise)), _p(cost), feas.ctypes.data_as(C.POINTER(C.c_ubyte)), _p(viol), _p(states),
-        _p(fr), _p(ctl), _p(ctr), _p(cg), _nthreads(nthreads))
+        _p(fr), _p(ctl), _p(ctr), _p(cg), _p(mg), _nthreads(nthreads))
     assert rc == 0
-    out = dict(cost=cost, feasible=feas, violation=viol, c_track=ctr, c_game=cg)
+    out = dict(cost=cost, feasible=feas, violation=viol, c_track=ctr, c_game=cg, margins=mg)
     if want_states:
         out["states"] = states
     if want_frenet:

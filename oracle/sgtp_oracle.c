@@ -270,6 +270,9 @@ typedef struct {
     double cost, viol;
     int feasible;
     double c_track, c_game;
+    /* distances of the indicator arguments to their thresholds (used by the
+       parity tests to recognise near-threshold candidates) */
+    double m_bd, m_obs, m_game;
 } orc_sample_result;
 
 static int problem_init(orc_problem *P)
@@ -378,7 +381,7 @@ static orc_sample_result eval_candidate(const orc_problem *P, const double *u, d
     r.c_track = c_state + c_ctrl + c_smooth;
 
     /* game-aware cost, summed over opponents (Eq. game_cost) */
-    double c_game = 0.0, rho_obs = INFINITY;
+    double c_game = 0.0, rho_obs = INFINITY, m_game = INFINITY;
     const double dbar_i = d_tail / (double)P->n_tail;
     for (int j = 0; j < P->n_opp; ++j) {
         const orc_opp_summary *o = &P->opp_sum[j];
@@ -386,6 +389,8 @@ static orc_sample_result eval_candidate(const orc_problem *P, const double *u, d
         const double ds_H = ds_t + (s_prev - P->s_t) - (o->sH - o->s0);
         /* contest-state term (Eq. c_contest) */
         const double c_contest = -p->w_contest * ((fabs(ds_H) < p->s_contest) ? 1.0 : 0.0);
+        m_game = fmin(m_game, fabs(fabs(ds_H) - p->s_contest));
+        m_game = fmin(m_game, fmin(fabs(ds_t - p->s_role), fabs(ds_t - p->s_contest)));
         /* longitudinal advantage (Eq. c_long) with adaptive alpha */
         const double alpha = 1.0 / (1.0 + fabs(ds_t) / (p->s_contest + p->eps_alpha));
         const double c_long = -p->w_long * alpha * ds_H;
@@ -410,6 +415,9 @@ static orc_sample_result eval_candidate(const orc_problem *P, const double *u, d
     /* least-violation measure (Sec. III-B, fallback) */
     r.viol = fmax(0.0, p->m_bd - rho_bd) + fmax(0.0, p->d_col - rho_obs);
     if (isnan(r.viol)) r.viol = INFINITY;
+    r.m_bd = fabs(rho_bd - p->m_bd);
+    r.m_obs = P->n_opp > 0 ? fabs(rho_obs - p->d_col) : INFINITY;
+    r.m_game = m_game;
     return r;
 }
 
@@ -420,7 +428,7 @@ typedef struct {
     const orc_problem *P;
     const int32_t *k_list;
     int n, begin, end;
-    double *cost, *viol, *states, *frenet, *controls, *c_track, *c_game;
+    double *cost, *viol, *states, *frenet, *controls, *c_track, *c_game, *margins;
     unsigned char *feas;
 } orc_job;
 
@@ -440,6 +448,7 @@ static void *job_run(void *arg)
         J->feas[i] = (unsigned char)r.feasible;
         if (J->c_track) J->c_track[i] = r.c_track;
         if (J->c_game) J->c_game[i] = r.c_game;
+        if (J->margins) { J->margins[3 * i] = r.m_bd; J->margins[3 * i + 1] = r.m_obs; J->margins[3 * i + 2] = r.m_game; }
         if (J->controls) memcpy(J->controls + (size_t)i * T * 2, u, sizeof(double) * (size_t)T * 2);
     }
     free(u);
@@ -447,7 +456,8 @@ static void *job_run(void *arg)
 }
 
 static void run_jobs(const orc_problem *P, const int32_t *k_list, int n, int nthreads, double *cost, unsigned char *feas,
-                     double *viol, double *states, double *frenet, double *controls, double *c_track, double *c_game)
+                     double *viol, double *states, double *frenet, double *controls, double *c_track, double *c_game,
+                     double *margins)
 {
     if (nthreads < 1) nthreads = 1;
     if (nthreads > n) nthreads = n > 0 ? n : 1;
@@ -459,7 +469,7 @@ static void run_jobs(const orc_problem *P, const int32_t *k_list, int n, int nth
         J->begin = (int)((int64_t)n * t / nthreads);
         J->end = (int)((int64_t)n * (t + 1) / nthreads);
         J->cost = cost; J->viol = viol; J->feas = feas; J->states = states; J->frenet = frenet;
-        J->controls = controls; J->c_track = c_track; J->c_game = c_game;
+        J->controls = controls; J->c_track = c_track; J->c_game = c_game; J->margins = margins;
     }
     for (int t = 1; t < nthreads; ++t) pthread_create(&th[t], NULL, job_run, &jobs[t]);
     job_run(&jobs[0]);
@@ -510,13 +520,13 @@ int orc_rollout_costs(const orc_params *p, const double *xr, const double *wl, c
                       int T, const int32_t *k_list, int n, uint64_t seed, uint32_t race, uint32_t agent,
                       uint32_t round, uint32_t stream, int game_on, int zero_noise,
                       double *cost, unsigned char *feas, double *viol, double *states, double *frenet,
-                      double *controls, double *c_track, double *c_game, int nthreads)
+                      double *controls, double *c_track, double *c_game, double *margins, int nthreads)
 {
     orc_problem P;
     if (setup_problem(&P, p, xr, wl, wr, N, x0, u_nom, vref_scale, opp, n_opp, T, seed, race, agent, round,
                       stream, game_on, zero_noise))
         return -1;
-    run_jobs(&P, k_list, n, nthreads, cost, feas, viol, states, frenet, controls, c_track, c_game);
+    run_jobs(&P, k_list, n, nthreads, cost, feas, viol, states, frenet, controls, c_track, c_game, margins);
     teardown_problem(&P);
     return 0;
 }
@@ -557,7 +567,7 @@ int orc_best_response(const orc_params *p, const double *xr, const double *wl, c
     double *cost = (double *)malloc(sizeof(double) * (size_t)K);
     double *viol = (double *)malloc(sizeof(double) * (size_t)K);
     unsigned char *feas = (unsigned char *)malloc((size_t)K);
-    run_jobs(&P, NULL, K, nthreads, cost, feas, viol, NULL, NULL, NULL, NULL, NULL);
+    run_jobs(&P, NULL, K, nthreads, cost, feas, viol, NULL, NULL, NULL, NULL, NULL, NULL);
     const int ks = orc_select(cost, feas, viol, K, any_feasible);
     *k_star = ks;
     double *u = (double *)malloc(sizeof(double) * (size_t)T * 2);

@@ -1,0 +1,119 @@
+"""ctypes declarations of the C ABI in ``include/sgtp.h`` (argument
+marshalling only; every step of the path runs in the CUDA library)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+PARAM_FIELDS = [
+    "dt", "wheelbase", "a_min", "a_max", "delta_max", "v_min", "v_max", "sigma_a", "sigma_delta",
+    "Q", "R", "S", "w_game", "w_contest", "w_long", "w_block", "w_safety",
+    "s_contest", "s_role", "mu_tail", "g_safe", "eps_alpha", "m_bd", "d_col",
+]
+
+MAX_AGENTS = 16
+MAX_T = 128
+DEBUG_SKIP_BARRIER_ARRIVAL = 1
+
+STATUS = {0: "SGTP_OK", 1: "SGTP_E_INVALID", 2: "SGTP_E_CUDA", 3: "SGTP_E_NOMEM", 4: "SGTP_E_TIMEOUT",
+          5: "SGTP_E_DEVICE", 6: "SGTP_E_UNSUPPORTED"}
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("dt", C.c_float), ("wheelbase", C.c_float), ("a_min", C.c_float), ("a_max", C.c_float),
+        ("delta_max", C.c_float), ("v_min", C.c_float), ("v_max", C.c_float),
+        ("sigma_a", C.c_float), ("sigma_delta", C.c_float),
+        ("Q", C.c_float * 4), ("R", C.c_float * 2), ("S", C.c_float * 2),
+        ("w_game", C.c_float), ("w_contest", C.c_float), ("w_long", C.c_float), ("w_block", C.c_float),
+        ("w_safety", C.c_float), ("s_contest", C.c_float), ("s_role", C.c_float), ("mu_tail", C.c_float),
+        ("g_safe", C.c_float), ("eps_alpha", C.c_float), ("m_bd", C.c_float), ("d_col", C.c_float),
+    ]
+
+
+class LaunchOpts(C.Structure):
+    _fields_ = [("block", C.c_int32), ("samples_per_thread", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("window", C.c_int32), ("wait_timeout_ns", C.c_int64), ("debug_flags", C.c_int32)]
+
+
+class Race(C.Structure):
+    _fields_ = [("track_id", C.c_int32), ("n_v", C.c_int32), ("T", C.c_int32), ("ego", C.c_int32),
+                ("race_tag", C.c_uint32)]
+
+
+def make_params(d: dict) -> Params:
+    P = Params()
+    for f in PARAM_FIELDS:
+        v = d[f]
+        if f in ("Q", "R", "S"):
+            arr = getattr(P, f)
+            for i, x in enumerate(v):
+                arr[i] = float(x)
+        else:
+            setattr(P, f, float(v))
+    return P
+
+
+def lib():
+    """Load libsgtp.so (building it with nvcc when missing or stale).  Raises
+    if the library cannot be built or loaded: there is no other path."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = C.CDLL(path)
+            vp, sz, i32, u32, u64, f32 = C.c_void_p, C.c_size_t, C.c_int32, C.c_uint32, C.c_uint64, C.c_float
+            L.sgtp_track_create.argtypes = [vp, vp, vp, i32, vp, C.POINTER(vp)]
+            L.sgtp_track_create_many.argtypes = [vp, vp, vp, vp, i32, vp, C.POINTER(vp)]
+            L.sgtp_track_destroy.argtypes = [vp]
+            L.sgtp_track_destroy.restype = None
+            L.sgtp_track_info.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(f32)]
+            L.sgtp_br_workspace_bytes.argtypes = [i32, i32]
+            L.sgtp_br_workspace_bytes.restype = sz
+            L.sgtp_rollout_costs.argtypes = [vp, i32, C.POINTER(Params), vp, vp, f32, vp, i32, i32, i32, u64, u32,
+                                             u32, u32, i32, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+            L.sgtp_best_response.argtypes = [vp, i32, C.POINTER(Params), vp, vp, f32, vp, i32, i32, i32, u64, u32,
+                                             u32, u32, i32, vp, vp, vp, vp, vp, sz, vp]
+            L.sgtp_last_error.restype = C.c_char_p
+            L.sgtp_version.restype = C.c_char_p
+            L.sgtp_launch_count.restype = C.c_int64
+            if hasattr(L, "sgtp_plan_workspace_bytes"):
+                L.sgtp_plan_workspace_bytes.argtypes = [i32, i32, i32]
+                L.sgtp_plan_workspace_bytes.restype = sz
+                L.sgtp_ibr_plan.argtypes = [vp, i32, C.POINTER(Params), i32, vp, vp, vp, i32, i32, i32, i32, u64,
+                                            u32, vp, vp, vp, vp, vp, C.POINTER(LaunchOpts), vp, sz, vp]
+                L.sgtp_batch_create.argtypes = [vp, C.POINTER(Race), i32, i32, i32, C.POINTER(vp)]
+                L.sgtp_batch_destroy.argtypes = [vp]
+                L.sgtp_batch_destroy.restype = None
+                L.sgtp_batch_sizes.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                               C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(sz)]
+                L.sgtp_batch_plan.argtypes = [vp, C.POINTER(Params), vp, vp, vp, u64, vp, vp, vp, vp, vp,
+                                              C.POINTER(LaunchOpts), vp, sz, vp]
+            _lib = L
+    return _lib
+
+
+def check(status: int, what: str = ""):
+    if status != 0:
+        msg = lib().sgtp_last_error().decode(errors="replace")
+        raise RuntimeError(f"{what}: {STATUS.get(status, status)}: {msg}")
+
+
+# every symbol include/sgtp.h declares (checked by the CPU test-suite)
+EXPORTS = [
+    "sgtp_track_create", "sgtp_track_create_many", "sgtp_track_destroy", "sgtp_track_info",
+    "sgtp_br_workspace_bytes", "sgtp_rollout_costs", "sgtp_best_response",
+    "sgtp_batch_create", "sgtp_batch_destroy", "sgtp_batch_sizes", "sgtp_batch_plan",
+    "sgtp_plan_workspace_bytes", "sgtp_ibr_plan",
+    "sgtp_last_error", "sgtp_version", "sgtp_launch_count",
+]
+
+
+def lib_path() -> str:
+    return os.path.abspath(_build.LIB)

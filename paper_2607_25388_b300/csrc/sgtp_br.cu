@@ -1,0 +1,595 @@
+// sgtp_br.cu -- raceline setup and the single best-response entry points.
+//
+//   sgtp_track_create*   raceline G (Sec. II, Preliminaries) on the device
+//   sgtp_rollout_costs   K candidates: cost (Eq. allc), h (Eq. selection), nu
+//   sgtp_best_response   the same, plus selection with the least-violation
+//                        fallback (Sec. III-B) and the re-rolled winner
+#include <atomic>
+#include <cmath>
+#include <cstring>
+
+#include "sgtp_host.hpp"
+#include "sgtp_rollout.cuh"
+
+using namespace sgtp;
+
+// ================================================================ host utils
+namespace sgtp {
+
+static thread_local std::string g_error;
+static std::atomic<long long> g_launches{0};
+
+sgtp_status set_error(sgtp_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_error = buf;
+    return s;
+}
+
+void count_launch(int n) { g_launches += n; }
+
+sgtp_status check_params(const sgtp_params *p)
+{
+    SGTP_CHECK(p != nullptr, "params is NULL");
+    SGTP_CHECK(p->dt > 0.f && std::isfinite(p->dt), "dt must be > 0");
+    SGTP_CHECK(p->wheelbase > 0.f, "wheelbase must be > 0");
+    SGTP_CHECK(p->a_min <= p->a_max, "a_min > a_max");
+    SGTP_CHECK(p->delta_max >= 0.f && p->delta_max < 1.5f, "delta_max must be in [0, 1.5)");
+    SGTP_CHECK(p->v_min <= p->v_max, "v_min > v_max");
+    SGTP_CHECK(p->sigma_a >= 0.f && p->sigma_delta >= 0.f, "negative sigma");
+    SGTP_CHECK(p->mu_tail > 0.f && p->mu_tail <= 1.f, "mu_tail must be in (0, 1]");
+    SGTP_CHECK(p->s_contest + p->eps_alpha > 0.f, "s_contest + eps must be > 0");
+    const float *f = (const float *)p;
+    for (size_t i = 0; i < sizeof(sgtp_params) / sizeof(float); ++i)
+        SGTP_CHECK(std::isfinite(f[i]), "params field %zu is not finite", i);
+    return SGTP_OK;
+}
+
+}  // namespace sgtp
+
+extern "C" const char *sgtp_last_error(void) { return g_error.c_str(); }
+extern "C" const char *sgtp_version(void) { return "sgtp-b300 0.1 (sm_103a)"; }
+extern "C" int64_t sgtp_launch_count(void) { return (int64_t)g_launches.load(); }
+
+// ================================================================ track prep
+// One CTA per track: per-segment chords, inverse squared lengths, width,
+// heading and speed increments; then a compensated (Kahan) running sum of the
+// segment lengths gives s_j in float32 to about one ulp of L.
+__global__ void track_prep_kernel(const float *xr, const float *wl, const float *wr, TrackDesc *desc, float4 *A,
+                                  float4 *B, float4 *W, float4 *C)
+{
+    TrackDesc d = desc[blockIdx.x];
+    for (int j = threadIdx.x; j < d.N; j += blockDim.x) {
+        const int g = d.offset + j;
+        const int gn = d.offset + (j + 1 == d.N ? 0 : j + 1);
+        const float x0 = xr[4 * g], y0 = xr[4 * g + 1], p0 = xr[4 * g + 2], v0 = xr[4 * g + 3];
+        const float x1 = xr[4 * gn], y1 = xr[4 * gn + 1], p1 = xr[4 * gn + 2], v1 = xr[4 * gn + 3];
+        const float ex = x1 - x0, ey = y1 - y0;
+        const float l2 = __fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey));
+        A[g] = make_float4(x0, y0, ex, ey);
+        B[g] = make_float4(1.0f / l2, 0.f, sqrtf(l2), 0.f);
+        W[g] = make_float4(wl[g], wl[gn] - wl[g], wr[g], wr[gn] - wr[g]);
+        C[g] = make_float4(p0, wrap_angle(p1 - p0), v0, v1 - v0);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float sum = 0.f, comp = 0.f;
+        for (int j = 0; j < d.N; ++j) {
+            const int g = d.offset + j;
+            B[g].y = sum;
+            const float y = B[g].z - comp;
+            const float t = sum + y;
+            comp = (t - sum) - y;
+            sum = t;
+        }
+        desc[blockIdx.x].L = sum;
+    }
+}
+
+static sgtp_status track_create_impl(const float *xr, const float *wl, const float *wr, const int32_t *offsets,
+                                     int32_t n_tracks, void *stream, sgtp_track **out)
+{
+    SGTP_CHECK(out != nullptr, "out is NULL");
+    *out = nullptr;
+    SGTP_CHECK(xr && wl && wr && offsets, "NULL track array");
+    SGTP_CHECK(n_tracks >= 1 && n_tracks <= (1 << 20), "n_tracks out of range");
+    SGTP_CHECK(offsets[0] == 0, "offsets[0] must be 0");
+    for (int t = 0; t < n_tracks; ++t) {
+        const int N = offsets[t + 1] - offsets[t];
+        SGTP_CHECK(N >= 3 && N <= (1 << 20), "track %d: N=%d out of range [3, 2^20]", t, N);
+    }
+    const int total = offsets[n_tracks];
+    SGTP_CHECK(total <= (1 << 26), "too many waypoints");
+    for (int t = 0; t < n_tracks; ++t) {
+        const int o = offsets[t], N = offsets[t + 1] - o;
+        for (int j = 0; j < N; ++j) {
+            const int g = o + j, gn = o + (j + 1) % N;
+            for (int c = 0; c < 4; ++c) SGTP_CHECK(std::isfinite(xr[4 * g + c]), "track %d: non-finite waypoint", t);
+            SGTP_CHECK(std::isfinite(wl[g]) && std::isfinite(wr[g]) && wl[g] > 0.f && wr[g] > 0.f,
+                       "track %d: widths must be finite and > 0", t);
+            const float ex = xr[4 * gn] - xr[4 * g], ey = xr[4 * gn + 1] - xr[4 * g + 1];
+            SGTP_CHECK(ex * ex + ey * ey > 0.f, "track %d: zero-length segment %d", t, j);
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    sgtp_track *T = new sgtp_track();
+    T->n_tracks = n_tracks;
+    T->total = total;
+    cudaGetDevice(&T->device);
+    T->desc.resize(n_tracks);
+    for (int t = 0; t < n_tracks; ++t) T->desc[t] = TrackDesc{offsets[t], offsets[t + 1] - offsets[t], 0.f, 0};
+    float *d_xr = nullptr, *d_wl = nullptr, *d_wr = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(d_xr); cudaFree(d_wl); cudaFree(d_wr);
+    };
+    cudaError_t e = cudaSuccess;
+    const size_t seg = (size_t)total * sizeof(float4);
+    if ((e = cudaMalloc(&T->A, seg)) || (e = cudaMalloc(&T->B, seg)) || (e = cudaMalloc(&T->W, seg)) ||
+        (e = cudaMalloc(&T->C, seg)) || (e = cudaMalloc(&T->desc_dev, sizeof(TrackDesc) * n_tracks)) ||
+        (e = cudaMalloc(&d_xr, sizeof(float) * 4 * total)) || (e = cudaMalloc(&d_wl, sizeof(float) * total)) ||
+        (e = cudaMalloc(&d_wr, sizeof(float) * total))) {
+        cleanup();
+        sgtp_track_destroy(T);
+        return set_error(SGTP_E_NOMEM, "track allocation failed: %s", cudaGetErrorString(e));
+    }
+    if ((e = cudaMemcpyAsync(d_xr, xr, sizeof(float) * 4 * total, cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(d_wl, wl, sizeof(float) * total, cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(d_wr, wr, sizeof(float) * total, cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(T->desc_dev, T->desc.data(), sizeof(TrackDesc) * n_tracks, cudaMemcpyHostToDevice, s))) {
+        cleanup();
+        sgtp_track_destroy(T);
+        return set_error(SGTP_E_CUDA, "track upload failed: %s", cudaGetErrorString(e));
+    }
+    track_prep_kernel<<<n_tracks, 256, 0, s>>>(d_xr, d_wl, d_wr, T->desc_dev, T->A, T->B, T->W, T->C);
+    count_launch();
+    if ((e = cudaGetLastError()) ||
+        (e = cudaMemcpyAsync(T->desc.data(), T->desc_dev, sizeof(TrackDesc) * n_tracks, cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaStreamSynchronize(s))) {
+        cleanup();
+        sgtp_track_destroy(T);
+        return set_error(SGTP_E_CUDA, "track prep failed: %s", cudaGetErrorString(e));
+    }
+    cleanup();
+    *out = T;
+    return SGTP_OK;
+}
+
+extern "C" sgtp_status sgtp_track_create(const float *xr, const float *wl, const float *wr, int32_t N, void *stream,
+                                         sgtp_track **out)
+{
+    const int32_t off[2] = {0, N};
+    return track_create_impl(xr, wl, wr, off, 1, stream, out);
+}
+
+extern "C" sgtp_status sgtp_track_create_many(const float *xr, const float *wl, const float *wr,
+                                              const int32_t *offsets, int32_t n_tracks, void *stream,
+                                              sgtp_track **out)
+{
+    return track_create_impl(xr, wl, wr, offsets, n_tracks, stream, out);
+}
+
+extern "C" void sgtp_track_destroy(sgtp_track *T)
+{
+    if (!T) return;
+    cudaFree(T->A); cudaFree(T->B); cudaFree(T->W); cudaFree(T->C); cudaFree(T->desc_dev);
+    delete T;
+}
+
+extern "C" sgtp_status sgtp_track_info(const sgtp_track *trk, int32_t track_id, int32_t *n_tracks, int32_t *N,
+                                       float *length)
+{
+    SGTP_CHECK(trk != nullptr, "track is NULL");
+    SGTP_CHECK(track_id >= 0 && track_id < trk->n_tracks, "track_id out of range");
+    if (n_tracks) *n_tracks = trk->n_tracks;
+    if (N) *N = trk->desc[track_id].N;
+    if (length) *length = trk->desc[track_id].L;
+    return SGTP_OK;
+}
+
+// ================================================================ single BR
+// Workspace of one best response: a header followed by the per-problem
+// arrays (all 16-byte aligned).
+struct BRHeader {
+    unsigned long long key;     // running minimum selection key
+    int flag;                   // device-side check flags
+    int pad0;
+    float4 x0;
+    float s_t, d_t;
+    int j0, pad1;
+};
+
+struct BRLayout {
+    size_t ref, opp, osum, odbar, total;
+    BRLayout(int n_opp, int T)
+    {
+        auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+        ref = up(sizeof(BRHeader));
+        opp = up(ref + sizeof(float4) * (T + 1));
+        osum = up(opp + sizeof(float2) * (size_t)T * (n_opp > 0 ? n_opp : 1));
+        odbar = up(osum + sizeof(float4) * (n_opp > 0 ? n_opp : 1));
+        total = up(odbar + sizeof(float) * (n_opp > 0 ? n_opp : 1));
+    }
+};
+
+constexpr int kMaxMoves = 64;
+
+// Per-problem preparation (one CTA): Frenet of x_{i,t} by global search, the
+// reference trajectory (Sec. III-A, overall ranking), and for every opponent
+// prediction its positions, unwrapped progress and tail-mean offset, then
+// the pair terms that do not depend on the candidate: the current gap
+// Delta s_{ij,t}, alpha_{ij,t} and gamma_{block,ij}.
+__global__ void br_prep_kernel(TrackView tv, sgtp_params p, const float *x0, const float *opp, int n_opp, int T,
+                               float vscale, int n_tail, unsigned char *ws, size_t off_ref, size_t off_opp,
+                               size_t off_osum, size_t off_odbar)
+{
+    BRHeader *h = (BRHeader *)ws;
+    float4 *ref = (float4 *)(ws + off_ref);
+    float2 *opos = (float2 *)(ws + off_opp);
+    float4 *osum = (float4 *)(ws + off_osum);
+    float *odbar = (float *)(ws + off_odbar);
+    __shared__ float s0_sh[SGTP_MAX_AGENTS], sH_sh[SGTP_MAX_AGENTS];
+    __shared__ float s_t_sh;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const float invL = 1.0f / tv.L;
+    const SegWindow nowin{nullptr, nullptr, 0, 0};
+    if (warp == 0) {
+        const float4 x = make_float4(x0[0], x0[1], x0[2], x0[3]);
+        const int j = nearest_segment_warp(tv, x.x, x.y);
+        if (lane == 0) {
+            const FrenetPt f = frenet_at(tv, j, x.x, x.y);
+            h->key = ~0ull;
+            h->flag = 0;
+            h->x0 = x;
+            h->s_t = f.s;
+            h->d_t = f.d;
+            h->j0 = j;
+            s_t_sh = f.s;
+            // s^r_0 = s_{i,t}; s^r_{tau+1} = s^r_tau + dt * v^r(s^r_tau)
+            int jr = j;
+            float sr = f.s;
+            ref[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int tau = 0; tau < T; ++tau) {
+                const float4 r0 = reference_at(tv, jr, sr);
+                sr = __fmaf_rn(p.dt, __fmul_rn(vscale, r0.w), sr);
+                float4 r1 = reference_at(tv, jr, sr);
+                r1.w = __fmul_rn(r1.w, vscale);
+                ref[tau + 1] = r1;
+            }
+        }
+    }
+    for (int o = warp - 1; o >= 0 && o < n_opp; o += (nwarps > 1 ? nwarps - 1 : n_opp)) {
+        const float *q = opp + (size_t)o * (T + 1) * 4;
+        int j = nearest_segment_warp(tv, q[0], q[1]);
+        if (lane == 0) {
+            const FrenetPt f0 = frenet_at(tv, j, q[0], q[1]);
+            float s = f0.s, dsum = 0.f;
+            int flag = 0;
+            for (int tau = 1; tau <= T; ++tau) {
+                const float px = q[4 * tau], py = q[4 * tau + 1];
+                const FrenetPt f = frenet_walk(tv, nowin, j, px, py, kMaxMoves, flag);
+                s = s + wrap_len(f.s - s, tv.L, invL);
+                if (tau > T - n_tail) dsum = dsum + f.d;
+                opos[(size_t)(tau - 1) * n_opp + o] = make_float2(px, py);
+            }
+            if (flag) atomicOr(&h->flag, 1);
+            s0_sh[o] = f0.s;
+            sH_sh[o] = s;
+            odbar[o] = dsum / (float)n_tail;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < n_opp) {
+        const int o = threadIdx.x;
+        const float ds_t = wrap_len(s_t_sh - s0_sh[o], tv.L, invL);
+        const float alpha = 1.0f / (1.0f + fabsf(ds_t) / (p.s_contest + p.eps_alpha));
+        const float gamma = (ds_t > p.s_role && ds_t < p.s_contest) ? p.w_block : 0.f;
+        osum[o] = make_float4(ds_t, alpha, gamma, sH_sh[o] - s0_sh[o]);
+    }
+}
+
+struct BRSmemLayout {
+    int Wn, T, n_opp;
+    size_t sA, sB, ref, ubar, opp, osum, odbar, total;
+    __host__ __device__ BRSmemLayout(int Wn_, int T_, int n_opp_) : Wn(Wn_), T(T_), n_opp(n_opp_)
+    {
+        auto up = [](size_t x) { return (x + 15) & ~(size_t)15; };
+        sA = 16;
+        sB = sA + sizeof(float4) * Wn;
+        ref = sB + sizeof(float4) * Wn;
+        ubar = up(ref + sizeof(float4) * (T + 1));
+        opp = up(ubar + sizeof(float2) * T);
+        osum = up(opp + sizeof(float2) * (size_t)T * n_opp);
+        odbar = up(osum + sizeof(float4) * n_opp);
+        total = up(odbar + sizeof(float) * n_opp);
+    }
+};
+
+// Stage the track window [w0, w0+Wn) mod N into shared memory with bulk
+// (TMA) copies, one or two pieces per array; the caller waits on bar.
+__device__ __forceinline__ void stage_window(const TrackView &tv, int w0, int Wn, float4 *sA, float4 *sB,
+                                             unsigned long long *bar)
+{
+    const int n1 = min(Wn, tv.N - w0);
+    mbar_expect_tx(bar, (unsigned)(2 * Wn * sizeof(float4)));
+    bulk_g2s(sA, tv.A + w0, (unsigned)(n1 * sizeof(float4)), bar);
+    bulk_g2s(sB, tv.B + w0, (unsigned)(n1 * sizeof(float4)), bar);
+    if (n1 < Wn) {
+        bulk_g2s(sA + n1, tv.A, (unsigned)((Wn - n1) * sizeof(float4)), bar);
+        bulk_g2s(sB + n1, tv.B, (unsigned)((Wn - n1) * sizeof(float4)), bar);
+    }
+}
+
+struct BRArgs {
+    TrackView tv;
+    sgtp_params p;
+    const unsigned char *ws;
+    size_t off_ref, off_opp, off_osum, off_odbar;
+    const float *u_nom;
+    int T, n_opp, K, n_tail, Wn, back;
+    uint2 key;
+    unsigned agent_round, race;
+    int game_on;
+    // outputs (costs mode)
+    float *cost, *viol, *states, *frenet, *controls;
+    unsigned char *feas;
+    long long timeout_ns;
+};
+
+template <int MAXO, bool KEY_MODE>
+__global__ void __launch_bounds__(256) br_rollout_kernel(BRArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned long long cta_key;
+    __shared__ int cta_flag;
+    const BRSmemLayout L(a.Wn, a.T, a.n_opp);
+    unsigned long long *bar = (unsigned long long *)smem;
+    float4 *sA = (float4 *)(smem + L.sA);
+    float4 *sB = (float4 *)(smem + L.sB);
+    float4 *sref = (float4 *)(smem + L.ref);
+    float2 *subar = (float2 *)(smem + L.ubar);
+    float2 *sopp = (float2 *)(smem + L.opp);
+    float4 *sosum = (float4 *)(smem + L.osum);
+    float *sodbar = (float *)(smem + L.odbar);
+    const BRHeader *h = (const BRHeader *)a.ws;
+    const int j0 = h->j0;
+    const int w0 = wrap_index(j0 - a.back, a.tv.N);
+    if (threadIdx.x == 0) {
+        cta_key = ~0ull;
+        cta_flag = 0;
+        mbar_init(bar, 1);
+        stage_window(a.tv, w0, a.Wn, sA, sB, bar);
+    }
+    const float4 *gref = (const float4 *)(a.ws + a.off_ref);
+    for (int i = threadIdx.x; i <= a.T; i += blockDim.x) sref[i] = gref[i];
+    for (int i = threadIdx.x; i < a.T; i += blockDim.x) subar[i] = make_float2(a.u_nom[2 * i], a.u_nom[2 * i + 1]);
+    const float2 *gopp = (const float2 *)(a.ws + a.off_opp);
+    for (int i = threadIdx.x; i < a.T * a.n_opp; i += blockDim.x) sopp[i] = gopp[i];
+    const float4 *gosum = (const float4 *)(a.ws + a.off_osum);
+    const float *godbar = (const float *)(a.ws + a.off_odbar);
+    for (int i = threadIdx.x; i < a.n_opp; i += blockDim.x) { sosum[i] = gosum[i]; sodbar[i] = godbar[i]; }
+    __syncthreads();
+    if (!mbar_wait_bounded(bar, 0, (unsigned long long)a.timeout_ns)) cta_flag = SGTP_E_TIMEOUT;
+    __syncthreads();
+
+    BRView bv;
+    bv.tv = a.tv;
+    bv.win = SegWindow{sA, sB, w0, a.Wn};
+    bv.ubar = subar; bv.ref = sref; bv.opp = sopp; bv.osum = sosum; bv.odbar = sodbar;
+    bv.x0 = h->x0; bv.s_t = h->s_t; bv.d_t = h->d_t; bv.j0 = j0;
+    bv.T = a.T; bv.n_opp = a.n_opp; bv.n_tail = a.n_tail;
+    bv.invL = 1.0f / a.tv.L;
+    bv.max_moves = kMaxMoves;
+    bv.key = a.key; bv.ctr_agent_round = a.agent_round; bv.ctr_race = a.race; bv.stream_bit = 0u;
+
+    int flag = 0;
+    unsigned long long best = ~0ull;
+    const unsigned k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cta_flag == 0 && k < (unsigned)a.K) {
+        if (KEY_MODE) {
+            const SampleResult r = run_candidate<MAXO, false>(bv, a.p, k, a.game_on != 0, false, flag, nullptr,
+                                                              nullptr, nullptr);
+            best = make_key(r.feasible, r.cost, r.viol, k);
+        } else {
+            float *st = a.states ? a.states + (size_t)k * (a.T + 1) * 4 : nullptr;
+            float *fr = a.frenet ? a.frenet + (size_t)k * (a.T + 1) * 2 : nullptr;
+            float *uo = a.controls ? a.controls + (size_t)k * a.T * 2 : nullptr;
+            SampleResult r;
+            if (st || fr || uo)
+                r = run_candidate<MAXO, true>(bv, a.p, k, a.game_on != 0, false, flag, st, fr, uo);
+            else
+                r = run_candidate<MAXO, false>(bv, a.p, k, a.game_on != 0, false, flag, nullptr, nullptr, nullptr);
+            a.cost[k] = r.cost;
+            a.viol[k] = r.viol;
+            a.feas[k] = r.feasible ? 1 : 0;
+        }
+    }
+    if (flag) atomicOr(&cta_flag, SGTP_E_DEVICE << 8);
+    if (KEY_MODE) {
+        best = warp_min_u64(best);
+        if ((threadIdx.x & 31) == 0) atomicMin(&cta_key, best);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        BRHeader *hw = (BRHeader *)a.ws;
+        if (KEY_MODE) atomicMin(&hw->key, cta_key);
+        if (cta_flag) atomicOr(&hw->flag, cta_flag);
+    }
+}
+
+// Selection result and re-roll of the winner (one warp, lane 0).
+template <int MAXO>
+__global__ void br_finalize_kernel(BRArgs a, int *k_star, float *u_star, float *xi_star, int *any_feasible)
+{
+    __shared__ float2 subar[SGTP_MAX_T];
+    for (int i = threadIdx.x; i < a.T; i += blockDim.x) subar[i] = make_float2(a.u_nom[2 * i], a.u_nom[2 * i + 1]);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const BRHeader *h = (const BRHeader *)a.ws;
+    const unsigned long long key = h->key;
+    const unsigned k = (unsigned)(key & 0x7fffffffull);
+    BRView bv;
+    bv.tv = a.tv;
+    bv.win = SegWindow{nullptr, nullptr, 0, 0};
+    bv.ubar = subar;
+    bv.ref = (const float4 *)(a.ws + a.off_ref);
+    bv.opp = (const float2 *)(a.ws + a.off_opp);
+    bv.osum = (const float4 *)(a.ws + a.off_osum);
+    bv.odbar = (const float *)(a.ws + a.off_odbar);
+    bv.x0 = h->x0; bv.s_t = h->s_t; bv.d_t = h->d_t; bv.j0 = h->j0;
+    bv.T = a.T; bv.n_opp = a.n_opp; bv.n_tail = a.n_tail;
+    bv.invL = 1.0f / a.tv.L;
+    bv.max_moves = kMaxMoves;
+    bv.key = a.key; bv.ctr_agent_round = a.agent_round; bv.ctr_race = a.race; bv.stream_bit = 0u;
+    int flag = 0;
+    run_candidate<MAXO, true>(bv, a.p, k, a.game_on != 0, false, flag, xi_star, nullptr, u_star);
+    *k_star = (int)k;
+    *any_feasible = (key >> 63) ? 0 : 1;
+}
+
+// ---------------------------------------------------------------- dispatch
+template <int MAXO>
+static void launch_rollout(const BRArgs &a, bool key_mode, cudaStream_t s, int grid, size_t smem)
+{
+    if (key_mode) {
+        br_rollout_kernel<MAXO, true><<<grid, 256, smem, s>>>(a);
+    } else {
+        br_rollout_kernel<MAXO, false><<<grid, 256, smem, s>>>(a);
+    }
+}
+
+static sgtp_status br_common(const sgtp_track *trk, int32_t track_id, const sgtp_params *p, const float *x0,
+                             const float *u_nom, float vref_scale, const float *opp, int32_t n_opp, int32_t T,
+                             int32_t K, uint64_t seed, uint32_t race, uint32_t agent, uint32_t round,
+                             int32_t game_on, void *ws, size_t ws_bytes, BRArgs &a, int &maxo)
+{
+    SGTP_CHECK(trk != nullptr, "track is NULL");
+    SGTP_CHECK(track_id >= 0 && track_id < trk->n_tracks, "track_id %d out of range", track_id);
+    sgtp_status st = check_params(p);
+    if (st) return st;
+    SGTP_CHECK(x0 && u_nom, "x0 / u_nom is NULL");
+    SGTP_CHECK(n_opp >= 0 && n_opp <= SGTP_MAX_AGENTS - 1, "n_opp=%d out of range [0, %d]", n_opp,
+               SGTP_MAX_AGENTS - 1);
+    SGTP_CHECK(n_opp == 0 || opp != nullptr, "opp is NULL with n_opp > 0");
+    SGTP_CHECK(T >= 1 && T <= SGTP_MAX_T, "T=%d out of range [1, %d]", T, SGTP_MAX_T);
+    SGTP_CHECK(K >= 1 && K <= SGTP_MAX_K, "K=%d out of range [1, 2^30]", K);
+    SGTP_CHECK(agent < (1u << 16) && round < (1u << 16) && race < (1u << 31), "agent/round/race out of range");
+    SGTP_CHECK(std::isfinite(vref_scale) && vref_scale >= 0.f, "vref_scale must be finite and >= 0");
+    const BRLayout lay(n_opp, T);
+    SGTP_CHECK(ws != nullptr && ws_bytes >= lay.total, "workspace too small: need %zu bytes", lay.total);
+    SGTP_CHECK(((uintptr_t)ws & 255u) == 0, "workspace must be 256-byte aligned");
+    a = BRArgs{};
+    a.tv = track_view(trk, track_id);
+    a.p = *p;
+    a.ws = (const unsigned char *)ws;
+    a.off_ref = lay.ref; a.off_opp = lay.opp; a.off_osum = lay.osum; a.off_odbar = lay.odbar;
+    a.u_nom = u_nom;
+    a.T = T; a.n_opp = n_opp; a.K = K;
+    a.n_tail = tail_count(p->mu_tail, T);
+    a.Wn = a.tv.N < 1024 ? a.tv.N : 1024;
+    a.back = a.Wn >= 256 ? 64 : a.Wn / 4;
+    a.key = make_uint2((unsigned)seed, (unsigned)(seed >> 32));
+    a.agent_round = agent | (round << 16);
+    a.race = race;
+    a.game_on = game_on;
+    a.timeout_ns = 1000000000ll;
+    maxo = n_opp <= 1 ? 1 : n_opp <= 3 ? 3 : n_opp <= 9 ? 9 : 15;
+    return SGTP_OK;
+}
+
+static sgtp_status br_launch(const BRArgs &a, int maxo, bool key_mode, const float *x0, const float *opp,
+                             float vref_scale, cudaStream_t s)
+{
+    const BRSmemLayout L(a.Wn, a.T, a.n_opp);
+    const int grid = (a.K + 255) / 256;
+    br_prep_kernel<<<1, 32 * (1 + (a.n_opp < 8 ? (a.n_opp > 0 ? a.n_opp : 1) : 8)), 0, s>>>(
+        a.tv, a.p, x0, opp, a.n_opp, a.T, vref_scale, a.n_tail, (unsigned char *)a.ws, a.off_ref, a.off_opp,
+        a.off_osum, a.off_odbar);
+    switch (maxo) {
+        case 1: {
+            static bool set = false;
+            if (!set) { cudaFuncSetAttribute(br_rollout_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                        cudaFuncSetAttribute(br_rollout_kernel<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); set = true; }
+            launch_rollout<1>(a, key_mode, s, grid, L.total);
+            break;
+        }
+        case 3: {
+            static bool set = false;
+            if (!set) { cudaFuncSetAttribute(br_rollout_kernel<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                        cudaFuncSetAttribute(br_rollout_kernel<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); set = true; }
+            launch_rollout<3>(a, key_mode, s, grid, L.total);
+            break;
+        }
+        case 9: {
+            static bool set = false;
+            if (!set) { cudaFuncSetAttribute(br_rollout_kernel<9, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                        cudaFuncSetAttribute(br_rollout_kernel<9, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); set = true; }
+            launch_rollout<9>(a, key_mode, s, grid, L.total);
+            break;
+        }
+        default: {
+            static bool set = false;
+            if (!set) { cudaFuncSetAttribute(br_rollout_kernel<15, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                        cudaFuncSetAttribute(br_rollout_kernel<15, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); set = true; }
+            launch_rollout<15>(a, key_mode, s, grid, L.total);
+            break;
+        }
+    }
+    count_launch(2);
+    SGTP_CUDA(cudaGetLastError());
+    return SGTP_OK;
+}
+
+extern "C" size_t sgtp_br_workspace_bytes(int32_t n_opp, int32_t T)
+{
+    if (n_opp < 0 || T < 1) return 0;
+    return BRLayout(n_opp, T).total;
+}
+
+extern "C" sgtp_status sgtp_rollout_costs(const sgtp_track *trk, int32_t track_id, const sgtp_params *p,
+                                          const float *x0, const float *u_nom, float vref_scale, const float *opp,
+                                          int32_t n_opp, int32_t T, int32_t K, uint64_t seed, uint32_t race,
+                                          uint32_t agent, uint32_t round, int32_t game_on, float *cost,
+                                          uint8_t *feasible, float *violation, float *states, float *frenet,
+                                          float *controls, void *workspace, size_t workspace_bytes, void *stream)
+{
+    BRArgs a;
+    int maxo;
+    sgtp_status st = br_common(trk, track_id, p, x0, u_nom, vref_scale, opp, n_opp, T, K, seed, race, agent, round,
+                               game_on, workspace, workspace_bytes, a, maxo);
+    if (st) return st;
+    SGTP_CHECK(cost && feasible && violation, "cost/feasible/violation is NULL");
+    a.cost = cost; a.feas = feasible; a.viol = violation;
+    a.states = states; a.frenet = frenet; a.controls = controls;
+    return br_launch(a, maxo, false, x0, opp, vref_scale, (cudaStream_t)stream);
+}
+
+extern "C" sgtp_status sgtp_best_response(const sgtp_track *trk, int32_t track_id, const sgtp_params *p,
+                                          const float *x0, const float *u_nom, float vref_scale, const float *opp,
+                                          int32_t n_opp, int32_t T, int32_t K, uint64_t seed, uint32_t race,
+                                          uint32_t agent, uint32_t round, int32_t game_on, int32_t *k_star,
+                                          float *u_star, float *xi_star, int32_t *any_feasible, void *workspace,
+                                          size_t workspace_bytes, void *stream)
+{
+    BRArgs a;
+    int maxo;
+    sgtp_status st = br_common(trk, track_id, p, x0, u_nom, vref_scale, opp, n_opp, T, K, seed, race, agent, round,
+                               game_on, workspace, workspace_bytes, a, maxo);
+    if (st) return st;
+    SGTP_CHECK(k_star && u_star && xi_star && any_feasible, "NULL output");
+    cudaStream_t s = (cudaStream_t)stream;
+    st = br_launch(a, maxo, true, x0, opp, vref_scale, s);
+    if (st) return st;
+    switch (maxo) {
+        case 1: br_finalize_kernel<1><<<1, 32, 0, s>>>(a, k_star, u_star, xi_star, any_feasible); break;
+        case 3: br_finalize_kernel<3><<<1, 32, 0, s>>>(a, k_star, u_star, xi_star, any_feasible); break;
+        case 9: br_finalize_kernel<9><<<1, 32, 0, s>>>(a, k_star, u_star, xi_star, any_feasible); break;
+        default: br_finalize_kernel<15><<<1, 32, 0, s>>>(a, k_star, u_star, xi_star, any_feasible); break;
+    }
+    count_launch();
+    SGTP_CUDA(cudaGetLastError());
+    return SGTP_OK;
+}

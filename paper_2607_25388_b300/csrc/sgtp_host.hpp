@@ -1,0 +1,66 @@
+// sgtp_host.hpp -- host-side pieces shared by the ABI translation units:
+// the track object, error text, launch counting and argument checks.
+#pragma once
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "sgtp.h"
+#include "sgtp_device.cuh"
+
+struct sgtp_track {
+    int n_tracks = 0;
+    int total = 0;                         // segments over all tracks
+    float4 *A = nullptr, *B = nullptr, *W = nullptr, *C = nullptr;
+    sgtp::TrackDesc *desc_dev = nullptr;
+    std::vector<sgtp::TrackDesc> desc;     // host copy (L filled after prep)
+    int device = 0;
+};
+
+namespace sgtp {
+
+sgtp_status set_error(sgtp_status s, const char *fmt, ...);
+void count_launch(int n = 1);
+
+inline TrackView track_view(const sgtp_track *t, int id)
+{
+    const TrackDesc &d = t->desc[id];
+    TrackView v;
+    v.A = t->A + d.offset; v.B = t->B + d.offset; v.W = t->W + d.offset; v.C = t->C + d.offset;
+    v.N = d.N; v.L = d.L;
+    return v;
+}
+
+// Per-vehicle tail count of the blocking term: ceil(mu * H - 1e-4) clamped
+// to [1, H], evaluated in double on the host so that every kernel sees the
+// same integer.
+inline int tail_count(float mu, int T)
+{
+    double v = (double)mu * (double)T - 1e-4;
+    int n = (int)v;
+    if ((double)n < v) n += 1;
+    if (n < 1) n = 1;
+    if (n > T) n = T;
+    return n;
+}
+
+inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+sgtp_status check_params(const sgtp_params *p);
+
+}  // namespace sgtp
+
+#define SGTP_CUDA(x)                                                                                  \
+    do {                                                                                              \
+        cudaError_t e_ = (x);                                                                         \
+        if (e_ != cudaSuccess) return sgtp::set_error(SGTP_E_CUDA, "%s: %s", #x, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define SGTP_CHECK(cond, ...)                                            \
+    do {                                                                 \
+        if (!(cond)) return sgtp::set_error(SGTP_E_INVALID, __VA_ARGS__); \
+    } while (0)

@@ -1,0 +1,72 @@
+"""Shared helpers of the GPU parity tests: comparison rules against the
+FP64 oracle.
+
+Tolerances (written here once and used by every parity test):
+
+* states, Frenet progress/offset: |gpu - oracle| <= STATE_RTOL * max(1, |oracle|)
+  with STATE_RTOL = 1e-4 (relative; absolute below magnitude 1).
+* cost: same rule with COST_RTOL = 1e-4, for candidates not near a threshold.
+* feasibility flags: exact, except candidates whose oracle indicator
+  arguments lie within a guard band of their threshold (boundary clearance
+  within GUARD_DIST of m_bd, obstacle clearance within GUARD_DIST of d_col,
+  |Delta s| within GUARD_PROG of s_contest / s_role).  The bands bound the
+  float32 rounding of coordinates up to a few km (ulp 2.4e-4 m at 3 km)
+  accumulated over at most 128 steps.
+* selected index: equal, unless the oracle costs (or violations) of the two
+  picks differ by less than SELECT_RTOL = 1e-5 relative, or either pick is
+  near a threshold.
+"""
+import numpy as np
+
+STATE_RTOL = 1e-4
+COST_RTOL = 1e-4
+SELECT_RTOL = 1e-5
+GUARD_DIST = 2e-3
+GUARD_PROG = 2e-2
+
+
+def assert_rel_close(gpu, ref, rtol, what, mask=None):
+    gpu = np.asarray(gpu, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    err = np.abs(gpu - ref) / np.maximum(1.0, np.abs(ref))
+    if mask is not None:
+        err = err[mask]
+    worst = float(err.max()) if err.size else 0.0
+    assert worst <= rtol, f"{what}: worst relative error {worst:.3e} > {rtol:.1e}"
+    return worst
+
+
+def borderline(margins):
+    """Candidates whose oracle indicator arguments sit within the guard band."""
+    m = np.asarray(margins)
+    return (m[:, 0] <= GUARD_DIST) | (m[:, 1] <= GUARD_DIST) | (m[:, 2] <= GUARD_PROG)
+
+
+def check_candidates(gpu, orc, what=""):
+    """Element-wise comparison of per-candidate outputs; returns the number
+    of borderline candidates excluded from the exact checks."""
+    bl = borderline(orc["margins"])
+    ok = ~bl
+    feas_g = np.asarray(gpu["feasible"]).astype(bool)
+    feas_o = np.asarray(orc["feasible"]).astype(bool)
+    bad = np.nonzero((feas_g != feas_o) & ok)[0]
+    assert bad.size == 0, f"{what}: feasibility differs at k={bad[:10]} (of {bad.size})"
+    assert_rel_close(np.asarray(gpu["cost"])[ok], orc["cost"][ok], COST_RTOL, f"{what} cost")
+    assert_rel_close(np.asarray(gpu["violation"])[ok], orc["violation"][ok], COST_RTOL, f"{what} violation")
+    return int(bl.sum())
+
+
+def selection_ok(k_gpu, k_orc, orc_cost, orc_feas, orc_viol, orc_margins=None):
+    """Selected index equal, or an allowed near-tie (see module docstring)."""
+    if k_gpu == k_orc:
+        return True
+    if orc_margins is not None:
+        bl = borderline(orc_margins)
+        if bl[k_gpu] or bl[k_orc]:
+            return True
+    fg, fo = bool(orc_feas[k_gpu]), bool(orc_feas[k_orc])
+    if fg != fo:
+        return False
+    vg = orc_cost[k_gpu] if fo else orc_viol[k_gpu]
+    vo = orc_cost[k_orc] if fo else orc_viol[k_orc]
+    return abs(vg - vo) <= SELECT_RTOL * max(1.0, abs(vo))
