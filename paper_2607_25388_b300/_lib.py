@@ -39,7 +39,8 @@ class Params(C.Structure):
 
 class LaunchOpts(C.Structure):
     _fields_ = [("block", C.c_int32), ("samples_per_thread", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("window", C.c_int32), ("wait_timeout_ns", C.c_int64), ("debug_flags", C.c_int32)]
+                ("window", C.c_int32), ("wait_timeout_ns", C.c_int64), ("debug_flags", C.c_int32),
+                ("trace_ns", C.c_void_p)]
 
 
 class Race(C.Structure):

@@ -57,37 +57,43 @@ extern "C" int64_t sgtp_launch_count(void) { return (int64_t)g_launches.load(); 
 
 // ================================================================ track prep
 // One CTA per track: per-segment chords, inverse squared lengths, width,
-// heading and speed increments; then a compensated (Kahan) running sum of the
-// segment lengths gives s_j in float32 to about one ulp of L.
-__global__ void track_prep_kernel(const float *xr, const float *wl, const float *wr, TrackDesc *desc, float4 *A,
-                                  float4 *B, float4 *W, float4 *C)
+// heading and speed increments for the ring-extended arrays; then a
+// compensated (Kahan) running sum of the segment lengths gives s_j in float32
+// to about one ulp of L.
+__global__ void track_prep_kernel(const float *xr, const float *wl, const float *wr, const int *src_off,
+                                  TrackDesc *desc, float4 *A, float *I, float4 *SB, float2 *SW, float4 *C)
 {
-    TrackDesc d = desc[blockIdx.x];
-    for (int j = threadIdx.x; j < d.N; j += blockDim.x) {
-        const int g = d.offset + j;
-        const int gn = d.offset + (j + 1 == d.N ? 0 : j + 1);
-        const float x0 = xr[4 * g], y0 = xr[4 * g + 1], p0 = xr[4 * g + 2], v0 = xr[4 * g + 3];
-        const float x1 = xr[4 * gn], y1 = xr[4 * gn + 1], p1 = xr[4 * gn + 2], v1 = xr[4 * gn + 3];
-        const float ex = x1 - x0, ey = y1 - y0;
+    const TrackDesc d = desc[blockIdx.x];
+    const int so = src_off[blockIdx.x];
+    const int next = ext_len_dev(d.N);
+    for (int j = threadIdx.x; j < next; j += blockDim.x) {
+        const int g = j % d.N;
+        const int gn = g + 1 == d.N ? 0 : g + 1;
+        const float *p0 = xr + 4 * (size_t)(so + g), *p1 = xr + 4 * (size_t)(so + gn);
+        const float ex = p1[0] - p0[0], ey = p1[1] - p0[1];
         const float l2 = __fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey));
-        A[g] = make_float4(x0, y0, ex, ey);
-        B[g] = make_float4(1.0f / l2, 0.f, sqrtf(l2), 0.f);
-        W[g] = make_float4(wl[g], wl[gn] - wl[g], wr[g], wr[gn] - wr[g]);
-        C[g] = make_float4(p0, wrap_angle(p1 - p0), v0, v1 - v0);
+        const int o = d.offset + j;
+        A[o] = make_float4(p0[0], p0[1], ex, ey);
+        I[o] = 1.0f / l2;
+        SB[o] = make_float4(0.f, sqrtf(l2), wl[so + g], wl[so + gn] - wl[so + g]);
+        SW[o] = make_float2(wr[so + g], wr[so + gn] - wr[so + g]);
+        C[o] = make_float4(p0[2], wrap_angle(p1[2] - p0[2]), p0[3], p1[3] - p0[3]);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         float sum = 0.f, comp = 0.f;
         for (int j = 0; j < d.N; ++j) {
-            const int g = d.offset + j;
-            B[g].y = sum;
-            const float y = B[g].z - comp;
+            const int o = d.offset + j;
+            SB[o].x = sum;
+            const float y = SB[o].y - comp;
             const float t = sum + y;
             comp = (t - sum) - y;
             sum = t;
         }
         desc[blockIdx.x].L = sum;
     }
+    __syncthreads();
+    for (int j = d.N + threadIdx.x; j < next; j += blockDim.x) SB[d.offset + j].x = SB[d.offset + j % d.N].x;
 }
 
 static sgtp_status track_create_impl(const float *xr, const float *wl, const float *wr, const int32_t *offsets,
@@ -102,8 +108,8 @@ static sgtp_status track_create_impl(const float *xr, const float *wl, const flo
         const int N = offsets[t + 1] - offsets[t];
         SGTP_CHECK(N >= 3 && N <= (1 << 20), "track %d: N=%d out of range [3, 2^20]", t, N);
     }
-    const int total = offsets[n_tracks];
-    SGTP_CHECK(total <= (1 << 26), "too many waypoints");
+    const int total_src = offsets[n_tracks];
+    SGTP_CHECK(total_src <= (1 << 26), "too many waypoints");
     for (int t = 0; t < n_tracks; ++t) {
         const int o = offsets[t], N = offsets[t + 1] - o;
         for (int j = 0; j < N; ++j) {
@@ -118,33 +124,42 @@ static sgtp_status track_create_impl(const float *xr, const float *wl, const flo
     cudaStream_t s = (cudaStream_t)stream;
     sgtp_track *T = new sgtp_track();
     T->n_tracks = n_tracks;
-    T->total = total;
     cudaGetDevice(&T->device);
     T->desc.resize(n_tracks);
-    for (int t = 0; t < n_tracks; ++t) T->desc[t] = TrackDesc{offsets[t], offsets[t + 1] - offsets[t], 0.f, 0};
+    long long total = 0;
+    for (int t = 0; t < n_tracks; ++t) {
+        const int N = offsets[t + 1] - offsets[t];
+        T->desc[t] = TrackDesc{(int)total, N, 0.f, 0};
+        total += ext_len(N);
+    }
+    T->total = total;
+    SGTP_CHECK(total < (1ll << 31), "tracks too large");
     float *d_xr = nullptr, *d_wl = nullptr, *d_wr = nullptr;
+    int *d_off = nullptr;
     auto cleanup = [&]() {
-        cudaFree(d_xr); cudaFree(d_wl); cudaFree(d_wr);
+        cudaFree(d_xr); cudaFree(d_wl); cudaFree(d_wr); cudaFree(d_off);
     };
     cudaError_t e = cudaSuccess;
-    const size_t seg = (size_t)total * sizeof(float4);
-    if ((e = cudaMalloc(&T->A, seg)) || (e = cudaMalloc(&T->B, seg)) || (e = cudaMalloc(&T->W, seg)) ||
-        (e = cudaMalloc(&T->C, seg)) || (e = cudaMalloc(&T->desc_dev, sizeof(TrackDesc) * n_tracks)) ||
-        (e = cudaMalloc(&d_xr, sizeof(float) * 4 * total)) || (e = cudaMalloc(&d_wl, sizeof(float) * total)) ||
-        (e = cudaMalloc(&d_wr, sizeof(float) * total))) {
+    if ((e = cudaMalloc(&T->A, sizeof(float4) * total)) || (e = cudaMalloc(&T->I, sizeof(float) * total)) ||
+        (e = cudaMalloc(&T->SB, sizeof(float4) * total)) || (e = cudaMalloc(&T->SW, sizeof(float2) * total)) ||
+        (e = cudaMalloc(&T->C, sizeof(float4) * total)) ||
+        (e = cudaMalloc(&T->desc_dev, sizeof(TrackDesc) * n_tracks)) ||
+        (e = cudaMalloc(&d_xr, sizeof(float) * 4 * total_src)) || (e = cudaMalloc(&d_wl, sizeof(float) * total_src)) ||
+        (e = cudaMalloc(&d_wr, sizeof(float) * total_src)) || (e = cudaMalloc(&d_off, sizeof(int) * n_tracks))) {
         cleanup();
         sgtp_track_destroy(T);
         return set_error(SGTP_E_NOMEM, "track allocation failed: %s", cudaGetErrorString(e));
     }
-    if ((e = cudaMemcpyAsync(d_xr, xr, sizeof(float) * 4 * total, cudaMemcpyHostToDevice, s)) ||
-        (e = cudaMemcpyAsync(d_wl, wl, sizeof(float) * total, cudaMemcpyHostToDevice, s)) ||
-        (e = cudaMemcpyAsync(d_wr, wr, sizeof(float) * total, cudaMemcpyHostToDevice, s)) ||
+    if ((e = cudaMemcpyAsync(d_xr, xr, sizeof(float) * 4 * total_src, cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(d_wl, wl, sizeof(float) * total_src, cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(d_wr, wr, sizeof(float) * total_src, cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(d_off, offsets, sizeof(int) * n_tracks, cudaMemcpyHostToDevice, s)) ||
         (e = cudaMemcpyAsync(T->desc_dev, T->desc.data(), sizeof(TrackDesc) * n_tracks, cudaMemcpyHostToDevice, s))) {
         cleanup();
         sgtp_track_destroy(T);
         return set_error(SGTP_E_CUDA, "track upload failed: %s", cudaGetErrorString(e));
     }
-    track_prep_kernel<<<n_tracks, 256, 0, s>>>(d_xr, d_wl, d_wr, T->desc_dev, T->A, T->B, T->W, T->C);
+    track_prep_kernel<<<n_tracks, 256, 0, s>>>(d_xr, d_wl, d_wr, d_off, T->desc_dev, T->A, T->I, T->SB, T->SW, T->C);
     count_launch();
     if ((e = cudaGetLastError()) ||
         (e = cudaMemcpyAsync(T->desc.data(), T->desc_dev, sizeof(TrackDesc) * n_tracks, cudaMemcpyDeviceToHost, s)) ||
@@ -175,7 +190,7 @@ extern "C" sgtp_status sgtp_track_create_many(const float *xr, const float *wl, 
 extern "C" void sgtp_track_destroy(sgtp_track *T)
 {
     if (!T) return;
-    cudaFree(T->A); cudaFree(T->B); cudaFree(T->W); cudaFree(T->C); cudaFree(T->desc_dev);
+    cudaFree(T->A); cudaFree(T->I); cudaFree(T->SB); cudaFree(T->SW); cudaFree(T->C); cudaFree(T->desc_dev);
     delete T;
 }
 
@@ -192,14 +207,14 @@ extern "C" sgtp_status sgtp_track_info(const sgtp_track *trk, int32_t track_id, 
 
 // ================================================================ single BR
 // Workspace of one best response: a header followed by the per-problem
-// arrays (all 16-byte aligned).
+// arrays (all 256-byte aligned).
 struct BRHeader {
     unsigned long long key;     // running minimum selection key
     int flag;                   // device-side check flags
-    int pad0;
+    int j0;                     // nearest segment of x_{i,t}
     float4 x0;
     float s_t, d_t;
-    int j0, pad1;
+    int pad[2];
 };
 
 struct BRLayout {
@@ -207,15 +222,14 @@ struct BRLayout {
     BRLayout(int n_opp, int T)
     {
         auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+        const int no = n_opp > 0 ? n_opp : 1;
         ref = up(sizeof(BRHeader));
         opp = up(ref + sizeof(float4) * (T + 1));
-        osum = up(opp + sizeof(float2) * (size_t)T * (n_opp > 0 ? n_opp : 1));
-        odbar = up(osum + sizeof(float4) * (n_opp > 0 ? n_opp : 1));
-        total = up(odbar + sizeof(float) * (n_opp > 0 ? n_opp : 1));
+        osum = up(opp + sizeof(float2) * (size_t)T * no);
+        odbar = up(osum + sizeof(float4) * no);
+        total = up(odbar + sizeof(float) * no);
     }
 };
-
-constexpr int kMaxMoves = 64;
 
 // Per-problem preparation (one CTA): Frenet of x_{i,t} by global search, the
 // reference trajectory (Sec. III-A, overall ranking), and for every opponent
@@ -235,7 +249,7 @@ __global__ void br_prep_kernel(TrackView tv, sgtp_params p, const float *x0, con
     __shared__ float s_t_sh;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const float invL = 1.0f / tv.L;
-    const SegWindow nowin{nullptr, nullptr, 0, 0};
+    const SegWindow nowin{nullptr, nullptr, nullptr, nullptr, 0, 0};
     if (warp == 0) {
         const float4 x = make_float4(x0[0], x0[1], x0[2], x0[3]);
         const int j = nearest_segment_warp(tv, x.x, x.y);
@@ -248,29 +262,20 @@ __global__ void br_prep_kernel(TrackView tv, sgtp_params p, const float *x0, con
             h->d_t = f.d;
             h->j0 = j;
             s_t_sh = f.s;
-            // s^r_0 = s_{i,t}; s^r_{tau+1} = s^r_tau + dt * v^r(s^r_tau)
-            int jr = j;
-            float sr = f.s;
-            ref[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int tau = 0; tau < T; ++tau) {
-                const float4 r0 = reference_at(tv, jr, sr);
-                sr = __fmaf_rn(p.dt, __fmul_rn(vscale, r0.w), sr);
-                float4 r1 = reference_at(tv, jr, sr);
-                r1.w = __fmul_rn(r1.w, vscale);
-                ref[tau + 1] = r1;
-            }
+            reference_traj(tv, SegWindow{nullptr, nullptr, nullptr, nullptr, 0, 0}, nullptr, j, f.s, p.dt, vscale,
+                           T, ref);
         }
     }
     for (int o = warp - 1; o >= 0 && o < n_opp; o += (nwarps > 1 ? nwarps - 1 : n_opp)) {
         const float *q = opp + (size_t)o * (T + 1) * 4;
-        int j = nearest_segment_warp(tv, q[0], q[1]);
+        const int j = nearest_segment_warp(tv, q[0], q[1]);
         if (lane == 0) {
             const FrenetPt f0 = frenet_at(tv, j, q[0], q[1]);
             float s = f0.s, dsum = 0.f;
-            int flag = 0;
+            int flag = 0, r = j, dr = 0;      // window-less walk: r is the global index
             for (int tau = 1; tau <= T; ++tau) {
                 const float px = q[4 * tau], py = q[4 * tau + 1];
-                const FrenetPt f = frenet_walk(tv, nowin, j, px, py, kMaxMoves, flag);
+                const FrenetPt f = frenet_walk(tv, nowin, r, dr, px, py, flag);
                 s = s + wrap_len(f.s - s, tv.L, invL);
                 if (tau > T - n_tail) dsum = dsum + f.d;
                 opos[(size_t)(tau - 1) * n_opp + o] = make_float2(px, py);
@@ -292,14 +297,12 @@ __global__ void br_prep_kernel(TrackView tv, sgtp_params p, const float *x0, con
 }
 
 struct BRSmemLayout {
-    int Wn, T, n_opp;
-    size_t sA, sB, ref, ubar, opp, osum, odbar, total;
-    __host__ __device__ BRSmemLayout(int Wn_, int T_, int n_opp_) : Wn(Wn_), T(T_), n_opp(n_opp_)
+    WindowSmem win;
+    size_t ref, ubar, opp, osum, odbar, total;
+    __host__ __device__ BRSmemLayout(int Wn, int T, int n_opp) : win(16, Wn)
     {
         auto up = [](size_t x) { return (x + 15) & ~(size_t)15; };
-        sA = 16;
-        sB = sA + sizeof(float4) * Wn;
-        ref = sB + sizeof(float4) * Wn;
+        ref = up(win.end);
         ubar = up(ref + sizeof(float4) * (T + 1));
         opp = up(ubar + sizeof(float2) * T);
         osum = up(opp + sizeof(float2) * (size_t)T * n_opp);
@@ -307,21 +310,6 @@ struct BRSmemLayout {
         total = up(odbar + sizeof(float) * n_opp);
     }
 };
-
-// Stage the track window [w0, w0+Wn) mod N into shared memory with bulk
-// (TMA) copies, one or two pieces per array; the caller waits on bar.
-__device__ __forceinline__ void stage_window(const TrackView &tv, int w0, int Wn, float4 *sA, float4 *sB,
-                                             unsigned long long *bar)
-{
-    const int n1 = min(Wn, tv.N - w0);
-    mbar_expect_tx(bar, (unsigned)(2 * Wn * sizeof(float4)));
-    bulk_g2s(sA, tv.A + w0, (unsigned)(n1 * sizeof(float4)), bar);
-    bulk_g2s(sB, tv.B + w0, (unsigned)(n1 * sizeof(float4)), bar);
-    if (n1 < Wn) {
-        bulk_g2s(sA + n1, tv.A, (unsigned)((Wn - n1) * sizeof(float4)), bar);
-        bulk_g2s(sB + n1, tv.B, (unsigned)((Wn - n1) * sizeof(float4)), bar);
-    }
-}
 
 struct BRArgs {
     TrackView tv;
@@ -339,6 +327,20 @@ struct BRArgs {
     long long timeout_ns;
 };
 
+__device__ __forceinline__ BRView make_view(const BRArgs &a, const BRHeader *h, const SegWindow &win)
+{
+    BRView bv;
+    bv.tv = a.tv;
+    bv.win = win;
+    bv.x0 = h->x0; bv.s_t = h->s_t; bv.d_t = h->d_t;
+    bv.r0 = wrap_index(h->j0 - win.w0, a.tv.N);
+    if (win.Wn == 0) bv.r0 = h->j0;
+    bv.T = a.T; bv.n_opp = a.n_opp; bv.n_tail = a.n_tail;
+    bv.invL = 1.0f / a.tv.L;
+    bv.key = a.key; bv.ctr_agent_round = a.agent_round; bv.ctr_race = a.race; bv.stream_bit = 0u;
+    return bv;
+}
+
 template <int MAXO, bool KEY_MODE>
 __global__ void __launch_bounds__(256) br_rollout_kernel(BRArgs a)
 {
@@ -347,22 +349,19 @@ __global__ void __launch_bounds__(256) br_rollout_kernel(BRArgs a)
     __shared__ int cta_flag;
     const BRSmemLayout L(a.Wn, a.T, a.n_opp);
     unsigned long long *bar = (unsigned long long *)smem;
-    float4 *sA = (float4 *)(smem + L.sA);
-    float4 *sB = (float4 *)(smem + L.sB);
     float4 *sref = (float4 *)(smem + L.ref);
     float2 *subar = (float2 *)(smem + L.ubar);
     float2 *sopp = (float2 *)(smem + L.opp);
     float4 *sosum = (float4 *)(smem + L.osum);
     float *sodbar = (float *)(smem + L.odbar);
     const BRHeader *h = (const BRHeader *)a.ws;
-    const int j0 = h->j0;
-    const int w0 = wrap_index(j0 - a.back, a.tv.N);
+    const int w0 = window_start(h->j0, a.back, a.tv.N);
     if (threadIdx.x == 0) {
         cta_key = ~0ull;
         cta_flag = 0;
         mbar_init(bar, 1);
-        stage_window(a.tv, w0, a.Wn, sA, sB, bar);
     }
+    const SegWindow win = stage_window_issue(a.tv, w0, a.Wn, smem, L.win, bar, threadIdx.x == 0);
     const float4 *gref = (const float4 *)(a.ws + a.off_ref);
     for (int i = threadIdx.x; i <= a.T; i += blockDim.x) sref[i] = gref[i];
     for (int i = threadIdx.x; i < a.T; i += blockDim.x) subar[i] = make_float2(a.u_nom[2 * i], a.u_nom[2 * i + 1]);
@@ -372,18 +371,11 @@ __global__ void __launch_bounds__(256) br_rollout_kernel(BRArgs a)
     const float *godbar = (const float *)(a.ws + a.off_odbar);
     for (int i = threadIdx.x; i < a.n_opp; i += blockDim.x) { sosum[i] = gosum[i]; sodbar[i] = godbar[i]; }
     __syncthreads();
-    if (!mbar_wait_bounded(bar, 0, (unsigned long long)a.timeout_ns)) cta_flag = SGTP_E_TIMEOUT;
+    if (threadIdx.x == 0 && !mbar_wait_bounded(bar, 0, (unsigned long long)a.timeout_ns)) cta_flag = SGTP_E_TIMEOUT;
     __syncthreads();
 
-    BRView bv;
-    bv.tv = a.tv;
-    bv.win = SegWindow{sA, sB, w0, a.Wn};
+    BRView bv = make_view(a, h, win);
     bv.ubar = subar; bv.ref = sref; bv.opp = sopp; bv.osum = sosum; bv.odbar = sodbar;
-    bv.x0 = h->x0; bv.s_t = h->s_t; bv.d_t = h->d_t; bv.j0 = j0;
-    bv.T = a.T; bv.n_opp = a.n_opp; bv.n_tail = a.n_tail;
-    bv.invL = 1.0f / a.tv.L;
-    bv.max_moves = kMaxMoves;
-    bv.key = a.key; bv.ctr_agent_round = a.agent_round; bv.ctr_race = a.race; bv.stream_bit = 0u;
 
     int flag = 0;
     unsigned long long best = ~0ull;
@@ -420,7 +412,7 @@ __global__ void __launch_bounds__(256) br_rollout_kernel(BRArgs a)
     }
 }
 
-// Selection result and re-roll of the winner (one warp, lane 0).
+// Selection result and re-roll of the winner (lane 0; window-less walk).
 template <int MAXO>
 __global__ void br_finalize_kernel(BRArgs a, int *k_star, float *u_star, float *xi_star, int *any_feasible)
 {
@@ -431,19 +423,12 @@ __global__ void br_finalize_kernel(BRArgs a, int *k_star, float *u_star, float *
     const BRHeader *h = (const BRHeader *)a.ws;
     const unsigned long long key = h->key;
     const unsigned k = (unsigned)(key & 0x7fffffffull);
-    BRView bv;
-    bv.tv = a.tv;
-    bv.win = SegWindow{nullptr, nullptr, 0, 0};
+    BRView bv = make_view(a, h, SegWindow{nullptr, nullptr, nullptr, nullptr, 0, 0});
     bv.ubar = subar;
     bv.ref = (const float4 *)(a.ws + a.off_ref);
     bv.opp = (const float2 *)(a.ws + a.off_opp);
     bv.osum = (const float4 *)(a.ws + a.off_osum);
     bv.odbar = (const float *)(a.ws + a.off_odbar);
-    bv.x0 = h->x0; bv.s_t = h->s_t; bv.d_t = h->d_t; bv.j0 = h->j0;
-    bv.T = a.T; bv.n_opp = a.n_opp; bv.n_tail = a.n_tail;
-    bv.invL = 1.0f / a.tv.L;
-    bv.max_moves = kMaxMoves;
-    bv.key = a.key; bv.ctr_agent_round = a.agent_round; bv.ctr_race = a.race; bv.stream_bit = 0u;
     int flag = 0;
     run_candidate<MAXO, true>(bv, a.p, k, a.game_on != 0, false, flag, xi_star, nullptr, u_star);
     *k_star = (int)k;
@@ -452,14 +437,24 @@ __global__ void br_finalize_kernel(BRArgs a, int *k_star, float *u_star, float *
 
 // ---------------------------------------------------------------- dispatch
 template <int MAXO>
-static void launch_rollout(const BRArgs &a, bool key_mode, cudaStream_t s, int grid, size_t smem)
+static sgtp_status launch_rollout(const BRArgs &a, bool key_mode, cudaStream_t s, int grid, size_t smem)
 {
-    if (key_mode) {
-        br_rollout_kernel<MAXO, true><<<grid, 256, smem, s>>>(a);
-    } else {
-        br_rollout_kernel<MAXO, false><<<grid, 256, smem, s>>>(a);
+    static bool configured = false;
+    if (!configured) {
+        SGTP_CUDA(cudaFuncSetAttribute(br_rollout_kernel<MAXO, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024));
+        SGTP_CUDA(cudaFuncSetAttribute(br_rollout_kernel<MAXO, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024));
+        configured = true;
     }
+    if (key_mode)
+        br_rollout_kernel<MAXO, true><<<grid, 256, smem, s>>>(a);
+    else
+        br_rollout_kernel<MAXO, false><<<grid, 256, smem, s>>>(a);
+    return SGTP_OK;
 }
+
+static int maxo_bucket(int n) { return n <= 1 ? 1 : n <= 3 ? 3 : n <= 9 ? 9 : 15; }
 
 static sgtp_status br_common(const sgtp_track *trk, int32_t track_id, const sgtp_params *p, const float *x0,
                              const float *u_nom, float vref_scale, const float *opp, int32_t n_opp, int32_t T,
@@ -489,14 +484,14 @@ static sgtp_status br_common(const sgtp_track *trk, int32_t track_id, const sgtp
     a.u_nom = u_nom;
     a.T = T; a.n_opp = n_opp; a.K = K;
     a.n_tail = tail_count(p->mu_tail, T);
-    a.Wn = a.tv.N < 1024 ? a.tv.N : 1024;
+    a.Wn = window_len(a.tv.N, 0);
     a.back = a.Wn >= 256 ? 64 : a.Wn / 4;
     a.key = make_uint2((unsigned)seed, (unsigned)(seed >> 32));
     a.agent_round = agent | (round << 16);
     a.race = race;
     a.game_on = game_on;
     a.timeout_ns = 1000000000ll;
-    maxo = n_opp <= 1 ? 1 : n_opp <= 3 ? 3 : n_opp <= 9 ? 9 : 15;
+    maxo = maxo_bucket(n_opp);
     return SGTP_OK;
 }
 
@@ -508,36 +503,14 @@ static sgtp_status br_launch(const BRArgs &a, int maxo, bool key_mode, const flo
     br_prep_kernel<<<1, 32 * (1 + (a.n_opp < 8 ? (a.n_opp > 0 ? a.n_opp : 1) : 8)), 0, s>>>(
         a.tv, a.p, x0, opp, a.n_opp, a.T, vref_scale, a.n_tail, (unsigned char *)a.ws, a.off_ref, a.off_opp,
         a.off_osum, a.off_odbar);
+    sgtp_status st;
     switch (maxo) {
-        case 1: {
-            static bool set = false;
-            if (!set) { cudaFuncSetAttribute(br_rollout_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-                        cudaFuncSetAttribute(br_rollout_kernel<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); set = true; }
-            launch_rollout<1>(a, key_mode, s, grid, L.total);
-            break;
-        }
-        case 3: {
-            static bool set = false;
-            if (!set) { cudaFuncSetAttribute(br_rollout_kernel<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-                        cudaFuncSetAttribute(br_rollout_kernel<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); set = true; }
-            launch_rollout<3>(a, key_mode, s, grid, L.total);
-            break;
-        }
-        case 9: {
-            static bool set = false;
-            if (!set) { cudaFuncSetAttribute(br_rollout_kernel<9, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-                        cudaFuncSetAttribute(br_rollout_kernel<9, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); set = true; }
-            launch_rollout<9>(a, key_mode, s, grid, L.total);
-            break;
-        }
-        default: {
-            static bool set = false;
-            if (!set) { cudaFuncSetAttribute(br_rollout_kernel<15, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-                        cudaFuncSetAttribute(br_rollout_kernel<15, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); set = true; }
-            launch_rollout<15>(a, key_mode, s, grid, L.total);
-            break;
-        }
+        case 1: st = launch_rollout<1>(a, key_mode, s, grid, L.total); break;
+        case 3: st = launch_rollout<3>(a, key_mode, s, grid, L.total); break;
+        case 9: st = launch_rollout<9>(a, key_mode, s, grid, L.total); break;
+        default: st = launch_rollout<15>(a, key_mode, s, grid, L.total); break;
     }
+    if (st) return st;
     count_launch(2);
     SGTP_CUDA(cudaGetLastError());
     return SGTP_OK;

@@ -14,8 +14,10 @@
 
 struct sgtp_track {
     int n_tracks = 0;
-    int total = 0;                         // segments over all tracks
-    float4 *A = nullptr, *B = nullptr, *W = nullptr, *C = nullptr;
+    long long total = 0;                   // elements over all (ring-extended) tracks
+    float4 *A = nullptr, *SB = nullptr, *C = nullptr;
+    float *I = nullptr;
+    float2 *SW = nullptr;
     sgtp::TrackDesc *desc_dev = nullptr;
     std::vector<sgtp::TrackDesc> desc;     // host copy (L filled after prep)
     int device = 0;
@@ -30,9 +32,25 @@ inline TrackView track_view(const sgtp_track *t, int id)
 {
     const TrackDesc &d = t->desc[id];
     TrackView v;
-    v.A = t->A + d.offset; v.B = t->B + d.offset; v.W = t->W + d.offset; v.C = t->C + d.offset;
+    v.A = t->A + d.offset; v.I = t->I + d.offset; v.SB = t->SB + d.offset; v.SW = t->SW + d.offset;
+    v.C = t->C + d.offset;
     v.N = d.N; v.L = d.L;
     return v;
+}
+
+// Elements of one ring-extended track (multiple of 4).
+inline int ext_len(int N) { return (N + kWinMax + 3) & ~3; }
+
+// Window length for a track of N segments: the requested window (default
+// 512), at most kWinMax, at least 8, a multiple of 4.
+inline int window_len(int N, int requested)
+{
+    int w = requested > 0 ? requested : 512;
+    if (w > kWinMax) w = kWinMax;
+    const int n4 = (N + 3) & ~3;
+    if (w > n4) w = n4;
+    if (w < 8) w = 8;
+    return (w + 3) & ~3;
 }
 
 // Per-vehicle tail count of the blocking term: ceil(mu * H - 1e-4) clamped

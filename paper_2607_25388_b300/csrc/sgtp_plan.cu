@@ -22,8 +22,6 @@ using namespace sgtp;
 
 namespace {
 
-constexpr int kMaxMoves = 64;
-
 struct RaceDev {
     int track_id, n_v, T, ego;
     unsigned race_tag;
@@ -46,7 +44,9 @@ struct AgentDev {
 
 struct PlanArgs {
     const TrackDesc *tdesc;
-    const float4 *A, *B, *W, *C;
+    const float4 *A, *SB, *C;
+    const float *I;
+    const float2 *SW;
     sgtp_params p;
     const RaceDev *races;     // NULL: single race `one`
     RaceDev one;
@@ -73,7 +73,13 @@ struct PlanArgs {
     int Wn, back;
     long long timeout_ns;
     int debug_flags;
+    long long *trace;          // optional phase stamps (CTA 0)
 };
+
+__device__ __forceinline__ void stamp(const PlanArgs &a, int i)
+{
+    if (a.trace && blockIdx.x == 0 && threadIdx.x == 0) a.trace[i] = (long long)global_ns();
+}
 
 __device__ __forceinline__ RaceDev get_race(const PlanArgs &a, int r) { return a.races ? a.races[r] : a.one; }
 
@@ -92,7 +98,8 @@ __device__ __forceinline__ TrackView get_track(const PlanArgs &a, int id)
 {
     const TrackDesc d = a.tdesc[id];
     TrackView v;
-    v.A = a.A + d.offset; v.B = a.B + d.offset; v.W = a.W + d.offset; v.C = a.C + d.offset;
+    v.A = a.A + d.offset; v.I = a.I + d.offset; v.SB = a.SB + d.offset; v.SW = a.SW + d.offset;
+    v.C = a.C + d.offset;
     v.N = d.N; v.L = d.L;
     return v;
 }
@@ -117,10 +124,7 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
     return v;
 }
 
-__device__ __forceinline__ int ld_status(const int *p)
-{
-    return *(const volatile int *)p;
-}
+__device__ __forceinline__ int ld_status(const int *p) { return *(const volatile int *)p; }
 
 // Grid-wide barrier of a cooperative launch.  Every wait has a limit: a CTA
 // whose wait runs out records SGTP_E_TIMEOUT and returns false, and every
@@ -151,7 +155,7 @@ __device__ bool grid_barrier(const PlanArgs &a, bool skip_arrival)
                     atomicOr(a.status, SGTP_E_TIMEOUT);
                     break;
                 }
-                __nanosleep(128);
+                __nanosleep(64);
             }
         }
         __threadfence();
@@ -161,128 +165,145 @@ __device__ bool grid_barrier(const PlanArgs &a, bool skip_arrival)
     return ok_sh != 0;
 }
 
-// Roll out one selected (or nominal) control sequence of a vehicle, from the
-// same noise, control and dynamics functions as the sample evaluation, and
-// write its states, controls and Frenet summary.  One thread.
-__device__ void reroll(const PlanArgs &a, const TrackView &tv, const AgentDev &ag, int T, int n_tail,
-                       const float *U, unsigned k, bool zero_noise, unsigned agent_round, unsigned race_tag,
-                       float *U_out, float2 *pos_out, float *xi_a, float *xi_b, float *u_hist, float2 *summ_out,
-                       int &flag)
-{
-    const SegWindow nowin{nullptr, nullptr, 0, 0};
-    const float invL = 1.0f / tv.L;
-    float x = ag.x0.x, y = ag.x0.y, psi = ag.x0.z, v = ag.x0.w;
-    float s = ag.s_t, dsum = 0.f;
-    int j = ag.j0;
-    if (pos_out) pos_out[0] = make_float2(x, y);
-    if (xi_a) { xi_a[0] = x; xi_a[1] = y; xi_a[2] = psi; xi_a[3] = v; }
-    if (xi_b) { xi_b[0] = x; xi_b[1] = y; xi_b[2] = psi; xi_b[3] = v; }
-    for (int m = 0; 2 * m < T; ++m) {
-        float2 z[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-        if (!zero_noise) {
-            const uint4 w = philox4x32_10(make_uint4(k, (unsigned)m, agent_round, race_tag), a.key);
-            z[0] = box_muller(w.x, w.y);
-            z[1] = box_muller(w.z, w.w);
-        }
-        for (int h = 0; h < 2; ++h) {
-            const int tau = 2 * m + h;
-            if (tau >= T) break;
-            const float2 ub = make_float2(__ldcg(U + 2 * tau), __ldcg(U + 2 * tau + 1));
-            const float2 u = sample_control(a.p, ub, z[h]);
-            if (U_out) { U_out[2 * tau] = u.x; U_out[2 * tau + 1] = u.y; }
-            if (u_hist) { u_hist[2 * tau] = u.x; u_hist[2 * tau + 1] = u.y; }
-            bicycle_step(a.p, x, y, psi, v, u.x, u.y);
-            const FrenetPt f = frenet_walk(tv, nowin, j, x, y, kMaxMoves, flag);
-            s = s + wrap_len(f.s - s, tv.L, invL);
-            const int st = tau + 1;
-            if (st > T - n_tail) dsum = dsum + f.d;
-            if (pos_out) pos_out[st] = make_float2(x, y);
-            if (xi_a) { xi_a[4 * st] = x; xi_a[4 * st + 1] = y; xi_a[4 * st + 2] = psi; xi_a[4 * st + 3] = v; }
-            if (xi_b) { xi_b[4 * st] = x; xi_b[4 * st + 1] = y; xi_b[4 * st + 2] = psi; xi_b[4 * st + 3] = v; }
-        }
-    }
-    if (summ_out) *summ_out = make_float2(s - ag.s_t, dsum / (float)n_tail);
-}
-
+// Shared memory of the plan kernel: TMA barrier, track window (A, I, SB,
+// SW) plus the heading/speed array C used by the reference recursion, and the
+// per-best-response arrays.
 struct PlanSmem {
-    size_t sA, sB, ref, ubar, opp, osum, odbar, total;
-    __host__ __device__ PlanSmem(int Wn, int maxT, int maxO)
+    WindowSmem win;
+    size_t C, ref, ubar, opp, osum, odbar, ctl, total;
+    __host__ __device__ PlanSmem(int Wn, int maxT, int maxO) : win(16, Wn)
     {
         auto up = [](size_t x) { return (x + 15) & ~(size_t)15; };
-        sA = 16;
-        sB = sA + sizeof(float4) * Wn;
-        ref = sB + sizeof(float4) * Wn;
+        C = up(win.end);
+        ref = up(C + sizeof(float4) * Wn);
         ubar = up(ref + sizeof(float4) * (maxT + 1));
         opp = up(ubar + sizeof(float2) * maxT);
         osum = up(opp + sizeof(float2) * (size_t)maxT * maxO);
         odbar = up(osum + sizeof(float4) * maxO);
-        total = up(odbar + sizeof(float) * maxO);
+        ctl = up(odbar + sizeof(float) * maxO);
+        total = up(ctl + sizeof(float2) * maxT);
     }
 };
 
+// Stage the window of vehicle A's track (and C when with_c); thread 0 issues,
+// everybody waits at the caller's __syncthreads after mbar_wait.
+__device__ __forceinline__ SegWindow stage_for(const PlanArgs &a, const TrackView &tv, int j0, unsigned char *smem,
+                                               const PlanSmem &SL, unsigned long long *mbar, bool with_c)
+{
+    const int Wn = min(a.Wn, (tv.N + 3) & ~3);
+    const int back = min(a.back, Wn / 4);
+    const int w0 = window_start(j0, back, tv.N);
+    const SegWindow w = stage_window_issue(tv, w0, Wn, smem, SL.win, mbar, false);
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(mbar, (unsigned)Wn * (16u + 4u + 16u + 8u + (with_c ? 16u : 0u)));
+        bulk_g2s(smem + SL.win.A, tv.A + w0, (unsigned)Wn * 16u, mbar);
+        bulk_g2s(smem + SL.win.I, tv.I + w0, (unsigned)Wn * 4u, mbar);
+        bulk_g2s(smem + SL.win.SB, tv.SB + w0, (unsigned)Wn * 16u, mbar);
+        bulk_g2s(smem + SL.win.SW, tv.SW + w0, (unsigned)Wn * 8u, mbar);
+        if (with_c) bulk_g2s(smem + SL.C, tv.C + w0, (unsigned)Wn * 16u, mbar);
+    }
+    return w;
+}
+
+// Sequential rollout of given controls (smem ctl[T]) from x0 with the window
+// walk: writes positions, states and the Frenet summary of a prediction.
+__device__ void roll_controls(const PlanArgs &a, const TrackView &tv, const SegWindow &w, const AgentDev &A, int T,
+                              int n_tail, const float2 *ctl, float2 *pos_out, float *xi_a, float *xi_b,
+                              float2 *summ_out, int &flag)
+{
+    const float invL = 1.0f / tv.L;
+    float x = A.x0.x, y = A.x0.y, psi = A.x0.z, v = A.x0.w;
+    float s = A.s_t, dsum = 0.f;
+    int r = wrap_index(A.j0 - w.w0, tv.N), dr = 0;
+    if (pos_out) pos_out[0] = make_float2(x, y);
+    if (xi_a) *(float4 *)xi_a = A.x0;
+    if (xi_b) *(float4 *)xi_b = A.x0;
+    for (int tau = 0; tau < T; ++tau) {
+        const float2 u = ctl[tau];
+        bicycle_step(a.p, x, y, psi, v, u.x, u.y);
+        const FrenetPt f = frenet_walk(tv, w, r, dr, x, y, flag);
+        s = s + wrap_len(f.s - s, tv.L, invL);
+        const int st = tau + 1;
+        if (st > T - n_tail) dsum = dsum + f.d;
+        if (pos_out) pos_out[st] = make_float2(x, y);
+        const float4 sv = make_float4(x, y, psi, v);
+        if (xi_a) ((float4 *)xi_a)[st] = sv;
+        if (xi_b) ((float4 *)xi_b)[st] = sv;
+    }
+    if (summ_out) *summ_out = make_float2(s - A.s_t, dsum / (float)n_tail);
+}
+
 template <int MAXO>
-__global__ void __launch_bounds__(256, 2) plan_kernel(PlanArgs a)
+__global__ void __launch_bounds__(256, 3) plan_kernel(PlanArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long cta_key;
-    __shared__ int abort_sh;
+    __shared__ int abort_sh, j0_sh;
+    __shared__ unsigned ks_sh;
     const PlanSmem SL(a.Wn, a.maxT, MAXO);
     unsigned long long *mbar = (unsigned long long *)smem;
-    float4 *sA = (float4 *)(smem + SL.sA);
-    float4 *sB = (float4 *)(smem + SL.sB);
+    const float4 *sC = (const float4 *)(smem + SL.C);
     float4 *sref = (float4 *)(smem + SL.ref);
     float2 *subar = (float2 *)(smem + SL.ubar);
     float2 *sopp = (float2 *)(smem + SL.opp);
     float4 *sosum = (float4 *)(smem + SL.osum);
     float *sodbar = (float *)(smem + SL.odbar);
+    float2 *sctl = (float2 *)(smem + SL.ctl);
 
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int gwarp = blockIdx.x * nwarps + warp, total_warps = gridDim.x * nwarps;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool skip = (a.debug_flags & SGTP_DEBUG_SKIP_BARRIER_ARRIVAL) && blockIdx.x == 0;
     int flag = 0;
     unsigned phase = 0;
     bool ok = true;
     if (threadIdx.x == 0) mbar_init(mbar, 1);
+    stamp(a, 0);
 
-    // ------------------------------------------------------------ setup
-    for (int ag = gwarp; ag < a.n_agents; ag += total_warps) {
+    // ------------------------------------------------------------ setup (one CTA per vehicle)
+    for (int ag = blockIdx.x; ag < a.n_agents; ag += gridDim.x) {
         const int ri = find_race(a, ag, [](const RaceDev &r) { return r.agent_off; });
         const RaceDev R = get_race(a, ri);
         const int i = ag - R.agent_off;
         const TrackView tv = get_track(a, R.track_id);
         const float4 x0 = make_float4(a.X0[4 * ag], a.X0[4 * ag + 1], a.X0[4 * ag + 2], a.X0[4 * ag + 3]);
-        const int j0 = nearest_segment_warp(tv, x0.x, x0.y);
-        if (lane == 0) {
-            const FrenetPt f = frenet_at(tv, j0, x0.x, x0.y);
-            AgentDev A;
-            A.x0 = x0; A.s_t = f.s; A.d_t = f.d; A.j0 = j0; A.race = ri;
+        __syncthreads();
+        if (warp == 0) {
+            const int j = nearest_segment_warp(tv, x0.x, x0.y);
+            if (lane == 0) j0_sh = j;
+        }
+        for (int q = threadIdx.x; q < R.T; q += blockDim.x) {
+            // nominal controls, clipped: the zero-noise sample
+            const float *U = a.U_io + R.u_off + (size_t)i * R.T * 2;
+            sctl[q] = sample_control(a.p, make_float2(U[2 * q], U[2 * q + 1]), make_float2(0.f, 0.f));
+        }
+        __syncthreads();
+        const int j0 = j0_sh;
+        const SegWindow w = stage_for(a, tv, j0, smem, SL, mbar, true);
+        if (threadIdx.x == 0) {
+            if (!mbar_wait_bounded(mbar, phase, (unsigned long long)a.timeout_ns)) atomicOr(a.status, SGTP_E_TIMEOUT);
+        }
+        phase ^= 1u;
+        __syncthreads();
+        const FrenetPt f = frenet_at(tv, j0, x0.x, x0.y);
+        AgentDev A;
+        A.x0 = x0; A.s_t = f.s; A.d_t = f.d; A.j0 = j0; A.race = ri;
+        if (threadIdx.x == 0) {
             a.agents[ag] = A;
-            // reference progress recursion s^r_{tau+1} = s^r_tau + dt v^r(s^r_tau)
-            const float vs = a.vref[ag];
-            float4 *ref = a.ref + (size_t)R.pos_off + (size_t)i * (R.T + 1);
-            int jr = j0;
-            float sr = f.s;
-            ref[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int tau = 0; tau < R.T; ++tau) {
-                const float4 r0 = reference_at(tv, jr, sr);
-                sr = __fmaf_rn(a.p.dt, __fmul_rn(vs, r0.w), sr);
-                float4 r1 = reference_at(tv, jr, sr);
-                r1.w = __fmul_rn(r1.w, vs);
-                ref[tau + 1] = r1;
-            }
-            // nominal rollout: round-0 predictions
-            reroll(a, tv, A, R.T, R.n_tail, a.U_io + R.u_off + (size_t)i * R.T * 2, 0u, true, 0u, 0u, nullptr,
-                   a.pos[0] + R.pos_off + (size_t)i * (R.T + 1), nullptr, nullptr, nullptr, a.summ[0] + ag, flag);
+            reference_traj(tv, w, sC, j0, f.s, a.p.dt, a.vref[ag], R.T,
+                           a.ref + (size_t)R.pos_off + (size_t)i * (R.T + 1));
+        } else if (threadIdx.x == 32) {
+            roll_controls(a, tv, w, A, R.T, R.n_tail, sctl, a.pos[0] + R.pos_off + (size_t)i * (R.T + 1), nullptr,
+                          nullptr, a.summ[0] + ag, flag);
         }
     }
     {
         // fresh selection keys for every best response of the plan
         const RaceDev last = get_race(a, a.n_races - 1);
-        const int n_keys = a.races ? (last.ks_off + (a.L + 1) * last.n_v + 1) : ((a.L + 1) * a.one.n_v + 1);
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_keys; i += gridDim.x * blockDim.x)
-            a.keys[i] = ~0ull;
+        const int n_keys = last.ks_off + (a.L + 1) * last.n_v + 1;
+        for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_keys; q += gridDim.x * blockDim.x)
+            a.keys[q] = ~0ull;
     }
     ok = grid_barrier(a, skip);
+    stamp(a, 1);
 
     for (int round = 0; ok && round <= a.L + 1; ++round) {
         const bool extra = round == a.L + 1;
@@ -290,7 +311,7 @@ __global__ void __launch_bounds__(256, 2) plan_kernel(PlanArgs a)
         const int n_items = extra ? a.items_ego : a.items_all;
         const int i0 = (int)((long long)n_items * blockIdx.x / gridDim.x);
         const int i1 = (int)((long long)n_items * (blockIdx.x + 1) / gridDim.x);
-        int cur = -1;                 // current vehicle (global index) staged
+        int cur = -1;                 // vehicle (global index) staged
         unsigned long long *cur_slot = nullptr;
         BRView bv;
         for (int item = i0; item < i1; ++item) {
@@ -315,21 +336,8 @@ __global__ void __launch_bounds__(256, 2) plan_kernel(PlanArgs a)
                 if (threadIdx.x == 0 && cur_slot) atomicMin(cur_slot, cta_key);
                 const TrackView tv = get_track(a, R.track_id);
                 const AgentDev A = load_agent(a.agents + ag);
-                const int Wn = min(a.Wn, tv.N);
-                const int back = min(a.back, Wn / 4);
-                const int w0 = wrap_index(A.j0 - back, tv.N);
-                if (threadIdx.x == 0) {
-                    cta_key = ~0ull;
-                    // track window by bulk copy (TMA)
-                    const int n1 = min(Wn, tv.N - w0);
-                    mbar_expect_tx(mbar, (unsigned)(2 * Wn * sizeof(float4)));
-                    bulk_g2s(sA, tv.A + w0, (unsigned)(n1 * sizeof(float4)), mbar);
-                    bulk_g2s(sB, tv.B + w0, (unsigned)(n1 * sizeof(float4)), mbar);
-                    if (n1 < Wn) {
-                        bulk_g2s(sA + n1, tv.A, (unsigned)((Wn - n1) * sizeof(float4)), mbar);
-                        bulk_g2s(sB + n1, tv.B, (unsigned)((Wn - n1) * sizeof(float4)), mbar);
-                    }
-                }
+                if (threadIdx.x == 0) cta_key = ~0ull;
+                const SegWindow w = stage_for(a, tv, A.j0, smem, SL, mbar, false);
                 const int T = R.T, n_opp = R.n_v - 1;
                 const float *U = a.U_io + R.u_off + (size_t)i * T * 2;
                 for (int q = threadIdx.x; q < T; q += blockDim.x) subar[q] = make_float2(__ldcg(U + 2 * q), __ldcg(U + 2 * q + 1));
@@ -353,12 +361,12 @@ __global__ void __launch_bounds__(256, 2) plan_kernel(PlanArgs a)
                     sodbar[o] = sm.y;
                 }
                 bv.tv = tv;
-                bv.win = SegWindow{sA, sB, w0, Wn};
+                bv.win = w;
                 bv.ubar = subar; bv.ref = sref; bv.opp = sopp; bv.osum = sosum; bv.odbar = sodbar;
-                bv.x0 = A.x0; bv.s_t = A.s_t; bv.d_t = A.d_t; bv.j0 = A.j0;
+                bv.x0 = A.x0; bv.s_t = A.s_t; bv.d_t = A.d_t;
+                bv.r0 = wrap_index(A.j0 - w.w0, tv.N);
                 bv.T = T; bv.n_opp = n_opp; bv.n_tail = R.n_tail;
                 bv.invL = 1.0f / tv.L;
-                bv.max_moves = kMaxMoves;
                 bv.key = a.key;
                 bv.ctr_agent_round = (unsigned)i | ((unsigned)round << 16);
                 bv.ctr_race = R.race_tag;
@@ -389,10 +397,10 @@ __global__ void __launch_bounds__(256, 2) plan_kernel(PlanArgs a)
         __syncthreads();
         if (threadIdx.x == 0 && cur_slot) atomicMin(cur_slot, cta_key);
         if (!grid_barrier(a, skip)) break;
+        stamp(a, 2 + 2 * round);
 
-        // -------------------------------------------------------- winners
-        for (int ag = gwarp; ag < a.n_agents; ag += total_warps) {
-            if (lane != 0) continue;
+        // -------------------------------------------------------- winners (one CTA per vehicle)
+        for (int ag = blockIdx.x; ag < a.n_agents; ag += gridDim.x) {
             const AgentDev A = load_agent(a.agents + ag);
             const RaceDev R = get_race(a, A.race);
             const int i = ag - R.agent_off;
@@ -400,30 +408,57 @@ __global__ void __launch_bounds__(256, 2) plan_kernel(PlanArgs a)
             const bool active = !extra || i == R.ego;
             const size_t xo = (size_t)R.xi_off + (size_t)i * (T + 1) * 4;
             const size_t uo = (size_t)R.u_off + (size_t)i * T * 2;
+            __syncthreads();
             if (!active) {
-                if (a.xi_hist) {
-                    for (int q = 0; q < (T + 1) * 4; ++q)
+                if (a.xi_hist)
+                    for (int q = threadIdx.x; q < (T + 1) * 4; q += blockDim.x)
                         a.xi_hist[(size_t)round * a.xi_total + xo + q] = __ldcg(a.xi_out + xo + q);
-                }
-                if (a.u_hist) {
-                    for (int q = 0; q < T * 2; ++q)
+                if (a.u_hist)
+                    for (int q = threadIdx.x; q < T * 2; q += blockDim.x)
                         a.u_hist[(size_t)round * a.u_total + uo + q] = __ldcg(a.U_io + uo + q);
-                }
                 continue;
             }
             const int slot = extra ? (a.L + 1) * R.n_v : round * R.n_v + i;
-            const unsigned long long key = __ldcg(a.keys + R.ks_off + slot);
-            const unsigned ks = (unsigned)(key & 0x7fffffffull);
-            a.k_star_out[R.ks_off + slot] = (int)ks;
             const TrackView tv = get_track(a, R.track_id);
-            float *xi_final = (round == a.L || extra) ? a.xi_out + xo : nullptr;
-            float *xi_h = a.xi_hist ? a.xi_hist + (size_t)round * a.xi_total + xo : nullptr;
-            float *u_h = a.u_hist ? a.u_hist + (size_t)round * a.u_total + uo : nullptr;
-            reroll(a, tv, A, T, R.n_tail, a.U_io + uo, ks, false, (unsigned)i | ((unsigned)round << 16),
-                   R.race_tag, a.U_io + uo, extra ? nullptr : a.pos[bout] + R.pos_off + (size_t)i * (T + 1),
-                   xi_final, xi_h, u_h, extra ? nullptr : a.summ[bout] + ag, flag);
+            const SegWindow w = stage_for(a, tv, A.j0, smem, SL, mbar, false);
+            if (threadIdx.x == 0) {
+                const unsigned long long key = __ldcg(a.keys + R.ks_off + slot);
+                ks_sh = (unsigned)(key & 0x7fffffffull);
+                a.k_star_out[R.ks_off + slot] = (int)ks_sh;
+            }
+            __syncthreads();
+            // controls of the selected sample, one step per thread (same noise,
+            // same clipping as its evaluation): warm start U-bar <- U^(k*)
+            const unsigned ks = ks_sh;
+            const unsigned ar = (unsigned)i | ((unsigned)round << 16);
+            for (int q = threadIdx.x; q < T; q += blockDim.x) {
+                const uint4 wv = philox4x32_10(make_uint4(ks, (unsigned)(q >> 1), ar, R.race_tag), a.key);
+                const float2 z = (q & 1) ? box_muller(wv.z, wv.w) : box_muller(wv.x, wv.y);
+                const float2 ub = make_float2(__ldcg(a.U_io + uo + 2 * q), __ldcg(a.U_io + uo + 2 * q + 1));
+                const float2 u = sample_control(a.p, ub, z);
+                sctl[q] = u;
+                a.U_io[uo + 2 * q] = u.x;
+                a.U_io[uo + 2 * q + 1] = u.y;
+                if (a.u_hist) {
+                    a.u_hist[(size_t)round * a.u_total + uo + 2 * q] = u.x;
+                    a.u_hist[(size_t)round * a.u_total + uo + 2 * q + 1] = u.y;
+                }
+            }
+            if (threadIdx.x == 0) {
+                if (!mbar_wait_bounded(mbar, phase, (unsigned long long)a.timeout_ns)) atomicOr(a.status, SGTP_E_TIMEOUT);
+            }
+            phase ^= 1u;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float *xi_final = (round == a.L || extra) ? a.xi_out + xo : nullptr;
+                float *xi_h = a.xi_hist ? a.xi_hist + (size_t)round * a.xi_total + xo : nullptr;
+                roll_controls(a, tv, w, A, T, R.n_tail, sctl,
+                              extra ? nullptr : a.pos[bout] + R.pos_off + (size_t)i * (T + 1), xi_final, xi_h,
+                              extra ? nullptr : a.summ[bout] + ag, flag);
+            }
         }
         if (round <= a.L) ok = grid_barrier(a, skip);
+        stamp(a, 3 + 2 * round);
     }
     if (flag) atomicOr(a.status, SGTP_E_DEVICE << 8);
 }
@@ -488,7 +523,7 @@ void fill_common(PlanArgs &a, const sgtp_track *trk, const sgtp_params *p, int K
                  int *status, const sgtp_launch_opts *opts)
 {
     a.tdesc = trk->desc_dev;
-    a.A = trk->A; a.B = trk->B; a.W = trk->W; a.C = trk->C;
+    a.A = trk->A; a.I = trk->I; a.SB = trk->SB; a.SW = trk->SW; a.C = trk->C;
     a.p = *p;
     a.K = K; a.L = L;
     a.tiles = (K + 255) / 256;
@@ -496,10 +531,11 @@ void fill_common(PlanArgs &a, const sgtp_track *trk, const sgtp_params *p, int K
     a.key = make_uint2((unsigned)seed, (unsigned)(seed >> 32));
     a.xi_out = xi_out; a.k_star_out = k_star_out; a.xi_hist = xi_hist; a.u_hist = u_hist;
     a.status = status;
-    a.Wn = (opts && opts->window > 0) ? opts->window : 1024;
-    a.back = 64;
+    a.Wn = window_len(kWinMax, opts ? opts->window : 0);
+    a.back = 48;
     a.timeout_ns = (opts && opts->wait_timeout_ns > 0) ? opts->wait_timeout_ns : 1000000000ll;
     a.debug_flags = opts ? opts->debug_flags : 0;
+    a.trace = opts ? (long long *)opts->trace_ns : nullptr;
 }
 
 void attach_workspace(PlanArgs &a, const Layout &lay, void *ws)

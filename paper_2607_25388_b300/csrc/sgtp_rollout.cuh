@@ -5,7 +5,7 @@
 //   x_{tau+1} = f(x_tau, u_tau), kinematic bicycle, Euler   (Sec. II)
 //   c = c_track (Eq. ctrack) + w_game * sum_j c_game,ij     (Eqs. game_cost, allc)
 //   h = b * o (Eqs. selection-boundary, selection-vehicle), nu (fallback)
-// The horizon loop keeps the state, the running cost sums, the running
+// The horizon loop keeps the state, one running cost sum, the running
 // boundary clearance and one running minimum distance per opponent in
 // registers; nothing of the trajectory is stored unless asked for.
 #pragma once
@@ -25,10 +25,9 @@ struct BRView {
     const float *odbar;   // [n_opp]      tail-mean lateral offset of each opponent
     float4 x0;
     float s_t, d_t;
-    int j0;
+    int r0;               // window-local segment of x0
     int T, n_opp, n_tail;
     float invL;
-    int max_moves;
     // noise counter words
     uint2 key;
     unsigned ctr_agent_round, ctr_race, stream_bit;
@@ -39,13 +38,13 @@ struct SampleState {
     float x, y, psi, v;
     float a_prev, d_prev;
     float s;          // unwrapped progress
-    int j;            // current nearest segment
-    float c_state, c_ctrl, c_smooth;
+    int r, dr;        // window-local nearest segment, last shift
+    float c;          // running c_track
     float rho_bd, d_tail;
     float g2[MAXO];
 };
 
-// Clipped control of candidate k at step tau from a normal pair z.
+// Clipped control from a nominal control and a normal pair z (Pi_U).
 __device__ __forceinline__ float2 sample_control(const sgtp_params &p, float2 ubar, float2 z)
 {
     const float a = fminf(fmaxf(__fmaf_rn(p.sigma_a, z.x, ubar.x), p.a_min), p.a_max);
@@ -82,26 +81,25 @@ __device__ __forceinline__ void sample_init(SampleState<MAXO> &S, const BRView &
     S.x = bv.x0.x; S.y = bv.x0.y; S.psi = bv.x0.z; S.v = bv.x0.w;
     S.a_prev = 0.f; S.d_prev = 0.f;
     S.s = bv.s_t;
-    S.j = bv.j0;
-    S.c_state = 0.f; S.c_ctrl = 0.f; S.c_smooth = 0.f;
+    S.r = bv.r0; S.dr = 0;
+    S.c = 0.f;
     S.rho_bd = __int_as_float(0x7f800000);
     S.d_tail = 0.f;
 #pragma unroll
     for (int o = 0; o < MAXO; ++o) S.g2[o] = __int_as_float(0x7f800000);
 }
 
-// Advance candidate by one step tau with control u; optional per-step output.
+// Advance a candidate by one step tau with control u; optional outputs.
 template <int MAXO, bool OUT>
 __device__ __forceinline__ void sample_step(SampleState<MAXO> &S, const BRView &bv, const sgtp_params &p, int tau,
                                             float2 u, int &flag, float *st_out, float *fr_out)
 {
     // control cost, tau = 0..H-1, and smoothness, tau = 1..H-1 (Eq. ctrack)
-    S.c_ctrl = __fmaf_rn(p.R[0], __fmul_rn(u.x, u.x), S.c_ctrl);
-    S.c_ctrl = __fmaf_rn(p.R[1], __fmul_rn(u.y, u.y), S.c_ctrl);
+    float cc = __fmaf_rn(p.R[0], __fmul_rn(u.x, u.x), __fmul_rn(p.R[1], __fmul_rn(u.y, u.y)));
     if (tau > 0) {
         const float da = u.x - S.a_prev, dd = u.y - S.d_prev;
-        S.c_smooth = __fmaf_rn(p.S[0], __fmul_rn(da, da), S.c_smooth);
-        S.c_smooth = __fmaf_rn(p.S[1], __fmul_rn(dd, dd), S.c_smooth);
+        cc = __fmaf_rn(p.S[0], __fmul_rn(da, da), cc);
+        cc = __fmaf_rn(p.S[1], __fmul_rn(dd, dd), cc);
     }
     S.a_prev = u.x; S.d_prev = u.y;
 
@@ -109,22 +107,20 @@ __device__ __forceinline__ void sample_step(SampleState<MAXO> &S, const BRView &
     const int st = tau + 1;
 
     // Frenet of the new state, progress unwrapped along the rollout
-    const FrenetPt f = frenet_walk(bv.tv, bv.win, S.j, S.x, S.y, bv.max_moves, flag);
+    const FrenetPt f = frenet_walk(bv.tv, bv.win, S.r, S.dr, S.x, S.y, flag);
     S.s = S.s + wrap_len(f.s - S.s, bv.tv.L, bv.invL);
 
     // tracking term, tau = 1..H (Eq. ctrack), heading error wrapped
     const float4 r = bv.ref[st];
     const float ex = S.x - r.x, ey = S.y - r.y, ep = wrap_angle(S.psi - r.z), ev = S.v - r.w;
-    float cs = __fmul_rn(p.Q[0], __fmul_rn(ex, ex));
-    cs = __fmaf_rn(p.Q[1], __fmul_rn(ey, ey), cs);
-    cs = __fmaf_rn(p.Q[2], __fmul_rn(ep, ep), cs);
-    cs = __fmaf_rn(p.Q[3], __fmul_rn(ev, ev), cs);
-    S.c_state = S.c_state + cs;
+    cc = __fmaf_rn(p.Q[0], __fmul_rn(ex, ex), cc);
+    cc = __fmaf_rn(p.Q[1], __fmul_rn(ey, ey), cc);
+    cc = __fmaf_rn(p.Q[2], __fmul_rn(ep, ep), cc);
+    cc = __fmaf_rn(p.Q[3], __fmul_rn(ev, ev), cc);
+    S.c = S.c + cc;
 
-    // boundary clearance (Sec. III-B) with widths interpolated at the foot point
-    const float4 w = __ldg(bv.tv.W + S.j);
-    const float wl = __fmaf_rn(f.t, w.y, w.x), wr = __fmaf_rn(f.t, w.w, w.z);
-    S.rho_bd = fminf(S.rho_bd, fminf(wr + f.d, wl - f.d));
+    // boundary clearance (Sec. III-B) with widths at the foot point
+    S.rho_bd = fminf(S.rho_bd, fminf(f.wr + f.d, f.wl - f.d));
 
     // tail lateral offsets (blocking term)
     if (st > bv.T - bv.n_tail) S.d_tail = S.d_tail + f.d;
@@ -158,7 +154,6 @@ template <int MAXO>
 __device__ __forceinline__ SampleResult sample_finish(const SampleState<MAXO> &S, const BRView &bv,
                                                       const sgtp_params &p, bool game_on)
 {
-    const float c_track = S.c_state + S.c_ctrl + S.c_smooth;
     const float dbar_i = S.d_tail / (float)bv.n_tail;
     const float prog_i = S.s - bv.s_t;
     float c_game = 0.f;
@@ -179,7 +174,7 @@ __device__ __forceinline__ SampleResult sample_finish(const SampleState<MAXO> &S
         }
     }
     SampleResult r;
-    r.cost = game_on ? __fmaf_rn(p.w_game, c_game, c_track) : c_track;
+    r.cost = game_on ? __fmaf_rn(p.w_game, c_game, S.c) : S.c;
     const bool b = S.rho_bd >= p.m_bd;
     const bool ob = rho_obs >= p.d_col;
     r.feasible = b && ob;

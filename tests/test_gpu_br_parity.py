@@ -6,7 +6,8 @@ import pytest
 
 import oracle as O
 from paper_2607_25388_b300 import scenario as S
-from tests.parity_util import (STATE_RTOL, assert_rel_close, borderline, check_candidates, selection_ok)
+from tests.parity_util import (STATE_RTOL, assert_frenet_close, assert_rel_close, check_candidates,
+                               selection_ok)
 
 pytestmark = pytest.mark.gpu
 
@@ -61,7 +62,7 @@ def test_oval_single_response_all_candidates():
     p = S.params_fullscale()
     g, o, _ = run_both(sc.track, p, sc.X0[0], sc.U0[0], 1.0, sc.opp, sc.T, sc.K, rnd=1)
     assert_rel_close(g["states"], o["states"], STATE_RTOL, "states")
-    assert_rel_close(g["frenet"], o["frenet"], STATE_RTOL, "frenet")
+    assert_frenet_close(g["frenet"], o["frenet"], o["states"])
     assert_rel_close(g["controls"], o["controls"], STATE_RTOL, "controls")
     nb = check_candidates(g, o, "oval")
     assert nb <= 0.01 * sc.K
@@ -89,7 +90,7 @@ def test_fuzzed_small_problems(seed, n_opp, T, K):
     g, o, _ = run_both(td, p, x0, u_nom, float(np.float32(rng.uniform(0.8, 1.0))), opp, T, K, seed=seed,
                        agent=int(rng.integers(0, 9)), rnd=int(rng.integers(0, 6)), game_on=bool(seed % 2))
     assert_rel_close(g["states"], o["states"], STATE_RTOL, "states")
-    assert_rel_close(g["frenet"], o["frenet"], STATE_RTOL, "frenet")
+    assert_frenet_close(g["frenet"], o["frenet"], o["states"])
     check_candidates(g, o, f"fuzz{seed}")
 
 
