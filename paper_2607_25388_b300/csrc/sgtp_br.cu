@@ -56,12 +56,13 @@ extern "C" const char *sgtp_version(void) { return "sgtp-b300 0.1 (sm_103a)"; }
 extern "C" int64_t sgtp_launch_count(void) { return (int64_t)g_launches.load(); }
 
 // ================================================================ track prep
-// One CTA per track: per-segment chords, inverse squared lengths, width,
-// heading and speed increments for the ring-extended arrays; then a
+// One CTA per track: per waypoint the sum of the unit chords meeting there
+// (bisector direction), per segment the chord, its inverse squared length,
+// width, heading and speed increments, for the ring-extended arrays; then a
 // compensated (Kahan) running sum of the segment lengths gives s_j in float32
 // to about one ulp of L.
 __global__ void track_prep_kernel(const float *xr, const float *wl, const float *wr, const int *src_off,
-                                  TrackDesc *desc, float4 *A, float *I, float4 *SB, float2 *SW, float4 *C)
+                                  TrackDesc *desc, float4 *A, float4 *B, float4 *W, float *S, float4 *C)
 {
     const TrackDesc d = desc[blockIdx.x];
     const int so = src_off[blockIdx.x];
@@ -69,14 +70,17 @@ __global__ void track_prep_kernel(const float *xr, const float *wl, const float 
     for (int j = threadIdx.x; j < next; j += blockDim.x) {
         const int g = j % d.N;
         const int gn = g + 1 == d.N ? 0 : g + 1;
-        const float *p0 = xr + 4 * (size_t)(so + g), *p1 = xr + 4 * (size_t)(so + gn);
+        const int gp = g == 0 ? d.N - 1 : g - 1;
+        const float *p0 = xr + 4 * (size_t)(so + g), *p1 = xr + 4 * (size_t)(so + gn), *pm = xr + 4 * (size_t)(so + gp);
         const float ex = p1[0] - p0[0], ey = p1[1] - p0[1];
+        const float fx = p0[0] - pm[0], fy = p0[1] - pm[1];
         const float l2 = __fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey));
+        const float len = sqrtf(l2);
+        const float lp = sqrtf(__fadd_rn(__fmul_rn(fx, fx), __fmul_rn(fy, fy)));
         const int o = d.offset + j;
-        A[o] = make_float4(p0[0], p0[1], ex, ey);
-        I[o] = 1.0f / l2;
-        SB[o] = make_float4(0.f, sqrtf(l2), wl[so + g], wl[so + gn] - wl[so + g]);
-        SW[o] = make_float2(wr[so + g], wr[so + gn] - wr[so + g]);
+        A[o] = make_float4(p0[0], p0[1], ex / len + fx / lp, ey / len + fy / lp);
+        B[o] = make_float4(ex, ey, 1.0f / l2, len);
+        W[o] = make_float4(wl[so + g], wl[so + gn] - wl[so + g], wr[so + g], wr[so + gn] - wr[so + g]);
         C[o] = make_float4(p0[2], wrap_angle(p1[2] - p0[2]), p0[3], p1[3] - p0[3]);
     }
     __syncthreads();
@@ -84,8 +88,8 @@ __global__ void track_prep_kernel(const float *xr, const float *wl, const float 
         float sum = 0.f, comp = 0.f;
         for (int j = 0; j < d.N; ++j) {
             const int o = d.offset + j;
-            SB[o].x = sum;
-            const float y = SB[o].y - comp;
+            S[o] = sum;
+            const float y = B[o].w - comp;
             const float t = sum + y;
             comp = (t - sum) - y;
             sum = t;
@@ -93,7 +97,7 @@ __global__ void track_prep_kernel(const float *xr, const float *wl, const float 
         desc[blockIdx.x].L = sum;
     }
     __syncthreads();
-    for (int j = d.N + threadIdx.x; j < next; j += blockDim.x) SB[d.offset + j].x = SB[d.offset + j % d.N].x;
+    for (int j = d.N + threadIdx.x; j < next; j += blockDim.x) S[d.offset + j] = S[d.offset + j % d.N];
 }
 
 static sgtp_status track_create_impl(const float *xr, const float *wl, const float *wr, const int32_t *offsets,
@@ -140,9 +144,9 @@ static sgtp_status track_create_impl(const float *xr, const float *wl, const flo
         cudaFree(d_xr); cudaFree(d_wl); cudaFree(d_wr); cudaFree(d_off);
     };
     cudaError_t e = cudaSuccess;
-    if ((e = cudaMalloc(&T->A, sizeof(float4) * total)) || (e = cudaMalloc(&T->I, sizeof(float) * total)) ||
-        (e = cudaMalloc(&T->SB, sizeof(float4) * total)) || (e = cudaMalloc(&T->SW, sizeof(float2) * total)) ||
-        (e = cudaMalloc(&T->C, sizeof(float4) * total)) ||
+    if ((e = cudaMalloc(&T->A, sizeof(float4) * total)) || (e = cudaMalloc(&T->B, sizeof(float4) * total)) ||
+        (e = cudaMalloc(&T->W, sizeof(float4) * total)) || (e = cudaMalloc(&T->C, sizeof(float4) * total)) ||
+        (e = cudaMalloc(&T->S, sizeof(float) * total)) ||
         (e = cudaMalloc(&T->desc_dev, sizeof(TrackDesc) * n_tracks)) ||
         (e = cudaMalloc(&d_xr, sizeof(float) * 4 * total_src)) || (e = cudaMalloc(&d_wl, sizeof(float) * total_src)) ||
         (e = cudaMalloc(&d_wr, sizeof(float) * total_src)) || (e = cudaMalloc(&d_off, sizeof(int) * n_tracks))) {
@@ -159,7 +163,7 @@ static sgtp_status track_create_impl(const float *xr, const float *wl, const flo
         sgtp_track_destroy(T);
         return set_error(SGTP_E_CUDA, "track upload failed: %s", cudaGetErrorString(e));
     }
-    track_prep_kernel<<<n_tracks, 256, 0, s>>>(d_xr, d_wl, d_wr, d_off, T->desc_dev, T->A, T->I, T->SB, T->SW, T->C);
+    track_prep_kernel<<<n_tracks, 256, 0, s>>>(d_xr, d_wl, d_wr, d_off, T->desc_dev, T->A, T->B, T->W, T->S, T->C);
     count_launch();
     if ((e = cudaGetLastError()) ||
         (e = cudaMemcpyAsync(T->desc.data(), T->desc_dev, sizeof(TrackDesc) * n_tracks, cudaMemcpyDeviceToHost, s)) ||
@@ -190,7 +194,7 @@ extern "C" sgtp_status sgtp_track_create_many(const float *xr, const float *wl, 
 extern "C" void sgtp_track_destroy(sgtp_track *T)
 {
     if (!T) return;
-    cudaFree(T->A); cudaFree(T->I); cudaFree(T->SB); cudaFree(T->SW); cudaFree(T->C); cudaFree(T->desc_dev);
+    cudaFree(T->A); cudaFree(T->B); cudaFree(T->W); cudaFree(T->S); cudaFree(T->C); cudaFree(T->desc_dev);
     delete T;
 }
 
@@ -213,8 +217,8 @@ struct BRHeader {
     int flag;                   // device-side check flags
     int j0;                     // nearest segment of x_{i,t}
     float4 x0;
-    float s_t, d_t;
-    int pad[2];
+    float s_t, d_t, t0;         // Frenet of x_{i,t}, segment parameter
+    int pad;
 };
 
 struct BRLayout {
@@ -235,81 +239,105 @@ struct BRLayout {
 // reference trajectory (Sec. III-A, overall ranking), and for every opponent
 // prediction its positions, unwrapped progress and tail-mean offset, then
 // the pair terms that do not depend on the candidate: the current gap
-// Delta s_{ij,t}, alpha_{ij,t} and gamma_{block,ij}.
-__global__ void br_prep_kernel(TrackView tv, sgtp_params p, const float *x0, const float *opp, int n_opp, int T,
-                               float vscale, int n_tail, unsigned char *ws, size_t off_ref, size_t off_opp,
-                               size_t off_osum, size_t off_odbar)
+// Delta s_{ij,t}, alpha_{ij,t} and gamma_{block,ij}.  The opponents'
+// projections run one (opponent, step) pair per thread; the progress is then
+// unwrapped in step order by one thread per opponent.
+__global__ void __launch_bounds__(256) br_prep_kernel(TrackView tv, sgtp_params p, const float *x0, const float *opp,
+                                                      int n_opp, int T, float vscale, int n_tail, unsigned char *ws,
+                                                      size_t off_ref, size_t off_opp, size_t off_osum,
+                                                      size_t off_odbar, int Wn, int back, long long timeout_ns)
 {
+    using Tl = Tile<1>;
     BRHeader *h = (BRHeader *)ws;
     float4 *ref = (float4 *)(ws + off_ref);
     float2 *opos = (float2 *)(ws + off_opp);
     float4 *osum = (float4 *)(ws + off_osum);
     float *odbar = (float *)(ws + off_odbar);
-    __shared__ float s0_sh[SGTP_MAX_AGENTS], sH_sh[SGTP_MAX_AGENTS];
-    __shared__ float s_t_sh;
+    float2 *ofr = (float2 *)(g_smem + BRTile<1>::kBytes);          // [T][n_opp] raw (s, d)
+    __shared__ float s0_sh[SGTP_MAX_AGENTS], t0_sh[SGTP_MAX_AGENTS], sH_sh[SGTP_MAX_AGENTS];
+    __shared__ int j0_sh[SGTP_MAX_AGENTS + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const float invL = 1.0f / tv.L;
-    const SegWindow nowin{nullptr, nullptr, nullptr, nullptr, 0, 0};
-    if (warp == 0) {
-        const float4 x = make_float4(x0[0], x0[1], x0[2], x0[3]);
-        const int j = nearest_segment_warp(tv, x.x, x.y);
-        if (lane == 0) {
-            const FrenetPt f = frenet_at(tv, j, x.x, x.y);
-            h->key = ~0ull;
-            h->flag = 0;
-            h->x0 = x;
-            h->s_t = f.s;
-            h->d_t = f.d;
-            h->j0 = j;
-            s_t_sh = f.s;
-            reference_traj(tv, SegWindow{nullptr, nullptr, nullptr, nullptr, 0, 0}, nullptr, j, f.s, p.dt, vscale,
-                           T, ref);
-        }
+    if (threadIdx.x == 0) h->flag = 0;
+    // global nearest segment of x_{i,t} (slot 0) and of each opponent's first state
+    for (int q = warp; q <= n_opp; q += nwarps) {
+        const float *pt = q == 0 ? x0 : opp + (size_t)(q - 1) * (T + 1) * 4;
+        const int j = nearest_segment_warp(tv, pt[0], pt[1]);
+        if (lane == 0) j0_sh[q] = j;
     }
-    for (int o = warp - 1; o >= 0 && o < n_opp; o += (nwarps > 1 ? nwarps - 1 : n_opp)) {
+    __syncthreads();
+    const int j0 = j0_sh[0];
+    const float4 xs = make_float4(x0[0], x0[1], x0[2], x0[3]);
+    if (threadIdx.x == 0) {
+        BRScalars &S = Tl::sc();
+        mbar_init(Tl::bar(), 1);
+        S.tv = tv;
+        S.Wn = Wn;
+        S.w0 = window_start(j0, back, tv.N);
+        S.invL = invL;
+        Tl::stage_window(tv, S.w0, Wn, true);
+    }
+    if (threadIdx.x < n_opp) {
+        const int o = threadIdx.x;
         const float *q = opp + (size_t)o * (T + 1) * 4;
-        const int j = nearest_segment_warp(tv, q[0], q[1]);
-        if (lane == 0) {
-            const FrenetPt f0 = frenet_at(tv, j, q[0], q[1]);
-            float s = f0.s, dsum = 0.f;
-            int flag = 0, r = j, dr = 0;      // window-less walk: r is the global index
-            for (int tau = 1; tau <= T; ++tau) {
-                const float px = q[4 * tau], py = q[4 * tau + 1];
-                const FrenetPt f = frenet_walk(tv, nowin, r, dr, px, py, flag);
-                s = s + wrap_len(f.s - s, tv.L, invL);
-                if (tau > T - n_tail) dsum = dsum + f.d;
-                opos[(size_t)(tau - 1) * n_opp + o] = make_float2(px, py);
-            }
-            if (flag) atomicOr(&h->flag, 1);
-            s0_sh[o] = f0.s;
-            sH_sh[o] = s;
-            odbar[o] = dsum / (float)n_tail;
-        }
+        const FrenetPt f0 = frenet_at(tv, j0_sh[o + 1], q[0], q[1]);
+        s0_sh[o] = f0.s;
+        t0_sh[o] = f0.t;
     }
+    for (int q = threadIdx.x; q < T * n_opp; q += blockDim.x) {
+        const int tau = q / n_opp, o = q - tau * n_opp;
+        const float *pt = opp + ((size_t)o * (T + 1) + tau + 1) * 4;
+        opos[q] = make_float2(pt[0], pt[1]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!mbar_wait_bounded(Tl::bar(), 0, (unsigned long long)timeout_ns)) atomicOr(&h->flag, SGTP_E_TIMEOUT);
+    }
+    __syncthreads();
+    const BRScalars &S = Tl::sc();
+    const SegWindow w = Tl::win(S.w0, S.Wn);
+    if (threadIdx.x == 0) {
+        const FrenetPt f = frenet_at(tv, j0, xs.x, xs.y);
+        h->key = ~0ull;
+        h->x0 = xs;
+        h->s_t = f.s;
+        h->d_t = f.d;
+        h->t0 = f.t;
+        h->j0 = j0;
+        reference_traj(tv, w, Tl::C(), j0, f.s, p.dt, vscale, T, ref);
+    }
+    // every (opponent, step) projection in parallel
+    int flag = 0;
+    for (int q = threadIdx.x; q < T * n_opp; q += blockDim.x) {
+        const int tau = q / n_opp, o = q - tau * n_opp;
+        const float *q0 = opp + (size_t)o * (T + 1) * 4;
+        const float *pt = q0 + (size_t)(tau + 1) * 4;
+        const int jo = j0_sh[o + 1];
+        const float ch = sqrtf((pt[0] - q0[0]) * (pt[0] - q0[0]) + (pt[1] - q0[1]) * (pt[1] - q0[1]));
+        const int guess = wrap_index(jo - w.w0, tv.N) + min((int)(ch / __ldg(tv.B + jo).w), 4 * kWinTile);
+        const FrenetPt f = frenet_search(tv, w, guess, pt[0], pt[1]);
+        flag |= f.flag;
+        ofr[q] = make_float2(f.s, f.d);
+    }
+    if (flag) atomicOr(&h->flag, SGTP_E_DEVICE << 8);
     __syncthreads();
     if (threadIdx.x < n_opp) {
         const int o = threadIdx.x;
-        const float ds_t = wrap_len(s_t_sh - s0_sh[o], tv.L, invL);
+        float s = s0_sh[o], dsum = 0.f;
+        for (int tau = 1; tau <= T; ++tau) {
+            const float2 f = ofr[(size_t)(tau - 1) * n_opp + o];
+            s = s + wrap_len(f.x - s, tv.L, invL);
+            if (tau > T - n_tail) dsum = dsum + f.y;
+        }
+        sH_sh[o] = s;
+        odbar[o] = dsum / (float)n_tail;
+        const float st = h->s_t;
+        const float ds_t = wrap_len(st - s0_sh[o], tv.L, invL);
         const float alpha = 1.0f / (1.0f + fabsf(ds_t) / (p.s_contest + p.eps_alpha));
         const float gamma = (ds_t > p.s_role && ds_t < p.s_contest) ? p.w_block : 0.f;
-        osum[o] = make_float4(ds_t, alpha, gamma, sH_sh[o] - s0_sh[o]);
+        osum[o] = make_float4(ds_t, alpha, gamma, s - s0_sh[o]);
     }
 }
-
-struct BRSmemLayout {
-    WindowSmem win;
-    size_t ref, ubar, opp, osum, odbar, total;
-    __host__ __device__ BRSmemLayout(int Wn, int T, int n_opp) : win(16, Wn)
-    {
-        auto up = [](size_t x) { return (x + 15) & ~(size_t)15; };
-        ref = up(win.end);
-        ubar = up(ref + sizeof(float4) * (T + 1));
-        opp = up(ubar + sizeof(float2) * T);
-        osum = up(opp + sizeof(float2) * (size_t)T * n_opp);
-        odbar = up(osum + sizeof(float4) * n_opp);
-        total = up(odbar + sizeof(float) * n_opp);
-    }
-};
 
 struct BRArgs {
     TrackView tv;
@@ -327,63 +355,62 @@ struct BRArgs {
     long long timeout_ns;
 };
 
-__device__ __forceinline__ BRView make_view(const BRArgs &a, const BRHeader *h, const SegWindow &win)
+// Stage one best response's tile: scalars, track window (TMA), reference,
+// nominal controls, opponent pairs and pair terms.  Ends with the window
+// copies complete and a __syncthreads.  Returns false if the wait timed out.
+template <int MAXO>
+__device__ bool br_stage(const BRArgs &a)
 {
-    BRView bv;
-    bv.tv = a.tv;
-    bv.win = win;
-    bv.x0 = h->x0; bv.s_t = h->s_t; bv.d_t = h->d_t;
-    bv.r0 = wrap_index(h->j0 - win.w0, a.tv.N);
-    if (win.Wn == 0) bv.r0 = h->j0;
-    bv.T = a.T; bv.n_opp = a.n_opp; bv.n_tail = a.n_tail;
-    bv.invL = 1.0f / a.tv.L;
-    bv.key = a.key; bv.ctr_agent_round = a.agent_round; bv.ctr_race = a.race; bv.stream_bit = 0u;
-    return bv;
+    using T = Tile<MAXO>;
+    __shared__ int ok_sh;
+    const BRHeader *h = (const BRHeader *)a.ws;
+    if (threadIdx.x == 0) {
+        BRScalars &S = T::sc();
+        mbar_init(T::bar(), 1);
+        const int j0 = h->j0;
+        S.tv = a.tv;
+        S.x0 = h->x0; S.s_t = h->s_t; S.d_t = h->d_t;
+        S.Wn = a.Wn;
+        S.w0 = window_start(j0, a.back, a.tv.N);
+        S.r0 = wrap_index(j0 - S.w0, a.tv.N);
+        S.pos0 = (float)S.r0 + h->t0;
+        S.vel0 = __fdiv_rn(__fmul_rn(a.p.dt, h->x0.w), __ldg(a.tv.B + j0).w);
+        S.T = a.T; S.n_opp = a.n_opp; S.n_tail = a.n_tail;
+        S.invL = 1.0f / a.tv.L;
+        S.key = a.key; S.ctr_agent_round = a.agent_round; S.ctr_race = a.race; S.stream_bit = 0u;
+        T::stage_window(a.tv, S.w0, S.Wn, false);
+    }
+    const float4 *gref = (const float4 *)(a.ws + a.off_ref);
+    for (int i = threadIdx.x; i <= a.T; i += blockDim.x) T::ref()[i] = gref[i];
+    for (int i = threadIdx.x; i < a.T; i += blockDim.x) T::ubar()[i] = make_float2(a.u_nom[2 * i], a.u_nom[2 * i + 1]);
+    const float2 *gopp = (const float2 *)(a.ws + a.off_opp);
+    const int n_opp = a.n_opp;
+    stage_opponents<MAXO>(a.T, n_opp, [&](int tau, int o) { return gopp[(size_t)(tau - 1) * n_opp + o]; });
+    const float4 *gosum = (const float4 *)(a.ws + a.off_osum);
+    const float *godbar = (const float *)(a.ws + a.off_odbar);
+    for (int i = threadIdx.x; i < n_opp; i += blockDim.x) { T::osum()[i] = gosum[i]; T::odbar()[i] = godbar[i]; }
+    __syncthreads();
+    if (threadIdx.x == 0) ok_sh = mbar_wait_bounded(T::bar(), 0, (unsigned long long)a.timeout_ns) ? 1 : 0;
+    __syncthreads();
+    return ok_sh != 0;
 }
 
 template <int MAXO, bool KEY_MODE>
-__global__ void __launch_bounds__(256) br_rollout_kernel(BRArgs a)
+__global__ void __launch_bounds__(256, 3) br_rollout_kernel(BRArgs a)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    using T = Tile<MAXO>;
     __shared__ unsigned long long cta_key;
     __shared__ int cta_flag;
-    const BRSmemLayout L(a.Wn, a.T, a.n_opp);
-    unsigned long long *bar = (unsigned long long *)smem;
-    float4 *sref = (float4 *)(smem + L.ref);
-    float2 *subar = (float2 *)(smem + L.ubar);
-    float2 *sopp = (float2 *)(smem + L.opp);
-    float4 *sosum = (float4 *)(smem + L.osum);
-    float *sodbar = (float *)(smem + L.odbar);
-    const BRHeader *h = (const BRHeader *)a.ws;
-    const int w0 = window_start(h->j0, a.back, a.tv.N);
-    if (threadIdx.x == 0) {
-        cta_key = ~0ull;
-        cta_flag = 0;
-        mbar_init(bar, 1);
-    }
-    const SegWindow win = stage_window_issue(a.tv, w0, a.Wn, smem, L.win, bar, threadIdx.x == 0);
-    const float4 *gref = (const float4 *)(a.ws + a.off_ref);
-    for (int i = threadIdx.x; i <= a.T; i += blockDim.x) sref[i] = gref[i];
-    for (int i = threadIdx.x; i < a.T; i += blockDim.x) subar[i] = make_float2(a.u_nom[2 * i], a.u_nom[2 * i + 1]);
-    const float2 *gopp = (const float2 *)(a.ws + a.off_opp);
-    for (int i = threadIdx.x; i < a.T * a.n_opp; i += blockDim.x) sopp[i] = gopp[i];
-    const float4 *gosum = (const float4 *)(a.ws + a.off_osum);
-    const float *godbar = (const float *)(a.ws + a.off_odbar);
-    for (int i = threadIdx.x; i < a.n_opp; i += blockDim.x) { sosum[i] = gosum[i]; sodbar[i] = godbar[i]; }
-    __syncthreads();
-    if (threadIdx.x == 0 && !mbar_wait_bounded(bar, 0, (unsigned long long)a.timeout_ns)) cta_flag = SGTP_E_TIMEOUT;
-    __syncthreads();
-
-    BRView bv = make_view(a, h, win);
-    bv.ubar = subar; bv.ref = sref; bv.opp = sopp; bv.osum = sosum; bv.odbar = sodbar;
-
+    if (threadIdx.x == 0) { cta_key = ~0ull; cta_flag = 0; }
+    const bool ok = br_stage<MAXO>(a);
+    const BRScalars &S = T::sc();
     int flag = 0;
     unsigned long long best = ~0ull;
     const unsigned k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cta_flag == 0 && k < (unsigned)a.K) {
+    if (ok && k < (unsigned)a.K) {
         if (KEY_MODE) {
-            const SampleResult r = run_candidate<MAXO, false>(bv, a.p, k, a.game_on != 0, false, flag, nullptr,
-                                                              nullptr, nullptr);
+            const SampleResult r = run_candidate<MAXO, false>(S, a.p, a.key, k, a.game_on != 0, flag, nullptr, nullptr,
+                                                              nullptr);
             best = make_key(r.feasible, r.cost, r.viol, k);
         } else {
             float *st = a.states ? a.states + (size_t)k * (a.T + 1) * 4 : nullptr;
@@ -391,14 +418,15 @@ __global__ void __launch_bounds__(256) br_rollout_kernel(BRArgs a)
             float *uo = a.controls ? a.controls + (size_t)k * a.T * 2 : nullptr;
             SampleResult r;
             if (st || fr || uo)
-                r = run_candidate<MAXO, true>(bv, a.p, k, a.game_on != 0, false, flag, st, fr, uo);
+                r = run_candidate<MAXO, true>(S, a.p, a.key, k, a.game_on != 0, flag, st, fr, uo);
             else
-                r = run_candidate<MAXO, false>(bv, a.p, k, a.game_on != 0, false, flag, nullptr, nullptr, nullptr);
+                r = run_candidate<MAXO, false>(S, a.p, a.key, k, a.game_on != 0, flag, nullptr, nullptr, nullptr);
             a.cost[k] = r.cost;
             a.viol[k] = r.viol;
             a.feas[k] = r.feasible ? 1 : 0;
         }
     }
+    if (!ok && threadIdx.x == 0) atomicOr(&cta_flag, SGTP_E_TIMEOUT);
     if (flag) atomicOr(&cta_flag, SGTP_E_DEVICE << 8);
     if (KEY_MODE) {
         best = warp_min_u64(best);
@@ -412,32 +440,51 @@ __global__ void __launch_bounds__(256) br_rollout_kernel(BRArgs a)
     }
 }
 
-// Selection result and re-roll of the winner (lane 0; window-less walk).
+// Selection result and re-roll of the winner: the selected sample's
+// controls one step per thread (same noise and clipping as its evaluation),
+// then the bicycle recurrence by one thread (same arithmetic), so the
+// returned trajectory is bit-identical to the evaluated one.
 template <int MAXO>
 __global__ void br_finalize_kernel(BRArgs a, int *k_star, float *u_star, float *xi_star, int *any_feasible)
 {
-    __shared__ float2 subar[SGTP_MAX_T];
-    for (int i = threadIdx.x; i < a.T; i += blockDim.x) subar[i] = make_float2(a.u_nom[2 * i], a.u_nom[2 * i + 1]);
-    __syncthreads();
-    if (threadIdx.x != 0) return;
+    using Tl = Tile<MAXO>;
+    __shared__ unsigned ks_sh;
     const BRHeader *h = (const BRHeader *)a.ws;
-    const unsigned long long key = h->key;
-    const unsigned k = (unsigned)(key & 0x7fffffffull);
-    BRView bv = make_view(a, h, SegWindow{nullptr, nullptr, nullptr, nullptr, 0, 0});
-    bv.ubar = subar;
-    bv.ref = (const float4 *)(a.ws + a.off_ref);
-    bv.opp = (const float2 *)(a.ws + a.off_opp);
-    bv.osum = (const float4 *)(a.ws + a.off_osum);
-    bv.odbar = (const float *)(a.ws + a.off_odbar);
-    int flag = 0;
-    run_candidate<MAXO, true>(bv, a.p, k, a.game_on != 0, false, flag, xi_star, nullptr, u_star);
-    *k_star = (int)k;
-    *any_feasible = (key >> 63) ? 0 : 1;
+    if (threadIdx.x == 0) {
+        const unsigned long long key = h->key;
+        ks_sh = (unsigned)(key & 0x7fffffffull);
+        *k_star = (int)ks_sh;
+        *any_feasible = (key >> 63) ? 0 : 1;
+    }
+    __syncthreads();
+    const unsigned k = ks_sh;
+    for (int q = threadIdx.x; q < a.T; q += blockDim.x) {
+        const uint4 wv = philox4x32_10(make_uint4(k, (unsigned)(q >> 1), a.agent_round, a.race), a.key);
+        const float2 z = (q & 1) ? box_muller(wv.z, wv.w) : box_muller(wv.x, wv.y);
+        const float2 u = sample_control(a.p, make_float2(a.u_nom[2 * q], a.u_nom[2 * q + 1]), z);
+        Tl::ctl()[q] = u;
+        u_star[2 * q] = u.x;
+        u_star[2 * q + 1] = u.y;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const float4 x0 = h->x0;
+        float x = x0.x, y = x0.y, psi = x0.z, v = x0.w;
+        ((float4 *)xi_star)[0] = x0;
+        for (int tau = 0; tau < a.T; ++tau) {
+            const float2 u = Tl::ctl()[tau];
+            bicycle_step(a.p, x, y, psi, v, u.x, u.y);
+            ((float4 *)xi_star)[tau + 1] = make_float4(x, y, psi, v);
+        }
+    }
 }
 
 // ---------------------------------------------------------------- dispatch
 template <int MAXO>
-static sgtp_status launch_rollout(const BRArgs &a, bool key_mode, cudaStream_t s, int grid, size_t smem)
+static size_t br_smem(const BRArgs &) { return BRTile<MAXO>::kBytes; }
+
+template <int MAXO>
+static sgtp_status launch_rollout(const BRArgs &a, bool key_mode, cudaStream_t s, int grid)
 {
     static bool configured = false;
     if (!configured) {
@@ -445,12 +492,14 @@ static sgtp_status launch_rollout(const BRArgs &a, bool key_mode, cudaStream_t s
                                        200 * 1024));
         SGTP_CUDA(cudaFuncSetAttribute(br_rollout_kernel<MAXO, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024));
+        SGTP_CUDA(cudaFuncSetAttribute(br_finalize_kernel<MAXO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024));
         configured = true;
     }
     if (key_mode)
-        br_rollout_kernel<MAXO, true><<<grid, 256, smem, s>>>(a);
+        br_rollout_kernel<MAXO, true><<<grid, 256, br_smem<MAXO>(a), s>>>(a);
     else
-        br_rollout_kernel<MAXO, false><<<grid, 256, smem, s>>>(a);
+        br_rollout_kernel<MAXO, false><<<grid, 256, br_smem<MAXO>(a), s>>>(a);
     return SGTP_OK;
 }
 
@@ -484,7 +533,7 @@ static sgtp_status br_common(const sgtp_track *trk, int32_t track_id, const sgtp
     a.u_nom = u_nom;
     a.T = T; a.n_opp = n_opp; a.K = K;
     a.n_tail = tail_count(p->mu_tail, T);
-    a.Wn = window_len(a.tv.N, 0);
+    a.Wn = window_len(a.tv.N, kWinTile);
     a.back = a.Wn >= 256 ? 64 : a.Wn / 4;
     a.key = make_uint2((unsigned)seed, (unsigned)(seed >> 32));
     a.agent_round = agent | (round << 16);
@@ -498,17 +547,22 @@ static sgtp_status br_common(const sgtp_track *trk, int32_t track_id, const sgtp
 static sgtp_status br_launch(const BRArgs &a, int maxo, bool key_mode, const float *x0, const float *opp,
                              float vref_scale, cudaStream_t s)
 {
-    const BRSmemLayout L(a.Wn, a.T, a.n_opp);
     const int grid = (a.K + 255) / 256;
-    br_prep_kernel<<<1, 32 * (1 + (a.n_opp < 8 ? (a.n_opp > 0 ? a.n_opp : 1) : 8)), 0, s>>>(
-        a.tv, a.p, x0, opp, a.n_opp, a.T, vref_scale, a.n_tail, (unsigned char *)a.ws, a.off_ref, a.off_opp,
-        a.off_osum, a.off_odbar);
+    static bool prep_configured = false;
+    if (!prep_configured) {
+        SGTP_CUDA(cudaFuncSetAttribute(br_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        prep_configured = true;
+    }
+    const size_t prep_smem = BRTile<1>::kBytes + sizeof(float2) * (size_t)a.T * (a.n_opp > 0 ? a.n_opp : 1);
+    br_prep_kernel<<<1, 256, prep_smem, s>>>(a.tv, a.p, x0, opp, a.n_opp, a.T, vref_scale, a.n_tail,
+                                             (unsigned char *)a.ws, a.off_ref, a.off_opp, a.off_osum, a.off_odbar,
+                                             a.Wn, a.back, a.timeout_ns);
     sgtp_status st;
     switch (maxo) {
-        case 1: st = launch_rollout<1>(a, key_mode, s, grid, L.total); break;
-        case 3: st = launch_rollout<3>(a, key_mode, s, grid, L.total); break;
-        case 9: st = launch_rollout<9>(a, key_mode, s, grid, L.total); break;
-        default: st = launch_rollout<15>(a, key_mode, s, grid, L.total); break;
+        case 1: st = launch_rollout<1>(a, key_mode, s, grid); break;
+        case 3: st = launch_rollout<3>(a, key_mode, s, grid); break;
+        case 9: st = launch_rollout<9>(a, key_mode, s, grid); break;
+        default: st = launch_rollout<15>(a, key_mode, s, grid); break;
     }
     if (st) return st;
     count_launch(2);
@@ -557,10 +611,12 @@ extern "C" sgtp_status sgtp_best_response(const sgtp_track *trk, int32_t track_i
     st = br_launch(a, maxo, true, x0, opp, vref_scale, s);
     if (st) return st;
     switch (maxo) {
-        case 1: br_finalize_kernel<1><<<1, 32, 0, s>>>(a, k_star, u_star, xi_star, any_feasible); break;
-        case 3: br_finalize_kernel<3><<<1, 32, 0, s>>>(a, k_star, u_star, xi_star, any_feasible); break;
-        case 9: br_finalize_kernel<9><<<1, 32, 0, s>>>(a, k_star, u_star, xi_star, any_feasible); break;
-        default: br_finalize_kernel<15><<<1, 32, 0, s>>>(a, k_star, u_star, xi_star, any_feasible); break;
+        case 1: br_finalize_kernel<1><<<1, 128, br_smem<1>(a), s>>>(a, k_star, u_star, xi_star, any_feasible); break;
+        case 3: br_finalize_kernel<3><<<1, 128, br_smem<3>(a), s>>>(a, k_star, u_star, xi_star, any_feasible); break;
+        case 9: br_finalize_kernel<9><<<1, 128, br_smem<9>(a), s>>>(a, k_star, u_star, xi_star, any_feasible); break;
+        default:
+            br_finalize_kernel<15><<<1, 128, br_smem<15>(a), s>>>(a, k_star, u_star, xi_star, any_feasible);
+            break;
     }
     count_launch();
     SGTP_CUDA(cudaGetLastError());

@@ -22,18 +22,20 @@ constexpr int kWinMax = 1024;
 constexpr int kMaxMoves = 64;
 
 // ---------------------------------------------------------------- track
-// Device raceline of one closed track; per segment j (waypoint j to j+1 mod N),
-// arrays of length N + kWinMax (entry j >= N repeats entry j mod N):
-//   A[j]  = (x_j, y_j, ex_j, ey_j)             chord e_j = P_{j+1} - P_j
-//   I[j]  = 1 / |e_j|^2
-//   SB[j] = (s_j, |e_j|, wL_j, wL_{j+1} - wL_j)  s_j cumulative arc length
-//   SW[j] = (wR_j, wR_{j+1} - wR_j)
-//   C[j]  = (psi_j, wrap(psi_{j+1} - psi_j), v_j, v_{j+1} - v_j)
+// Device raceline of one closed track; per waypoint/segment j (segment j runs
+// from waypoint j to j+1 mod N), arrays of length N + kWinMax (entry j >= N
+// repeats entry j mod N):
+//   A[j] = (x_j, y_j, bx_j, by_j)   waypoint and the direction u_{j-1} + u_j
+//                                   (sum of the unit chords meeting there)
+//   B[j] = (ex_j, ey_j, 1/|e_j|^2, |e_j|)   chord e_j = P_{j+1} - P_j
+//   W[j] = (wL_j, wL_{j+1} - wL_j, wR_j, wR_{j+1} - wR_j)
+//   S[j] = s_j                      cumulative arc length
+//   C[j] = (psi_j, wrap(psi_{j+1} - psi_j), v_j, v_{j+1} - v_j)
 struct TrackView {
     const float4 *A;
-    const float *I;
-    const float4 *SB;
-    const float2 *SW;
+    const float4 *B;
+    const float4 *W;
+    const float *S;
     const float4 *C;
     int N;
     float L;
@@ -50,9 +52,9 @@ struct TrackDesc {
 // Shared-memory window of a track: local index r <-> segment (w0 + r) mod N.
 struct SegWindow {
     const float4 *A;
-    const float *I;
-    const float4 *SB;
-    const float2 *SW;
+    const float4 *B;
+    const float4 *W;
+    const float *S;
     int w0, Wn;
 };
 
@@ -68,106 +70,175 @@ __device__ __forceinline__ int wrap_index(int j, int N)
 struct FrenetPt {
     float s, d, t;
     float wl, wr;   // widths at the foot point
+    int m;          // segment (window-local, or global without a window)
+    int flag;       // the search hit its move limit
 };
 
-__device__ __forceinline__ float seg_dist2(const float4 &a, float inv_l2, float px, float py, float &t, float &cr)
+// ---- packed float pairs (Blackwell f32x2 arithmetic)
+typedef unsigned long long f2p;
+__device__ __forceinline__ f2p pk(float a, float b)
+{
+    f2p r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 upk(f2p v)
+{
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ f2p sub2(f2p a, f2p b)
+{
+    f2p d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2p mul2(f2p a, f2p b)
+{
+    f2p d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2p fma2(f2p a, f2p b, f2p c)
+{
+    f2p d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// Squared distance from p to segment (vertex a.xy, chord b); t is the
+// clamped parameter, cr the cross product e x (p - a) (sign of d).
+__device__ __forceinline__ float seg_dist2(const float4 &a, const float4 &b, float px, float py, float &t, float &cr)
 {
     const float dx = px - a.x, dy = py - a.y;
-    float u = __fmul_rn(__fmaf_rn(dx, a.z, __fmul_rn(dy, a.w)), inv_l2);
+    float u = __fmul_rn(__fmaf_rn(dx, b.x, __fmul_rn(dy, b.y)), b.z);
     u = fminf(fmaxf(u, 0.0f), 1.0f);
-    const float ex = __fmaf_rn(-u, a.z, dx), ey = __fmaf_rn(-u, a.w, dy);
+    const float ex = __fmaf_rn(-u, b.x, dx), ey = __fmaf_rn(-u, b.y, dy);
     t = u;
-    cr = __fmaf_rn(a.z, dy, -__fmul_rn(a.w, dx));
+    cr = __fmaf_rn(b.x, dy, -__fmul_rn(b.y, dx));
     return __fmaf_rn(ex, ex, __fmul_rn(ey, ey));
 }
 
 // Segment data at window-local index r (shared memory inside the window,
 // global memory outside it).
-__device__ __forceinline__ void seg_at(const TrackView &tv, const SegWindow &w, int r, float4 &a, float &il)
+struct SegData {
+    float4 a, b, w;
+    float s;
+};
+__device__ __forceinline__ SegData seg_at(const TrackView &tv, const SegWindow &w, int r)
 {
+    SegData d;
     if ((unsigned)r < (unsigned)w.Wn) {
-        a = w.A[r];
-        il = w.I[r];
+        d.a = w.A[r]; d.b = w.B[r]; d.w = w.W[r]; d.s = w.S[r];
     } else {
         const int j = wrap_index(w.w0 + r, tv.N);
-        a = __ldg(tv.A + j);
-        il = __ldg(tv.I + j);
+        d.a = __ldg(tv.A + j); d.b = __ldg(tv.B + j); d.w = __ldg(tv.W + j); d.s = __ldg(tv.S + j);
     }
+    return d;
 }
 
-__device__ __forceinline__ void seg_tail(const TrackView &tv, const SegWindow &w, int r, float4 &sb, float2 &sw)
+__device__ __forceinline__ FrenetPt frenet_result(const SegData &g, int m, float t, float d2, float cr)
 {
-    if ((unsigned)r < (unsigned)w.Wn) {
-        sb = w.SB[r];
-        sw = w.SW[r];
-    } else {
-        const int j = wrap_index(w.w0 + r, tv.N);
-        sb = __ldg(tv.SB + j);
-        sw = __ldg(tv.SW + j);
-    }
-}
-
-// Frenet projection s(x; G), d(x; G) (Sec. II) as a local search from a
-// predicted segment c: the nearer of c's neighbours is followed while it is
-// strictly nearer (the left one also on ties), so the result is a local
-// minimum of the point-to-segment distance over the segment index; for points
-// within the track's reach it is the global nearest segment.  r is the
-// window-local segment index (updated); dr the last shift (a prediction of
-// the next one).  A search longer than kMaxMoves stops and sets flag.
-__device__ __forceinline__ FrenetPt frenet_walk(const TrackView &tv, const SegWindow &w, int &r, int &dr, float px,
-                                                float py, int &flag)
-{
-    const int c = r + dr;
-    float4 a0, a1, a2;
-    float i0, i1, i2;
-    if (c >= 1 && c + 1 < w.Wn) {
-        a0 = w.A[c - 1]; a1 = w.A[c]; a2 = w.A[c + 1];
-        i0 = w.I[c - 1]; i1 = w.I[c]; i2 = w.I[c + 1];
-    } else {
-        seg_at(tv, w, c - 1, a0, i0);
-        seg_at(tv, w, c, a1, i1);
-        seg_at(tv, w, c + 1, a2, i2);
-    }
-    float t0, t1, t2, c0, c1, c2;
-    const float d0 = seg_dist2(a0, i0, px, py, t0, c0);
-    const float d1 = seg_dist2(a1, i1, px, py, t1, c1);
-    const float d2 = seg_dist2(a2, i2, px, py, t2, c2);
-    int best = c;
-    float bd = d1, bt = t1, bc = c1;
-    if (d0 <= d1 && d0 <= d2) {
-        best = c - 1; bd = d0; bt = t0; bc = c0;
-        // keep walking backward while strictly nearer
-        for (int it = 0; it < kMaxMoves; ++it) {
-            float4 a; float il, t, cr;
-            seg_at(tv, w, best - 1, a, il);
-            const float dd = seg_dist2(a, il, px, py, t, cr);
-            if (!(dd <= bd)) break;
-            best -= 1; bd = dd; bt = t; bc = cr;
-            if (it == kMaxMoves - 1) flag = 1;
-        }
-    } else if (d2 < d1) {
-        best = c + 1; bd = d2; bt = t2; bc = c2;
-        for (int it = 0; it < kMaxMoves; ++it) {
-            float4 a; float il, t, cr;
-            seg_at(tv, w, best + 1, a, il);
-            const float dd = seg_dist2(a, il, px, py, t, cr);
-            if (!(dd < bd)) break;
-            best += 1; bd = dd; bt = t; bc = cr;
-            if (it == kMaxMoves - 1) flag = 1;
-        }
-    }
-    dr = best - r;
-    r = best;
-    float4 sb;
-    float2 sw;
-    seg_tail(tv, w, best, sb, sw);
-    const float dist = __fmul_rn(bd, rsqrtf(fmaxf(bd, 1e-30f)));
+    const float dist = __fmul_rn(d2, rsqrtf(fmaxf(d2, 1e-30f)));
     FrenetPt f;
-    f.s = __fmaf_rn(bt, sb.y, sb.x);
-    f.d = bc >= 0.0f ? dist : -dist;
-    f.t = bt;
-    f.wl = __fmaf_rn(bt, sb.w, sb.z);
-    f.wr = __fmaf_rn(bt, sw.y, sw.x);
+    f.s = __fmaf_rn(t, g.b.w, g.s);
+    f.d = cr >= 0.0f ? dist : -dist;
+    f.t = t;
+    f.wl = __fmaf_rn(t, g.w.y, g.w.x);
+    f.wr = __fmaf_rn(t, g.w.w, g.w.z);
+    f.m = m;
+    f.flag = 0;
+    return f;
+}
+
+// General local search by distance: starting at segment r, move to the next
+// segment while it is strictly nearer, else to the previous one while it is
+// at least as near (lowest index on ties); the result is a local minimum of
+// the point-to-segment distance over the segment index, which for points
+// within the track's reach is the global nearest segment of Sec. II's
+// projection.  A search longer than kMaxMoves stops and sets flag.
+static __device__ __noinline__ FrenetPt frenet_search(const TrackView tv, const SegWindow w, int r, float px, float py)
+{
+    int flag = 0;
+    SegData g = seg_at(tv, w, r);
+    float t, cr;
+    float bd = seg_dist2(g.a, g.b, px, py, t, cr);
+    bool moved = false;
+    for (int it = 0; it < kMaxMoves; ++it) {
+        const SegData gn = seg_at(tv, w, r + 1);
+        float tn, cn;
+        const float dn = seg_dist2(gn.a, gn.b, px, py, tn, cn);
+        if (!(dn < bd)) break;
+        r += 1; bd = dn; t = tn; cr = cn; g = gn; moved = true;
+        if (it == kMaxMoves - 1) flag = 1;
+    }
+    if (!moved) {
+        for (int it = 0; it < kMaxMoves; ++it) {
+            const SegData gp = seg_at(tv, w, r - 1);
+            float tp, cp;
+            const float dp = seg_dist2(gp.a, gp.b, px, py, tp, cp);
+            if (!(dp <= bd)) break;
+            r -= 1; bd = dp; t = tp; cr = cp; g = gp;
+            if (it == kMaxMoves - 1) flag = 1;
+        }
+    }
+    FrenetPt f = frenet_result(g, r, t, bd, cr);
+    f.flag = flag;
+    return f;
+}
+
+// Frenet projection s(x; G), d(x; G) (Sec. II) of a rollout state.
+// Two consecutive segments j-1, j of the polyline are equidistant from p
+// exactly on the bisector of their angle at waypoint j (where both feet are
+// interior) or inside the wedge where both feet are the waypoint itself; so,
+// within the track's reach (closer than any non-adjacent segment), p's
+// nearest segment is j when p lies strictly past waypoint j's bisector
+// line and not past waypoint j+1's, a side test against the direction
+// u_{j-1} + u_j (one dot product; ties go to the lower index, as in the
+// definition).  The sample carries a continuous segment position pos
+// (window-local index plus parameter) and its last advance vel; the
+// bisectors at c, c+1, c+2 around the predicted position decide between c
+// and c+1; if neither, the distance search above takes over.
+__device__ __forceinline__ FrenetPt frenet_step(const TrackView &tv, const SegWindow &w, int &r, float &pos,
+                                                float &vel, float px, float py, int &flag)
+{
+    const int c = __float2int_rd(pos + vel - 0.5f);
+    FrenetPt f;
+    bool done = false;
+    if (c >= 0 && c + 2 < w.Wn) {
+        const f2p pp = pk(px, py);
+        const float4 v0 = w.A[c], v1 = w.A[c + 1], v2 = w.A[c + 2];
+        const float2 d0 = upk(sub2(pp, pk(v0.x, v0.y)));
+        const float2 d1 = upk(sub2(pp, pk(v1.x, v1.y)));
+        const float2 d2 = upk(sub2(pp, pk(v2.x, v2.y)));
+        const bool p0 = __fmaf_rn(d0.x, v0.z, __fmul_rn(d0.y, v0.w)) > 0.f;
+        const bool p1 = __fmaf_rn(d1.x, v1.z, __fmul_rn(d1.y, v1.w)) > 0.f;
+        const bool p2 = __fmaf_rn(d2.x, v2.z, __fmul_rn(d2.y, v2.w)) > 0.f;
+        if (p0 && !p2) {
+            const int m = p1 ? c + 1 : c;
+            const float2 dm = p1 ? d1 : d0;
+            const float4 b = w.B[m];
+            float t = __fmul_rn(__fmaf_rn(dm.x, b.x, __fmul_rn(dm.y, b.y)), b.z);
+            t = fminf(fmaxf(t, 0.0f), 1.0f);
+            const float2 e = upk(fma2(pk(-t, -t), pk(b.x, b.y), pk(dm.x, dm.y)));
+            const float q2 = __fmaf_rn(e.x, e.x, __fmul_rn(e.y, e.y));
+            const float cr = __fmaf_rn(b.x, dm.y, -__fmul_rn(b.y, dm.x));
+            SegData g;
+            g.b = b; g.w = w.W[m]; g.s = w.S[m];
+            f = frenet_result(g, m, t, q2, cr);
+            done = true;
+        }
+    }
+    if (!done) {
+        const int start = (c < r - kMaxMoves || c > r + kMaxMoves) ? r : c;
+        f = frenet_search(tv, w, start, px, py);
+        flag |= f.flag;
+    }
+    const float np = (float)f.m + f.t;
+    vel = np - pos;
+    pos = np;
+    r = f.m;
     return f;
 }
 
@@ -178,9 +249,8 @@ __device__ __forceinline__ int nearest_segment_warp(const TrackView &tv, float p
     const int lane = threadIdx.x & 31;
     unsigned long long best = ~0ull;
     for (int j = lane; j < tv.N; j += 32) {
-        const float4 a = __ldg(tv.A + j);
         float t, cr;
-        const float d2 = seg_dist2(a, __ldg(tv.I + j), px, py, t, cr);
+        const float d2 = seg_dist2(__ldg(tv.A + j), __ldg(tv.B + j), px, py, t, cr);
         const unsigned long long key = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)j;
         best = key < best ? key : best;
     }
@@ -195,19 +265,11 @@ __device__ __forceinline__ int nearest_segment_warp(const TrackView &tv, float p
 // Projection on a known segment j (global index).
 __device__ __forceinline__ FrenetPt frenet_at(const TrackView &tv, int j, float px, float py)
 {
-    const float4 a = __ldg(tv.A + j);
+    SegData g;
+    g.a = __ldg(tv.A + j); g.b = __ldg(tv.B + j); g.w = __ldg(tv.W + j); g.s = __ldg(tv.S + j);
     float t, cr;
-    const float d2 = seg_dist2(a, __ldg(tv.I + j), px, py, t, cr);
-    const float4 sb = __ldg(tv.SB + j);
-    const float2 sw = __ldg(tv.SW + j);
-    const float dist = __fmul_rn(d2, rsqrtf(fmaxf(d2, 1e-30f)));
-    FrenetPt f;
-    f.s = __fmaf_rn(t, sb.y, sb.x);
-    f.d = cr >= 0.0f ? dist : -dist;
-    f.t = t;
-    f.wl = __fmaf_rn(t, sb.w, sb.z);
-    f.wr = __fmaf_rn(t, sw.y, sw.x);
-    return f;
+    const float d2 = seg_dist2(g.a, g.b, px, py, t, cr);
+    return frenet_result(g, j, t, d2, cr);
 }
 
 // Wrap a progress difference into (-L/2, L/2].
@@ -227,42 +289,44 @@ __device__ __forceinline__ float wrap_angle(float a) { return __fmaf_rn(-kTwoPi,
 // position inside a segment is ((hi - lap L) - s_j) + lo with an exact lap
 // subtraction, so the reference stays within a few float ulps of the exact
 // recursion however long the track.  One thread.  Segment data comes from
-// the shared-memory window (A, SB and C) when it holds the segment, else
+// the shared-memory window (A, B, S and C) when it holds the segment, else
 // from global memory.  j0 is the global segment of s0 (s0 in [0, L)).
 __device__ __forceinline__ void reference_traj(const TrackView &tv, const SegWindow &w, const float4 *Cw, int j0,
                                                float s0, float dt, float vscale, int T, float4 *ref)
 {
     float hi = s0, lo = 0.f;
-    int q = j0;                         // unwrapped segment index: segment q mod N of lap q div N
-    auto fetch = [&](int qq, float4 &a, float4 &sb, float4 &c) {
-        const int j = wrap_index(qq, tv.N);
-        const int rl = w.Wn > 0 ? wrap_index(qq - w.w0, tv.N) : -1;
-        if (rl >= 0 && rl < w.Wn) {
-            a = w.A[rl]; sb = w.SB[rl]; c = Cw[rl];
-        } else {
-            a = __ldg(tv.A + j); sb = __ldg(tv.SB + j); c = __ldg(tv.C + j);
-        }
-    };
-    auto lap_of = [&](int qq) { return (qq - wrap_index(qq, tv.N)) / tv.N; };
+    int j = j0, lap = 0;                                      // segment j of lap `lap`
+    int rl = w.Wn > 0 ? wrap_index(j0 - w.w0, tv.N) : -1;    // its window-local index
     auto locate = [&]() -> float4 {
-        float4 a, sb, c;
+        float4 va, vb, c;
+        float sj;
         for (int it = 0; it < 2 * tv.N + 2; ++it) {
-            fetch(q, a, sb, c);
-            const int j = wrap_index(q, tv.N);
-            const float lapL = (float)lap_of(q) * tv.L;
-            const float hm = hi - lapL;                    // exact: hi and lapL within a factor 2
-            const float sn = (j + 1 == tv.N) ? tv.L : sb.x + sb.y;
-            if (hm < sb.x) { q -= 1; continue; }
-            if (hm >= sn) { q += 1; continue; }
-            const float u = ((hm - sb.x) + lo) / sb.y;
+            if ((unsigned)rl < (unsigned)w.Wn) {
+                va = w.A[rl]; vb = w.B[rl]; sj = w.S[rl]; c = Cw[rl];
+            } else {
+                va = __ldg(tv.A + j); vb = __ldg(tv.B + j); sj = __ldg(tv.S + j); c = __ldg(tv.C + j);
+            }
+            const float hm = hi - (float)lap * tv.L;          // exact: within a factor 2 of lap L
+            const float sn = (j + 1 == tv.N) ? tv.L : sj + vb.w;
+            if (hm < sj) {
+                --j; --rl;
+                if (j < 0) { j = tv.N - 1; --lap; }
+                continue;
+            }
+            if (hm >= sn) {
+                ++j; ++rl;
+                if (j == tv.N) { j = 0; ++lap; }
+                continue;
+            }
+            const float u = ((hm - sj) + lo) / vb.w;
             float4 o;
-            o.x = __fmaf_rn(u, a.z, a.x);
-            o.y = __fmaf_rn(u, a.w, a.y);
+            o.x = __fmaf_rn(u, vb.x, va.x);
+            o.y = __fmaf_rn(u, vb.y, va.y);
             o.z = __fmaf_rn(u, c.y, c.x);
             o.w = __fmaf_rn(u, c.w, c.z);
             return o;
         }
-        return make_float4(a.x, a.y, c.x, c.z);
+        return make_float4(va.x, va.y, c.x, c.z);
     };
     ref[0] = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 r_cur = locate();
@@ -291,17 +355,21 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         if (r > 0) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
-        const unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        const unsigned long long p0 = (unsigned long long)c.x * 0xD2511F53ull;
+        const unsigned long long p1 = (unsigned long long)c.z * 0xCD9E8D57ull;
+        c = make_uint4((unsigned)(p1 >> 32) ^ c.y ^ k.x, (unsigned)p1, (unsigned)(p0 >> 32) ^ c.w ^ k.y,
+                       (unsigned)p0);
     }
     return c;
 }
 
-// Uniform in (0,1) from the top 23 bits (exact in float32).
+// Uniform in (0,1) from the top 23 bits: ((w >> 9) + 1/2) 2^-23, exact in
+// float32.  One funnel shift builds the float 1 + (w >> 9) 2^-23 in [1, 2)
+// (exponent bits 0x3f8 above the 23 mantissa bits); subtracting 1 - 2^-24 is
+// exact (Sterbenz) and leaves the uniform.
 __device__ __forceinline__ float uniform_open(unsigned w)
 {
-    return __fmaf_rn((float)(w >> 9), 1.1920928955078125e-7f, 5.9604644775390625e-8f);
+    return __uint_as_float(__funnelshift_r(w, 0x7Fu, 9)) - 0.99999994039535522461f;
 }
 
 // Box-Muller pair from two words: (sqrt(-2 ln u1) cos 2pi u2, ... sin ...).
@@ -310,8 +378,10 @@ __device__ __forceinline__ float uniform_open(unsigned w)
 __device__ __forceinline__ float2 box_muller(unsigned w0, unsigned w1)
 {
     const float u1 = uniform_open(w0), u2 = uniform_open(w1);
-    const float m = fmaxf(-2.0f * __logf(u1), 1e-30f);   // __logf may overshoot 0 for u1 -> 1
-    const float r = m * rsqrtf(m);
+    // -2 ln u1 = (-2 ln 2) log2 u1; the approximate log2 may overshoot 0 as u1 -> 1
+    const float m = fmaxf(-1.38629436111989061883f * __log2f(u1), 0.f);
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(m));
     float sn, cs;
     __sincosf(__fmaf_rn(kTwoPi, u2, -kPi), &sn, &cs);
     return make_float2(-r * cs, -r * sn);
@@ -412,14 +482,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsig
 
 // Shared-memory layout of a track window (16-byte aligned pieces).
 struct WindowSmem {
-    unsigned A, I, SB, SW, end;
+    unsigned A, B, W, S, end;
     __host__ __device__ WindowSmem(unsigned base, int Wn)
     {
         A = base;
-        I = A + 16u * Wn;
-        SB = I + 4u * Wn;
-        SW = SB + 16u * Wn;
-        end = SW + 8u * Wn;
+        B = A + 16u * Wn;
+        W = B + 16u * Wn;
+        S = W + 16u * Wn;
+        end = S + 4u * Wn;
     }
 };
 
@@ -432,23 +502,26 @@ __device__ __forceinline__ int window_start(int j0, int back, int N)
 }
 
 // Issue the bulk copies of window [w0, w0+Wn) (Wn a multiple of 4) of track
-// tv into shared memory at smem + layout; one thread; completes on bar.
+// tv into shared memory at smem + layout (one thread; completes on bar), plus
+// the C array into cdst when it is given.
 __device__ __forceinline__ SegWindow stage_window_issue(const TrackView &tv, int w0, int Wn, unsigned char *smem,
-                                                       const WindowSmem &ly, unsigned long long *bar, bool issue)
+                                                       const WindowSmem &ly, unsigned long long *bar, bool issue,
+                                                       void *cdst = nullptr)
 {
     SegWindow w;
     w.A = (const float4 *)(smem + ly.A);
-    w.I = (const float *)(smem + ly.I);
-    w.SB = (const float4 *)(smem + ly.SB);
-    w.SW = (const float2 *)(smem + ly.SW);
+    w.B = (const float4 *)(smem + ly.B);
+    w.W = (const float4 *)(smem + ly.W);
+    w.S = (const float *)(smem + ly.S);
     w.w0 = w0;
     w.Wn = Wn;
     if (issue) {
-        mbar_expect_tx(bar, (unsigned)Wn * (16u + 4u + 16u + 8u));
+        mbar_expect_tx(bar, (unsigned)Wn * (cdst ? 68u : 52u));
         bulk_g2s(smem + ly.A, tv.A + w0, (unsigned)Wn * 16u, bar);
-        bulk_g2s(smem + ly.I, tv.I + w0, (unsigned)Wn * 4u, bar);
-        bulk_g2s(smem + ly.SB, tv.SB + w0, (unsigned)Wn * 16u, bar);
-        bulk_g2s(smem + ly.SW, tv.SW + w0, (unsigned)Wn * 8u, bar);
+        bulk_g2s(smem + ly.B, tv.B + w0, (unsigned)Wn * 16u, bar);
+        bulk_g2s(smem + ly.W, tv.W + w0, (unsigned)Wn * 16u, bar);
+        bulk_g2s(smem + ly.S, tv.S + w0, (unsigned)Wn * 4u, bar);
+        if (cdst) bulk_g2s(cdst, tv.C + w0, (unsigned)Wn * 16u, bar);
     }
     return w;
 }

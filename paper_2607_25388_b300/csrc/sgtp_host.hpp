@@ -15,9 +15,8 @@
 struct sgtp_track {
     int n_tracks = 0;
     long long total = 0;                   // elements over all (ring-extended) tracks
-    float4 *A = nullptr, *SB = nullptr, *C = nullptr;
-    float *I = nullptr;
-    float2 *SW = nullptr;
+    float4 *A = nullptr, *B = nullptr, *W = nullptr, *C = nullptr;
+    float *S = nullptr;
     sgtp::TrackDesc *desc_dev = nullptr;
     std::vector<sgtp::TrackDesc> desc;     // host copy (L filled after prep)
     int device = 0;
@@ -32,7 +31,7 @@ inline TrackView track_view(const sgtp_track *t, int id)
 {
     const TrackDesc &d = t->desc[id];
     TrackView v;
-    v.A = t->A + d.offset; v.I = t->I + d.offset; v.SB = t->SB + d.offset; v.SW = t->SW + d.offset;
+    v.A = t->A + d.offset; v.B = t->B + d.offset; v.W = t->W + d.offset; v.S = t->S + d.offset;
     v.C = t->C + d.offset;
     v.N = d.N; v.L = d.L;
     return v;

@@ -40,13 +40,14 @@ struct AgentDev {
     float4 x0;
     float s_t, d_t;
     int j0, race;
+    float t0;                 // segment parameter of x_{i,t}
+    float pad[3];
 };
 
 struct PlanArgs {
     const TrackDesc *tdesc;
-    const float4 *A, *SB, *C;
-    const float *I;
-    const float2 *SW;
+    const float4 *A, *B, *W, *C;
+    const float *S;
     sgtp_params p;
     const RaceDev *races;     // NULL: single race `one`
     RaceDev one;
@@ -87,10 +88,11 @@ __device__ __forceinline__ RaceDev get_race(const PlanArgs &a, int r) { return a
 __device__ __forceinline__ AgentDev load_agent(const AgentDev *p)
 {
     const float4 *q = (const float4 *)p;
-    const float4 u = __ldcg(q), w = __ldcg(q + 1);
+    const float4 u = __ldcg(q), w = __ldcg(q + 1), z = __ldcg(q + 2);
     AgentDev A;
     A.x0 = u;
     A.s_t = w.x; A.d_t = w.y; A.j0 = __float_as_int(w.z); A.race = __float_as_int(w.w);
+    A.t0 = z.x;
     return A;
 }
 
@@ -98,7 +100,7 @@ __device__ __forceinline__ TrackView get_track(const PlanArgs &a, int id)
 {
     const TrackDesc d = a.tdesc[id];
     TrackView v;
-    v.A = a.A + d.offset; v.I = a.I + d.offset; v.SB = a.SB + d.offset; v.SW = a.SW + d.offset;
+    v.A = a.A + d.offset; v.B = a.B + d.offset; v.W = a.W + d.offset; v.S = a.S + d.offset;
     v.C = a.C + d.offset;
     v.N = d.N; v.L = d.L;
     return v;
@@ -165,97 +167,39 @@ __device__ bool grid_barrier(const PlanArgs &a, bool skip_arrival)
     return ok_sh != 0;
 }
 
-// Shared memory of the plan kernel: TMA barrier, track window (A, I, SB,
-// SW) plus the heading/speed array C used by the reference recursion, and the
-// per-best-response arrays.
-struct PlanSmem {
-    WindowSmem win;
-    size_t C, ref, ubar, opp, osum, odbar, ctl, total;
-    __host__ __device__ PlanSmem(int Wn, int maxT, int maxO) : win(16, Wn)
-    {
-        auto up = [](size_t x) { return (x + 15) & ~(size_t)15; };
-        C = up(win.end);
-        ref = up(C + sizeof(float4) * Wn);
-        ubar = up(ref + sizeof(float4) * (maxT + 1));
-        opp = up(ubar + sizeof(float2) * maxT);
-        osum = up(opp + sizeof(float2) * (size_t)maxT * maxO);
-        odbar = up(osum + sizeof(float4) * maxO);
-        ctl = up(odbar + sizeof(float) * maxO);
-        total = up(ctl + sizeof(float2) * maxT);
-    }
-};
-
-// Stage the window of vehicle A's track (and C when with_c); thread 0 issues,
-// everybody waits at the caller's __syncthreads after mbar_wait.
-__device__ __forceinline__ SegWindow stage_for(const PlanArgs &a, const TrackView &tv, int j0, unsigned char *smem,
-                                               const PlanSmem &SL, unsigned long long *mbar, bool with_c)
+// Stage the window of a vehicle's track around segment j0 (thread 0 issues
+// the bulk copies; the caller waits); fills the tile scalars' window fields.
+template <int MAXO>
+__device__ __forceinline__ void stage_vehicle_window(const PlanArgs &a, const TrackView &tv, int j0, bool with_c)
 {
-    const int Wn = min(a.Wn, (tv.N + 3) & ~3);
-    const int back = min(a.back, Wn / 4);
-    const int w0 = window_start(j0, back, tv.N);
-    const SegWindow w = stage_window_issue(tv, w0, Wn, smem, SL.win, mbar, false);
+    using T = Tile<MAXO>;
     if (threadIdx.x == 0) {
-        mbar_expect_tx(mbar, (unsigned)Wn * (16u + 4u + 16u + 8u + (with_c ? 16u : 0u)));
-        bulk_g2s(smem + SL.win.A, tv.A + w0, (unsigned)Wn * 16u, mbar);
-        bulk_g2s(smem + SL.win.I, tv.I + w0, (unsigned)Wn * 4u, mbar);
-        bulk_g2s(smem + SL.win.SB, tv.SB + w0, (unsigned)Wn * 16u, mbar);
-        bulk_g2s(smem + SL.win.SW, tv.SW + w0, (unsigned)Wn * 8u, mbar);
-        if (with_c) bulk_g2s(smem + SL.C, tv.C + w0, (unsigned)Wn * 16u, mbar);
+        BRScalars &S = T::sc();
+        const int Wn = min(a.Wn, (tv.N + 3) & ~3);
+        const int back = min(a.back, Wn / 4);
+        S.tv = tv;
+        S.Wn = Wn;
+        S.w0 = window_start(j0, back, tv.N);
+        S.invL = 1.0f / tv.L;
+        T::stage_window(tv, S.w0, Wn, with_c);
     }
-    return w;
-}
-
-// Sequential rollout of given controls (smem ctl[T]) from x0 with the window
-// walk: writes positions, states and the Frenet summary of a prediction.
-__device__ void roll_controls(const PlanArgs &a, const TrackView &tv, const SegWindow &w, const AgentDev &A, int T,
-                              int n_tail, const float2 *ctl, float2 *pos_out, float *xi_a, float *xi_b,
-                              float2 *summ_out, int &flag)
-{
-    const float invL = 1.0f / tv.L;
-    float x = A.x0.x, y = A.x0.y, psi = A.x0.z, v = A.x0.w;
-    float s = A.s_t, dsum = 0.f;
-    int r = wrap_index(A.j0 - w.w0, tv.N), dr = 0;
-    if (pos_out) pos_out[0] = make_float2(x, y);
-    if (xi_a) *(float4 *)xi_a = A.x0;
-    if (xi_b) *(float4 *)xi_b = A.x0;
-    for (int tau = 0; tau < T; ++tau) {
-        const float2 u = ctl[tau];
-        bicycle_step(a.p, x, y, psi, v, u.x, u.y);
-        const FrenetPt f = frenet_walk(tv, w, r, dr, x, y, flag);
-        s = s + wrap_len(f.s - s, tv.L, invL);
-        const int st = tau + 1;
-        if (st > T - n_tail) dsum = dsum + f.d;
-        if (pos_out) pos_out[st] = make_float2(x, y);
-        const float4 sv = make_float4(x, y, psi, v);
-        if (xi_a) ((float4 *)xi_a)[st] = sv;
-        if (xi_b) ((float4 *)xi_b)[st] = sv;
-    }
-    if (summ_out) *summ_out = make_float2(s - A.s_t, dsum / (float)n_tail);
 }
 
 template <int MAXO>
 __global__ void __launch_bounds__(256, 3) plan_kernel(PlanArgs a)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    using Tl = Tile<MAXO>;
     __shared__ unsigned long long cta_key;
     __shared__ int abort_sh, j0_sh;
     __shared__ unsigned ks_sh;
-    const PlanSmem SL(a.Wn, a.maxT, MAXO);
-    unsigned long long *mbar = (unsigned long long *)smem;
-    const float4 *sC = (const float4 *)(smem + SL.C);
-    float4 *sref = (float4 *)(smem + SL.ref);
-    float2 *subar = (float2 *)(smem + SL.ubar);
-    float2 *sopp = (float2 *)(smem + SL.opp);
-    float4 *sosum = (float4 *)(smem + SL.osum);
-    float *sodbar = (float *)(smem + SL.odbar);
-    float2 *sctl = (float2 *)(smem + SL.ctl);
+    BRScalars &S = Tl::sc();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool skip = (a.debug_flags & SGTP_DEBUG_SKIP_BARRIER_ARRIVAL) && blockIdx.x == 0;
     int flag = 0;
     unsigned phase = 0;
     bool ok = true;
-    if (threadIdx.x == 0) mbar_init(mbar, 1);
+    if (threadIdx.x == 0) mbar_init(Tl::bar(), 1);
     stamp(a, 0);
 
     // ------------------------------------------------------------ setup (one CTA per vehicle)
@@ -273,27 +217,27 @@ __global__ void __launch_bounds__(256, 3) plan_kernel(PlanArgs a)
         for (int q = threadIdx.x; q < R.T; q += blockDim.x) {
             // nominal controls, clipped: the zero-noise sample
             const float *U = a.U_io + R.u_off + (size_t)i * R.T * 2;
-            sctl[q] = sample_control(a.p, make_float2(U[2 * q], U[2 * q + 1]), make_float2(0.f, 0.f));
+            Tl::ctl()[q] = sample_control(a.p, make_float2(U[2 * q], U[2 * q + 1]), make_float2(0.f, 0.f));
         }
         __syncthreads();
         const int j0 = j0_sh;
-        const SegWindow w = stage_for(a, tv, j0, smem, SL, mbar, true);
+        stage_vehicle_window<MAXO>(a, tv, j0, true);
         if (threadIdx.x == 0) {
-            if (!mbar_wait_bounded(mbar, phase, (unsigned long long)a.timeout_ns)) atomicOr(a.status, SGTP_E_TIMEOUT);
+            if (!mbar_wait_bounded(Tl::bar(), phase, (unsigned long long)a.timeout_ns)) atomicOr(a.status, SGTP_E_TIMEOUT);
         }
         phase ^= 1u;
         __syncthreads();
         const FrenetPt f = frenet_at(tv, j0, x0.x, x0.y);
         AgentDev A;
-        A.x0 = x0; A.s_t = f.s; A.d_t = f.d; A.j0 = j0; A.race = ri;
-        if (threadIdx.x == 0) {
+        A.x0 = x0; A.s_t = f.s; A.d_t = f.d; A.j0 = j0; A.race = ri; A.t0 = f.t;
+        if (threadIdx.x == 32) {
+            // reference recursion (warp 1) alongside the nominal rollout's dynamics (warp 0)
             a.agents[ag] = A;
-            reference_traj(tv, w, sC, j0, f.s, a.p.dt, a.vref[ag], R.T,
+            reference_traj(tv, Tl::win(S.w0, S.Wn), Tl::C(), j0, f.s, a.p.dt, a.vref[ag], R.T,
                            a.ref + (size_t)R.pos_off + (size_t)i * (R.T + 1));
-        } else if (threadIdx.x == 32) {
-            roll_controls(a, tv, w, A, R.T, R.n_tail, sctl, a.pos[0] + R.pos_off + (size_t)i * (R.T + 1), nullptr,
-                          nullptr, a.summ[0] + ag, flag);
         }
+        roll_cooperative<MAXO>(a.p, x0, f.s, j0, R.T, R.n_tail, a.pos[0] + R.pos_off + (size_t)i * (R.T + 1), nullptr,
+                               nullptr, a.summ[0] + ag, flag);
     }
     {
         // fresh selection keys for every best response of the plan
@@ -313,7 +257,6 @@ __global__ void __launch_bounds__(256, 3) plan_kernel(PlanArgs a)
         const int i1 = (int)((long long)n_items * (blockIdx.x + 1) / gridDim.x);
         int cur = -1;                 // vehicle (global index) staged
         unsigned long long *cur_slot = nullptr;
-        BRView bv;
         for (int item = i0; item < i1; ++item) {
             int ri, i, t;
             if (!extra) {
@@ -336,19 +279,30 @@ __global__ void __launch_bounds__(256, 3) plan_kernel(PlanArgs a)
                 if (threadIdx.x == 0 && cur_slot) atomicMin(cur_slot, cta_key);
                 const TrackView tv = get_track(a, R.track_id);
                 const AgentDev A = load_agent(a.agents + ag);
-                if (threadIdx.x == 0) cta_key = ~0ull;
-                const SegWindow w = stage_for(a, tv, A.j0, smem, SL, mbar, false);
                 const int T = R.T, n_opp = R.n_v - 1;
-                const float *U = a.U_io + R.u_off + (size_t)i * T * 2;
-                for (int q = threadIdx.x; q < T; q += blockDim.x) subar[q] = make_float2(__ldcg(U + 2 * q), __ldcg(U + 2 * q + 1));
-                const float4 *gref = a.ref + (size_t)R.pos_off + (size_t)i * (T + 1);
-                for (int q = threadIdx.x; q <= T; q += blockDim.x) sref[q] = __ldcg(gref + q);
-                const float2 *pin = a.pos[bin] + R.pos_off;
-                for (int q = threadIdx.x; q < T * n_opp; q += blockDim.x) {
-                    const int tau = q / n_opp, o = q - tau * n_opp;
-                    const int jv = o < i ? o : o + 1;
-                    sopp[q] = __ldcg(pin + (size_t)jv * (T + 1) + tau + 1);
+                stage_vehicle_window<MAXO>(a, tv, A.j0, false);
+                if (threadIdx.x == 0) {
+                    cta_key = ~0ull;
+                    S.x0 = A.x0; S.s_t = A.s_t; S.d_t = A.d_t;
+                    S.r0 = wrap_index(A.j0 - S.w0, tv.N);
+                    S.pos0 = (float)S.r0 + A.t0;
+                    S.vel0 = __fdiv_rn(__fmul_rn(a.p.dt, A.x0.w), __ldg(tv.B + A.j0).w);
+                    S.T = T; S.n_opp = n_opp; S.n_tail = R.n_tail;
+                    S.key = a.key;
+                    S.ctr_agent_round = (unsigned)i | ((unsigned)round << 16);
+                    S.ctr_race = R.race_tag;
+                    S.stream_bit = 0u;
                 }
+                const float *U = a.U_io + R.u_off + (size_t)i * T * 2;
+                for (int q = threadIdx.x; q < T; q += blockDim.x)
+                    Tl::ubar()[q] = make_float2(__ldcg(U + 2 * q), __ldcg(U + 2 * q + 1));
+                const float4 *gref = a.ref + (size_t)R.pos_off + (size_t)i * (T + 1);
+                for (int q = threadIdx.x; q <= T; q += blockDim.x) Tl::ref()[q] = __ldcg(gref + q);
+                const float2 *pin = a.pos[bin] + R.pos_off;
+                stage_opponents<MAXO>(T, n_opp, [&](int tau, int o) {
+                    const int jv = o < i ? o : o + 1;
+                    return __ldcg(pin + (size_t)jv * (T + 1) + tau);
+                });
                 if (threadIdx.x < n_opp) {
                     const int o = threadIdx.x;
                     const int jv = o < i ? o : o + 1;
@@ -357,25 +311,14 @@ __global__ void __launch_bounds__(256, 3) plan_kernel(PlanArgs a)
                     const float ds_t = wrap_len(A.s_t - B.s_t, tv.L, 1.0f / tv.L);
                     const float alpha = 1.0f / (1.0f + fabsf(ds_t) / (a.p.s_contest + a.p.eps_alpha));
                     const float gamma = (ds_t > a.p.s_role && ds_t < a.p.s_contest) ? a.p.w_block : 0.f;
-                    sosum[o] = make_float4(ds_t, alpha, gamma, sm.x);
-                    sodbar[o] = sm.y;
+                    Tl::osum()[o] = make_float4(ds_t, alpha, gamma, sm.x);
+                    Tl::odbar()[o] = sm.y;
                 }
-                bv.tv = tv;
-                bv.win = w;
-                bv.ubar = subar; bv.ref = sref; bv.opp = sopp; bv.osum = sosum; bv.odbar = sodbar;
-                bv.x0 = A.x0; bv.s_t = A.s_t; bv.d_t = A.d_t;
-                bv.r0 = wrap_index(A.j0 - w.w0, tv.N);
-                bv.T = T; bv.n_opp = n_opp; bv.n_tail = R.n_tail;
-                bv.invL = 1.0f / tv.L;
-                bv.key = a.key;
-                bv.ctr_agent_round = (unsigned)i | ((unsigned)round << 16);
-                bv.ctr_race = R.race_tag;
-                bv.stream_bit = 0u;
                 cur = ag;
                 cur_slot = a.keys + R.ks_off + (extra ? (a.L + 1) * R.n_v : round * R.n_v + i);
                 __syncthreads();
                 if (threadIdx.x == 0) {
-                    if (!mbar_wait_bounded(mbar, phase, (unsigned long long)a.timeout_ns))
+                    if (!mbar_wait_bounded(Tl::bar(), phase, (unsigned long long)a.timeout_ns))
                         atomicOr(a.status, SGTP_E_TIMEOUT);
                     abort_sh = (ld_status(a.status) & 0xff) != 0;
                 }
@@ -386,8 +329,8 @@ __global__ void __launch_bounds__(256, 3) plan_kernel(PlanArgs a)
             const unsigned k = (unsigned)t * blockDim.x + threadIdx.x;
             unsigned long long best = ~0ull;
             if (k < (unsigned)a.K) {
-                const SampleResult r = run_candidate<MAXO, false>(bv, a.p, k, round > 0, false, flag, nullptr,
-                                                                  nullptr, nullptr);
+                const SampleResult r = run_candidate<MAXO, false>(S, a.p, a.key, k, round > 0, flag, nullptr, nullptr,
+                                                                  nullptr);
                 best = make_key(r.feasible, r.cost, r.viol, k);
             }
             best = warp_min_u64(best);
@@ -420,7 +363,7 @@ __global__ void __launch_bounds__(256, 3) plan_kernel(PlanArgs a)
             }
             const int slot = extra ? (a.L + 1) * R.n_v : round * R.n_v + i;
             const TrackView tv = get_track(a, R.track_id);
-            const SegWindow w = stage_for(a, tv, A.j0, smem, SL, mbar, false);
+            stage_vehicle_window<MAXO>(a, tv, A.j0, false);
             if (threadIdx.x == 0) {
                 const unsigned long long key = __ldcg(a.keys + R.ks_off + slot);
                 ks_sh = (unsigned)(key & 0x7fffffffull);
@@ -436,7 +379,7 @@ __global__ void __launch_bounds__(256, 3) plan_kernel(PlanArgs a)
                 const float2 z = (q & 1) ? box_muller(wv.z, wv.w) : box_muller(wv.x, wv.y);
                 const float2 ub = make_float2(__ldcg(a.U_io + uo + 2 * q), __ldcg(a.U_io + uo + 2 * q + 1));
                 const float2 u = sample_control(a.p, ub, z);
-                sctl[q] = u;
+                Tl::ctl()[q] = u;
                 a.U_io[uo + 2 * q] = u.x;
                 a.U_io[uo + 2 * q + 1] = u.y;
                 if (a.u_hist) {
@@ -445,17 +388,15 @@ __global__ void __launch_bounds__(256, 3) plan_kernel(PlanArgs a)
                 }
             }
             if (threadIdx.x == 0) {
-                if (!mbar_wait_bounded(mbar, phase, (unsigned long long)a.timeout_ns)) atomicOr(a.status, SGTP_E_TIMEOUT);
+                if (!mbar_wait_bounded(Tl::bar(), phase, (unsigned long long)a.timeout_ns)) atomicOr(a.status, SGTP_E_TIMEOUT);
             }
             phase ^= 1u;
             __syncthreads();
-            if (threadIdx.x == 0) {
-                float *xi_final = (round == a.L || extra) ? a.xi_out + xo : nullptr;
-                float *xi_h = a.xi_hist ? a.xi_hist + (size_t)round * a.xi_total + xo : nullptr;
-                roll_controls(a, tv, w, A, T, R.n_tail, sctl,
-                              extra ? nullptr : a.pos[bout] + R.pos_off + (size_t)i * (T + 1), xi_final, xi_h,
-                              extra ? nullptr : a.summ[bout] + ag, flag);
-            }
+            float *xi_final = (round == a.L || extra) ? a.xi_out + xo : nullptr;
+            float *xi_h = a.xi_hist ? a.xi_hist + (size_t)round * a.xi_total + xo : nullptr;
+            roll_cooperative<MAXO>(a.p, A.x0, A.s_t, A.j0, T, R.n_tail,
+                                   extra ? nullptr : a.pos[bout] + R.pos_off + (size_t)i * (T + 1), xi_final, xi_h,
+                                   extra ? nullptr : a.summ[bout] + ag, flag);
         }
         if (round <= a.L) ok = grid_barrier(a, skip);
         stamp(a, 3 + 2 * round);
@@ -487,7 +428,7 @@ template <int MAXO>
 sgtp_status launch_plan_t(PlanArgs &a, const sgtp_launch_opts *opts, cudaStream_t s)
 {
     const int block = 256;
-    const size_t smem = PlanSmem(a.Wn, a.maxT, MAXO).total;
+    const size_t smem = BRTile<MAXO>::kBytes;
     static int configured = 0;
     if (!configured) {
         SGTP_CUDA(cudaFuncSetAttribute(plan_kernel<MAXO>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
@@ -523,7 +464,7 @@ void fill_common(PlanArgs &a, const sgtp_track *trk, const sgtp_params *p, int K
                  int *status, const sgtp_launch_opts *opts)
 {
     a.tdesc = trk->desc_dev;
-    a.A = trk->A; a.I = trk->I; a.SB = trk->SB; a.SW = trk->SW; a.C = trk->C;
+    a.A = trk->A; a.B = trk->B; a.W = trk->W; a.S = trk->S; a.C = trk->C;
     a.p = *p;
     a.K = K; a.L = L;
     a.tiles = (K + 255) / 256;
@@ -531,7 +472,7 @@ void fill_common(PlanArgs &a, const sgtp_track *trk, const sgtp_params *p, int K
     a.key = make_uint2((unsigned)seed, (unsigned)(seed >> 32));
     a.xi_out = xi_out; a.k_star_out = k_star_out; a.xi_hist = xi_hist; a.u_hist = u_hist;
     a.status = status;
-    a.Wn = window_len(kWinMax, opts ? opts->window : 0);
+    a.Wn = window_len(kWinTile, opts ? opts->window : 0);
     a.back = 48;
     a.timeout_ns = (opts && opts->wait_timeout_ns > 0) ? opts->wait_timeout_ns : 1000000000ll;
     a.debug_flags = opts ? opts->debug_flags : 0;

@@ -5,43 +5,94 @@
 //   x_{tau+1} = f(x_tau, u_tau), kinematic bicycle, Euler   (Sec. II)
 //   c = c_track (Eq. ctrack) + w_game * sum_j c_game,ij     (Eqs. game_cost, allc)
 //   h = b * o (Eqs. selection-boundary, selection-vehicle), nu (fallback)
-// The horizon loop keeps the state, one running cost sum, the running
+// The horizon loop keeps the state, a running cost pair, the running
 // boundary clearance and one running minimum distance per opponent in
-// registers; nothing of the trajectory is stored unless asked for.
+// registers; nothing of the trajectory is stored unless asked for.  Paired
+// quantities (x/y errors, a/delta controls, two opponents) use the packed
+// f32x2 arithmetic of sm_100-class GPUs.
+//
+// Every per-problem array lives in shared memory at a compile-time offset
+// (BRTile below), so the sample loop holds no pointers in registers.
 #pragma once
 
 #include "sgtp_device.cuh"
 
 namespace sgtp {
 
-// Read-only view of one best-response problem, staged in shared memory.
-struct BRView {
-    TrackView tv;
-    SegWindow win;
-    const float2 *ubar;   // [T]          nominal controls
-    const float4 *ref;    // [T+1]        reference states, row 0 unused
-    const float2 *opp;    // [T][n_opp]   opponent positions at tau = 1..T (row tau-1)
-    const float4 *osum;   // [n_opp]      (ds_t, alpha, gamma, prog)
-    const float *odbar;   // [n_opp]      tail-mean lateral offset of each opponent
+constexpr int kWinTile = 512;          // track window of a best-response tile (segments)
+constexpr float kFarAway = 1.0e15f;    // position of an absent opponent slot
+
+// Scalars of one best-response problem (shared memory).
+struct BRScalars {
+    TrackView tv;         // global track (slow path only)
     float4 x0;
     float s_t, d_t;
+    float pos0, vel0;     // continuous segment position of x0 (window-local) and its predicted advance
     int r0;               // window-local segment of x0
+    int w0, Wn;           // window
     int T, n_opp, n_tail;
     float invL;
-    // noise counter words
-    uint2 key;
+    uint2 key;            // noise counter words
     unsigned ctr_agent_round, ctr_race, stream_bit;
+    int pad[3];
 };
 
+// Shared-memory tile of one best response: fixed offsets for a given MAXO.
 template <int MAXO>
-struct SampleState {
-    float x, y, psi, v;
-    float a_prev, d_prev;
-    float s;          // unwrapped progress
-    int r, dr;        // window-local nearest segment, last shift
-    float c;          // running c_track
-    float rho_bd, d_tail;
-    float g2[MAXO];
+struct BRTile {
+    static constexpr int NP = (MAXO + 1) / 2;           // opponent pairs per step
+    static constexpr unsigned kBar = 0;                 // TMA mbarrier (8 B)
+    static constexpr unsigned kScal = 16;
+    static constexpr unsigned kA = (kScal + sizeof(BRScalars) + 15) & ~15u;
+    static constexpr unsigned kB = kA + 16u * kWinTile;
+    static constexpr unsigned kW = kB + 16u * kWinTile;
+    static constexpr unsigned kS = kW + 16u * kWinTile;
+    static constexpr unsigned kC = kS + 4u * kWinTile;   // heading/speed window (setup only)
+    static constexpr unsigned kRef = kC + 16u * kWinTile;
+    static constexpr unsigned kUbar = kRef + 16u * (SGTP_MAX_T + 1);
+    static constexpr unsigned kOpp = kUbar + 8u * SGTP_MAX_T;
+    static constexpr unsigned kOsum = kOpp + 16u * SGTP_MAX_T * NP;
+    static constexpr unsigned kOdbar = kOsum + 16u * SGTP_MAX_AGENTS;
+    static constexpr unsigned kCtl = kOdbar + 4u * SGTP_MAX_AGENTS;
+    static constexpr unsigned kSt = kCtl + 8u * SGTP_MAX_T;          // states of one rollout (T+1)
+    static constexpr unsigned kFr = kSt + 16u * (SGTP_MAX_T + 1);     // their raw Frenet (s, d)
+    static constexpr unsigned kBytes = kFr + 8u * SGTP_MAX_T;
+};
+
+extern __shared__ __align__(16) unsigned char g_smem[];
+
+template <int MAXO>
+struct Tile {
+    using L = BRTile<MAXO>;
+    static __device__ __forceinline__ unsigned long long *bar() { return (unsigned long long *)(g_smem + L::kBar); }
+    static __device__ __forceinline__ BRScalars &sc() { return *(BRScalars *)(g_smem + L::kScal); }
+    static __device__ __forceinline__ float4 *A() { return (float4 *)(g_smem + L::kA); }
+    static __device__ __forceinline__ float4 *B() { return (float4 *)(g_smem + L::kB); }
+    static __device__ __forceinline__ float4 *W() { return (float4 *)(g_smem + L::kW); }
+    static __device__ __forceinline__ float *S() { return (float *)(g_smem + L::kS); }
+    static __device__ __forceinline__ float4 *C() { return (float4 *)(g_smem + L::kC); }
+    static __device__ __forceinline__ float4 *ref() { return (float4 *)(g_smem + L::kRef); }
+    static __device__ __forceinline__ float2 *ubar() { return (float2 *)(g_smem + L::kUbar); }
+    static __device__ __forceinline__ float4 *opp() { return (float4 *)(g_smem + L::kOpp); }
+    static __device__ __forceinline__ float4 *osum() { return (float4 *)(g_smem + L::kOsum); }
+    static __device__ __forceinline__ float *odbar() { return (float *)(g_smem + L::kOdbar); }
+    static __device__ __forceinline__ float2 *ctl() { return (float2 *)(g_smem + L::kCtl); }
+    static __device__ __forceinline__ float4 *st() { return (float4 *)(g_smem + L::kSt); }
+    static __device__ __forceinline__ float2 *fr() { return (float2 *)(g_smem + L::kFr); }
+    static __device__ __forceinline__ SegWindow win(int w0, int Wn)
+    {
+        return SegWindow{A(), B(), W(), S(), w0, Wn};
+    }
+    // Issue the window's bulk copies (one thread; completes on bar()).
+    static __device__ __forceinline__ void stage_window(const TrackView &tv, int w0, int Wn, bool with_c)
+    {
+        mbar_expect_tx(bar(), (unsigned)Wn * (with_c ? 68u : 52u));
+        bulk_g2s(A(), tv.A + w0, (unsigned)Wn * 16u, bar());
+        bulk_g2s(B(), tv.B + w0, (unsigned)Wn * 16u, bar());
+        bulk_g2s(W(), tv.W + w0, (unsigned)Wn * 16u, bar());
+        bulk_g2s(S(), tv.S + w0, (unsigned)Wn * 4u, bar());
+        if (with_c) bulk_g2s(C(), tv.C + w0, (unsigned)Wn * 16u, bar());
+    }
 };
 
 // Clipped control from a nominal control and a normal pair z (Pi_U).
@@ -69,77 +120,97 @@ __device__ __forceinline__ void bicycle_step(const sgtp_params &p, float &x, flo
     x = x1; y = y1; psi = psi1; v = v1;
 }
 
-// Noise words of candidate k at steps 2m, 2m+1.
-__device__ __forceinline__ uint4 noise_block(const BRView &bv, unsigned k, int m)
+// Normal pairs of candidate k at steps 2m and 2m+1 (one Philox block).
+// The key comes from a kernel parameter, so that the round keys of the
+// Weyl schedule stay in the uniform datapath.
+__device__ __forceinline__ void noise_pair(const BRScalars &S, uint2 key, unsigned k, int m, float2 &z0, float2 &z1)
 {
-    return philox4x32_10(make_uint4(k, (unsigned)m | bv.stream_bit, bv.ctr_agent_round, bv.ctr_race), bv.key);
+    const uint4 w = philox4x32_10(make_uint4(k, (unsigned)m | S.stream_bit, S.ctr_agent_round, S.ctr_race), key);
+    z0 = box_muller(w.x, w.y);
+    z1 = box_muller(w.z, w.w);
 }
 
 template <int MAXO>
-__device__ __forceinline__ void sample_init(SampleState<MAXO> &S, const BRView &bv)
+struct SampleState {
+    float x, y, psi, v;
+    float a_prev, d_prev;
+    float s;          // unwrapped progress
+    int r;            // nearest segment (window-local)
+    float pos, vel;   // continuous segment position and its last advance
+    f2p cost;         // running c_track, two partial sums
+    float rho_bd, d_tail;
+    float g2[2 * BRTile<MAXO>::NP];
+};
+
+template <int MAXO>
+__device__ __forceinline__ void sample_init(SampleState<MAXO> &St, const BRScalars &S)
 {
-    S.x = bv.x0.x; S.y = bv.x0.y; S.psi = bv.x0.z; S.v = bv.x0.w;
-    S.a_prev = 0.f; S.d_prev = 0.f;
-    S.s = bv.s_t;
-    S.r = bv.r0; S.dr = 0;
-    S.c = 0.f;
-    S.rho_bd = __int_as_float(0x7f800000);
-    S.d_tail = 0.f;
+    St.x = S.x0.x; St.y = S.x0.y; St.psi = S.x0.z; St.v = S.x0.w;
+    St.a_prev = 0.f; St.d_prev = 0.f;
+    St.s = S.s_t;
+    St.r = S.r0;
+    St.pos = S.pos0; St.vel = S.vel0;
+    St.cost = pk(0.f, 0.f);
+    St.rho_bd = __int_as_float(0x7f800000);
+    St.d_tail = 0.f;
 #pragma unroll
-    for (int o = 0; o < MAXO; ++o) S.g2[o] = __int_as_float(0x7f800000);
+    for (int o = 0; o < 2 * BRTile<MAXO>::NP; ++o) St.g2[o] = __int_as_float(0x7f800000);
 }
 
 // Advance a candidate by one step tau with control u; optional outputs.
 template <int MAXO, bool OUT>
-__device__ __forceinline__ void sample_step(SampleState<MAXO> &S, const BRView &bv, const sgtp_params &p, int tau,
-                                            float2 u, int &flag, float *st_out, float *fr_out)
+__device__ __forceinline__ void sample_step(SampleState<MAXO> &St, const BRScalars &S, const sgtp_params &p,
+                                            int tau, float2 u, int &flag, float *st_out, float *fr_out)
 {
+    using T = Tile<MAXO>;
     // control cost, tau = 0..H-1, and smoothness, tau = 1..H-1 (Eq. ctrack)
-    float cc = __fmaf_rn(p.R[0], __fmul_rn(u.x, u.x), __fmul_rn(p.R[1], __fmul_rn(u.y, u.y)));
+    const f2p uu = pk(u.x, u.y);
+    f2p acc = fma2(mul2(uu, uu), pk(p.R[0], p.R[1]), St.cost);
     if (tau > 0) {
-        const float da = u.x - S.a_prev, dd = u.y - S.d_prev;
-        cc = __fmaf_rn(p.S[0], __fmul_rn(da, da), cc);
-        cc = __fmaf_rn(p.S[1], __fmul_rn(dd, dd), cc);
+        const f2p du = sub2(uu, pk(St.a_prev, St.d_prev));
+        acc = fma2(mul2(du, du), pk(p.S[0], p.S[1]), acc);
     }
-    S.a_prev = u.x; S.d_prev = u.y;
+    St.a_prev = u.x; St.d_prev = u.y;
 
-    bicycle_step(p, S.x, S.y, S.psi, S.v, u.x, u.y);
+    bicycle_step(p, St.x, St.y, St.psi, St.v, u.x, u.y);
     const int st = tau + 1;
 
     // Frenet of the new state, progress unwrapped along the rollout
-    const FrenetPt f = frenet_walk(bv.tv, bv.win, S.r, S.dr, S.x, S.y, flag);
-    S.s = S.s + wrap_len(f.s - S.s, bv.tv.L, bv.invL);
+    const FrenetPt f = frenet_step(S.tv, T::win(S.w0, S.Wn), St.r, St.pos, St.vel, St.x, St.y, flag);
+    St.s = St.s + wrap_len(f.s - St.s, S.tv.L, S.invL);
 
     // tracking term, tau = 1..H (Eq. ctrack), heading error wrapped
-    const float4 r = bv.ref[st];
-    const float ex = S.x - r.x, ey = S.y - r.y, ep = wrap_angle(S.psi - r.z), ev = S.v - r.w;
-    cc = __fmaf_rn(p.Q[0], __fmul_rn(ex, ex), cc);
-    cc = __fmaf_rn(p.Q[1], __fmul_rn(ey, ey), cc);
-    cc = __fmaf_rn(p.Q[2], __fmul_rn(ep, ep), cc);
-    cc = __fmaf_rn(p.Q[3], __fmul_rn(ev, ev), cc);
-    S.c = S.c + cc;
+    const float4 r = T::ref()[st];
+    const f2p exy = sub2(pk(St.x, St.y), pk(r.x, r.y));
+    acc = fma2(mul2(exy, exy), pk(p.Q[0], p.Q[1]), acc);
+    const f2p epv = pk(wrap_angle(St.psi - r.z), St.v - r.w);
+    St.cost = fma2(mul2(epv, epv), pk(p.Q[2], p.Q[3]), acc);
 
     // boundary clearance (Sec. III-B) with widths at the foot point
-    S.rho_bd = fminf(S.rho_bd, fminf(f.wr + f.d, f.wl - f.d));
+    St.rho_bd = fminf(St.rho_bd, fminf(f.wr + f.d, f.wl - f.d));
 
     // tail lateral offsets (blocking term)
-    if (st > bv.T - bv.n_tail) S.d_tail = S.d_tail + f.d;
+    if (st > S.T - S.n_tail) St.d_tail = St.d_tail + f.d;
 
-    // time-aligned distances to every opponent (Eq. Dmin)
-    const float2 *op = bv.opp + (size_t)tau * bv.n_opp;
+    // time-aligned distances to every opponent (Eq. Dmin), two at a time
+    constexpr int NP = BRTile<MAXO>::NP;
+    const float4 *row = T::opp() + tau * NP;
+    const f2p X = pk(St.x, St.x), Y = pk(St.y, St.y);
 #pragma unroll
-    for (int o = 0; o < MAXO; ++o) {
-        if (o < bv.n_opp) {
-            const float2 q = op[o];
-            const float dx = S.x - q.x, dy = S.y - q.y;
-            S.g2[o] = fminf(S.g2[o], __fmaf_rn(dx, dx, __fmul_rn(dy, dy)));
-        }
+    for (int q = 0; q < NP; ++q) {
+        const float4 o = row[q];
+        const f2p dx = sub2(X, pk(o.x, o.y));
+        const f2p dy = sub2(Y, pk(o.z, o.w));
+        const float2 d2 = upk(fma2(dx, dx, mul2(dy, dy)));
+        St.g2[2 * q] = fminf(St.g2[2 * q], d2.x);
+        St.g2[2 * q + 1] = fminf(St.g2[2 * q + 1], d2.y);
     }
     if (OUT) {
         if (st_out) {
-            st_out[4 * st + 0] = S.x; st_out[4 * st + 1] = S.y; st_out[4 * st + 2] = S.psi; st_out[4 * st + 3] = S.v;
+            st_out[4 * st + 0] = St.x; st_out[4 * st + 1] = St.y; st_out[4 * st + 2] = St.psi;
+            st_out[4 * st + 3] = St.v;
         }
-        if (fr_out) { fr_out[2 * st] = S.s; fr_out[2 * st + 1] = f.d; }
+        if (fr_out) { fr_out[2 * st] = St.s; fr_out[2 * st + 1] = f.d; }
     }
 }
 
@@ -151,22 +222,25 @@ struct SampleResult {
 // Terminal game cost per opponent (Eqs. c_contest, c_long, c_block,
 // c_safety), total cost (Eq. allc), feasibility and violation (Sec. III-B).
 template <int MAXO>
-__device__ __forceinline__ SampleResult sample_finish(const SampleState<MAXO> &S, const BRView &bv,
+__device__ __forceinline__ SampleResult sample_finish(const SampleState<MAXO> &St, const BRScalars &S,
                                                       const sgtp_params &p, bool game_on)
 {
-    const float dbar_i = S.d_tail / (float)bv.n_tail;
-    const float prog_i = S.s - bv.s_t;
+    using T = Tile<MAXO>;
+    const float2 cp = upk(St.cost);
+    const float c_track = cp.x + cp.y;
+    const float dbar_i = St.d_tail / (float)S.n_tail;
+    const float prog_i = St.s - S.s_t;
     float c_game = 0.f;
     float rho_obs = __int_as_float(0x7f800000);
 #pragma unroll
     for (int o = 0; o < MAXO; ++o) {
-        if (o < bv.n_opp) {
-            const float4 os = bv.osum[o];            // ds_t, alpha, gamma, prog_j
+        if (o < S.n_opp) {
+            const float4 os = T::osum()[o];          // ds_t, alpha, gamma, prog_j
             const float ds_H = os.x + (prog_i - os.w);
             const float c_contest = fabsf(ds_H) < p.s_contest ? -p.w_contest : 0.f;
             const float c_long = -p.w_long * os.y * ds_H;
-            const float c_block = os.z != 0.f ? -os.z / (1.f + fabsf(dbar_i - bv.odbar[o])) : 0.f;
-            const float g = sqrtf(S.g2[o]);
+            const float c_block = os.z != 0.f ? -os.z / (1.f + fabsf(dbar_i - T::odbar()[o])) : 0.f;
+            const float g = sqrtf(St.g2[o]);
             const float sh = fmaxf(0.f, p.g_safe - g);
             const float c_safety = p.w_safety * sh * sh;
             c_game = c_game + (c_contest + c_long + c_block + c_safety);
@@ -174,45 +248,117 @@ __device__ __forceinline__ SampleResult sample_finish(const SampleState<MAXO> &S
         }
     }
     SampleResult r;
-    r.cost = game_on ? __fmaf_rn(p.w_game, c_game, S.c) : S.c;
-    const bool b = S.rho_bd >= p.m_bd;
+    r.cost = game_on ? __fmaf_rn(p.w_game, c_game, c_track) : c_track;
+    const bool b = St.rho_bd >= p.m_bd;
     const bool ob = rho_obs >= p.d_col;
     r.feasible = b && ob;
-    r.viol = fmaxf(0.f, p.m_bd - S.rho_bd) + fmaxf(0.f, p.d_col - rho_obs);
+    r.viol = fmaxf(0.f, p.m_bd - St.rho_bd) + fmaxf(0.f, p.d_col - rho_obs);
     return r;
 }
 
 // Full candidate: noise, controls, rollout, finish.  Optional outputs are
 // written when OUT (states (T+1)x4, frenet (T+1)x2, controls Tx2).
 template <int MAXO, bool OUT>
-__device__ __forceinline__ SampleResult run_candidate(const BRView &bv, const sgtp_params &p, unsigned k, bool game_on,
-                                                      bool zero_noise, int &flag, float *st_out, float *fr_out,
-                                                      float *u_out)
+__device__ __forceinline__ SampleResult run_candidate(const BRScalars &S, const sgtp_params &p, uint2 key,
+                                                      unsigned k, bool game_on, int &flag, float *st_out,
+                                                      float *fr_out, float *u_out)
 {
-    SampleState<MAXO> S;
-    sample_init(S, bv);
+    using T = Tile<MAXO>;
+    SampleState<MAXO> St;
+    sample_init(St, S);
     if (OUT) {
-        if (st_out) { st_out[0] = S.x; st_out[1] = S.y; st_out[2] = S.psi; st_out[3] = S.v; }
-        if (fr_out) { fr_out[0] = bv.s_t; fr_out[1] = bv.d_t; }
+        if (st_out) { st_out[0] = St.x; st_out[1] = St.y; st_out[2] = St.psi; st_out[3] = St.v; }
+        if (fr_out) { fr_out[0] = S.s_t; fr_out[1] = S.d_t; }
     }
-    for (int m = 0; 2 * m < bv.T; ++m) {
-        float2 z0 = make_float2(0.f, 0.f), z1 = z0;
-        if (!zero_noise) {
-            const uint4 w = noise_block(bv, k, m);
-            z0 = box_muller(w.x, w.y);
-            z1 = box_muller(w.z, w.w);
-        }
+    const int Tn = S.T;
+    for (int m = 0; 2 * m < Tn; ++m) {
+        float2 z0, z1;
+        noise_pair(S, key, k, m, z0, z1);
         const int t0 = 2 * m;
-        const float2 u0 = sample_control(p, bv.ubar[t0], z0);
+        const float2 u0 = sample_control(p, T::ubar()[t0], z0);
         if (OUT && u_out) { u_out[2 * t0] = u0.x; u_out[2 * t0 + 1] = u0.y; }
-        sample_step<MAXO, OUT>(S, bv, p, t0, u0, flag, st_out, fr_out);
-        if (t0 + 1 < bv.T) {
-            const float2 u1 = sample_control(p, bv.ubar[t0 + 1], z1);
+        sample_step<MAXO, OUT>(St, S, p, t0, u0, flag, st_out, fr_out);
+        if (t0 + 1 < Tn) {
+            const float2 u1 = sample_control(p, T::ubar()[t0 + 1], z1);
             if (OUT && u_out) { u_out[2 * t0 + 2] = u1.x; u_out[2 * t0 + 3] = u1.y; }
-            sample_step<MAXO, OUT>(S, bv, p, t0 + 1, u1, flag, st_out, fr_out);
+            sample_step<MAXO, OUT>(St, S, p, t0 + 1, u1, flag, st_out, fr_out);
         }
     }
-    return sample_finish(S, bv, p, game_on);
+    return sample_finish(St, S, p, game_on);
+}
+
+// Stage one best response's opponent positions into the pair layout:
+// src(tau, o) gives opponent o's position at step tau = 1..T.  Absent slots
+// hold a far-away point.  Cooperative over the CTA's threads.
+template <int MAXO, typename F>
+__device__ __forceinline__ void stage_opponents(int T, int n_opp, F src)
+{
+    constexpr int NP = BRTile<MAXO>::NP;
+    float4 *dst = Tile<MAXO>::opp();
+    for (int q = threadIdx.x; q < T * NP; q += blockDim.x) {
+        const int tau = q / NP, pr = q - tau * NP;
+        const int o0 = 2 * pr, o1 = 2 * pr + 1;
+        const float2 p0 = o0 < n_opp ? src(tau + 1, o0) : make_float2(kFarAway, kFarAway);
+        const float2 p1 = o1 < n_opp ? src(tau + 1, o1) : make_float2(kFarAway, kFarAway);
+        dst[q] = make_float4(p0.x, p1.x, p0.y, p1.y);
+    }
+}
+
+// Roll out the controls ctl()[0..T) from x0 cooperatively: one thread runs
+// the bicycle recurrence (the same arithmetic as the sample loop, so the
+// states are bit-identical to the evaluated candidate's) into st(); then
+// every thread projects one state onto the track by the distance search of
+// frenet_search from a guess (the chord from x0 in segment lengths), which
+// reaches the same nearest segment as the sample loop's walk; then one
+// thread unwraps the progress in step order.  Outputs (any may be NULL):
+// positions (T+1), states twice (T+1)x4, and the prediction summary
+// (progress gain s_H - s_t, tail-mean offset).  Uses the tile's window,
+// which must be staged.  All threads of the CTA must call it.
+template <int MAXO>
+__device__ void roll_cooperative(const sgtp_params &p, float4 x0, float s_t, int j0, int T, int n_tail,
+                                 float2 *pos_out, float *xi_a, float *xi_b, float2 *summ_out, int &flag)
+{
+    using Tl = Tile<MAXO>;
+    const BRScalars &S = Tl::sc();
+    float4 *st = Tl::st();
+    float2 *fr = Tl::fr();
+    if (threadIdx.x == 0) {
+        float x = x0.x, y = x0.y, psi = x0.z, v = x0.w;
+        st[0] = x0;
+        for (int tau = 0; tau < T; ++tau) {
+            const float2 u = Tl::ctl()[tau];
+            bicycle_step(p, x, y, psi, v, u.x, u.y);
+            st[tau + 1] = make_float4(x, y, psi, v);
+        }
+    }
+    __syncthreads();
+    const SegWindow w = Tl::win(S.w0, S.Wn);
+    const int r0 = wrap_index(j0 - S.w0, S.tv.N);
+    const float inv_len0 = 1.0f / __ldg(S.tv.B + j0).w;
+    for (int q = threadIdx.x; q < T; q += blockDim.x) {
+        const float4 v = st[q + 1];
+        const float ch = sqrtf((v.x - x0.x) * (v.x - x0.x) + (v.y - x0.y) * (v.y - x0.y));
+        const int guess = r0 + min((int)(ch * inv_len0), 4 * kWinTile);
+        const FrenetPt f = frenet_search(S.tv, w, guess, v.x, v.y);
+        flag |= f.flag;
+        fr[q] = make_float2(f.s, f.d);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && summ_out) {
+        float s = s_t, dsum = 0.f;
+        for (int tau = 0; tau < T; ++tau) {
+            const float2 f = fr[tau];
+            s = s + wrap_len(f.x - s, S.tv.L, S.invL);
+            if (tau + 1 > T - n_tail) dsum = dsum + f.y;
+        }
+        *summ_out = make_float2(s - s_t, dsum / (float)n_tail);
+    }
+    for (int q = threadIdx.x; q <= T; q += blockDim.x) {
+        const float4 v = st[q];
+        if (pos_out) pos_out[q] = make_float2(v.x, v.y);
+        if (xi_a) ((float4 *)xi_a)[q] = v;
+        if (xi_b) ((float4 *)xi_b)[q] = v;
+    }
 }
 
 }  // namespace sgtp

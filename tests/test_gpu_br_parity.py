@@ -64,7 +64,7 @@ def test_oval_single_response_all_candidates():
     assert_rel_close(g["states"], o["states"], STATE_RTOL, "states")
     assert_frenet_close(g["frenet"], o["frenet"], o["states"])
     assert_rel_close(g["controls"], o["controls"], STATE_RTOL, "controls")
-    nb = check_candidates(g, o, "oval")
+    nb = check_candidates(g, o, "oval", pos_scale=float(np.abs(sc.track.xr[:, :2]).max()))
     assert nb <= 0.01 * sc.K
     assert 0 < o["feasible"].sum() < sc.K        # the case exercises both branches
 
@@ -91,7 +91,7 @@ def test_fuzzed_small_problems(seed, n_opp, T, K):
                        agent=int(rng.integers(0, 9)), rnd=int(rng.integers(0, 6)), game_on=bool(seed % 2))
     assert_rel_close(g["states"], o["states"], STATE_RTOL, "states")
     assert_frenet_close(g["frenet"], o["frenet"], o["states"])
-    check_candidates(g, o, f"fuzz{seed}")
+    check_candidates(g, o, f"fuzz{seed}", pos_scale=float(np.abs(td.xr[:, :2]).max()))
 
 
 def test_zero_noise_makes_every_sample_the_nominal():
@@ -164,4 +164,4 @@ def test_full_size_ten_car_response_on_sampled_candidates():
     kl = np.unique(np.concatenate([np.arange(0, 64), np.random.default_rng(0).integers(0, K, 128), [K - 1]]))
     g, o, _ = run_both(sc.track, p, sc.X0[0], sc.U0[0], 1.0, opp, T, K, k_list=kl, seed=11, agent=0, rnd=3)
     assert_rel_close(g["states"], o["states"], STATE_RTOL, "states")
-    check_candidates(g, o, "ten-car sample")
+    check_candidates(g, o, "ten-car sample", pos_scale=float(np.abs(sc.track.xr[:, :2]).max()))
