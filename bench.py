@@ -38,8 +38,8 @@ WORKLOAD = "ten-car IBR plan: n_v=10, K=16384, T=60, dt=0.05, L=5 (+ extra ego),
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -218,7 +218,7 @@ def run_ours(args):
     ost = torch.empty(1, dtype=torch.int32).pin_memory()
     dX = torch.empty_like(X0); dV = torch.empty_like(vref)
     e2e_ev = []
-    for s in range(max(3, args.steps)):
+    for s in range(max(3, min(args.steps, 300))):
         flush.fill_(float(s))
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
