@@ -82,7 +82,7 @@ def lib():
         L.orc_rollout_costs.argtypes = [
             C.POINTER(OrcParams), dp, dp, dp, C.c_int, dp, dp, C.c_double, dp, C.c_int, C.c_int,
             C.POINTER(C.c_int32), C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int,
-            C.c_int, dp, C.POINTER(C.c_ubyte), dp, dp, dp, dp, dp, dp, dp, C.c_int]
+            C.c_int, dp, C.POINTER(C.c_ubyte), dp, dp, dp, dp, dp, dp, dp, dp, C.c_int, C.c_int]
         L.orc_eval_controls.argtypes = [
             C.POINTER(OrcParams), dp, dp, dp, C.c_int, dp, dp, C.c_int, C.c_double, dp, C.c_int, C.c_int,
             C.c_int, dp, C.POINTER(C.c_ubyte), dp, dp, dp]
@@ -90,6 +90,10 @@ def lib():
             C.POINTER(OrcParams), dp, dp, dp, C.c_int, dp, dp, C.c_double, dp, C.c_int, C.c_int, C.c_int,
             C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int, C.POINTER(C.c_int), dp, dp,
             C.POINTER(C.c_int), dp, C.c_int]
+        L.orc_best_response_mixed.argtypes = [
+            C.POINTER(OrcParams), dp, dp, dp, C.c_int, dp, dp, C.c_double, dp, C.c_int, C.c_int, C.c_int,
+            C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int, dp, C.c_int, C.POINTER(C.c_int),
+            dp, dp, C.POINTER(C.c_int), dp, dp, C.c_int]
         L.orc_select.argtypes = [dp, C.POINTER(C.c_ubyte), dp, C.c_int, C.POINTER(C.c_int)]
         L.orc_select.restype = C.c_int
         L.orc_ibr_plan.argtypes = [
@@ -199,8 +203,9 @@ def rollout(params, x0, u, T):
 
 def rollout_costs(params, track: Track, x0, u_nom, vref_scale, opp, T, K=None, k_list=None, seed=0, race=0,
                   agent=0, rnd=0, stream=0, game_on=True, zero_noise=False, want_states=False,
-                  want_frenet=False, want_controls=False, nthreads=None):
-    """Per-candidate outputs for k in k_list (or 0..K-1)."""
+                  want_frenet=False, want_controls=False, nthreads=None, prop=None, K_prop=0):
+    """Per-candidate outputs for k in k_list (or 0..K-1); prop / K_prop as
+    in :func:`best_response`."""
     opp = _d(opp).reshape(-1, T + 1, 4) if opp is not None and np.size(opp) else np.zeros((0, T + 1, 4))
     n_opp = opp.shape[0]
     if k_list is not None:
@@ -215,11 +220,13 @@ def rollout_costs(params, track: Track, x0, u_nom, vref_scale, opp, T, K=None, k
     states = np.zeros((n, T + 1, 4)) if want_states else None
     fr = np.zeros((n, T + 1, 2)) if want_frenet else None
     ctl = np.zeros((n, T, 2)) if want_controls else None
+    pr = _d(prop).reshape(T, 4) if prop is not None else None
     rc = lib().orc_rollout_costs(
         C.byref(make_params(params)), *track.args(), _p(_d(x0)), _p(_d(u_nom)), float(np.float32(vref_scale)),
         _p(opp) if n_opp else None, n_opp, T, klp, n, seed, race, agent, rnd, stream, int(bool(game_on)),
         int(bool(zero_noise)), _p(cost), feas.ctypes.data_as(C.POINTER(C.c_ubyte)), _p(viol), _p(states),
-        _p(fr), _p(ctl), _p(ctr), _p(cg), _p(mg), _nthreads(nthreads))
+        _p(fr), _p(ctl), _p(ctr), _p(cg), _p(mg), _p(pr), int(K_prop) if pr is not None else 0,
+        _nthreads(nthreads))
     assert rc == 0
     out = dict(cost=cost, feasible=feas, violation=viol, c_track=ctr, c_game=cg, margins=mg)
     if want_states:
@@ -259,19 +266,26 @@ def select(cost, feas, viol):
 
 
 def best_response(params, track: Track, x0, u_nom, vref_scale, opp, T, K, seed=0, race=0, agent=0, rnd=0,
-                  stream=0, game_on=True, want_costs=False, nthreads=None):
+                  stream=0, game_on=True, want_costs=False, nthreads=None, prop=None, K_prop=0):
+    """One best response.  ``prop`` (T x 4: mean a, mean delta, sigma a,
+    sigma delta) with ``K_prop`` draws the first K_prop samples from the
+    proposal (noise stream 1); the rest come from the plain sampler."""
     opp = _d(opp).reshape(-1, T + 1, 4) if opp is not None and np.size(opp) else np.zeros((0, T + 1, 4))
     ks = C.c_int(); anyf = C.c_int()
     u_star = np.zeros((T, 2)); xi = np.zeros((T + 1, 4))
     costs = np.zeros(K) if want_costs else None
-    rc = lib().orc_best_response(
+    viols = np.zeros(K) if want_costs else None
+    pr = _d(prop).reshape(T, 4) if prop is not None else None
+    rc = lib().orc_best_response_mixed(
         C.byref(make_params(params)), *track.args(), _p(_d(x0)), _p(_d(u_nom)), float(np.float32(vref_scale)),
         _p(opp) if opp.shape[0] else None, opp.shape[0], T, K, seed, race, agent, rnd, stream,
-        int(bool(game_on)), C.byref(ks), _p(u_star), _p(xi), C.byref(anyf), _p(costs), _nthreads(nthreads))
+        int(bool(game_on)), _p(pr), int(K_prop) if pr is not None else 0, C.byref(ks), _p(u_star), _p(xi),
+        C.byref(anyf), _p(costs), _p(viols), _nthreads(nthreads))
     assert rc == 0
     out = dict(k_star=ks.value, u_star=u_star, xi_star=xi, any_feasible=bool(anyf.value))
     if want_costs:
         out["costs"] = costs
+        out["viols"] = viols
     return out
 
 

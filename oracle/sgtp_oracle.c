@@ -259,6 +259,10 @@ typedef struct {
     uint64_t seed;
     uint32_t race, agent, round, stream;
     int game_on, zero_noise;
+    /* optional per-step proposal (T x 4: mean a, mean delta, sigma a,
+       sigma delta) for the first K_prop samples */
+    const double *prop;
+    int K_prop;
     /* per-problem data */
     double *xref;            /* (T+1) x 4 reference states, index 0 unused */
     orc_opp_summary *opp_sum;
@@ -302,17 +306,24 @@ static void problem_free(orc_problem *P) { free(P->xref); free(P->opp_sum); }
 
 /* Sampled controls of candidate k (Sec. II, Algorithm Formulation):
  * u = Pi_U(u_nom + eps), Pi_U clipping a to [a_min,a_max], delta to
- * [-delta_max, delta_max]. */
+ * [-delta_max, delta_max].  With a proposal (not in the paper), candidates
+ * k < K_prop draw u = Pi_U(mean_tau + sigma_tau z) instead, their noise
+ * taken from counter stream 1 so that it never repeats a plain sample's. */
 static void sample_controls(const orc_problem *P, uint32_t k, double *u)
 {
     const orc_params *p = P->p;
+    const int from_prop = P->prop != NULL && k < (uint32_t)P->K_prop;
     for (int tau = 0; tau < P->T; ++tau) {
         double za = 0.0, zd = 0.0;
-        if (!P->zero_noise) orc_std_normals(P->seed, P->race, P->agent, P->round, P->stream, k, tau, &za, &zd);
-        const double ua = P->u_nom[2 * tau] + p->sigma_a * za;
-        const double ud = P->u_nom[2 * tau + 1] + p->sigma_delta * zd;
-        u[2 * tau] = clampd(ua, p->a_min, p->a_max);
-        u[2 * tau + 1] = clampd(ud, -p->delta_max, p->delta_max);
+        if (!P->zero_noise)
+            orc_std_normals(P->seed, P->race, P->agent, P->round, from_prop ? 1u : P->stream, k, tau, &za, &zd);
+        double ma = P->u_nom[2 * tau], md = P->u_nom[2 * tau + 1], sa = p->sigma_a, sd = p->sigma_delta;
+        if (from_prop) {
+            const double *q = P->prop + 4 * tau;
+            ma = q[0]; md = q[1]; sa = q[2]; sd = q[3];
+        }
+        u[2 * tau] = clampd(ma + sa * za, p->a_min, p->a_max);
+        u[2 * tau + 1] = clampd(md + sd * zd, -p->delta_max, p->delta_max);
     }
 }
 
@@ -514,18 +525,22 @@ static void teardown_problem(orc_problem *P) { problem_free(P); track_free(&P->t
 
 /* Per-candidate costs, flags and violations (Alg. 1, sampling, cost and
  * feasibility steps).  k_list (n entries) selects which k to evaluate; when it
- * is NULL, k = 0..n-1.  Optional per-candidate outputs may be NULL. */
+ * is NULL, k = 0..n-1.  Optional per-candidate outputs may be NULL; prop
+ * (T x 4, may be NULL) and K_prop add the proposal of sample_controls. */
 int orc_rollout_costs(const orc_params *p, const double *xr, const double *wl, const double *wr, int N,
                       const double *x0, const double *u_nom, double vref_scale, const double *opp, int n_opp,
                       int T, const int32_t *k_list, int n, uint64_t seed, uint32_t race, uint32_t agent,
                       uint32_t round, uint32_t stream, int game_on, int zero_noise,
                       double *cost, unsigned char *feas, double *viol, double *states, double *frenet,
-                      double *controls, double *c_track, double *c_game, double *margins, int nthreads)
+                      double *controls, double *c_track, double *c_game, double *margins, const double *prop,
+                      int K_prop, int nthreads)
 {
     orc_problem P;
     if (setup_problem(&P, p, xr, wl, wr, N, x0, u_nom, vref_scale, opp, n_opp, T, seed, race, agent, round,
                       stream, game_on, zero_noise))
         return -1;
+    P.prop = prop;
+    P.K_prop = prop ? K_prop : 0;
     run_jobs(&P, k_list, n, nthreads, cost, feas, viol, states, frenet, controls, c_track, c_game, margins);
     teardown_problem(&P);
     return 0;
@@ -552,18 +567,24 @@ int orc_eval_controls(const orc_params *p, const double *xr, const double *wl, c
 }
 
 /* One best response (Alg. 1, one pass of the vehicle loop): all K samples,
- * selection, and the selected trajectory xi* ((T+1)x4) and controls U* (Tx2). */
-int orc_best_response(const orc_params *p, const double *xr, const double *wl, const double *wr, int N,
-                      const double *x0, const double *u_nom, double vref_scale, const double *opp, int n_opp,
-                      int T, int K, uint64_t seed, uint32_t race, uint32_t agent, uint32_t round, uint32_t stream,
-                      int game_on, int *k_star, double *u_star, double *xi_star, int *any_feasible,
-                      double *cost_out, int nthreads)
+ * selection, and the selected trajectory xi* ((T+1)x4) and controls U* (Tx2).
+ * prop (T x 4, may be NULL) and K_prop add the proposal of sample_controls;
+ * cost_out (K, may be NULL) receives every candidate's cost and viol_out (K,
+ * may be NULL) every violation. */
+int orc_best_response_mixed(const orc_params *p, const double *xr, const double *wl, const double *wr, int N,
+                            const double *x0, const double *u_nom, double vref_scale, const double *opp, int n_opp,
+                            int T, int K, uint64_t seed, uint32_t race, uint32_t agent, uint32_t round,
+                            uint32_t stream, int game_on, const double *prop, int K_prop, int *k_star,
+                            double *u_star, double *xi_star, int *any_feasible, double *cost_out,
+                            double *viol_out, int nthreads)
 {
     orc_problem P;
-    if (K < 1) return -1;
+    if (K < 1 || K_prop < 0 || K_prop > K) return -1;
     if (setup_problem(&P, p, xr, wl, wr, N, x0, u_nom, vref_scale, opp, n_opp, T, seed, race, agent, round,
                       stream, game_on, 0))
         return -1;
+    P.prop = prop;
+    P.K_prop = prop ? K_prop : 0;
     double *cost = (double *)malloc(sizeof(double) * (size_t)K);
     double *viol = (double *)malloc(sizeof(double) * (size_t)K);
     unsigned char *feas = (unsigned char *)malloc((size_t)K);
@@ -575,9 +596,21 @@ int orc_best_response(const orc_params *p, const double *xr, const double *wl, c
     eval_candidate(&P, u, xi_star, NULL);
     if (u_star) memcpy(u_star, u, sizeof(double) * (size_t)T * 2);
     if (cost_out) memcpy(cost_out, cost, sizeof(double) * (size_t)K);
+    if (viol_out) memcpy(viol_out, viol, sizeof(double) * (size_t)K);
     free(u); free(cost); free(viol); free(feas);
     teardown_problem(&P);
     return 0;
+}
+
+int orc_best_response(const orc_params *p, const double *xr, const double *wl, const double *wr, int N,
+                      const double *x0, const double *u_nom, double vref_scale, const double *opp, int n_opp,
+                      int T, int K, uint64_t seed, uint32_t race, uint32_t agent, uint32_t round, uint32_t stream,
+                      int game_on, int *k_star, double *u_star, double *xi_star, int *any_feasible,
+                      double *cost_out, int nthreads)
+{
+    return orc_best_response_mixed(p, xr, wl, wr, N, x0, u_nom, vref_scale, opp, n_opp, T, K, seed, race, agent,
+                                   round, stream, game_on, NULL, 0, k_star, u_star, xi_star, any_feasible, cost_out,
+                                   NULL, nthreads);
 }
 
 /* Zero-noise (nominal) rollout of a control sequence, controls clipped to

@@ -96,6 +96,26 @@ def lib():
                                                C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(sz)]
                 L.sgtp_batch_plan.argtypes = [vp, C.POINTER(Params), vp, vp, vp, u64, vp, vp, vp, vp, vp,
                                               C.POINTER(LaunchOpts), vp, sz, vp]
+            # learned proposal (include/sgtp_mlp.h)
+            L.sgtp_mlp_param_count.argtypes = [i32]
+            L.sgtp_mlp_param_count.restype = sz
+            L.sgtp_mlp_create.argtypes = [i32, u64, vp, C.POINTER(vp)]
+            L.sgtp_mlp_destroy.argtypes = [vp]
+            L.sgtp_mlp_destroy.restype = None
+            L.sgtp_mlp_reserve.argtypes = [vp, i32]
+            L.sgtp_mlp_forward.argtypes = [vp, vp, i32, vp, vp]
+            L.sgtp_mlp_proposal.argtypes = [vp, vp, i32, f32, f32, vp, vp]
+            L.sgtp_mlp_train_step.argtypes = [vp, vp, vp, i32, f32, vp, vp, i32, vp]
+            L.sgtp_mlp_get_params.argtypes = [vp, vp]
+            L.sgtp_mlp_set_params.argtypes = [vp, vp]
+            L.sgtp_mlp_info.argtypes = [vp, C.POINTER(i32), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                        C.POINTER(vp)]
+            L.sgtp_best_response_mixed.argtypes = [vp, i32, C.POINTER(Params), vp, vp, f32, vp, i32, i32, i32,
+                                                   u64, u32, u32, u32, i32, vp, i32, vp, vp, vp, vp, vp, vp, sz,
+                                                   vp]
+            L.sgtp_ibr_plan_learned.argtypes = [vp, i32, C.POINTER(Params), i32, vp, vp, vp, i32, i32, i32, i32,
+                                                u64, u32, vp, i32, vp, vp, vp, vp, vp, vp, vp,
+                                                C.POINTER(LaunchOpts), vp, sz, vp]
             _lib = L
     return _lib
 
@@ -106,13 +126,16 @@ def check(status: int, what: str = ""):
         raise RuntimeError(f"{what}: {STATUS.get(status, status)}: {msg}")
 
 
-# every symbol include/sgtp.h declares (checked by the CPU test-suite)
+# every symbol include/*.h declares (checked by the CPU test-suite)
 EXPORTS = [
     "sgtp_track_create", "sgtp_track_create_many", "sgtp_track_destroy", "sgtp_track_info",
     "sgtp_br_workspace_bytes", "sgtp_rollout_costs", "sgtp_best_response",
     "sgtp_batch_create", "sgtp_batch_destroy", "sgtp_batch_sizes", "sgtp_batch_plan",
     "sgtp_plan_workspace_bytes", "sgtp_ibr_plan",
     "sgtp_last_error", "sgtp_version", "sgtp_launch_count",
+    "sgtp_mlp_param_count", "sgtp_mlp_create", "sgtp_mlp_destroy", "sgtp_mlp_reserve", "sgtp_mlp_forward",
+    "sgtp_mlp_proposal", "sgtp_mlp_train_step", "sgtp_mlp_get_params", "sgtp_mlp_set_params", "sgtp_mlp_info",
+    "sgtp_best_response_mixed", "sgtp_ibr_plan_learned",
 ]
 
 

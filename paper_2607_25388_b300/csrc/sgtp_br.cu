@@ -353,6 +353,9 @@ struct BRArgs {
     float *cost, *viol, *states, *frenet, *controls;
     unsigned char *feas;
     long long timeout_ns;
+    // proposal (learned sampler): per step (mean a, mean delta, sigma a, sigma delta)
+    const float *prop;
+    int K_prop;
 };
 
 // Stage one best response's tile: scalars, track window (TMA), reference,
@@ -378,11 +381,15 @@ __device__ bool br_stage(const BRArgs &a)
         S.T = a.T; S.n_opp = a.n_opp; S.n_tail = a.n_tail;
         S.invL = 1.0f / a.tv.L;
         S.key = a.key; S.ctr_agent_round = a.agent_round; S.ctr_race = a.race; S.stream_bit = 0u;
+        S.K_prop = a.prop ? a.K_prop : 0;
         T::stage_window(a.tv, S.w0, S.Wn, false);
     }
     const float4 *gref = (const float4 *)(a.ws + a.off_ref);
     for (int i = threadIdx.x; i <= a.T; i += blockDim.x) T::ref()[i] = gref[i];
-    for (int i = threadIdx.x; i < a.T; i += blockDim.x) T::ubar()[i] = make_float2(a.u_nom[2 * i], a.u_nom[2 * i + 1]);
+    for (int i = threadIdx.x; i < a.T; i += blockDim.x) {
+        T::dist()[i] = make_float4(a.u_nom[2 * i], a.u_nom[2 * i + 1], a.p.sigma_a, a.p.sigma_delta);
+        if (a.prop) T::dist()[SGTP_MAX_T + i] = ((const float4 *)a.prop)[i];
+    }
     const float2 *gopp = (const float2 *)(a.ws + a.off_opp);
     const int n_opp = a.n_opp;
     stage_opponents<MAXO>(a.T, n_opp, [&](int tau, int o) { return gopp[(size_t)(tau - 1) * n_opp + o]; });
@@ -440,12 +447,23 @@ __global__ void __launch_bounds__(256, 3) br_rollout_kernel(BRArgs a)
     }
 }
 
+// Value of the ranked float of a selection key (inverse of float_order).
+__device__ __forceinline__ float key_value(unsigned long long key)
+{
+    const unsigned ord = (unsigned)((key >> 31) & 0xffffffffull);
+    const unsigned u = (ord & 0x80000000u) ? (ord & 0x7fffffffu) : ~ord;
+    return __uint_as_float(u);
+}
+
 // Selection result and re-roll of the winner: the selected sample's
 // controls one step per thread (same noise and clipping as its evaluation),
 // then the bicycle recurrence by one thread (same arithmetic), so the
-// returned trajectory is bit-identical to the evaluated one.
+// returned trajectory is bit-identical to the evaluated one.  cost_star
+// (optional) receives the ranked value of the winner: its cost when a
+// feasible sample exists, else its violation.
 template <int MAXO>
-__global__ void br_finalize_kernel(BRArgs a, int *k_star, float *u_star, float *xi_star, int *any_feasible)
+__global__ void br_finalize_kernel(BRArgs a, int *k_star, float *u_star, float *xi_star, int *any_feasible,
+                                   float *cost_star)
 {
     using Tl = Tile<MAXO>;
     __shared__ unsigned ks_sh;
@@ -455,13 +473,18 @@ __global__ void br_finalize_kernel(BRArgs a, int *k_star, float *u_star, float *
         ks_sh = (unsigned)(key & 0x7fffffffull);
         *k_star = (int)ks_sh;
         *any_feasible = (key >> 63) ? 0 : 1;
+        if (cost_star) *cost_star = key_value(key);
     }
     __syncthreads();
     const unsigned k = ks_sh;
+    const bool prop = a.prop && k < (unsigned)a.K_prop;
     for (int q = threadIdx.x; q < a.T; q += blockDim.x) {
-        const uint4 wv = philox4x32_10(make_uint4(k, (unsigned)(q >> 1), a.agent_round, a.race), a.key);
+        const unsigned sbit = prop ? 0x80000000u : 0u;
+        const uint4 wv = philox4x32_10(make_uint4(k, (unsigned)(q >> 1) | sbit, a.agent_round, a.race), a.key);
         const float2 z = (q & 1) ? box_muller(wv.z, wv.w) : box_muller(wv.x, wv.y);
-        const float2 u = sample_control(a.p, make_float2(a.u_nom[2 * q], a.u_nom[2 * q + 1]), z);
+        const float4 d = prop ? ((const float4 *)a.prop)[q]
+                              : make_float4(a.u_nom[2 * q], a.u_nom[2 * q + 1], a.p.sigma_a, a.p.sigma_delta);
+        const float2 u = sample_control_d(a.p, d, z);
         Tl::ctl()[q] = u;
         u_star[2 * q] = u.x;
         u_star[2 * q + 1] = u.y;
@@ -589,9 +612,43 @@ extern "C" sgtp_status sgtp_rollout_costs(const sgtp_track *trk, int32_t track_i
                                game_on, workspace, workspace_bytes, a, maxo);
     if (st) return st;
     SGTP_CHECK(cost && feasible && violation, "cost/feasible/violation is NULL");
+    a.prop = nullptr;
+    a.K_prop = 0;
     a.cost = cost; a.feas = feasible; a.viol = violation;
     a.states = states; a.frenet = frenet; a.controls = controls;
     return br_launch(a, maxo, false, x0, opp, vref_scale, (cudaStream_t)stream);
+}
+
+static sgtp_status best_response_impl(const sgtp_track *trk, int32_t track_id, const sgtp_params *p, const float *x0,
+                                      const float *u_nom, float vref_scale, const float *opp, int32_t n_opp, int32_t T,
+                                      int32_t K, uint64_t seed, uint32_t race, uint32_t agent, uint32_t round,
+                                      int32_t game_on, const float *prop, int32_t K_prop, int32_t *k_star,
+                                      float *u_star, float *xi_star, int32_t *any_feasible, float *cost_star,
+                                      void *workspace, size_t workspace_bytes, void *stream)
+{
+    BRArgs a;
+    int maxo;
+    sgtp_status st = br_common(trk, track_id, p, x0, u_nom, vref_scale, opp, n_opp, T, K, seed, race, agent, round,
+                               game_on, workspace, workspace_bytes, a, maxo);
+    if (st) return st;
+    SGTP_CHECK(k_star && u_star && xi_star && any_feasible, "NULL output");
+    SGTP_CHECK(prop == nullptr || (K_prop >= 0 && K_prop <= K), "K_prop out of range [0, K]");
+    a.prop = prop;
+    a.K_prop = prop ? K_prop : 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = br_launch(a, maxo, true, x0, opp, vref_scale, s);
+    if (st) return st;
+    switch (maxo) {
+        case 1: br_finalize_kernel<1><<<1, 128, br_smem<1>(a), s>>>(a, k_star, u_star, xi_star, any_feasible, cost_star); break;
+        case 3: br_finalize_kernel<3><<<1, 128, br_smem<3>(a), s>>>(a, k_star, u_star, xi_star, any_feasible, cost_star); break;
+        case 9: br_finalize_kernel<9><<<1, 128, br_smem<9>(a), s>>>(a, k_star, u_star, xi_star, any_feasible, cost_star); break;
+        default:
+            br_finalize_kernel<15><<<1, 128, br_smem<15>(a), s>>>(a, k_star, u_star, xi_star, any_feasible, cost_star);
+            break;
+    }
+    count_launch();
+    SGTP_CUDA(cudaGetLastError());
+    return SGTP_OK;
 }
 
 extern "C" sgtp_status sgtp_best_response(const sgtp_track *trk, int32_t track_id, const sgtp_params *p,
@@ -601,24 +658,23 @@ extern "C" sgtp_status sgtp_best_response(const sgtp_track *trk, int32_t track_i
                                           float *u_star, float *xi_star, int32_t *any_feasible, void *workspace,
                                           size_t workspace_bytes, void *stream)
 {
-    BRArgs a;
-    int maxo;
-    sgtp_status st = br_common(trk, track_id, p, x0, u_nom, vref_scale, opp, n_opp, T, K, seed, race, agent, round,
-                               game_on, workspace, workspace_bytes, a, maxo);
-    if (st) return st;
-    SGTP_CHECK(k_star && u_star && xi_star && any_feasible, "NULL output");
-    cudaStream_t s = (cudaStream_t)stream;
-    st = br_launch(a, maxo, true, x0, opp, vref_scale, s);
-    if (st) return st;
-    switch (maxo) {
-        case 1: br_finalize_kernel<1><<<1, 128, br_smem<1>(a), s>>>(a, k_star, u_star, xi_star, any_feasible); break;
-        case 3: br_finalize_kernel<3><<<1, 128, br_smem<3>(a), s>>>(a, k_star, u_star, xi_star, any_feasible); break;
-        case 9: br_finalize_kernel<9><<<1, 128, br_smem<9>(a), s>>>(a, k_star, u_star, xi_star, any_feasible); break;
-        default:
-            br_finalize_kernel<15><<<1, 128, br_smem<15>(a), s>>>(a, k_star, u_star, xi_star, any_feasible);
-            break;
-    }
-    count_launch();
-    SGTP_CUDA(cudaGetLastError());
-    return SGTP_OK;
+    return best_response_impl(trk, track_id, p, x0, u_nom, vref_scale, opp, n_opp, T, K, seed, race, agent, round,
+                              game_on, nullptr, 0, k_star, u_star, xi_star, any_feasible, nullptr, workspace,
+                              workspace_bytes, stream);
+}
+
+extern "C" sgtp_status sgtp_best_response_mixed(const sgtp_track *trk, int32_t track_id, const sgtp_params *p,
+                                                const float *x0, const float *u_nom, float vref_scale,
+                                                const float *opp, int32_t n_opp, int32_t T, int32_t K,
+                                                uint64_t seed, uint32_t race, uint32_t agent, uint32_t round,
+                                                int32_t game_on, const float *prop, int32_t K_prop, int32_t *k_star,
+                                                float *u_star, float *xi_star, int32_t *any_feasible,
+                                                float *cost_star, void *workspace, size_t workspace_bytes,
+                                                void *stream)
+{
+    SGTP_CHECK(prop != nullptr, "prop is NULL");
+    SGTP_CHECK(((uintptr_t)prop & 15u) == 0, "prop must be 16-byte aligned");
+    return best_response_impl(trk, track_id, p, x0, u_nom, vref_scale, opp, n_opp, T, K, seed, race, agent, round,
+                              game_on, prop, K_prop, k_star, u_star, xi_star, any_feasible, cost_star, workspace,
+                              workspace_bytes, stream);
 }

@@ -12,6 +12,9 @@
 #include "sgtp.h"
 #include "sgtp_device.cuh"
 
+struct sgtp_mlp;
+const float *sgtp_mlp_master(const sgtp_mlp *M);
+
 struct sgtp_track {
     int n_tracks = 0;
     long long total = 0;                   // elements over all (ring-extended) tracks

@@ -15,7 +15,10 @@
 #include <cmath>
 #include <cstring>
 
+#include <cuda_bf16.h>
+
 #include "sgtp_host.hpp"
+#include "sgtp_mlp.h"
 #include "sgtp_rollout.cuh"
 
 using namespace sgtp;
@@ -75,6 +78,13 @@ struct PlanArgs {
     long long timeout_ns;
     int debug_flags;
     long long *trace;          // optional phase stamps (CTA 0)
+    // learned proposal
+    const __nv_bfloat16 *mlp_wb;   // BF16 parameters (NULL: plain sampler only)
+    const float *mlp_wf;           // FP32 master parameters (biases)
+    int K_prop;                    // proposal samples per best response
+    float4 *prop;                  // per vehicle: maxT steps (mean a, mean delta, sigma a, sigma delta)
+    float *feat_out;               // optional: (L+2) x n_agents x 64 features of each best response
+    float4 *prop_out;              // optional: (L+2) x n_agents x maxT proposals of each best response
 };
 
 __device__ __forceinline__ void stamp(const PlanArgs &a, int i)
@@ -185,6 +195,178 @@ __device__ __forceinline__ void stage_vehicle_window(const PlanArgs &a, const Tr
     }
 }
 
+// ---------------------------------------------------------------- learned proposal
+// Features of vehicle i before a best response (layout in sgtp_mlp.h):
+// Frenet-relative ego state, raceline curvature ahead, and the nine nearest
+// opponents by |Delta s| (ties by index after rounding |Delta s| to mm).
+__device__ void compute_features(const PlanArgs &a, const RaceDev &R, int i, int bin, bool game_on, float *f)
+{
+    const TrackView tv = get_track(a, R.track_id);
+    const AgentDev A = load_agent(a.agents + R.agent_off + i);
+    const float invL = 1.0f / tv.L;
+    const float4 c0 = __ldg(tv.C + A.j0);
+    const float e = wrap_angle(A.x0.z - (c0.x + A.t0 * c0.y));
+    float sn, cs;
+    sincosf(e, &sn, &cs);
+    f[0] = A.d_t / 5.f;
+    f[1] = sn;
+    f[2] = cs;
+    f[3] = A.x0.w / 60.f;
+    const float ahead[4] = {0.f, 20.f, 40.f, 80.f};
+    for (int q = 0; q < 4; ++q) {
+        int j = A.j0;
+        float dist = ahead[q] + A.t0 * __ldg(tv.B + j).w;
+        for (int it = 0; it < tv.N; ++it) {
+            const float len = __ldg(tv.B + j).w;
+            if (dist < len) break;
+            dist -= len;
+            j = j + 1 == tv.N ? 0 : j + 1;
+        }
+        f[4 + q] = 100.f * __ldg(tv.C + j).y / __ldg(tv.B + j).w;
+    }
+    // opponents sorted by (|Delta s| in mm, index)
+    int order[SGTP_MAX_AGENTS];
+    float key[SGTP_MAX_AGENTS];
+    int n = 0;
+    for (int j = 0; j < R.n_v; ++j) {
+        if (j == i) continue;
+        const AgentDev B = load_agent(a.agents + R.agent_off + j);
+        const float k = floorf(fabsf(wrap_len(B.s_t - A.s_t, tv.L, invL)) * 1000.f);
+        int q = n++;
+        while (q > 0 && key[q - 1] > k) { key[q] = key[q - 1]; order[q] = order[q - 1]; --q; }
+        key[q] = k;
+        order[q] = j;
+    }
+    const float horizon_gain = A.x0.w * (float)R.T * a.p.dt;
+    for (int q = 0; q < 9; ++q) {
+        float *o = f + 8 + 6 * q;
+        if (q < n) {
+            const int j = order[q];
+            const AgentDev B = load_agent(a.agents + R.agent_off + j);
+            const float prog = __ldcg(a.summ[bin] + R.agent_off + j).x;
+            o[0] = 1.f;
+            o[1] = wrap_len(B.s_t - A.s_t, tv.L, invL) / 40.f;
+            o[2] = B.d_t / 5.f;
+            o[3] = (B.x0.w - A.x0.w) / 10.f;
+            o[4] = wrap_angle(B.x0.z - A.x0.z);
+            o[5] = (prog - horizon_gain) / 40.f;
+        } else {
+            for (int z = 0; z < 6; ++z) o[z] = 0.f;
+        }
+    }
+    f[62] = (float)n / 9.f;
+    f[63] = game_on ? 1.f : 0.f;
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float c[4], const unsigned a[4], const unsigned b[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// One layer of the network for one input row on the tensor cores: the row
+// sits in row 0 of a 16-row BF16 tile (rows 1..15 zero), weights W [N][K]
+// BF16 from global memory (L2 resident across proposals), FP32 accumulation;
+// output row 0 = act(acc + b) as BF16 into `next` (hidden layers) or FP32 into
+// `yout` (output layer).  Each warp owns up to four 8-column tiles at once so
+// the weight loads of several k-steps and tiles are in flight together.
+__device__ void mlp_layer(const __nv_bfloat16 *act, int lda, const __nv_bfloat16 *W, const float *bias, int N, int K,
+                          __nv_bfloat16 *next, float *yout)
+{
+    constexpr int NT = 4;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    for (int base = warp; base * 8 < N; base += nwarps * NT) {
+        float acc[NT][4];
+        const unsigned *wrow[NT];
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+            const int nrow = min((base + j * nwarps) * 8 + g, N - 1);
+            wrow[j] = (const unsigned *)(W + (size_t)nrow * K) + t;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
+        }
+        const unsigned *arow0 = (const unsigned *)(act + (size_t)g * lda) + t;
+        const unsigned *arow1 = (const unsigned *)(act + (size_t)(g + 8) * lda) + t;
+#pragma unroll 4
+        for (int k0 = 0; k0 < K; k0 += 16) {
+            const int kw = k0 >> 1;   // 32-bit words
+            unsigned af[4], bfr[NT][2];
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                bfr[j][0] = __ldg(wrow[j] + kw);
+                bfr[j][1] = __ldg(wrow[j] + kw + 4);
+            }
+            af[0] = arow0[kw];
+            af[1] = arow1[kw];
+            af[2] = arow0[kw + 4];
+            af[3] = arow1[kw + 4];
+#pragma unroll
+            for (int j = 0; j < NT; ++j) mma_bf16_16816(acc[j], af, bfr[j]);
+        }
+        if (g == 0) {
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                const int n0 = (base + j * nwarps) * 8;
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int c = n0 + 2 * t + q;
+                    if (c >= N) continue;
+                    const float v = acc[j][q] + bias[c];
+                    if (next) next[c] = __float2bfloat16(fmaxf(v, 0.f));
+                    else yout[c] = v;
+                }
+            }
+        }
+    }
+}
+
+// Proposal of vehicle i for its next best response: features, network, and
+// the per-step Gaussian (mean = sigma_plain * mu, sigma = sigma_plain *
+// exp(clamp(logsig, -5, 2))).  All threads of the CTA; smem scratch at buf.
+__device__ void proposal_for(const PlanArgs &a, const RaceDev &R, int i, int bin, bool game_on, int round,
+                             unsigned char *buf)
+{
+    float *x = (float *)buf;                                   // 64 features
+    float *y = x + 64;                                         // 4T outputs
+    __nv_bfloat16 *act0 = (__nv_bfloat16 *)(buf + 4 * (64 + 4 * SGTP_MAX_T));
+    const int lda = SGTP_MLP_HIDDEN + 8;
+    __nv_bfloat16 *act1 = act0 + 16 * lda;
+    const int ag = R.agent_off + i;
+    if (threadIdx.x == 0) compute_features(a, R, i, bin, game_on, x);
+    for (int q = threadIdx.x; q < 2 * 16 * lda; q += blockDim.x) act0[q] = __float2bfloat16(0.f);
+    __syncthreads();
+    if (a.feat_out && threadIdx.x < 64)
+        a.feat_out[((size_t)round * a.n_agents + ag) * 64 + threadIdx.x] = x[threadIdx.x];
+    if (!a.mlp_wb) return;
+    if (threadIdx.x < 64) act0[threadIdx.x] = __float2bfloat16(x[threadIdx.x]);
+    __syncthreads();
+    const int T = R.T, OUT = 4 * T, H = SGTP_MLP_HIDDEN;
+    long long off = 0;
+    const __nv_bfloat16 *cur = act0;
+    __nv_bfloat16 *nxt = act1;
+    for (int l = 0; l < 4; ++l) {
+        const int K = l == 0 ? SGTP_MLP_IN : H;
+        const int N = l == 3 ? OUT : H;
+        mlp_layer(cur, lda, a.mlp_wb + off, a.mlp_wf + off + (long long)N * K, N, K, l == 3 ? nullptr : nxt, y);
+        off += (long long)N * K + N;
+        __syncthreads();
+        const __nv_bfloat16 *t = cur; cur = nxt; nxt = (__nv_bfloat16 *)t;
+    }
+    float4 *dst = a.prop + (size_t)ag * a.maxT;
+    for (int q = threadIdx.x; q < T; q += blockDim.x) {
+        const float la = fminf(fmaxf(y[2 * T + q], -5.f), 2.f);
+        const float ld = fminf(fmaxf(y[3 * T + q], -5.f), 2.f);
+        const float4 d = make_float4(a.p.sigma_a * y[q], a.p.sigma_delta * y[T + q], a.p.sigma_a * expf(la),
+                                     a.p.sigma_delta * expf(ld));
+        dst[q] = d;
+        if (a.prop_out) a.prop_out[((size_t)round * a.n_agents + ag) * a.maxT + q] = d;
+    }
+}
+
 template <int MAXO>
 __global__ void __launch_bounds__(256, 3) plan_kernel(PlanArgs a)
 {
@@ -252,6 +434,18 @@ __global__ void __launch_bounds__(256, 3) plan_kernel(PlanArgs a)
     for (int round = 0; ok && round <= a.L + 1; ++round) {
         const bool extra = round == a.L + 1;
         const int bin = round & 1, bout = bin ^ 1;
+        if (a.mlp_wb || a.feat_out) {
+            // -------------------------------------------------- proposals (one CTA per vehicle)
+            for (int ag = blockIdx.x; ag < a.n_agents; ag += gridDim.x) {
+                const int ri = find_race(a, ag, [](const RaceDev &r) { return r.agent_off; });
+                const RaceDev R = get_race(a, ri);
+                const int i = ag - R.agent_off;
+                if (extra && i != R.ego) continue;
+                __syncthreads();
+                proposal_for(a, R, i, bin, round > 0, round, g_smem + Tl::L::kA);
+            }
+            if (!grid_barrier(a, skip)) break;
+        }
         const int n_items = extra ? a.items_ego : a.items_all;
         const int i0 = (int)((long long)n_items * blockIdx.x / gridDim.x);
         const int i1 = (int)((long long)n_items * (blockIdx.x + 1) / gridDim.x);
@@ -292,10 +486,14 @@ __global__ void __launch_bounds__(256, 3) plan_kernel(PlanArgs a)
                     S.ctr_agent_round = (unsigned)i | ((unsigned)round << 16);
                     S.ctr_race = R.race_tag;
                     S.stream_bit = 0u;
+                    S.K_prop = a.mlp_wb ? a.K_prop : 0;
                 }
                 const float *U = a.U_io + R.u_off + (size_t)i * T * 2;
-                for (int q = threadIdx.x; q < T; q += blockDim.x)
-                    Tl::ubar()[q] = make_float2(__ldcg(U + 2 * q), __ldcg(U + 2 * q + 1));
+                const float4 *P = a.prop + (size_t)ag * a.maxT;
+                for (int q = threadIdx.x; q < T; q += blockDim.x) {
+                    Tl::dist()[q] = make_float4(__ldcg(U + 2 * q), __ldcg(U + 2 * q + 1), a.p.sigma_a, a.p.sigma_delta);
+                    if (a.mlp_wb) Tl::dist()[SGTP_MAX_T + q] = __ldcg(P + q);
+                }
                 const float4 *gref = a.ref + (size_t)R.pos_off + (size_t)i * (T + 1);
                 for (int q = threadIdx.x; q <= T; q += blockDim.x) Tl::ref()[q] = __ldcg(gref + q);
                 const float2 *pin = a.pos[bin] + R.pos_off;
@@ -374,11 +572,15 @@ __global__ void __launch_bounds__(256, 3) plan_kernel(PlanArgs a)
             // same clipping as its evaluation): warm start U-bar <- U^(k*)
             const unsigned ks = ks_sh;
             const unsigned ar = (unsigned)i | ((unsigned)round << 16);
+            const bool from_prop = a.mlp_wb && ks < (unsigned)a.K_prop;
             for (int q = threadIdx.x; q < T; q += blockDim.x) {
-                const uint4 wv = philox4x32_10(make_uint4(ks, (unsigned)(q >> 1), ar, R.race_tag), a.key);
+                const unsigned sbit = from_prop ? 0x80000000u : 0u;
+                const uint4 wv = philox4x32_10(make_uint4(ks, (unsigned)(q >> 1) | sbit, ar, R.race_tag), a.key);
                 const float2 z = (q & 1) ? box_muller(wv.z, wv.w) : box_muller(wv.x, wv.y);
-                const float2 ub = make_float2(__ldcg(a.U_io + uo + 2 * q), __ldcg(a.U_io + uo + 2 * q + 1));
-                const float2 u = sample_control(a.p, ub, z);
+                const float4 d = from_prop ? __ldcg(a.prop + (size_t)ag * a.maxT + q)
+                                           : make_float4(__ldcg(a.U_io + uo + 2 * q), __ldcg(a.U_io + uo + 2 * q + 1),
+                                                         a.p.sigma_a, a.p.sigma_delta);
+                const float2 u = sample_control_d(a.p, d, z);
                 Tl::ctl()[q] = u;
                 a.U_io[uo + 2 * q] = u.x;
                 a.U_io[uo + 2 * q + 1] = u.y;
@@ -406,8 +608,8 @@ __global__ void __launch_bounds__(256, 3) plan_kernel(PlanArgs a)
 
 // ================================================================ host side
 struct Layout {
-    size_t bar, keys, agents, ref, pos0, pos1, summ0, summ1, total;
-    Layout(long long n_keys, long long n_agents, long long n_pos)
+    size_t bar, keys, agents, ref, pos0, pos1, summ0, summ1, prop, total;
+    Layout(long long n_keys, long long n_agents, long long n_pos, int maxT)
     {
         auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
         bar = 0;
@@ -418,7 +620,8 @@ struct Layout {
         pos1 = up(pos0 + sizeof(float2) * n_pos);
         summ0 = up(pos1 + sizeof(float2) * n_pos);
         summ1 = up(summ0 + sizeof(float2) * n_agents);
-        total = up(summ1 + sizeof(float2) * n_agents);
+        prop = up(summ1 + sizeof(float2) * n_agents);
+        total = up(prop + sizeof(float4) * n_agents * maxT);
     }
 };
 
@@ -490,6 +693,7 @@ void attach_workspace(PlanArgs &a, const Layout &lay, void *ws)
     a.pos[1] = (float2 *)(w + lay.pos1);
     a.summ[0] = (float2 *)(w + lay.summ0);
     a.summ[1] = (float2 *)(w + lay.summ1);
+    a.prop = (float4 *)(w + lay.prop);
 }
 
 }  // namespace
@@ -506,15 +710,15 @@ struct sgtp_batch {
 extern "C" size_t sgtp_plan_workspace_bytes(int32_t n_v, int32_t T, int32_t L)
 {
     if (n_v < 1 || T < 1 || L < 0) return 0;
-    return Layout((long long)(L + 1) * n_v + 1, n_v, (long long)n_v * (T + 1)).total;
+    return Layout((long long)(L + 1) * n_v + 1, n_v, (long long)n_v * (T + 1), T).total;
 }
 
-extern "C" sgtp_status sgtp_ibr_plan(const sgtp_track *trk, int32_t track_id, const sgtp_params *p, int32_t n_v,
-                                     const float *X0, float *U_io, const float *vref_scale, int32_t T, int32_t K,
-                                     int32_t L, int32_t ego, uint64_t seed, uint32_t race, float *xi_out,
-                                     int32_t *k_star_out, float *xi_hist, float *u_hist, int32_t *status_dev,
-                                     const sgtp_launch_opts *opts, void *workspace, size_t workspace_bytes,
-                                     void *stream)
+static sgtp_status ibr_plan_impl(const sgtp_track *trk, int32_t track_id, const sgtp_params *p, int32_t n_v,
+                                 const float *X0, float *U_io, const float *vref_scale, int32_t T, int32_t K, int32_t L,
+                                 int32_t ego, uint64_t seed, uint32_t race, float *xi_out, int32_t *k_star_out,
+                                 float *xi_hist, float *u_hist, int32_t *status_dev, const sgtp_launch_opts *opts,
+                                 const sgtp_mlp *mlp, int32_t K_prop, float *feat_out, float *prop_out,
+                                 void *workspace, size_t workspace_bytes, void *stream)
 {
     SGTP_CHECK(trk != nullptr, "track is NULL");
     SGTP_CHECK(track_id >= 0 && track_id < trk->n_tracks, "track_id out of range");
@@ -527,7 +731,7 @@ extern "C" sgtp_status sgtp_ibr_plan(const sgtp_track *trk, int32_t track_id, co
     SGTP_CHECK(ego >= 0 && ego < n_v, "ego out of range");
     SGTP_CHECK(race < (1u << 31), "race tag out of range");
     SGTP_CHECK(X0 && U_io && vref_scale && xi_out && k_star_out && status_dev, "NULL array");
-    const Layout lay((long long)(L + 1) * n_v + 1, n_v, (long long)n_v * (T + 1));
+    const Layout lay((long long)(L + 1) * n_v + 1, n_v, (long long)n_v * (T + 1), T);
     SGTP_CHECK(workspace && workspace_bytes >= lay.total, "workspace too small: need %zu bytes", lay.total);
     SGTP_CHECK(((uintptr_t)workspace & 255u) == 0, "workspace must be 256-byte aligned");
     PlanArgs a{};
@@ -545,8 +749,50 @@ extern "C" sgtp_status sgtp_ibr_plan(const sgtp_track *trk, int32_t track_id, co
     a.xi_total = (long long)n_v * (T + 1) * 4;
     a.u_total = (long long)n_v * T * 2;
     attach_workspace(a, lay, workspace);
+    if (mlp) {
+        int32_t mT = 0;
+        int64_t np = 0;
+        const void *wb = nullptr;
+        sgtp_status st2 = sgtp_mlp_info(mlp, &mT, &np, nullptr, &wb);
+        if (st2) return st2;
+        SGTP_CHECK(mT == T, "network horizon %d differs from T=%d", mT, T);
+        SGTP_CHECK(K_prop >= 0 && K_prop <= K, "K_prop out of range [0, K]");
+        a.mlp_wb = (const __nv_bfloat16 *)wb;
+        a.mlp_wf = sgtp_mlp_master(mlp);
+        a.K_prop = K_prop;
+    }
+    SGTP_CHECK(((uintptr_t)prop_out & 15u) == 0, "prop_out must be 16-byte aligned");
+    a.feat_out = feat_out;
+    a.prop_out = mlp ? (float4 *)prop_out : nullptr;
     return launch_plan(a, n_v - 1, opts, (cudaStream_t)stream);
 }
+
+extern "C" sgtp_status sgtp_ibr_plan(const sgtp_track *trk, int32_t track_id, const sgtp_params *p, int32_t n_v,
+                                     const float *X0, float *U_io, const float *vref_scale, int32_t T, int32_t K,
+                                     int32_t L, int32_t ego, uint64_t seed, uint32_t race, float *xi_out,
+                                     int32_t *k_star_out, float *xi_hist, float *u_hist, int32_t *status_dev,
+                                     const sgtp_launch_opts *opts, void *workspace, size_t workspace_bytes,
+                                     void *stream)
+{
+    return ibr_plan_impl(trk, track_id, p, n_v, X0, U_io, vref_scale, T, K, L, ego, seed, race, xi_out, k_star_out,
+                         xi_hist, u_hist, status_dev, opts, nullptr, 0, nullptr, nullptr, workspace, workspace_bytes,
+                         stream);
+}
+
+extern "C" sgtp_status sgtp_ibr_plan_learned(const sgtp_track *trk, int32_t track_id, const sgtp_params *p,
+                                             int32_t n_v, const float *X0, float *U_io, const float *vref_scale,
+                                             int32_t T, int32_t K, int32_t L, int32_t ego, uint64_t seed,
+                                             uint32_t race, const sgtp_mlp *mlp, int32_t K_prop, float *xi_out,
+                                             int32_t *k_star_out, float *xi_hist, float *u_hist, float *feat_out,
+                                             float *prop_out, int32_t *status_dev, const sgtp_launch_opts *opts,
+                                             void *workspace, size_t workspace_bytes, void *stream)
+{
+    return ibr_plan_impl(trk, track_id, p, n_v, X0, U_io, vref_scale, T, K, L, ego, seed, race, xi_out, k_star_out,
+                         xi_hist, u_hist, status_dev, opts, mlp, K_prop, feat_out, prop_out, workspace,
+                         workspace_bytes, stream);
+}
+
+
 
 extern "C" sgtp_status sgtp_batch_create(const sgtp_track *trk, const sgtp_race *races, int32_t n_races, int32_t K,
                                          int32_t L, sgtp_batch **out)
@@ -610,7 +856,7 @@ extern "C" sgtp_status sgtp_batch_sizes(const sgtp_batch *b, int64_t *agents, in
     if (u_elems) *u_elems = b->u_elems;
     if (xi_elems) *xi_elems = b->xi_elems;
     if (ks) *ks = b->ks;
-    if (workspace_bytes) *workspace_bytes = Layout(b->ks, b->agents, b->n_pos).total;
+    if (workspace_bytes) *workspace_bytes = Layout(b->ks, b->agents, b->n_pos, b->maxT).total;
     return SGTP_OK;
 }
 
@@ -624,7 +870,7 @@ extern "C" sgtp_status sgtp_batch_plan(const sgtp_batch *b, const sgtp_params *p
     sgtp_status st = check_params(p);
     if (st) return st;
     SGTP_CHECK(X0 && U_io && vref_scale && xi_out && k_star_out && status_dev, "NULL array");
-    const Layout lay(b->ks, b->agents, b->n_pos);
+    const Layout lay(b->ks, b->agents, b->n_pos, b->maxT);
     SGTP_CHECK(workspace && workspace_bytes >= lay.total, "workspace too small: need %zu bytes", lay.total);
     SGTP_CHECK(((uintptr_t)workspace & 255u) == 0, "workspace must be 256-byte aligned");
     // per-call tail counts depend on mu_tail: refresh the device race table

@@ -34,7 +34,8 @@ struct BRScalars {
     float invL;
     uint2 key;            // noise counter words
     unsigned ctr_agent_round, ctr_race, stream_bit;
-    int pad[3];
+    int K_prop;           // samples k < K_prop come from the proposal distribution
+    int pad[2];
 };
 
 // Shared-memory tile of one best response: fixed offsets for a given MAXO.
@@ -49,8 +50,8 @@ struct BRTile {
     static constexpr unsigned kS = kW + 16u * kWinTile;
     static constexpr unsigned kC = kS + 4u * kWinTile;   // heading/speed window (setup only)
     static constexpr unsigned kRef = kC + 16u * kWinTile;
-    static constexpr unsigned kUbar = kRef + 16u * (SGTP_MAX_T + 1);
-    static constexpr unsigned kOpp = kUbar + 8u * SGTP_MAX_T;
+    static constexpr unsigned kUbar = kRef + 16u * (SGTP_MAX_T + 1);   // float4 [2][T]: plain, proposal
+    static constexpr unsigned kOpp = kUbar + 32u * SGTP_MAX_T;
     static constexpr unsigned kOsum = kOpp + 16u * SGTP_MAX_T * NP;
     static constexpr unsigned kOdbar = kOsum + 16u * SGTP_MAX_AGENTS;
     static constexpr unsigned kCtl = kOdbar + 4u * SGTP_MAX_AGENTS;
@@ -72,7 +73,9 @@ struct Tile {
     static __device__ __forceinline__ float *S() { return (float *)(g_smem + L::kS); }
     static __device__ __forceinline__ float4 *C() { return (float4 *)(g_smem + L::kC); }
     static __device__ __forceinline__ float4 *ref() { return (float4 *)(g_smem + L::kRef); }
-    static __device__ __forceinline__ float2 *ubar() { return (float2 *)(g_smem + L::kUbar); }
+    // per-step sampling distribution (mean a, mean delta, sigma a, sigma delta):
+    // dist()[tau] for the plain sampler, dist()[SGTP_MAX_T + tau] for the proposal
+    static __device__ __forceinline__ float4 *dist() { return (float4 *)(g_smem + L::kUbar); }
     static __device__ __forceinline__ float4 *opp() { return (float4 *)(g_smem + L::kOpp); }
     static __device__ __forceinline__ float4 *osum() { return (float4 *)(g_smem + L::kOsum); }
     static __device__ __forceinline__ float *odbar() { return (float *)(g_smem + L::kOdbar); }
@@ -103,6 +106,19 @@ __device__ __forceinline__ float2 sample_control(const sgtp_params &p, float2 ub
     return make_float2(a, d);
 }
 
+// Clipped control from a per-step distribution d = (mean a, mean delta,
+// sigma a, sigma delta); for the plain sampler d = (U-bar, sigma_a,
+// sigma_delta) and the result equals sample_control's.
+__device__ __forceinline__ float2 sample_control_d(const sgtp_params &p, float4 d, float2 z)
+{
+    const float a = fminf(fmaxf(__fmaf_rn(d.z, z.x, d.x), p.a_min), p.a_max);
+    const float e = fminf(fmaxf(__fmaf_rn(d.w, z.y, d.y), -p.delta_max), p.delta_max);
+    return make_float2(a, e);
+}
+
+// Stream bit of the noise counter: 1 for proposal samples.
+__device__ __forceinline__ unsigned stream_bit_of(unsigned k, int K_prop) { return k < (unsigned)K_prop ? 0x80000000u : 0u; }
+
 // One forward-Euler step of the kinematic bicycle (rear-axle reference,
 // steering input, speed clamp), every right-hand side at the old state.
 __device__ __forceinline__ void bicycle_step(const sgtp_params &p, float &x, float &y, float &psi, float &v, float a,
@@ -123,9 +139,10 @@ __device__ __forceinline__ void bicycle_step(const sgtp_params &p, float &x, flo
 // Normal pairs of candidate k at steps 2m and 2m+1 (one Philox block).
 // The key comes from a kernel parameter, so that the round keys of the
 // Weyl schedule stay in the uniform datapath.
-__device__ __forceinline__ void noise_pair(const BRScalars &S, uint2 key, unsigned k, int m, float2 &z0, float2 &z1)
+__device__ __forceinline__ void noise_pair(const BRScalars &S, uint2 key, unsigned k, unsigned sbit, int m, float2 &z0,
+                                           float2 &z1)
 {
-    const uint4 w = philox4x32_10(make_uint4(k, (unsigned)m | S.stream_bit, S.ctr_agent_round, S.ctr_race), key);
+    const uint4 w = philox4x32_10(make_uint4(k, (unsigned)m | sbit, S.ctr_agent_round, S.ctr_race), key);
     z0 = box_muller(w.x, w.y);
     z1 = box_muller(w.z, w.w);
 }
@@ -271,15 +288,18 @@ __device__ __forceinline__ SampleResult run_candidate(const BRScalars &S, const 
         if (fr_out) { fr_out[0] = S.s_t; fr_out[1] = S.d_t; }
     }
     const int Tn = S.T;
+    const bool prop = k < (unsigned)S.K_prop;
+    const unsigned sbit = prop ? 0x80000000u : S.stream_bit;
+    const float4 *dist = T::dist() + (prop ? SGTP_MAX_T : 0);
     for (int m = 0; 2 * m < Tn; ++m) {
         float2 z0, z1;
-        noise_pair(S, key, k, m, z0, z1);
+        noise_pair(S, key, k, sbit, m, z0, z1);
         const int t0 = 2 * m;
-        const float2 u0 = sample_control(p, T::ubar()[t0], z0);
+        const float2 u0 = sample_control_d(p, dist[t0], z0);
         if (OUT && u_out) { u_out[2 * t0] = u0.x; u_out[2 * t0 + 1] = u0.y; }
         sample_step<MAXO, OUT>(St, S, p, t0, u0, flag, st_out, fr_out);
         if (t0 + 1 < Tn) {
-            const float2 u1 = sample_control(p, T::ubar()[t0 + 1], z1);
+            const float2 u1 = sample_control_d(p, dist[t0 + 1], z1);
             if (OUT && u_out) { u_out[2 * t0 + 2] = u1.x; u_out[2 * t0 + 3] = u1.y; }
             sample_step<MAXO, OUT>(St, S, p, t0 + 1, u1, flag, st_out, fr_out);
         }

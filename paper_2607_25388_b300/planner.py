@@ -14,8 +14,8 @@ import torch
 from . import _lib
 from ._lib import check, lib, make_params
 
-__all__ = ["Track", "rollout_costs", "best_response", "ibr_plan", "Batch", "launch_opts", "stream_ptr",
-           "br_workspace_bytes", "plan_workspace_bytes"]
+__all__ = ["Track", "rollout_costs", "best_response", "best_response_mixed", "ibr_plan", "Batch", "launch_opts",
+           "stream_ptr", "br_workspace_bytes", "plan_workspace_bytes"]
 
 
 def stream_ptr(stream=None) -> int:
@@ -168,10 +168,40 @@ def best_response(track: Track, params: dict, x0, u_nom, vref_scale, opp, T, K, 
     return out
 
 
+def best_response_mixed(track: Track, params: dict, x0, u_nom, vref_scale, opp, T, K, prop, K_prop, seed=0, race=0,
+                        agent=0, rnd=0, game_on=True, track_id=0, workspace=None, stream=None):
+    """One best response with the first K_prop samples drawn from the
+    per-step proposal prop (T, 4) (mean a, mean delta, sigma a, sigma
+    delta); also returns the selected cost."""
+    n_opp, opp_p, dev = _br_inputs(x0, u_nom, opp, T)
+    _dev(prop, "prop", shape=(T, 4))
+    out = dict(k_star=torch.empty(1, dtype=torch.int32, device=dev),
+               u_star=torch.empty((T, 2), dtype=torch.float32, device=dev),
+               xi_star=torch.empty((T + 1, 4), dtype=torch.float32, device=dev),
+               any_feasible=torch.empty(1, dtype=torch.int32, device=dev),
+               cost=torch.empty(1, dtype=torch.float32, device=dev))
+    nb = br_workspace_bytes(n_opp, T)
+    ws = workspace if workspace is not None else _ws(nb, dev)
+    P = make_params(params)
+    st = lib().sgtp_best_response_mixed(track.handle, track_id, C.byref(P), x0.data_ptr(), u_nom.data_ptr(),
+                                        float(vref_scale), opp_p, n_opp, T, K, int(seed), race, agent, rnd,
+                                        int(game_on), prop.data_ptr(), int(K_prop), out["k_star"].data_ptr(),
+                                        out["u_star"].data_ptr(), out["xi_star"].data_ptr(),
+                                        out["any_feasible"].data_ptr(), out["cost"].data_ptr(), ws.data_ptr(),
+                                        ws.numel(), stream_ptr(stream))
+    check(st, "sgtp_best_response_mixed")
+    return out
+
+
 def ibr_plan(track: Track, params: dict, X0, U_io, vref_scale, T, K, L, ego=0, seed=0, race=0, track_id=0,
-             want_hist=False, opts=None, workspace=None, out=None, stream=None):
+             want_hist=False, opts=None, workspace=None, out=None, stream=None, mlp=None, K_prop=0,
+             want_features=False, want_prop=False):
     """The SGTP planning call (Alg. 1) for one race; U_io is updated in place
-    (warm start).  Returns device tensors xi (n_v, T+1, 4), k_star, status."""
+    (warm start).  Returns device tensors xi (n_v, T+1, 4), k_star, status.
+    With ``mlp`` (a :class:`learned.Mlp`) K_prop samples of every best
+    response come from the network's proposal; ``want_features`` returns
+    the features of every best response ((L+2, n_v, 64)), ``want_prop`` the
+    proposals ((L+2, n_v, T, 4))."""
     n_v = X0.shape[0]
     dev = X0.device
     _dev(X0, "X0", shape=(n_v, 4))
@@ -188,6 +218,21 @@ def ibr_plan(track: Track, params: dict, X0, U_io, vref_scale, T, K, L, ego=0, s
     ws = workspace if workspace is not None else _ws(nb, dev)
     P = make_params(params)
     o = opts if opts is not None else launch_opts()
+    if mlp is not None or want_features or want_prop:
+        if want_features and "features" not in out:
+            out["features"] = torch.zeros((L + 2, n_v, 64), dtype=torch.float32, device=dev)
+        if want_prop and mlp is not None and "prop" not in out:
+            out["prop"] = torch.zeros((L + 2, n_v, T, 4), dtype=torch.float32, device=dev)
+        st = lib().sgtp_ibr_plan_learned(
+            track.handle, track_id, C.byref(P), n_v, X0.data_ptr(), U_io.data_ptr(), vref_scale.data_ptr(), T, K, L,
+            ego, int(seed), race, None if mlp is None else mlp.handle, int(K_prop), out["xi"].data_ptr(),
+            out["k_star"].data_ptr(), out["xi_hist"].data_ptr() if "xi_hist" in out else None,
+            out["u_hist"].data_ptr() if "u_hist" in out else None,
+            out["features"].data_ptr() if "features" in out else None,
+            out["prop"].data_ptr() if "prop" in out else None,
+            out["status"].data_ptr(), C.byref(o), ws.data_ptr(), ws.numel(), stream_ptr(stream))
+        check(st, "sgtp_ibr_plan_learned")
+        return out
     st = lib().sgtp_ibr_plan(track.handle, track_id, C.byref(P), n_v, X0.data_ptr(), U_io.data_ptr(),
                              vref_scale.data_ptr(), T, K, L, ego, int(seed), race, out["xi"].data_ptr(),
                              out["k_star"].data_ptr(),

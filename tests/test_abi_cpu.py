@@ -1,6 +1,7 @@
 """CPU-side checks of the C ABI: the library builds for sm_103a, loads,
-exports every symbol include/sgtp.h declares, and rejects invalid
-arguments before launching anything (no GPU needed for any of this)."""
+exports every symbol the headers under include/ declare, and rejects
+invalid arguments before launching anything (no GPU needed for any of
+this)."""
 import ctypes as C
 import os
 import re
@@ -15,18 +16,23 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_symbols():
-    txt = open(os.path.join(ROOT, "include", "sgtp.h")).read()
-    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(sgtp_[a-z_0-9]+)\s*\(", txt)))
+    syms = set()
+    inc = os.path.join(ROOT, "include")
+    for name in sorted(os.listdir(inc)):
+        if name.endswith(".h"):
+            txt = open(os.path.join(inc, name)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            syms |= set(re.findall(r"\b(sgtp_[a-z_0-9]+)\s*\(", txt))
+    return sorted(syms)
 
 
 def test_library_exports_every_declared_symbol():
     L = _lib.lib()
     syms = declared_symbols()
-    assert len(syms) >= 15
+    assert len(syms) >= 25
     missing = [s for s in syms if not hasattr(L, s)]
     assert not missing, missing
-    assert set(_lib.EXPORTS) <= set(syms)
+    assert set(_lib.EXPORTS) == set(syms)
     assert b"sm_103a" in L.sgtp_version()
 
 
@@ -67,6 +73,15 @@ def test_invalid_arguments_are_rejected_without_launch():
     xr = np.zeros((5, 4), np.float32); w = np.ones(5, np.float32)
     assert L.sgtp_track_create(xr.ctypes.data, w.ctypes.data, w.ctypes.data, 5, None, C.byref(h)) == 1
     assert b"zero-length" in L.sgtp_last_error()
+    # learned proposal: invalid sizes and NULL handles
+    assert L.sgtp_mlp_param_count(0) == 0 and L.sgtp_mlp_param_count(129) == 0
+    assert L.sgtp_mlp_param_count(60) == 64 * 256 + 256 + 2 * (256 * 256 + 256) + 240 * 256 + 240
+    m = C.c_void_p()
+    assert L.sgtp_mlp_create(0, 0, None, C.byref(m)) == 1 and not m.value
+    assert L.sgtp_mlp_reserve(None, 16) == 1
+    assert L.sgtp_mlp_forward(None, vp(16), 4, vp(16), None) == 1
+    assert L.sgtp_ibr_plan_learned(None, 0, C.byref(P), 2, vp(16), vp(16), vp(16), 10, 10, 1, 0, 0, 0, None, 0,
+                                   vp(16), vp(16), None, None, None, None, vp(16), None, vp(256), 1 << 20, None) == 1
     # bad params
     bad = _params(); bad.dt = -1.0
     assert L.sgtp_batch_plan(None, C.byref(bad), None, None, None, 0, None, None, None, None, None, None, None, 0,
