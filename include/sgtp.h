@@ -155,6 +155,38 @@ sgtp_status sgtp_best_response(const sgtp_track *trk, int32_t track_id, const sg
                                int32_t game_on, int32_t *k_star, float *u_star, float *xi_star,
                                int32_t *any_feasible, void *workspace, size_t workspace_bytes, void *stream);
 
+/* Scratch held by the library for sgtp_best_response_noalloc: the workspace
+ * of the largest best response the ABI accepts (SGTP_MAX_AGENTS-1 = 15
+ * opponents, T = SGTP_MAX_T = 128), 18 KiB. */
+#define SGTP_NOALLOC_SCRATCH_BYTES 18432
+
+/* sgtp_best_response without a caller-provided workspace (the paper has no
+ * counterpart: this is an engineering entry point).  The scratch is one
+ * statically allocated device array of SGTP_NOALLOC_SCRATCH_BYTES inside
+ * the library, so the call never asks any allocator for memory.  It serves
+ * callers that must not allocate while they run, for example a fixed-rate
+ * vehicle controller that re-plans every control period (an allocation can
+ * block for an unbounded time, and a failed one mid-race has no recovery),
+ * and plain C hosts that have no device allocator of their own.
+ *   - Arguments, outputs and results are those of sgtp_best_response.
+ *   - The first call on each device looks up the scratch's device address
+ *     (with that device current) and caches it; that lookup may initialise
+ *     the CUDA context and load the library's module, so make the first
+ *     call on a device before starting any stream capture.
+ *   - Nothing in the scratch has to start at zero: every call rewrites all
+ *     of it before reading it.
+ *   - All calls on one device share the one scratch: calls that overlap in
+ *     time (several streams, or several host threads without ordering)
+ *     race on it and give wrong results.  Issue them on one stream, or
+ *     order them with events.
+ *   - A problem whose workspace (sgtp_br_workspace_bytes) exceeds
+ *     SGTP_NOALLOC_SCRATCH_BYTES is rejected with SGTP_E_INVALID. */
+sgtp_status sgtp_best_response_noalloc(const sgtp_track *trk, int32_t track_id, const sgtp_params *p,
+                                       const float *x0, const float *u_nom, float vref_scale, const float *opp,
+                                       int32_t n_opp, int32_t T, int32_t K, uint64_t seed, uint32_t race,
+                                       uint32_t agent, uint32_t round, int32_t game_on, int32_t *k_star,
+                                       float *u_star, float *xi_star, int32_t *any_feasible, void *stream);
+
 /* ------------------------------------------------------------------ */
 /* The planning call (Alg. 1) and batches of independent races          */
 /* ------------------------------------------------------------------ */

@@ -81,6 +81,8 @@ def lib():
                                              u32, u32, i32, vp, vp, vp, vp, vp, vp, vp, sz, vp]
             L.sgtp_best_response.argtypes = [vp, i32, C.POINTER(Params), vp, vp, f32, vp, i32, i32, i32, u64, u32,
                                              u32, u32, i32, vp, vp, vp, vp, vp, sz, vp]
+            L.sgtp_best_response_noalloc.argtypes = [vp, i32, C.POINTER(Params), vp, vp, f32, vp, i32, i32, i32,
+                                                     u64, u32, u32, u32, i32, vp, vp, vp, vp, vp]
             L.sgtp_last_error.restype = C.c_char_p
             L.sgtp_version.restype = C.c_char_p
             L.sgtp_launch_count.restype = C.c_int64
@@ -129,7 +131,7 @@ def check(status: int, what: str = ""):
 # every symbol include/*.h declares (checked by the CPU test-suite)
 EXPORTS = [
     "sgtp_track_create", "sgtp_track_create_many", "sgtp_track_destroy", "sgtp_track_info",
-    "sgtp_br_workspace_bytes", "sgtp_rollout_costs", "sgtp_best_response",
+    "sgtp_br_workspace_bytes", "sgtp_rollout_costs", "sgtp_best_response", "sgtp_best_response_noalloc",
     "sgtp_batch_create", "sgtp_batch_destroy", "sgtp_batch_sizes", "sgtp_batch_plan",
     "sgtp_plan_workspace_bytes", "sgtp_ibr_plan",
     "sgtp_last_error", "sgtp_version", "sgtp_launch_count",

@@ -7,6 +7,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "sgtp_host.hpp"
 #include "sgtp_rollout.cuh"
@@ -677,4 +678,52 @@ extern "C" sgtp_status sgtp_best_response_mixed(const sgtp_track *trk, int32_t t
     return best_response_impl(trk, track_id, p, x0, u_nom, vref_scale, opp, n_opp, T, K, seed, race, agent, round,
                               game_on, prop, K_prop, k_star, u_star, xi_star, any_feasible, cost_star, workspace,
                               workspace_bytes, stream);
+}
+
+// ================================================================ no-allocation entry point
+// The scratch of sgtp_best_response_noalloc: a file-scope device array, so
+// the call itself never allocates.  Its callers are control loops that must
+// not wait on an allocator and hosts without a device allocator.
+static __device__ __align__(256) unsigned char g_br_scratch[SGTP_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void *g_scratch_addr[kMaxDevices] = {};
+}  // namespace
+
+extern "C" sgtp_status sgtp_best_response_noalloc(const sgtp_track *trk, int32_t track_id, const sgtp_params *p,
+                                                  const float *x0, const float *u_nom, float vref_scale,
+                                                  const float *opp, int32_t n_opp, int32_t T, int32_t K,
+                                                  uint64_t seed, uint32_t race, uint32_t agent, uint32_t round,
+                                                  int32_t game_on, int32_t *k_star, float *u_star, float *xi_star,
+                                                  int32_t *any_feasible, void *stream)
+{
+    SGTP_CHECK(n_opp >= 0 && n_opp <= SGTP_MAX_AGENTS - 1, "n_opp=%d out of range [0, %d]", n_opp,
+               SGTP_MAX_AGENTS - 1);
+    SGTP_CHECK(T >= 1 && T <= SGTP_MAX_T, "T=%d out of range [1, %d]", T, SGTP_MAX_T);
+    const size_t need = BRLayout(n_opp, T).total;
+    SGTP_CHECK(need <= (size_t)SGTP_NOALLOC_SCRATCH_BYTES,
+               "best response needs %zu bytes of scratch; the static scratch holds %d", need,
+               SGTP_NOALLOC_SCRATCH_BYTES);
+    int dev = -1;
+    SGTP_CUDA(cudaGetDevice(&dev));
+    SGTP_CHECK(dev >= 0 && dev < kMaxDevices, "device %d out of range [0, %d)", dev, kMaxDevices);
+    void *ws = nullptr;
+    {
+        // one address lookup per device, made with that device current
+        std::lock_guard<std::mutex> lock(g_scratch_mu);
+        if (!g_scratch_addr[dev]) {
+            void *addr = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&addr, g_br_scratch);
+            if (e != cudaSuccess)
+                return set_error(SGTP_E_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s",
+                                 cudaGetErrorString(e));
+            g_scratch_addr[dev] = addr;
+        }
+        ws = g_scratch_addr[dev];
+    }
+    return best_response_impl(trk, track_id, p, x0, u_nom, vref_scale, opp, n_opp, T, K, seed, race, agent, round,
+                              game_on, nullptr, 0, k_star, u_star, xi_star, any_feasible, nullptr, ws,
+                              SGTP_NOALLOC_SCRATCH_BYTES, stream);
 }

@@ -14,7 +14,7 @@ import torch
 from . import _lib
 from ._lib import check, lib, make_params
 
-__all__ = ["Track", "rollout_costs", "best_response", "best_response_mixed", "ibr_plan", "Batch", "launch_opts",
+__all__ = ["Track", "rollout_costs", "best_response", "best_response_noalloc", "best_response_mixed", "ibr_plan", "Batch", "launch_opts",
            "stream_ptr", "br_workspace_bytes", "plan_workspace_bytes"]
 
 
@@ -165,6 +165,27 @@ def best_response(track: Track, params: dict, x0, u_nom, vref_scale, opp, T, K, 
                                   out["k_star"].data_ptr(), out["u_star"].data_ptr(), out["xi_star"].data_ptr(),
                                   out["any_feasible"].data_ptr(), ws.data_ptr(), ws.numel(), stream_ptr(stream))
     check(st, "sgtp_best_response")
+    return out
+
+
+def best_response_noalloc(track: Track, params: dict, x0, u_nom, vref_scale, opp, T, K, seed=0, race=0, agent=0,
+                          rnd=0, game_on=True, track_id=0, out=None, stream=None):
+    """sgtp_best_response with the library's static scratch instead of a
+    workspace.  Calls that overlap in time share that scratch: issue them on
+    one stream."""
+    n_opp, opp_p, dev = _br_inputs(x0, u_nom, opp, T)
+    if out is None:
+        out = dict(k_star=torch.empty(1, dtype=torch.int32, device=dev),
+                   u_star=torch.empty((T, 2), dtype=torch.float32, device=dev),
+                   xi_star=torch.empty((T + 1, 4), dtype=torch.float32, device=dev),
+                   any_feasible=torch.empty(1, dtype=torch.int32, device=dev))
+    P = make_params(params)
+    st = lib().sgtp_best_response_noalloc(track.handle, track_id, C.byref(P), x0.data_ptr(), u_nom.data_ptr(),
+                                          float(vref_scale), opp_p, n_opp, T, K, int(seed), race, agent, rnd,
+                                          int(game_on), out["k_star"].data_ptr(), out["u_star"].data_ptr(),
+                                          out["xi_star"].data_ptr(), out["any_feasible"].data_ptr(),
+                                          stream_ptr(stream))
+    check(st, "sgtp_best_response_noalloc")
     return out
 
 
