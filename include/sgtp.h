@@ -200,9 +200,9 @@ typedef struct sgtp_launch_opts {
     int32_t window;               /* track segments staged in shared memory per CTA  */
     int64_t wait_timeout_ns;      /* limit of each device-side wait (default 1 s)    */
     int32_t debug_flags;          /* SGTP_DEBUG_*; 0 in production                   */
-    int64_t *trace_ns;            /* optional DEVICE buffer of 2*L+6 int64: %globaltimer
+    int64_t *trace_ns;            /* optional DEVICE buffer of 3*L+8 int64: %globaltimer
                                      stamps by CTA 0 at the start, after setup, and after
-                                     each round's sample phase and winner phase           */
+                                     each round's proposal, sample and winner phases      */
 } sgtp_launch_opts;
 
 /* Fault injection for tests: CTA 0 never arrives at the grid barrier, so

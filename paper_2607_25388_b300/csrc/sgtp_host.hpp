@@ -8,12 +8,16 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 
 #include "sgtp.h"
 #include "sgtp_device.cuh"
 
 struct sgtp_mlp;
 const float *sgtp_mlp_master(const sgtp_mlp *M);
+// BF16 weights in mma fragment order: per layer, per 8-row tile and 16-deep
+// k-step, 32 lanes x {b0, b1}; rows padded to a multiple of 8.
+const __nv_bfloat16 *sgtp_mlp_fragments(const sgtp_mlp *M);
 
 struct sgtp_track {
     int n_tracks = 0;

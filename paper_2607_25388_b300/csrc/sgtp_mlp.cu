@@ -212,6 +212,36 @@ __global__ void adam_kernel(float *w, const float *g, float *m, float *v, bf16 *
     }
 }
 
+// Inference copy of the weights in mma fragment order (bias-free): per layer,
+// per 8-row tile and 16-deep k-step, 32 lanes x {b0, b1} with lane (g, t)
+// holding W[n][k0+2t], W[n][k0+2t+1], W[n][k0+2t+8], W[n][k0+2t+9] for
+// n = 8 tile + g, k0 = 16 kstep; rows beyond N are zero.
+__host__ __device__ inline long long frag_off(int l, int out)
+{
+    long long o = 0;
+    for (int q = 0; q < l; ++q) o += (long long)((layer_out(q, out) + 7) & ~7) * layer_in(q);
+    return o;
+}
+
+__global__ void frag_kernel(const float *w, bf16 *frag, int out)
+{
+    const long long total = frag_off(4, out);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        int l = 0;
+        while (l < 3 && e >= frag_off(l + 1, out)) ++l;
+        const long long r = e - frag_off(l, out);
+        const int K = layer_in(l), N = layer_out(l, out), ksteps = K / 16;
+        const long long pair = r / 128;
+        const int lane = (int)((r % 128) / 4), slot = (int)(r % 4);
+        const int tile = (int)(pair / ksteps), ks = (int)(pair % ksteps);
+        const int n = tile * 8 + (lane >> 2);
+        const int k = ks * 16 + 2 * (lane & 3) + (slot & 1) + 8 * (slot >> 1);
+        const float v = n < N ? w[layer_off(l, out) + (long long)n * K + k] : 0.f;
+        frag[e] = __float2bfloat16(v);
+    }
+}
+
 __global__ void init_kernel(float *w, bf16 *wb, long long off, int out, int in, unsigned long long seed)
 {
     // Kaiming-uniform weights (bound sqrt(6/in)) from Philox, zero biases
@@ -251,12 +281,19 @@ struct sgtp_mlp {
     long long n_params = 0;
     float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
     bf16 *wb = nullptr;
+    bf16 *wfrag = nullptr;        // inference copy in mma fragment order
     long long step = 0;
     // training scratch (batch-sized, grown on demand at setup time)
     int cap = 0;
     bf16 *xb = nullptr, *h[3] = {nullptr, nullptr, nullptr}, *dzb = nullptr, *dhb = nullptr;
     float *outf = nullptr, *dout = nullptr, *dh = nullptr, *dzf = nullptr, *loss = nullptr;
 };
+
+static void refresh_fragments(sgtp_mlp *M, cudaStream_t s)
+{
+    frag_kernel<<<128, 256, 0, s>>>(M->w, M->wfrag, M->out);
+    count_launch();
+}
 
 extern "C" size_t sgtp_mlp_param_count(int32_t T)
 {
@@ -276,7 +313,8 @@ extern "C" sgtp_status sgtp_mlp_create(int32_t T, uint64_t seed, void *stream, s
     cudaError_t e;
     if ((e = cudaMalloc(&M->w, 4 * M->n_params)) || (e = cudaMalloc(&M->m, 4 * M->n_params)) ||
         (e = cudaMalloc(&M->v, 4 * M->n_params)) || (e = cudaMalloc(&M->g, 4 * M->n_params)) ||
-        (e = cudaMalloc(&M->wb, 2 * M->n_params)) || (e = cudaMalloc(&M->loss, 4))) {
+        (e = cudaMalloc(&M->wb, 2 * M->n_params)) || (e = cudaMalloc(&M->loss, 4)) ||
+        (e = cudaMalloc(&M->wfrag, 2 * frag_off(4, M->out)))) {
         sgtp_mlp_destroy(M);
         return set_error(SGTP_E_NOMEM, "MLP allocation failed: %s", cudaGetErrorString(e));
     }
@@ -287,6 +325,7 @@ extern "C" sgtp_status sgtp_mlp_create(int32_t T, uint64_t seed, void *stream, s
         init_kernel<<<64, 256, 0, s>>>(M->w, M->wb, layer_off(l, M->out), layer_out(l, M->out), layer_in(l), seed);
         count_launch();
     }
+    refresh_fragments(M, s);
     SGTP_CUDA(cudaGetLastError());
     SGTP_CUDA(cudaStreamSynchronize(s));
     *out = M;
@@ -308,6 +347,7 @@ extern "C" void sgtp_mlp_destroy(sgtp_mlp *M)
     if (!M) return;
     free_scratch(M);
     cudaFree(M->w); cudaFree(M->m); cudaFree(M->v); cudaFree(M->g); cudaFree(M->wb); cudaFree(M->loss);
+    cudaFree(M->wfrag);
     delete M;
 }
 
@@ -420,6 +460,7 @@ extern "C" sgtp_status sgtp_mlp_train_step(sgtp_mlp *M, const float *x, const fl
         const float c1 = 1.f - powf(b1, (float)M->step), c2 = 1.f - powf(b2, (float)M->step);
         adam_kernel<<<256, 256, 0, s>>>(M->w, M->g, M->m, M->v, M->wb, M->n_params, lr, b1, b2, 1e-8f, c1, c2);
         count_launch();
+        refresh_fragments(M, s);
     }
     SGTP_CUDA(cudaGetLastError());
     return SGTP_OK;
@@ -438,6 +479,7 @@ extern "C" sgtp_status sgtp_mlp_set_params(sgtp_mlp *M, const float *host_in)
     SGTP_CUDA(cudaMemcpy(M->w, host_in, 4 * M->n_params, cudaMemcpyHostToDevice));
     f32_to_bf16_kernel<<<256, 256>>>(M->w, M->wb, M->n_params);
     count_launch();
+    refresh_fragments(M, 0);
     SGTP_CUDA(cudaDeviceSynchronize());
     return SGTP_OK;
 }
@@ -453,5 +495,7 @@ extern "C" sgtp_status sgtp_mlp_info(const sgtp_mlp *M, int32_t *T, int64_t *n_p
     return SGTP_OK;
 }
 
-// FP32 master parameters on the device (library-internal accessor).
+// FP32 master parameters and the fragment-ordered BF16 weights on the
+// device (library-internal accessors).
 const float *sgtp_mlp_master(const sgtp_mlp *M) { return M ? M->w : nullptr; }
+const __nv_bfloat16 *sgtp_mlp_fragments(const sgtp_mlp *M) { return M ? M->wfrag : nullptr; }

@@ -199,63 +199,75 @@ __device__ __forceinline__ void stage_vehicle_window(const PlanArgs &a, const Tr
 // Features of vehicle i before a best response (layout in sgtp_mlp.h):
 // Frenet-relative ego state, raceline curvature ahead, and the nine nearest
 // opponents by |Delta s| (ties by index after rounding |Delta s| to mm).
-__device__ void compute_features(const PlanArgs &a, const RaceDev &R, int i, int bin, bool game_on, float *f)
+// All threads of the CTA; thread 0 writes the ego terms, threads 1..4 one
+// curvature each, threads 32.. one opponent each (rank by counting).
+// key_sh: SGTP_MAX_AGENTS floats of shared scratch.
+__device__ void compute_features(const PlanArgs &a, const RaceDev &R, int i, int bin, bool game_on, float *f,
+                                 float *key_sh)
 {
     const TrackView tv = get_track(a, R.track_id);
-    const AgentDev A = load_agent(a.agents + R.agent_off + i);
+    const int tid = threadIdx.x;
+    const int n_opp = R.n_v - 1;
     const float invL = 1.0f / tv.L;
-    const float4 c0 = __ldg(tv.C + A.j0);
-    const float e = wrap_angle(A.x0.z - (c0.x + A.t0 * c0.y));
-    float sn, cs;
-    sincosf(e, &sn, &cs);
-    f[0] = A.d_t / 5.f;
-    f[1] = sn;
-    f[2] = cs;
-    f[3] = A.x0.w / 60.f;
-    const float ahead[4] = {0.f, 20.f, 40.f, 80.f};
-    for (int q = 0; q < 4; ++q) {
-        int j = A.j0;
-        float dist = ahead[q] + A.t0 * __ldg(tv.B + j).w;
-        for (int it = 0; it < tv.N; ++it) {
-            const float len = __ldg(tv.B + j).w;
-            if (dist < len) break;
-            dist -= len;
-            j = j + 1 == tv.N ? 0 : j + 1;
+    const int jo = tid - 32;                 // opponent handled by this thread (vehicle index)
+    const bool opp_thread = jo >= 0 && jo < R.n_v && jo != i;
+    AgentDev A = load_agent(a.agents + R.agent_off + i);
+    AgentDev B;
+    float ds = 0.f;
+    if (opp_thread) {
+        B = load_agent(a.agents + R.agent_off + jo);
+        ds = wrap_len(B.s_t - A.s_t, tv.L, invL);
+        key_sh[jo] = floorf(fabsf(ds) * 1000.f);
+    }
+    if (tid == 0) {
+        const float4 c0 = __ldg(tv.C + A.j0);
+        const float e = wrap_angle(A.x0.z - (c0.x + A.t0 * c0.y));
+        float sn, cs;
+        sincosf(e, &sn, &cs);
+        f[0] = A.d_t / 5.f;
+        f[1] = sn;
+        f[2] = cs;
+        f[3] = A.x0.w / 60.f;
+        f[62] = (float)n_opp / 9.f;
+        f[63] = game_on ? 1.f : 0.f;
+    } else if (tid <= 4) {
+        // segment holding arc position s_i + ahead: jump by the local segment
+        // length, then step to the segment whose [S_j, S_j+1) holds it
+        const float ahead = tid == 1 ? 0.f : tid == 2 ? 20.f : tid == 3 ? 40.f : 80.f;
+        const float tgt = A.s_t + ahead;
+        const int N = tv.N;
+        auto sj = [&](int j) {
+            const int lap = j >= 0 ? j / N : -((-j + N - 1) / N);
+            return __ldg(tv.S + (j - lap * N)) + (float)lap * tv.L;
+        };
+        int j = A.j0 + (int)(ahead / __ldg(tv.B + A.j0).w);
+        for (int it = 0; it < 4 * N && sj(j) > tgt; ++it) --j;
+        for (int it = 0; it < 4 * N && sj(j + 1) <= tgt; ++it) ++j;
+        const int jm = ((j % N) + N) % N;
+        f[4 + tid - 1] = 100.f * __ldg(tv.C + jm).y / __ldg(tv.B + jm).w;
+    }
+    __syncthreads();
+    if (opp_thread) {
+        const float k = key_sh[jo];
+        int rank = 0;
+        for (int m = 0; m < R.n_v; ++m) {
+            if (m == i || m == jo) continue;
+            const float km = key_sh[m];
+            rank += (km < k || (km == k && m < jo)) ? 1 : 0;
         }
-        f[4 + q] = 100.f * __ldg(tv.C + j).y / __ldg(tv.B + j).w;
-    }
-    // opponents sorted by (|Delta s| in mm, index)
-    int order[SGTP_MAX_AGENTS];
-    float key[SGTP_MAX_AGENTS];
-    int n = 0;
-    for (int j = 0; j < R.n_v; ++j) {
-        if (j == i) continue;
-        const AgentDev B = load_agent(a.agents + R.agent_off + j);
-        const float k = floorf(fabsf(wrap_len(B.s_t - A.s_t, tv.L, invL)) * 1000.f);
-        int q = n++;
-        while (q > 0 && key[q - 1] > k) { key[q] = key[q - 1]; order[q] = order[q - 1]; --q; }
-        key[q] = k;
-        order[q] = j;
-    }
-    const float horizon_gain = A.x0.w * (float)R.T * a.p.dt;
-    for (int q = 0; q < 9; ++q) {
-        float *o = f + 8 + 6 * q;
-        if (q < n) {
-            const int j = order[q];
-            const AgentDev B = load_agent(a.agents + R.agent_off + j);
-            const float prog = __ldcg(a.summ[bin] + R.agent_off + j).x;
+        if (rank < 9) {
+            const float prog = __ldcg(a.summ[bin] + R.agent_off + jo).x;
+            const float horizon_gain = A.x0.w * (float)R.T * a.p.dt;
+            float *o = f + 8 + 6 * rank;
             o[0] = 1.f;
-            o[1] = wrap_len(B.s_t - A.s_t, tv.L, invL) / 40.f;
+            o[1] = ds / 40.f;
             o[2] = B.d_t / 5.f;
             o[3] = (B.x0.w - A.x0.w) / 10.f;
             o[4] = wrap_angle(B.x0.z - A.x0.z);
             o[5] = (prog - horizon_gain) / 40.f;
-        } else {
-            for (int z = 0; z < 6; ++z) o[z] = 0.f;
         }
     }
-    f[62] = (float)n / 9.f;
-    f[63] = game_on ? 1.f : 0.f;
+    if (tid >= 64 && tid < 64 + 9 * 6 && (tid - 64) / 6 >= n_opp) f[8 + (tid - 64)] = 0.f;
 }
 
 __device__ __forceinline__ void mma_bf16_16816(float c[4], const unsigned a[4], const unsigned b[2])
@@ -267,53 +279,55 @@ __device__ __forceinline__ void mma_bf16_16816(float c[4], const unsigned a[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// One layer of the network for one input row on the tensor cores: the row
-// sits in row 0 of a 16-row BF16 tile (rows 1..15 zero), weights W [N][K]
-// BF16 from global memory (L2 resident across proposals), FP32 accumulation;
-// output row 0 = act(acc + b) as BF16 into `next` (hidden layers) or FP32 into
-// `yout` (output layer).  Each warp owns up to four 8-column tiles at once so
-// the weight loads of several k-steps and tiles are in flight together.
-__device__ void mlp_layer(const __nv_bfloat16 *act, int lda, const __nv_bfloat16 *W, const float *bias, int N, int K,
+// One layer of the network for one input row on the tensor cores.  The row
+// (BF16, K values) sits in shared memory and is row 0 of the mma's A tile;
+// lanes of rows 1..15 feed zeros.  Weights come in the fragment order of
+// sgtp_mlp.cu (per 8-column tile and 16-deep k-step, 32 lanes x {b0, b1}),
+// so each warp's load is one coalesced 256-byte piece.  Each warp owns up
+// to four tiles at once so that their loads are in flight together.  Output
+// row 0 = act(acc + b): BF16 ReLU into `next`, or FP32 into `yout`.
+__device__ void mlp_layer(const __nv_bfloat16 *act, const uint2 *frag, const float *bias, int N, int K,
                           __nv_bfloat16 *next, float *yout)
 {
     constexpr int NT = 4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int g = lane >> 2, t = lane & 3;
-    for (int base = warp; base * 8 < N; base += nwarps * NT) {
+    const int ksteps = K >> 4, n_tiles = (N + 7) >> 3;
+    const unsigned *act32 = (const unsigned *)act;
+    for (int base = warp; base < n_tiles; base += nwarps * NT) {
         float acc[NT][4];
-        const unsigned *wrow[NT];
+        const uint2 *fp[NT];
 #pragma unroll
         for (int j = 0; j < NT; ++j) {
-            const int nrow = min((base + j * nwarps) * 8 + g, N - 1);
-            wrow[j] = (const unsigned *)(W + (size_t)nrow * K) + t;
+            const int tile = min(base + j * nwarps, n_tiles - 1);
+            fp[j] = frag + (size_t)tile * ksteps * 32 + lane;
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
         }
-        const unsigned *arow0 = (const unsigned *)(act + (size_t)g * lda) + t;
-        const unsigned *arow1 = (const unsigned *)(act + (size_t)(g + 8) * lda) + t;
 #pragma unroll 4
-        for (int k0 = 0; k0 < K; k0 += 16) {
-            const int kw = k0 >> 1;   // 32-bit words
-            unsigned af[4], bfr[NT][2];
+        for (int ks = 0; ks < ksteps; ++ks) {
+            uint2 bv[NT];
+#pragma unroll
+            for (int j = 0; j < NT; ++j) bv[j] = __ldg(fp[j] + ks * 32);
+            unsigned af[4] = {0u, 0u, 0u, 0u};
+            if (g == 0) {
+                af[0] = act32[ks * 8 + t];
+                af[2] = act32[ks * 8 + 4 + t];
+            }
 #pragma unroll
             for (int j = 0; j < NT; ++j) {
-                bfr[j][0] = __ldg(wrow[j] + kw);
-                bfr[j][1] = __ldg(wrow[j] + kw + 4);
+                const unsigned bf[2] = {bv[j].x, bv[j].y};
+                mma_bf16_16816(acc[j], af, bf);
             }
-            af[0] = arow0[kw];
-            af[1] = arow1[kw];
-            af[2] = arow0[kw + 4];
-            af[3] = arow1[kw + 4];
-#pragma unroll
-            for (int j = 0; j < NT; ++j) mma_bf16_16816(acc[j], af, bfr[j]);
         }
         if (g == 0) {
 #pragma unroll
             for (int j = 0; j < NT; ++j) {
-                const int n0 = (base + j * nwarps) * 8;
+                const int tile = base + j * nwarps;
+                if (tile >= n_tiles) continue;
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
-                    const int c = n0 + 2 * t + q;
+                    const int c = tile * 8 + 2 * t + q;
                     if (c >= N) continue;
                     const float v = acc[j][q] + bias[c];
                     if (next) next[c] = __float2bfloat16(fmaxf(v, 0.f));
@@ -326,18 +340,17 @@ __device__ void mlp_layer(const __nv_bfloat16 *act, int lda, const __nv_bfloat16
 
 // Proposal of vehicle i for its next best response: features, network, and
 // the per-step Gaussian (mean = sigma_plain * mu, sigma = sigma_plain *
-// exp(clamp(logsig, -5, 2))).  All threads of the CTA; smem scratch at buf.
+// exp(clamp(logsig, -5, 2))).  All threads of the CTA; shared scratch at buf.
 __device__ void proposal_for(const PlanArgs &a, const RaceDev &R, int i, int bin, bool game_on, int round,
                              unsigned char *buf)
 {
-    float *x = (float *)buf;                                   // 64 features
-    float *y = x + 64;                                         // 4T outputs
-    __nv_bfloat16 *act0 = (__nv_bfloat16 *)(buf + 4 * (64 + 4 * SGTP_MAX_T));
-    const int lda = SGTP_MLP_HIDDEN + 8;
-    __nv_bfloat16 *act1 = act0 + 16 * lda;
+    float *x = (float *)buf;                                    // 64 features
+    float *y = x + 64;                                          // 4T outputs
+    float *key_sh = y + 4 * SGTP_MAX_T;                         // SGTP_MAX_AGENTS keys
+    __nv_bfloat16 *act0 = (__nv_bfloat16 *)(key_sh + SGTP_MAX_AGENTS);
+    __nv_bfloat16 *act1 = act0 + SGTP_MLP_HIDDEN;
     const int ag = R.agent_off + i;
-    if (threadIdx.x == 0) compute_features(a, R, i, bin, game_on, x);
-    for (int q = threadIdx.x; q < 2 * 16 * lda; q += blockDim.x) act0[q] = __float2bfloat16(0.f);
+    compute_features(a, R, i, bin, game_on, x, key_sh);
     __syncthreads();
     if (a.feat_out && threadIdx.x < 64)
         a.feat_out[((size_t)round * a.n_agents + ag) * 64 + threadIdx.x] = x[threadIdx.x];
@@ -345,14 +358,16 @@ __device__ void proposal_for(const PlanArgs &a, const RaceDev &R, int i, int bin
     if (threadIdx.x < 64) act0[threadIdx.x] = __float2bfloat16(x[threadIdx.x]);
     __syncthreads();
     const int T = R.T, OUT = 4 * T, H = SGTP_MLP_HIDDEN;
-    long long off = 0;
+    long long off = 0, foff = 0;
     const __nv_bfloat16 *cur = act0;
     __nv_bfloat16 *nxt = act1;
     for (int l = 0; l < 4; ++l) {
         const int K = l == 0 ? SGTP_MLP_IN : H;
         const int N = l == 3 ? OUT : H;
-        mlp_layer(cur, lda, a.mlp_wb + off, a.mlp_wf + off + (long long)N * K, N, K, l == 3 ? nullptr : nxt, y);
+        mlp_layer(cur, (const uint2 *)(a.mlp_wb + foff), a.mlp_wf + off + (long long)N * K, N, K,
+                  l == 3 ? nullptr : nxt, y);
         off += (long long)N * K + N;
+        foff += (long long)((N + 7) & ~7) * K;
         __syncthreads();
         const __nv_bfloat16 *t = cur; cur = nxt; nxt = (__nv_bfloat16 *)t;
     }
@@ -446,6 +461,7 @@ __global__ void __launch_bounds__(256, 3) plan_kernel(PlanArgs a)
             }
             if (!grid_barrier(a, skip)) break;
         }
+        stamp(a, 2 + 3 * round);
         const int n_items = extra ? a.items_ego : a.items_all;
         const int i0 = (int)((long long)n_items * blockIdx.x / gridDim.x);
         const int i1 = (int)((long long)n_items * (blockIdx.x + 1) / gridDim.x);
@@ -538,7 +554,7 @@ __global__ void __launch_bounds__(256, 3) plan_kernel(PlanArgs a)
         __syncthreads();
         if (threadIdx.x == 0 && cur_slot) atomicMin(cur_slot, cta_key);
         if (!grid_barrier(a, skip)) break;
-        stamp(a, 2 + 2 * round);
+        stamp(a, 3 + 3 * round);
 
         // -------------------------------------------------------- winners (one CTA per vehicle)
         for (int ag = blockIdx.x; ag < a.n_agents; ag += gridDim.x) {
@@ -601,7 +617,7 @@ __global__ void __launch_bounds__(256, 3) plan_kernel(PlanArgs a)
                                    extra ? nullptr : a.summ[bout] + ag, flag);
         }
         if (round <= a.L) ok = grid_barrier(a, skip);
-        stamp(a, 3 + 2 * round);
+        stamp(a, 4 + 3 * round);
     }
     if (flag) atomicOr(a.status, SGTP_E_DEVICE << 8);
 }
@@ -757,7 +773,7 @@ static sgtp_status ibr_plan_impl(const sgtp_track *trk, int32_t track_id, const 
         if (st2) return st2;
         SGTP_CHECK(mT == T, "network horizon %d differs from T=%d", mT, T);
         SGTP_CHECK(K_prop >= 0 && K_prop <= K, "K_prop out of range [0, K]");
-        a.mlp_wb = (const __nv_bfloat16 *)wb;
+        a.mlp_wb = sgtp_mlp_fragments(mlp);
         a.mlp_wf = sgtp_mlp_master(mlp);
         a.K_prop = K_prop;
     }

@@ -242,11 +242,25 @@ def compare(mlp: Mlp, seeds, states_per_race: int, advance=10, K=16384, K_eq=409
 
 
 def summarize(res: dict) -> dict:
-    mp, me, ml = (float(res[k].mean()) for k in ("plain", "plain_eq", "learned"))
-    return dict(n_responses=int(res["plain"].size), mean_cost_plain=mp, mean_cost_plain_eq=me, mean_cost_learned=ml,
-                gap_learned=(ml - mp) / abs(mp), gap_plain_eq=(me - mp) / abs(mp),
-                feasible_plain=float(res["feas_plain"].mean()), feasible_plain_eq=float(res["feas_plain_eq"].mean()),
-                feasible_learned=float(res["feas_learned"].mean()), k_match=res["k_match"])
+    """Feasibility rates, and mean selected costs over the responses where
+    both compared samplers found a feasible sample (the cost of an
+    infeasible response is its violation, a different quantity).  The gap
+    is relative to |mean plain cost|, since costs can be negative."""
+    fp, fe, fl = (res[k].astype(bool) for k in ("feas_plain", "feas_plain_eq", "feas_learned"))
+    out = dict(n_responses=int(fp.size), feasible_plain=float(fp.mean()), feasible_plain_eq=float(fe.mean()),
+               feasible_learned=float(fl.mean()), k_match=res["k_match"])
+    for name, f2, c2 in (("learned", fl, res["learned"]), ("plain_eq", fe, res["plain_eq"])):
+        both = fp & f2
+        mp = float(res["plain"][both].mean()) if both.any() else float("nan")
+        m2 = float(c2[both].mean()) if both.any() else float("nan")
+        out[f"n_both_feasible_{name}"] = int(both.sum())
+        out[f"mean_cost_plain_vs_{name}"] = mp
+        out[f"mean_cost_{name}"] = m2
+        out[f"gap_{name}"] = (m2 - mp) / abs(mp) if both.any() else float("nan")
+        nb = ~fp & ~f2
+        out[f"mean_violation_plain_vs_{name}"] = float(res["plain"][nb].mean()) if nb.any() else float("nan")
+        out[f"mean_violation_{name}"] = float(c2[nb].mean()) if nb.any() else float("nan")
+    return out
 
 
 def plan_latency_ms(race: Race, params, K, L, mlp=None, K_prop=0, reps=50, warmup=5, seed=0):

@@ -47,7 +47,7 @@ def _ws(nbytes: int, device) -> torch.Tensor:
 def launch_opts(block=0, samples_per_thread=0, ctas_per_sm=0, window=0, wait_timeout_ns=0, debug_flags=0,
                 trace=None):
     """Launch shape of the persistent kernel (0 = library default).  trace:
-    optional int64 CUDA tensor of 2*L+6 entries for per-phase timestamps."""
+    optional int64 CUDA tensor of 3*L+8 entries for per-phase timestamps."""
     return _lib.LaunchOpts(int(block), int(samples_per_thread), int(ctas_per_sm), int(window), int(wait_timeout_ns),
                            int(debug_flags), None if trace is None else trace.data_ptr())
 
