@@ -139,6 +139,23 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Largest value of x over the ranks (the barrier-to-barrier time of the
+    slowest rank); identity for one rank.  Works with nccl or gloo."""
+    import torch
+    import torch.distributed as dist
+    if world <= 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step: float, steps: int, world: int, total_ms_max: float) -> float:
+    """Units processed by all ranks divided by the slowest rank's time."""
+    return units_per_rank_step * steps * world / (total_ms_max / 1e3)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -195,19 +212,19 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     times = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(times)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = t.item()
+    total_ms = max_over_ranks(sum(times), world, dev)
     status = out["status"].item()
 
     steps_per_plan = R.rollout_steps_plan(N_V, K, T, L)
-    value = steps_per_plan * args.steps * world / (total_ms / 1e3)
+    value = whole_job_rate(steps_per_plan, args.steps, world, total_ms)
     ms_per_step = total_ms / args.steps
     flops = R.flops_plan(N_V, K, T, L)
     achieved = flops / (statistics.mean(times) / 1e3) / 1e12
     peak = R.fp32_peak_tflops()
+    # DRAM bytes per launch from the committed ncu summary, while it still
+    # describes the kernel that ran (same source digest)
+    rec = R.recorded_traffic(os.path.join(ROOT, "profiles", "plan_kernel_ten_car_full.md"))
+    traffic = rec[0] if rec and rec[1] == R.kernel_source_digest() else None
 
     # ---- end to end through the public API with pinned host buffers
     hX = torch.as_tensor(sc.X0).pin_memory()
@@ -229,11 +246,7 @@ def run_ours(args):
         b.record(stream)
         e2e_ev.append((a, b))
     torch.cuda.synchronize()
-    e2e_ms = statistics.mean(a.elapsed_time(b) for a, b in e2e_ev)
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_ms = te.item()
+    e2e_ms = max_over_ranks(statistics.mean(a.elapsed_time(b) for a, b in e2e_ev), world, dev)
     h2d = hX.numel() * 4 + hU.numel() * 4 + hV.numel() * 4
     d2h = oxi.numel() * 4 + oks.numel() * 4 + ost.numel() * 4
 
@@ -252,7 +265,7 @@ def run_ours(args):
                     "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": traffic,
                          "kernel": "plan_kernel (persistent cooperative, 1 launch per plan)",
                          "peak_basis": "148 SMs x 128 FP32 lanes x 2 x 2032 MHz (unit counts, max clock)",
                          "flops_per_plan": flops},

@@ -53,6 +53,39 @@ def rollout_steps_plan(n_v: int, K: int, T: int, L: int) -> int:
     return ((L + 1) * n_v + 1) * K * T
 
 
+def kernel_source_digest() -> str:
+    """SHA-256 over the CUDA sources and ABI headers, so that a DRAM traffic
+    figure taken by ncu can be tied to the exact kernel it measured."""
+    import hashlib
+    import os
+    here = os.path.dirname(os.path.abspath(__file__))
+    files = []
+    for d, exts in ((os.path.join(here, "csrc"), (".cu", ".cuh", ".hpp")),
+                    (os.path.join(os.path.dirname(here), "include"), (".h",))):
+        files += sorted(os.path.join(d, f) for f in os.listdir(d) if f.endswith(exts))
+    h = hashlib.sha256()
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(profile_md: str):
+    """(bytes per launch, source digest) from a profile summary's
+    `traffic_bytes_per_launch:` and `source_sha256:` lines, or None."""
+    import os
+    import re
+    if not os.path.exists(profile_md):
+        return None
+    txt = open(profile_md).read()
+    t = re.search(r"^traffic_bytes_per_launch:\s*([0-9]+)", txt, re.M)
+    d = re.search(r"^source_sha256:\s*([0-9a-f]{64})", txt, re.M)
+    if not (t and d):
+        return None
+    return int(t.group(1)), d.group(1)
+
+
 def fp32_peak_tflops(sm_mhz: float = MAX_SM_MHZ, sms: int = SMS) -> float:
     """SMs x 128 FP32 lanes x 2 (FMA) x clock."""
     return sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
