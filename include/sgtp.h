@@ -192,12 +192,16 @@ sgtp_status sgtp_best_response_noalloc(const sgtp_track *trk, int32_t track_id, 
 /* ------------------------------------------------------------------ */
 
 /* Launch shape of the persistent kernel.  Any zero field takes the
- * library's choice.  Every shape gives bit-identical results. */
+ * library's choice.  Every shape gives bit-identical results (each sample is
+ * computed by one thread with the same code, and selection is an exact
+ * integer minimum).  Samples are processed in tiles of 256 consecutive k. */
 typedef struct sgtp_launch_opts {
-    int32_t block;                /* threads per CTA: 64, 128, 256 or 512            */
-    int32_t samples_per_thread;   /* 1, 2 or 4                                       */
-    int32_t ctas_per_sm;          /* resident CTAs per SM (<= occupancy limit)       */
-    int32_t window;               /* track segments staged in shared memory per CTA  */
+    int32_t block;                /* threads per CTA: 64, 128 or 256 (default 256)   */
+    int32_t samples_per_thread;   /* samples of a tile per thread: 0 or 256 / block  */
+    int32_t ctas_per_sm;          /* resident CTAs per SM (capped at the occupancy
+                                     limit; default the limit)                       */
+    int32_t window;               /* track segments staged in shared memory per CTA
+                                     (rounded to a multiple of 4, at most 512)       */
     int64_t wait_timeout_ns;      /* limit of each device-side wait (default 1 s)    */
     int32_t debug_flags;          /* SGTP_DEBUG_*; 0 in production                   */
     int64_t *trace_ns;            /* optional DEVICE buffer of 3*L+8 int64: %globaltimer
@@ -274,6 +278,38 @@ sgtp_status sgtp_ibr_plan(const sgtp_track *trk, int32_t track_id, const sgtp_pa
                           int32_t ego, uint64_t seed, uint32_t race, float *xi_out, int32_t *k_star_out,
                           float *xi_hist, float *u_hist, int32_t *status_dev, const sgtp_launch_opts *opts,
                           void *workspace, size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* CUDA graphs of planning calls                                        */
+/* ------------------------------------------------------------------ */
+typedef struct sgtp_graph sgtp_graph;   /* opaque, library owned */
+
+/* Capture one sgtp_ibr_plan call (same arguments; captured on an internal
+ * stream, nothing runs) into an instantiated CUDA graph.  Every pointer is
+ * fixed in the graph: between launches the caller rewrites X0, U_io and
+ * vref_scale in place (U_io also carries the warm start from the previous
+ * launch).  Returns SGTP_E_CUDA if the driver refuses the capture. */
+sgtp_status sgtp_graph_capture_plan(const sgtp_track *trk, int32_t track_id, const sgtp_params *p, int32_t n_v,
+                                    const float *X0, float *U_io, const float *vref_scale, int32_t T, int32_t K,
+                                    int32_t L, int32_t ego, uint64_t seed, uint32_t race, float *xi_out,
+                                    int32_t *k_star_out, float *xi_hist, float *u_hist, int32_t *status_dev,
+                                    const sgtp_launch_opts *opts, void *workspace, size_t workspace_bytes,
+                                    sgtp_graph **out);
+
+/* The same for one sgtp_batch_plan call. */
+sgtp_status sgtp_graph_capture_batch(const sgtp_batch *b, const sgtp_params *p, const float *X0, float *U_io,
+                                     const float *vref_scale, uint64_t seed, float *xi_out, int32_t *k_star_out,
+                                     float *xi_hist, float *u_hist, int32_t *status_dev,
+                                     const sgtp_launch_opts *opts, void *workspace, size_t workspace_bytes,
+                                     sgtp_graph **out);
+
+/* Change the noise seed of later launches (host-side update of the
+ * instantiated graph; does not touch any stream). */
+sgtp_status sgtp_graph_set_seed(sgtp_graph *g, uint64_t seed);
+
+/* Launch the graph on `stream` (results as from the captured call). */
+sgtp_status sgtp_graph_launch(sgtp_graph *g, void *stream);
+void sgtp_graph_destroy(sgtp_graph *g);
 
 /* ------------------------------------------------------------------ */
 /* Misc                                                                 */

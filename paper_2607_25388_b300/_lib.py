@@ -98,6 +98,15 @@ def lib():
                                                C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(sz)]
                 L.sgtp_batch_plan.argtypes = [vp, C.POINTER(Params), vp, vp, vp, u64, vp, vp, vp, vp, vp,
                                               C.POINTER(LaunchOpts), vp, sz, vp]
+            L.sgtp_graph_capture_plan.argtypes = [vp, i32, C.POINTER(Params), i32, vp, vp, vp, i32, i32, i32, i32,
+                                                  u64, u32, vp, vp, vp, vp, vp, C.POINTER(LaunchOpts), vp, sz,
+                                                  C.POINTER(vp)]
+            L.sgtp_graph_capture_batch.argtypes = [vp, C.POINTER(Params), vp, vp, vp, u64, vp, vp, vp, vp, vp,
+                                                   C.POINTER(LaunchOpts), vp, sz, C.POINTER(vp)]
+            L.sgtp_graph_set_seed.argtypes = [vp, u64]
+            L.sgtp_graph_launch.argtypes = [vp, vp]
+            L.sgtp_graph_destroy.argtypes = [vp]
+            L.sgtp_graph_destroy.restype = None
             # learned proposal (include/sgtp_mlp.h)
             L.sgtp_mlp_param_count.argtypes = [i32]
             L.sgtp_mlp_param_count.restype = sz
@@ -134,6 +143,8 @@ EXPORTS = [
     "sgtp_br_workspace_bytes", "sgtp_rollout_costs", "sgtp_best_response", "sgtp_best_response_noalloc",
     "sgtp_batch_create", "sgtp_batch_destroy", "sgtp_batch_sizes", "sgtp_batch_plan",
     "sgtp_plan_workspace_bytes", "sgtp_ibr_plan",
+    "sgtp_graph_capture_plan", "sgtp_graph_capture_batch", "sgtp_graph_set_seed", "sgtp_graph_launch",
+    "sgtp_graph_destroy",
     "sgtp_last_error", "sgtp_version", "sgtp_launch_count",
     "sgtp_mlp_param_count", "sgtp_mlp_create", "sgtp_mlp_destroy", "sgtp_mlp_reserve", "sgtp_mlp_forward",
     "sgtp_mlp_proposal", "sgtp_mlp_train_step", "sgtp_mlp_get_params", "sgtp_mlp_set_params", "sgtp_mlp_info",

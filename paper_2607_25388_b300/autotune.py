@@ -1,0 +1,139 @@
+"""Launch-shape autotuner of the persistent plan kernel.
+
+The search space is the launch shape of ``sgtp_launch_opts``: threads per
+CTA (64, 128, 256; a 256-sample tile is then processed 256/block samples per
+thread) and resident CTAs per SM.  Every shape computes each sample with the
+same code and selects by an exact integer minimum, so the plan must be
+bit-identical across shapes; the tuner checks that on every candidate and
+refuses a shape that differs.
+
+Results are cached in a JSON file keyed by (horizon bucket, opponent bucket,
+K, L, SM count, device name); ``lookup`` returns the cached shape for a
+planning problem, ``tune`` measures and stores it.  The cache path is
+``$SGTP_AUTOTUNE_CACHE`` or ``~/.cache/sgtp/autotune.json``.
+"""
+from __future__ import annotations
+
+import json
+import os
+import time
+
+import numpy as np
+import torch
+
+from . import scenario as S
+from .planner import Track, ibr_plan, launch_opts
+
+BLOCKS = (64, 128, 256)
+CTAS = (0, 1, 2, 3, 4, 6)        # 0 = the occupancy limit; larger values are capped by the library
+
+
+def cache_path() -> str:
+    return os.environ.get("SGTP_AUTOTUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "sgtp",
+                                                                "autotune.json"))
+
+
+def _t_bucket(T: int) -> int:
+    return (T + 15) // 16 * 16
+
+
+def _o_bucket(n_opp: int) -> int:
+    return 1 if n_opp <= 1 else 3 if n_opp <= 3 else 9 if n_opp <= 9 else 15
+
+
+def device_info(device=None):
+    """(SM count, device name) of the current (or given) CUDA device."""
+    d = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    props = torch.cuda.get_device_properties(d)
+    return props.multi_processor_count, props.name
+
+
+def key(n_v: int, T: int, K: int, L: int, info=None) -> str:
+    sms, name = info if info is not None else device_info()
+    return f"T{_t_bucket(T)}-o{_o_bucket(n_v - 1)}-K{K}-L{L}-sm{sms}-{name}"
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def lookup(n_v: int, T: int, K: int, L: int, path: str | None = None, info=None):
+    """Cached launch options for this problem shape, or None."""
+    ent = _load(path or cache_path()).get(key(n_v, T, K, L, info))
+    if not ent:
+        return None
+    return launch_opts(block=ent["block"], samples_per_thread=256 // ent["block"], ctas_per_sm=ent["ctas_per_sm"])
+
+
+def _time_plan(trk, params, sc, K, L, opts, reps, warmup):
+    X0, vs = torch.as_tensor(sc.X0).cuda(), torch.as_tensor(sc.vref_scale).cuda()
+    U0 = torch.as_tensor(sc.U0).cuda()
+    U = U0.clone()
+    out = None
+    for w in range(warmup):
+        U.copy_(U0)
+        out = ibr_plan(trk, params, X0, U, vs, sc.T, K, L, ego=sc.ego, seed=w, opts=opts, out=out)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    ts = []
+    for r in range(reps):
+        U.copy_(U0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        ibr_plan(trk, params, X0, U, vs, sc.T, K, L, ego=sc.ego, seed=r, opts=opts, out=out)
+        b.record(s)
+        ts.append((a, b))
+    torch.cuda.synchronize()
+    # result of a fixed seed, for the invariance check
+    U.copy_(U0)
+    res = ibr_plan(trk, params, X0, U, vs, sc.T, K, L, ego=sc.ego, seed=12345, opts=opts, want_hist=True)
+    torch.cuda.synchronize()
+    digest = tuple(v.cpu().numpy().tobytes() for k, v in sorted(res.items()) if k != "status") + (
+        U.cpu().numpy().tobytes(),)
+    return float(np.median([a.elapsed_time(b) for a, b in ts])), digest
+
+
+def store(n_v: int, T: int, K: int, L: int, entry: dict, path: str | None = None, info=None):
+    """Write one cache entry (atomic replace of the JSON file)."""
+    p = path or cache_path()
+    os.makedirs(os.path.dirname(p), exist_ok=True)
+    cache = _load(p)
+    cache[key(n_v, T, K, L, info)] = entry
+    tmp = p + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, p)
+
+
+def tune(n_v: int, T: int, K: int, L: int, params=None, reps=10, warmup=3, track_seed=777, path: str | None = None,
+         log=None):
+    """Time every candidate shape on a synthetic race of this shape (seeded
+    Fourier track, two-wide grid), check bit-identical plans, store and
+    return the fastest as a dict {block, ctas_per_sm, ms, default_ms}."""
+    params = params or S.params_fullscale()
+    sc = S.grid_race(S.fourier_track(track_seed), n_v, T, K, L, track_seed + 1)
+    trk = Track.from_data(sc.track)
+    base_ms, base_digest = _time_plan(trk, params, sc, K, L, launch_opts(), reps, warmup)
+    best = dict(block=256, ctas_per_sm=0, ms=base_ms)
+    seen = set()
+    for block in BLOCKS:
+        for ctas in CTAS:
+            opts = launch_opts(block=block, samples_per_thread=256 // block, ctas_per_sm=ctas)
+            ms, digest = _time_plan(trk, params, sc, K, L, opts, reps, warmup)
+            if digest != base_digest:
+                raise RuntimeError(f"launch shape block={block} ctas_per_sm={ctas} changed the plan")
+            if (block, round(ms, 4)) in seen:
+                continue
+            seen.add((block, round(ms, 4)))
+            if log:
+                log(f"block {block:3d} ctas/SM {ctas}: {ms:.4f} ms")
+            if ms < best["ms"]:
+                best = dict(block=block, ctas_per_sm=ctas, ms=ms)
+    best["default_ms"] = base_ms
+    best["tuned_at"] = time.strftime("%Y-%m-%dT%H:%M:%S")
+    store(n_v, T, K, L, best, path)
+    return best

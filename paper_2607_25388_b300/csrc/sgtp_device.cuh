@@ -158,7 +158,7 @@ __device__ __forceinline__ FrenetPt frenet_result(const SegData &g, int m, float
 // the point-to-segment distance over the segment index, which for points
 // within the track's reach is the global nearest segment of Sec. II's
 // projection.  A search longer than kMaxMoves stops and sets flag.
-static __device__ __noinline__ FrenetPt frenet_search(const TrackView tv, const SegWindow w, int r, float px, float py)
+static __device__ __forceinline__ FrenetPt frenet_search(const TrackView tv, const SegWindow w, int r, float px, float py)
 {
     int flag = 0;
     SegData g = seg_at(tv, w, r);

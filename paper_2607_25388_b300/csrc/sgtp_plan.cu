@@ -17,6 +17,8 @@
 
 #include <cuda_bf16.h>
 
+#include <atomic>
+
 #include "sgtp_host.hpp"
 #include "sgtp_mlp.h"
 #include "sgtp_rollout.cuh"
@@ -382,8 +384,12 @@ __device__ void proposal_for(const PlanArgs &a, const RaceDev &R, int i, int bin
     }
 }
 
-template <int MAXO>
-__global__ void __launch_bounds__(256, 3) plan_kernel(PlanArgs a)
+// MINB is the number of resident CTAs of 256 threads per SM the build is
+// sized for: 3 (80 registers, for plans with many sample tiles per round) or
+// 2 (128 registers, no spills, for plans with few tiles, where the latency
+// of one rollout dominates).  Both compute every sample with the same code.
+template <int MAXO, int MINB>
+__global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
 {
     using Tl = Tile<MAXO>;
     __shared__ unsigned long long cta_key;
@@ -540,12 +546,16 @@ __global__ void __launch_bounds__(256, 3) plan_kernel(PlanArgs a)
                 __syncthreads();
                 if (abort_sh) { ok = false; break; }
             }
-            const unsigned k = (unsigned)t * blockDim.x + threadIdx.x;
+            // a tile is 256 consecutive samples; 256 / blockDim.x per thread
             unsigned long long best = ~0ull;
-            if (k < (unsigned)a.K) {
-                const SampleResult r = run_candidate<MAXO, false>(S, a.p, a.key, k, round > 0, flag, nullptr, nullptr,
-                                                                  nullptr);
-                best = make_key(r.feasible, r.cost, r.viol, k);
+            for (unsigned j = threadIdx.x; j < 256u; j += blockDim.x) {
+                const unsigned k = (unsigned)t * 256u + j;
+                if (k < (unsigned)a.K) {
+                    const SampleResult r = run_candidate<MAXO, false>(S, a.p, a.key, k, round > 0, flag, nullptr,
+                                                                      nullptr, nullptr);
+                    const unsigned long long key = make_key(r.feasible, r.cost, r.viol, k);
+                    best = key < best ? key : best;
+                }
             }
             best = warp_min_u64(best);
             if (lane == 0) atomicMin(&cta_key, best);
@@ -643,33 +653,79 @@ struct Layout {
 
 int maxo_bucket(int n) { return n <= 1 ? 1 : n <= 3 ? 3 : n <= 9 ? 9 : 15; }
 
-template <int MAXO>
-sgtp_status launch_plan_t(PlanArgs &a, const sgtp_launch_opts *opts, cudaStream_t s)
+template <int MAXO, int MINB>
+sgtp_status configure_plan_t()
 {
-    const int block = 256;
-    const size_t smem = BRTile<MAXO>::kBytes;
-    static int configured = 0;
-    if (!configured) {
-        SGTP_CUDA(cudaFuncSetAttribute(plan_kernel<MAXO>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        configured = 1;
+    static std::atomic<int> configured{0};
+    if (!configured.load()) {
+        SGTP_CUDA(cudaFuncSetAttribute(plan_kernel<MAXO, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024));
+        configured.store(1);
     }
+    return SGTP_OK;
+}
+
+sgtp_status configure_plan_kernels()
+{
+    sgtp_status st;
+    if ((st = configure_plan_t<1, 2>()) || (st = configure_plan_t<3, 2>()) || (st = configure_plan_t<9, 2>()) ||
+        (st = configure_plan_t<15, 2>()) || (st = configure_plan_t<1, 3>()) || (st = configure_plan_t<3, 3>()) ||
+        (st = configure_plan_t<9, 3>()) || (st = configure_plan_t<15, 3>()))
+        return st;
+    return SGTP_OK;
+}
+
+template <int MAXO, int MINB>
+sgtp_status launch_plan_v(PlanArgs &a, int block, int ctas, cudaStream_t s)
+{
+    const size_t smem = BRTile<MAXO>::kBytes;
+    sgtp_status cst = configure_plan_t<MAXO, MINB>();
+    if (cst) return cst;
     int dev = 0, sms = 0, per_sm = 0;
     SGTP_CUDA(cudaGetDevice(&dev));
     SGTP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    SGTP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_kernel<MAXO>, block, smem));
+    SGTP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_kernel<MAXO, MINB>, block, smem));
     SGTP_CHECK(per_sm >= 1, "plan kernel does not fit on an SM (smem %zu)", smem);
-    if (opts && opts->ctas_per_sm > 0 && opts->ctas_per_sm < per_sm) per_sm = opts->ctas_per_sm;
+    if (ctas > 0 && ctas < per_sm) per_sm = ctas;
     const int grid = sms * per_sm;
     void *args[] = {&a};
     SGTP_CUDA(cudaMemsetAsync(a.bar, 0, 256, s));
     SGTP_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), s));
-    SGTP_CUDA(cudaLaunchCooperativeKernel((const void *)plan_kernel<MAXO>, grid, block, args, smem, s));
+    SGTP_CUDA(cudaLaunchCooperativeKernel((const void *)plan_kernel<MAXO, MINB>, grid, block, args, smem, s));
     count_launch();
     return SGTP_OK;
 }
 
+// Register budget: the 128-register build when at most two 256-thread CTAs
+// per SM are wanted -- explicitly, or by default when a Jacobi round has
+// fewer sample tiles than three CTAs per SM could take at once.
+template <int MAXO>
+sgtp_status launch_plan_t(PlanArgs &a, const sgtp_launch_opts *opts, cudaStream_t s)
+{
+    const int block = (opts && opts->block > 0) ? opts->block : 256;
+    int ctas = opts ? opts->ctas_per_sm : 0;
+    int dev = 0, sms = 0;
+    SGTP_CUDA(cudaGetDevice(&dev));
+    SGTP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int threads_per_sm = (ctas > 0 ? ctas : 0) * block;
+    bool wide;
+    if (ctas > 0) wide = threads_per_sm <= 512;
+    else wide = (long long)a.items_all < 3ll * sms;
+    if (wide && ctas == 0) ctas = 512 / block;
+    return wide ? launch_plan_v<MAXO, 2>(a, block, ctas, s) : launch_plan_v<MAXO, 3>(a, block, ctas, s);
+}
+
 sgtp_status launch_plan(PlanArgs &a, int max_opp, const sgtp_launch_opts *opts, cudaStream_t s)
 {
+    if (opts) {
+        SGTP_CHECK(opts->block == 0 || opts->block == 64 || opts->block == 128 || opts->block == 256,
+                   "block must be 64, 128 or 256 (got %d)", opts->block);
+        const int b = opts->block > 0 ? opts->block : 256;
+        SGTP_CHECK(opts->samples_per_thread == 0 || opts->samples_per_thread == 256 / b,
+                   "samples_per_thread must be 0 or 256/block = %d", 256 / b);
+        SGTP_CHECK(opts->ctas_per_sm >= 0 && opts->window >= 0 && opts->wait_timeout_ns >= 0,
+                   "negative launch option");
+    }
     switch (maxo_bucket(max_opp)) {
         case 1: return launch_plan_t<1>(a, opts, s);
         case 3: return launch_plan_t<3>(a, opts, s);
@@ -876,6 +932,22 @@ extern "C" sgtp_status sgtp_batch_sizes(const sgtp_batch *b, int64_t *agents, in
     return SGTP_OK;
 }
 
+// The tail counts of the race table depend on mu_tail: refresh the device
+// copy when the parameters change it (a blocking copy, never inside a graph
+// capture: the capture entry point refreshes before capturing).
+static sgtp_status refresh_tail_counts(const sgtp_batch *b, const sgtp_params *p)
+{
+    sgtp_batch *bm = const_cast<sgtp_batch *>(b);
+    bool changed = false;
+    for (auto &R : bm->races) {
+        const int nt = tail_count(p->mu_tail, R.T);
+        if (R.n_tail != nt) { R.n_tail = nt; changed = true; }
+    }
+    if (changed)
+        SGTP_CUDA(cudaMemcpy(bm->races_dev, bm->races.data(), sizeof(RaceDev) * b->n_races, cudaMemcpyHostToDevice));
+    return SGTP_OK;
+}
+
 extern "C" sgtp_status sgtp_batch_plan(const sgtp_batch *b, const sgtp_params *p, const float *X0, float *U_io,
                                        const float *vref_scale, uint64_t seed, float *xi_out, int32_t *k_star_out,
                                        float *xi_hist, float *u_hist, int32_t *status_dev,
@@ -889,17 +961,9 @@ extern "C" sgtp_status sgtp_batch_plan(const sgtp_batch *b, const sgtp_params *p
     const Layout lay(b->ks, b->agents, b->n_pos, b->maxT);
     SGTP_CHECK(workspace && workspace_bytes >= lay.total, "workspace too small: need %zu bytes", lay.total);
     SGTP_CHECK(((uintptr_t)workspace & 255u) == 0, "workspace must be 256-byte aligned");
-    // per-call tail counts depend on mu_tail: refresh the device race table
-    sgtp_batch *bm = const_cast<sgtp_batch *>(b);
-    bool changed = false;
-    for (auto &R : bm->races) {
-        const int nt = tail_count(p->mu_tail, R.T);
-        if (R.n_tail != nt) { R.n_tail = nt; changed = true; }
-    }
+    st = refresh_tail_counts(b, p);
+    if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    if (changed) {
-        SGTP_CUDA(cudaMemcpy(bm->races_dev, bm->races.data(), sizeof(RaceDev) * b->n_races, cudaMemcpyHostToDevice));
-    }
     PlanArgs a{};
     fill_common(a, b->trk, p, b->K, b->L, X0, U_io, vref_scale, seed, xi_out, k_star_out, xi_hist, u_hist,
                 status_dev, opts);
@@ -913,4 +977,123 @@ extern "C" sgtp_status sgtp_batch_plan(const sgtp_batch *b, const sgtp_params *p
     a.u_total = b->u_elems;
     attach_workspace(a, lay, workspace);
     return launch_plan(a, b->max_nv - 1, opts, s);
+}
+
+// ================================================================ CUDA graphs
+// A planning call captured once and replayed: the graph holds the two
+// memset nodes and the plan kernel node with every pointer fixed, so a
+// receding-horizon loop rewrites X0 / U_io in place and relaunches.
+struct sgtp_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t node = nullptr;   // the plan kernel node
+    cudaKernelNodeParams kp{};        // its launch configuration
+    PlanArgs args{};                  // its parameter block (seed updates)
+};
+
+extern "C" void sgtp_graph_destroy(sgtp_graph *G)
+{
+    if (!G) return;
+    if (G->exec) cudaGraphExecDestroy(G->exec);
+    if (G->graph) cudaGraphDestroy(G->graph);
+    delete G;
+}
+
+template <typename F>
+static sgtp_status capture_plan_graph(F body, sgtp_graph **out)
+{
+    SGTP_CHECK(out != nullptr, "out is NULL");
+    *out = nullptr;
+    sgtp_status st = configure_plan_kernels();
+    if (st) return st;
+    cudaStream_t cs = nullptr;
+    SGTP_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return set_error(SGTP_E_CUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+    }
+    st = body(cs);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (st || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        if (st) return st;
+        return set_error(SGTP_E_CUDA, "stream capture of the plan failed: %s", cudaGetErrorString(e));
+    }
+    sgtp_graph *G = new sgtp_graph();
+    G->graph = g;
+    size_t n = 0;
+    if ((e = cudaGraphGetNodes(g, nullptr, &n)) == cudaSuccess) {
+        std::vector<cudaGraphNode_t> nodes(n);
+        e = cudaGraphGetNodes(g, nodes.data(), &n);
+        for (size_t i = 0; e == cudaSuccess && i < n; ++i) {
+            cudaGraphNodeType t;
+            if ((e = cudaGraphNodeGetType(nodes[i], &t)) == cudaSuccess && t == cudaGraphNodeTypeKernel) G->node = nodes[i];
+        }
+    }
+    if (e == cudaSuccess && G->node) e = cudaGraphKernelNodeGetParams(G->node, &G->kp);
+    if (e == cudaSuccess && G->node) std::memcpy(&G->args, G->kp.kernelParams[0], sizeof(PlanArgs));
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&G->exec, g, 0);
+    if (e != cudaSuccess || !G->node) {
+        sgtp_graph_destroy(G);
+        return set_error(SGTP_E_CUDA, "graph setup failed: %s", e ? cudaGetErrorString(e) : "no kernel node");
+    }
+    *out = G;
+    return SGTP_OK;
+}
+
+extern "C" sgtp_status sgtp_graph_capture_plan(const sgtp_track *trk, int32_t track_id, const sgtp_params *p,
+                                               int32_t n_v, const float *X0, float *U_io, const float *vref_scale,
+                                               int32_t T, int32_t K, int32_t L, int32_t ego, uint64_t seed,
+                                               uint32_t race, float *xi_out, int32_t *k_star_out, float *xi_hist,
+                                               float *u_hist, int32_t *status_dev, const sgtp_launch_opts *opts,
+                                               void *workspace, size_t workspace_bytes, sgtp_graph **out)
+{
+    return capture_plan_graph(
+        [&](cudaStream_t cs) {
+            return sgtp_ibr_plan(trk, track_id, p, n_v, X0, U_io, vref_scale, T, K, L, ego, seed, race, xi_out,
+                                 k_star_out, xi_hist, u_hist, status_dev, opts, workspace, workspace_bytes, cs);
+        },
+        out);
+}
+
+extern "C" sgtp_status sgtp_graph_capture_batch(const sgtp_batch *b, const sgtp_params *p, const float *X0,
+                                                float *U_io, const float *vref_scale, uint64_t seed, float *xi_out,
+                                                int32_t *k_star_out, float *xi_hist, float *u_hist,
+                                                int32_t *status_dev, const sgtp_launch_opts *opts, void *workspace,
+                                                size_t workspace_bytes, sgtp_graph **out)
+{
+    SGTP_CHECK(b != nullptr, "batch is NULL");
+    sgtp_status st = check_params(p);
+    if (st) return st;
+    st = refresh_tail_counts(b, p);     // any table upload happens before the capture
+    if (st) return st;
+    return capture_plan_graph(
+        [&](cudaStream_t cs) {
+            return sgtp_batch_plan(b, p, X0, U_io, vref_scale, seed, xi_out, k_star_out, xi_hist, u_hist,
+                                   status_dev, opts, workspace, workspace_bytes, cs);
+        },
+        out);
+}
+
+extern "C" sgtp_status sgtp_graph_set_seed(sgtp_graph *G, uint64_t seed)
+{
+    SGTP_CHECK(G != nullptr, "graph is NULL");
+    G->args.key = make_uint2((unsigned)seed, (unsigned)(seed >> 32));
+    void *params[] = {&G->args};
+    cudaKernelNodeParams kp = G->kp;
+    kp.kernelParams = params;
+    kp.extra = nullptr;
+    SGTP_CUDA(cudaGraphExecKernelNodeSetParams(G->exec, G->node, &kp));
+    return SGTP_OK;
+}
+
+extern "C" sgtp_status sgtp_graph_launch(sgtp_graph *G, void *stream)
+{
+    SGTP_CHECK(G != nullptr, "graph is NULL");
+    SGTP_CUDA(cudaGraphLaunch(G->exec, (cudaStream_t)stream));
+    count_launch();
+    return SGTP_OK;
 }

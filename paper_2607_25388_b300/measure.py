@@ -1,0 +1,169 @@
+"""Timings of every workload configuration on the GPU (one JSON line each).
+
+    python -m paper_2607_25388_b300.measure [--reps 50]
+
+1. single best response on the oval (K = 1024, T = 40, one opponent);
+2. two-car plan (K = 8192, T = 50, L = 3);
+3. ten-car plan (K = 16384, T = 60, L = 5), direct launch and CUDA-graph replay;
+4. 256 independent races in one launch (n_v ~ U{2..10}, T ~ U{30..80}, K = 4096, L = 3), direct and graph;
+5. plan latency of the ten-car race: plain K = 16384, plain K = 4096, and the learned sampler with
+   2048 proposal + 2048 plain samples (network weights do not change the work).
+
+Times are CUDA-event medians over `reps` calls after warm-up, inputs resident on the device.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+import torch
+
+from . import roofline as R
+from . import scenario as S
+from .planner import Batch, PlanGraph, Track, best_response, ibr_plan, launch_opts
+
+
+def _median_ms(fn, reps, warmup=5):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    ev = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        fn()
+        b.record(s)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    return float(np.median([a.elapsed_time(b) for a, b in ev]))
+
+
+def _line(config, ms, steps, flops, **extra):
+    peak = R.fp32_peak_tflops()
+    d = dict(config=config, ms=ms, rollout_steps=steps, rollout_steps_per_s=steps / (ms / 1e3),
+             tflops=flops / (ms / 1e3) / 1e12, fp32_frac=flops / (ms / 1e3) / 1e12 / peak)
+    d.update(extra)
+    print(json.dumps(d), flush=True)
+    return d
+
+
+def config1(reps):
+    sc = S.single_br_oval()
+    p = S.params_fullscale()
+    trk = Track.from_data(sc.track)
+    x0, u = torch.as_tensor(sc.X0[0]).cuda(), torch.as_tensor(sc.U0[0]).cuda()
+    opp = torch.as_tensor(sc.opp).cuda()
+    ms = _median_ms(lambda: best_response(trk, p, x0, u, 1.0, opp, sc.T, sc.K, seed=1), reps)
+    return _line("1: oval single best response, K=1024, T=40, 1 opponent", ms, sc.K * sc.T,
+                 R.flops_best_response(sc.K, sc.T, 1), launches_per_call=3)
+
+
+def _plan_lines(name, sc, reps, graph=True):
+    p = S.params_fullscale()
+    trk = Track.from_data(sc.track)
+    n_v, T, K, L = sc.X0.shape[0], sc.T, sc.K, sc.L
+    X0, vs = torch.as_tensor(sc.X0).cuda(), torch.as_tensor(sc.vref_scale).cuda()
+    U0 = torch.as_tensor(sc.U0).cuda()
+    U = U0.clone()
+    out = {}
+    holder = {}
+
+    def direct():
+        U.copy_(U0)
+        holder["o"] = ibr_plan(trk, p, X0, U, vs, T, K, L, ego=sc.ego, seed=3, out=holder.get("o"))
+
+    steps, flops = R.rollout_steps_plan(n_v, K, T, L), R.flops_plan(n_v, K, T, L)
+    out["direct"] = _line(name + " (direct launch)", _median_ms(direct, reps), steps, flops)
+    if graph:
+        g = PlanGraph.capture_plan(trk, p, X0, U, vs, T, K, L, ego=sc.ego, seed=3)
+
+        def replay():
+            U.copy_(U0)
+            g.launch()
+
+        out["graph"] = _line(name + " (CUDA graph replay)", _median_ms(replay, reps), steps, flops)
+    return out
+
+
+def config2(reps):
+    return _plan_lines("2: two-car plan, K=8192, T=50, L=3", S.two_car_race(101), reps)
+
+
+def config3(reps):
+    return _plan_lines("3: ten-car plan, K=16384, T=60, L=5", S.ten_car_race(200), reps)
+
+
+def config4(reps):
+    p = S.params_fullscale()
+    races = S.batched_races()
+    K, L = races[0].K, races[0].L
+    trk = Track.from_many([sc.track for sc in races])
+    b = Batch(trk, [dict(track_id=r, n_v=sc.X0.shape[0], T=sc.T, ego=sc.ego, race_tag=r)
+                    for r, sc in enumerate(races)], K=K, L=L)
+    X0 = torch.as_tensor(np.concatenate([sc.X0 for sc in races])).cuda()
+    U0 = torch.as_tensor(np.concatenate([sc.U0.reshape(-1) for sc in races])).cuda()
+    vs = torch.as_tensor(np.concatenate([sc.vref_scale for sc in races])).cuda()
+    U = U0.clone()
+    ws = torch.empty(max(b.workspace_bytes, 256), dtype=torch.uint8, device="cuda")
+    holder = {}
+
+    def direct():
+        U.copy_(U0)
+        holder["o"] = b.plan(p, X0, U, vs, seed=5, workspace=ws, out=holder.get("o"))
+
+    steps = sum(R.rollout_steps_plan(sc.X0.shape[0], K, sc.T, L) for sc in races)
+    flops = sum(R.flops_plan(sc.X0.shape[0], K, sc.T, L) for sc in races)
+    n_agents = int(sum(sc.X0.shape[0] for sc in races))
+    res = {"direct": _line("4: 256 batched races, K=4096, L=3 (direct launch)", _median_ms(direct, reps), steps,
+                           flops, races=len(races), agents=n_agents)}
+    g = PlanGraph.capture_batch(b, p, X0, U, vs, seed=5)
+
+    def replay():
+        U.copy_(U0)
+        g.launch()
+
+    res["graph"] = _line("4: 256 batched races, K=4096, L=3 (CUDA graph replay)", _median_ms(replay, reps), steps,
+                         flops, races=len(races), agents=n_agents)
+    return res
+
+
+def config5(reps):
+    from .learned import Mlp
+    p = S.params_fullscale()
+    sc = S.ten_car_race(200)
+    trk = Track.from_data(sc.track)
+    n_v, T, L = 10, 60, 5
+    X0, vs = torch.as_tensor(sc.X0).cuda(), torch.as_tensor(sc.vref_scale).cuda()
+    U0 = torch.as_tensor(sc.U0).cuda()
+    U = U0.clone()
+    mlp = Mlp(T, seed=1)
+    res = {}
+    for name, K, net, kp in (("plain K=16384", 16384, None, 0), ("plain K=4096", 4096, None, 0),
+                             ("learned 2048+2048", 4096, mlp, 2048)):
+        holder = {}
+
+        def run():
+            U.copy_(U0)
+            holder["o"] = ibr_plan(trk, p, X0, U, vs, T, K, L, ego=0, seed=3, out=holder.get("o"), mlp=net, K_prop=kp)
+
+        res[name] = _line(f"5: ten-car plan latency, {name}", _median_ms(run, reps), R.rollout_steps_plan(n_v, K, T, L),
+                          R.flops_plan(n_v, K, T, L))
+    print(json.dumps(dict(config="5: latency ratio plain 16384 / learned 2048+2048",
+                          ratio=res["plain K=16384"]["ms"] / res["learned 2048+2048"]["ms"])), flush=True)
+    return res
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--reps", type=int, default=50)
+    ap.add_argument("--configs", type=str, default="1,2,3,4,5")
+    args = ap.parse_args(argv)
+    fns = {"1": config1, "2": config2, "3": config3, "4": config4, "5": config5}
+    for c in args.configs.split(","):
+        fns[c.strip()](args.reps)
+
+
+if __name__ == "__main__":
+    main()

@@ -14,7 +14,7 @@ import torch
 from . import _lib
 from ._lib import check, lib, make_params
 
-__all__ = ["Track", "rollout_costs", "best_response", "best_response_noalloc", "best_response_mixed", "ibr_plan", "Batch", "launch_opts",
+__all__ = ["Track", "rollout_costs", "best_response", "best_response_noalloc", "best_response_mixed", "PlanGraph", "ibr_plan", "Batch", "launch_opts",
            "stream_ptr", "br_workspace_bytes", "plan_workspace_bytes"]
 
 
@@ -238,6 +238,11 @@ def ibr_plan(track: Track, params: dict, X0, U_io, vref_scale, T, K, L, ego=0, s
     nb = plan_workspace_bytes(n_v, T, L)
     ws = workspace if workspace is not None else _ws(nb, dev)
     P = make_params(params)
+    if isinstance(opts, str):
+        if opts != "auto":
+            raise ValueError("opts must be launch options, None or 'auto'")
+        from . import autotune
+        opts = autotune.lookup(n_v, T, K, L)
     o = opts if opts is not None else launch_opts()
     if mlp is not None or want_features or want_prop:
         if want_features and "features" not in out:
@@ -264,6 +269,80 @@ def ibr_plan(track: Track, params: dict, X0, U_io, vref_scale, T, K, L, ego=0, s
     return out
 
 
+class PlanGraph:
+    """One planning call captured into a CUDA graph (``sgtp_graph_*``).
+
+    The graph replays with the tensors given here: rewrite X0, U_io and
+    vref_scale in place between launches (U_io keeps its warm start).
+    ``out`` holds the output tensors (xi, k_star, status, and xi_hist /
+    u_hist with want_hist)."""
+
+    def __init__(self, handle, keep, out):
+        self._h = handle
+        self._keep = keep
+        self.out = out
+
+    @classmethod
+    def capture_plan(cls, track: Track, params: dict, X0, U_io, vref_scale, T, K, L, ego=0, seed=0, race=0,
+                     track_id=0, want_hist=False, opts=None):
+        n_v = X0.shape[0]
+        dev = X0.device
+        _dev(X0, "X0", shape=(n_v, 4))
+        _dev(U_io, "U_io", shape=(n_v, T, 2))
+        _dev(vref_scale, "vref_scale", shape=(n_v,))
+        out = dict(xi=torch.empty((n_v, T + 1, 4), dtype=torch.float32, device=dev),
+                   k_star=torch.empty((L + 1) * n_v + 1, dtype=torch.int32, device=dev),
+                   status=torch.zeros(1, dtype=torch.int32, device=dev))
+        if want_hist:
+            out["xi_hist"] = torch.empty((L + 2, n_v, T + 1, 4), dtype=torch.float32, device=dev)
+            out["u_hist"] = torch.empty((L + 2, n_v, T, 2), dtype=torch.float32, device=dev)
+        ws = _ws(plan_workspace_bytes(n_v, T, L), dev)
+        P = make_params(params)
+        o = opts if opts is not None else launch_opts()
+        h = C.c_void_p()
+        st = lib().sgtp_graph_capture_plan(
+            track.handle, track_id, C.byref(P), n_v, X0.data_ptr(), U_io.data_ptr(), vref_scale.data_ptr(), T, K, L,
+            ego, int(seed), race, out["xi"].data_ptr(), out["k_star"].data_ptr(),
+            out["xi_hist"].data_ptr() if want_hist else None, out["u_hist"].data_ptr() if want_hist else None,
+            out["status"].data_ptr(), C.byref(o), ws.data_ptr(), ws.numel(), C.byref(h))
+        check(st, "sgtp_graph_capture_plan")
+        return cls(h, (track, X0, U_io, vref_scale, ws, P, o), out)
+
+    @classmethod
+    def capture_batch(cls, batch: "Batch", params: dict, X0, U_io, vref_scale, seed=0, want_hist=False, opts=None):
+        _dev(X0, "X0", shape=(batch.agents, 4))
+        _dev(U_io, "U_io", shape=(batch.u_elems,))
+        _dev(vref_scale, "vref_scale", shape=(batch.agents,))
+        out = batch._outputs(X0.device, want_hist)
+        ws = _ws(batch.workspace_bytes, X0.device)
+        P = make_params(params)
+        o = opts if opts is not None else launch_opts()
+        h = C.c_void_p()
+        st = lib().sgtp_graph_capture_batch(
+            batch.handle, C.byref(P), X0.data_ptr(), U_io.data_ptr(), vref_scale.data_ptr(), int(seed),
+            out["xi"].data_ptr(), out["k_star"].data_ptr(), out["xi_hist"].data_ptr() if want_hist else None,
+            out["u_hist"].data_ptr() if want_hist else None, out["status"].data_ptr(), C.byref(o), ws.data_ptr(),
+            ws.numel(), C.byref(h))
+        check(st, "sgtp_graph_capture_batch")
+        return cls(h, (batch, X0, U_io, vref_scale, ws, P, o), out)
+
+    def set_seed(self, seed: int):
+        check(lib().sgtp_graph_set_seed(self._h, int(seed)), "sgtp_graph_set_seed")
+
+    def launch(self, stream=None):
+        check(lib().sgtp_graph_launch(self._h, stream_ptr(stream)), "sgtp_graph_launch")
+        return self.out
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                lib().sgtp_graph_destroy(h)
+            except Exception:
+                pass
+            self._h = C.c_void_p()
+
+
 class Batch:
     """Independent races planned in one persistent launch (sgtp_batch_*)."""
 
@@ -285,6 +364,19 @@ class Batch:
         self.agents, self.u_elems, self.xi_elems, self.ks, self.workspace_bytes = a.value, u.value, x.value, \
             k.value, w.value
 
+    @property
+    def handle(self):
+        return self._h
+
+    def _outputs(self, dev, want_hist):
+        out = dict(xi=torch.empty(self.xi_elems, dtype=torch.float32, device=dev),
+                   k_star=torch.empty(self.ks, dtype=torch.int32, device=dev),
+                   status=torch.zeros(1, dtype=torch.int32, device=dev))
+        if want_hist:
+            out["xi_hist"] = torch.empty((self.L + 2) * self.xi_elems, dtype=torch.float32, device=dev)
+            out["u_hist"] = torch.empty((self.L + 2) * self.u_elems, dtype=torch.float32, device=dev)
+        return out
+
     def plan(self, params, X0, U_io, vref_scale, seed=0, want_hist=False, opts=None, workspace=None, out=None,
              stream=None):
         dev = X0.device
@@ -292,12 +384,7 @@ class Batch:
         _dev(U_io, "U_io", shape=(self.u_elems,))
         _dev(vref_scale, "vref_scale", shape=(self.agents,))
         if out is None:
-            out = dict(xi=torch.empty(self.xi_elems, dtype=torch.float32, device=dev),
-                       k_star=torch.empty(self.ks, dtype=torch.int32, device=dev),
-                       status=torch.zeros(1, dtype=torch.int32, device=dev))
-            if want_hist:
-                out["xi_hist"] = torch.empty((self.L + 2) * self.xi_elems, dtype=torch.float32, device=dev)
-                out["u_hist"] = torch.empty((self.L + 2) * self.u_elems, dtype=torch.float32, device=dev)
+            out = self._outputs(dev, want_hist)
         ws = workspace if workspace is not None else _ws(self.workspace_bytes, dev)
         P = make_params(params)
         o = opts if opts is not None else launch_opts()

@@ -1,0 +1,23 @@
+"""Host logic of the autotuner: cache keys bucket the problem shape, and a
+stored entry round-trips to launch options (no GPU needed)."""
+from paper_2607_25388_b300 import autotune as A
+
+
+def test_keys_bucket_horizon_and_opponents():
+    info = (148, "B300")
+    assert A.key(10, 60, 16384, 5, info) == A.key(10, 50, 16384, 5, info)     # T 49..64 share a bucket
+    assert A.key(10, 60, 16384, 5, info) != A.key(10, 65, 16384, 5, info)
+    assert A.key(5, 60, 4096, 3, info) == A.key(8, 60, 4096, 3, info)         # 4..9 opponents share one
+    assert A.key(3, 60, 4096, 3, info) != A.key(5, 60, 4096, 3, info)
+    assert A.key(10, 60, 16384, 5, info) != A.key(10, 60, 16384, 5, (132, "B300"))
+
+
+def test_cache_round_trip(tmp_path):
+    path = str(tmp_path / "tune.json")
+    info = (148, "B300")
+    assert A.lookup(10, 60, 16384, 5, path, info) is None
+    A.store(10, 60, 16384, 5, dict(block=128, ctas_per_sm=4, ms=0.8), path, info)
+    o = A.lookup(10, 60, 16384, 5, path, info)
+    assert (o.block, o.samples_per_thread, o.ctas_per_sm) == (128, 2, 4)
+    A.store(2, 30, 4096, 3, dict(block=64, ctas_per_sm=0, ms=0.1), path, info)
+    assert A.lookup(10, 60, 16384, 5, path, info).block == 128

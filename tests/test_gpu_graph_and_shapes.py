@@ -1,0 +1,95 @@
+"""Launch shapes and CUDA graphs of the planning call: every block size gives
+bit-identical plans; a captured graph replays to exactly the plan of a
+direct call (for its own seed and after a seed change); a captured batch
+replays to exactly the batch plan."""
+import numpy as np
+import pytest
+
+from paper_2607_25388_b300 import scenario as S
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def P():
+    from paper_2607_25388_b300 import planner
+    return planner
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a)).cuda()
+
+
+def plan(sc, p, K, L, seed, trk, opts=None):
+    U = dev(sc.U0.copy())
+    out = P().ibr_plan(trk, p, dev(sc.X0), U, dev(sc.vref_scale), sc.T, K, L, ego=sc.ego, seed=seed,
+                       want_hist=True, opts=opts)
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    res["U"] = U.cpu().numpy()
+    return res
+
+
+def test_block_sizes_give_identical_plans():
+    sc = S.ten_car_race(501, K=1000, T=50, L=2)        # K not a multiple of 256: a ragged last tile
+    p = S.params_fullscale()
+    trk = P().Track.from_data(sc.track)
+    ref = plan(sc, p, 1000, 2, 3, trk)
+    assert ref["status"][0] == 0
+    for block in (64, 128):
+        got = plan(sc, p, 1000, 2, 3, trk, P().launch_opts(block=block, samples_per_thread=256 // block))
+        for k in ("xi", "k_star", "U", "xi_hist", "u_hist"):
+            np.testing.assert_array_equal(got[k], ref[k], err_msg=f"block {block} {k}")
+
+
+def test_invalid_launch_shapes_are_rejected():
+    sc = S.two_car_race(502, K=256, T=20, L=1)
+    p = S.params_fullscale()
+    trk = P().Track.from_data(sc.track)
+    for o in (dict(block=96), dict(block=512), dict(block=128, samples_per_thread=1), dict(ctas_per_sm=-1)):
+        with pytest.raises(RuntimeError, match="SGTP_E_INVALID"):
+            plan(sc, p, 256, 1, 0, trk, P().launch_opts(**o))
+
+
+def test_graph_replay_equals_direct_plan_and_follows_seed_changes():
+    sc = S.ten_car_race(503, K=2048, T=60, L=2)
+    p = S.params_fullscale()
+    trk = P().Track.from_data(sc.track)
+    X0, U, vs = dev(sc.X0), dev(sc.U0.copy()), dev(sc.vref_scale)
+    g = P().PlanGraph.capture_plan(trk, p, X0, U, vs, sc.T, 2048, 2, ego=sc.ego, seed=11, want_hist=True)
+    for seed in (11, 12):
+        if seed != 11:
+            g.set_seed(seed)
+        U.copy_(dev(sc.U0))
+        out = g.launch()
+        torch.cuda.synchronize()
+        ref = plan(sc, p, 2048, 2, seed, trk)
+        assert out["status"].item() == 0
+        np.testing.assert_array_equal(out["xi"].cpu().numpy(), ref["xi"])
+        np.testing.assert_array_equal(out["k_star"].cpu().numpy(), ref["k_star"])
+        np.testing.assert_array_equal(out["u_hist"].cpu().numpy(), ref["u_hist"])
+        np.testing.assert_array_equal(U.cpu().numpy(), ref["U"])
+
+
+def test_batch_graph_replay_equals_batch_plan():
+    Pm = P()
+    p = S.params_fullscale()
+    races = [S.grid_race(S.fourier_track(600 + r, n_points=600), n_v, T, 512, 2, 90 + r)
+             for r, (n_v, T) in enumerate([(3, 40), (6, 33), (2, 70)])]
+    trk = Pm.Track.from_many([sc.track for sc in races])
+    b = Pm.Batch(trk, [dict(track_id=r, n_v=sc.X0.shape[0], T=sc.T, ego=sc.ego, race_tag=r)
+                       for r, sc in enumerate(races)], K=512, L=2)
+    X0 = dev(np.concatenate([sc.X0 for sc in races]))
+    U0 = np.concatenate([sc.U0.reshape(-1) for sc in races])
+    vs = dev(np.concatenate([sc.vref_scale for sc in races]))
+    U = dev(U0)
+    ref = b.plan(p, X0, U, vs, seed=7)
+    torch.cuda.synchronize()
+    ref = {k: v.cpu().numpy() for k, v in ref.items()}
+    U2 = dev(U0)
+    g = Pm.PlanGraph.capture_batch(b, p, X0, U2, vs, seed=7)
+    out = g.launch()
+    torch.cuda.synchronize()
+    assert out["status"].item() == 0
+    np.testing.assert_array_equal(out["xi"].cpu().numpy(), ref["xi"])
+    np.testing.assert_array_equal(out["k_star"].cpu().numpy(), ref["k_star"])
