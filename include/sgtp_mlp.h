@@ -118,6 +118,18 @@ sgtp_status sgtp_ibr_plan_learned(const sgtp_track *trk, int32_t track_id, const
                                   const sgtp_launch_opts *opts, void *workspace, size_t workspace_bytes,
                                   void *stream);
 
+/* sgtp_batch_plan with the learned proposal (every race's horizon must be
+ * the network's T).  feat_out / prop_out (optional) have (L+2) slots of
+ * agents x 64 features / agents x T x 4 proposal values, agents in the
+ * batch's order (race by race), with the semantics of
+ * sgtp_ibr_plan_learned. */
+sgtp_status sgtp_batch_plan_learned(const sgtp_batch *b, const sgtp_params *p, const sgtp_mlp *mlp, int32_t K_prop,
+                                   const float *X0, float *U_io, const float *vref_scale, uint64_t seed,
+                                   float *xi_out, int32_t *k_star_out, float *xi_hist, float *u_hist,
+                                   float *feat_out, float *prop_out, int32_t *status_dev,
+                                   const sgtp_launch_opts *opts, void *workspace, size_t workspace_bytes,
+                                   void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -124,6 +124,8 @@ def lib():
             L.sgtp_best_response_mixed.argtypes = [vp, i32, C.POINTER(Params), vp, vp, f32, vp, i32, i32, i32,
                                                    u64, u32, u32, u32, i32, vp, i32, vp, vp, vp, vp, vp, vp, sz,
                                                    vp]
+            L.sgtp_batch_plan_learned.argtypes = [vp, C.POINTER(Params), vp, i32, vp, vp, vp, u64, vp, vp, vp, vp,
+                                                  vp, vp, vp, C.POINTER(LaunchOpts), vp, sz, vp]
             L.sgtp_ibr_plan_learned.argtypes = [vp, i32, C.POINTER(Params), i32, vp, vp, vp, i32, i32, i32, i32,
                                                 u64, u32, vp, i32, vp, vp, vp, vp, vp, vp, vp,
                                                 C.POINTER(LaunchOpts), vp, sz, vp]
@@ -148,7 +150,7 @@ EXPORTS = [
     "sgtp_last_error", "sgtp_version", "sgtp_launch_count",
     "sgtp_mlp_param_count", "sgtp_mlp_create", "sgtp_mlp_destroy", "sgtp_mlp_reserve", "sgtp_mlp_forward",
     "sgtp_mlp_proposal", "sgtp_mlp_train_step", "sgtp_mlp_get_params", "sgtp_mlp_set_params", "sgtp_mlp_info",
-    "sgtp_best_response_mixed", "sgtp_ibr_plan_learned",
+    "sgtp_best_response_mixed", "sgtp_ibr_plan_learned", "sgtp_batch_plan_learned",
 ]
 
 

@@ -948,11 +948,11 @@ static sgtp_status refresh_tail_counts(const sgtp_batch *b, const sgtp_params *p
     return SGTP_OK;
 }
 
-extern "C" sgtp_status sgtp_batch_plan(const sgtp_batch *b, const sgtp_params *p, const float *X0, float *U_io,
-                                       const float *vref_scale, uint64_t seed, float *xi_out, int32_t *k_star_out,
-                                       float *xi_hist, float *u_hist, int32_t *status_dev,
-                                       const sgtp_launch_opts *opts, void *workspace, size_t workspace_bytes,
-                                       void *stream)
+static sgtp_status batch_plan_impl(const sgtp_batch *b, const sgtp_params *p, const float *X0, float *U_io,
+                                   const float *vref_scale, uint64_t seed, float *xi_out, int32_t *k_star_out,
+                                   float *xi_hist, float *u_hist, int32_t *status_dev, const sgtp_launch_opts *opts,
+                                   const sgtp_mlp *mlp, int32_t K_prop, float *feat_out, float *prop_out,
+                                   void *workspace, size_t workspace_bytes, void *stream)
 {
     SGTP_CHECK(b != nullptr, "batch is NULL");
     sgtp_status st = check_params(p);
@@ -976,7 +976,41 @@ extern "C" sgtp_status sgtp_batch_plan(const sgtp_batch *b, const sgtp_params *p
     a.xi_total = b->xi_elems;
     a.u_total = b->u_elems;
     attach_workspace(a, lay, workspace);
+    if (mlp) {
+        int32_t mT = 0;
+        sgtp_status st2 = sgtp_mlp_info(mlp, &mT, nullptr, nullptr, nullptr);
+        if (st2) return st2;
+        for (const auto &R : b->races) SGTP_CHECK(R.T == mT, "race horizon %d differs from the network's %d", R.T, mT);
+        SGTP_CHECK(K_prop >= 0 && K_prop <= b->K, "K_prop out of range [0, K]");
+        a.mlp_wb = sgtp_mlp_fragments(mlp);
+        a.mlp_wf = sgtp_mlp_master(mlp);
+        a.K_prop = K_prop;
+    }
+    SGTP_CHECK(((uintptr_t)prop_out & 15u) == 0, "prop_out must be 16-byte aligned");
+    a.feat_out = feat_out;
+    a.prop_out = mlp ? (float4 *)prop_out : nullptr;
     return launch_plan(a, b->max_nv - 1, opts, s);
+}
+
+extern "C" sgtp_status sgtp_batch_plan(const sgtp_batch *b, const sgtp_params *p, const float *X0, float *U_io,
+                                       const float *vref_scale, uint64_t seed, float *xi_out, int32_t *k_star_out,
+                                       float *xi_hist, float *u_hist, int32_t *status_dev,
+                                       const sgtp_launch_opts *opts, void *workspace, size_t workspace_bytes,
+                                       void *stream)
+{
+    return batch_plan_impl(b, p, X0, U_io, vref_scale, seed, xi_out, k_star_out, xi_hist, u_hist, status_dev, opts,
+                           nullptr, 0, nullptr, nullptr, workspace, workspace_bytes, stream);
+}
+
+extern "C" sgtp_status sgtp_batch_plan_learned(const sgtp_batch *b, const sgtp_params *p, const sgtp_mlp *mlp,
+                                               int32_t K_prop, const float *X0, float *U_io,
+                                               const float *vref_scale, uint64_t seed, float *xi_out,
+                                               int32_t *k_star_out, float *xi_hist, float *u_hist, float *feat_out,
+                                               float *prop_out, int32_t *status_dev, const sgtp_launch_opts *opts,
+                                               void *workspace, size_t workspace_bytes, void *stream)
+{
+    return batch_plan_impl(b, p, X0, U_io, vref_scale, seed, xi_out, k_star_out, xi_hist, u_hist, status_dev, opts,
+                           mlp, K_prop, feat_out, prop_out, workspace, workspace_bytes, stream);
 }
 
 // ================================================================ CUDA graphs

@@ -7,7 +7,8 @@
 3. ten-car plan (K = 16384, T = 60, L = 5), direct launch and CUDA-graph replay;
 4. 256 independent races in one launch (n_v ~ U{2..10}, T ~ U{30..80}, K = 4096, L = 3), direct and graph;
 5. plan latency of the ten-car race: plain K = 16384, plain K = 4096, and the learned sampler with
-   2048 proposal + 2048 plain samples (network weights do not change the work).
+   2048 proposal + 2048 plain samples (network weights do not change the work);
+5b. the same three samplers with 32 ten-car races per launch (per-plan time when the GPU is full).
 
 Times are CUDA-event medians over `reps` calls after warm-up, inputs resident on the device.
 """
@@ -155,12 +156,43 @@ def config5(reps):
     return res
 
 
+def config5_batched(reps, n_races=32):
+    """Per-plan time when many ten-car races share one launch (a serving
+    setting): plain K=16384 vs learned 2048+2048 vs plain K=4096."""
+    from .learned import Mlp
+    p = S.params_fullscale()
+    races = [S.ten_car_race(300 + r) for r in range(n_races)]
+    trk = Track.from_many([sc.track for sc in races])
+    X0 = torch.as_tensor(np.concatenate([sc.X0 for sc in races])).cuda()
+    U0 = torch.as_tensor(np.concatenate([sc.U0.reshape(-1) for sc in races])).cuda()
+    vs = torch.as_tensor(np.concatenate([sc.vref_scale for sc in races])).cuda()
+    U = U0.clone()
+    mlp = Mlp(60, seed=1)
+    res = {}
+    for name, K, net, kp in (("plain K=16384", 16384, None, 0), ("plain K=4096", 4096, None, 0),
+                             ("learned 2048+2048", 4096, mlp, 2048)):
+        b = Batch(trk, [dict(track_id=r, n_v=10, T=60, ego=0, race_tag=r) for r in range(n_races)], K=K, L=5)
+        holder = {}
+
+        def run():
+            U.copy_(U0)
+            holder["o"] = b.plan(p, X0, U, vs, seed=3, out=holder.get("o"), mlp=net, K_prop=kp)
+
+        ms = _median_ms(run, max(5, reps // 5))
+        res[name] = _line(f"5b: {n_races} ten-car races in one launch, {name} (ms per launch)", ms,
+                          n_races * R.rollout_steps_plan(10, K, 60, 5), n_races * R.flops_plan(10, K, 60, 5),
+                          ms_per_plan=ms / n_races)
+    print(json.dumps(dict(config=f"5b: per-plan time ratio plain 16384 / learned 2048+2048 ({n_races} races per launch)",
+                          ratio=res["plain K=16384"]["ms"] / res["learned 2048+2048"]["ms"])), flush=True)
+    return res
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--reps", type=int, default=50)
-    ap.add_argument("--configs", type=str, default="1,2,3,4,5")
+    ap.add_argument("--configs", type=str, default="1,2,3,4,5,5b")
     args = ap.parse_args(argv)
-    fns = {"1": config1, "2": config2, "3": config3, "4": config4, "5": config5}
+    fns = {"1": config1, "2": config2, "3": config3, "4": config4, "5": config5, "5b": config5_batched}
     for c in args.configs.split(","):
         fns[c.strip()](args.reps)
 

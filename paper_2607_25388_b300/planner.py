@@ -378,7 +378,9 @@ class Batch:
         return out
 
     def plan(self, params, X0, U_io, vref_scale, seed=0, want_hist=False, opts=None, workspace=None, out=None,
-             stream=None):
+             stream=None, mlp=None, K_prop=0):
+        """Plan every race in one launch; with ``mlp`` (a learned.Mlp) K_prop
+        samples of every best response come from the network's proposal."""
         dev = X0.device
         _dev(X0, "X0", shape=(self.agents, 4))
         _dev(U_io, "U_io", shape=(self.u_elems,))
@@ -388,6 +390,15 @@ class Batch:
         ws = workspace if workspace is not None else _ws(self.workspace_bytes, dev)
         P = make_params(params)
         o = opts if opts is not None else launch_opts()
+        if mlp is not None:
+            st = lib().sgtp_batch_plan_learned(
+                self._h, C.byref(P), mlp.handle, int(K_prop), X0.data_ptr(), U_io.data_ptr(), vref_scale.data_ptr(),
+                int(seed), out["xi"].data_ptr(), out["k_star"].data_ptr(),
+                out["xi_hist"].data_ptr() if "xi_hist" in out else None,
+                out["u_hist"].data_ptr() if "u_hist" in out else None, None, None, out["status"].data_ptr(),
+                C.byref(o), ws.data_ptr(), ws.numel(), stream_ptr(stream))
+            check(st, "sgtp_batch_plan_learned")
+            return out
         st = lib().sgtp_batch_plan(self._h, C.byref(P), X0.data_ptr(), U_io.data_ptr(), vref_scale.data_ptr(),
                                    int(seed), out["xi"].data_ptr(), out["k_star"].data_ptr(),
                                    out["xi_hist"].data_ptr() if "xi_hist" in out else None,

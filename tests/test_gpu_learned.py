@@ -301,3 +301,27 @@ def test_learned_plan_teacher_forced(net, case):
             assert_rel_close(g["xi_hist"][rnd][i], ww["states"][0], STATE_RTOL, f"xi r{rnd} a{i}")
             assert_rel_close(g["u_hist"][rnd][i], ww["controls"][0], STATE_RTOL, f"U r{rnd} a{i}")
             checked += 1
+
+
+def test_learned_batch_equals_learned_single_plans(net):
+    """Two ten-car races planned in one learned batch launch give exactly the
+    learned single-race plans (proposal phase included)."""
+    p = S.params_fullscale()
+    races = [S.ten_car_race(221 + r, K=512, T=60, L=1) for r in range(2)]
+    trk = P().Track.from_many([sc.track for sc in races])
+    b = P().Batch(trk, [dict(track_id=r, n_v=10, T=60, ego=0, race_tag=r) for r in range(2)], K=512, L=1)
+    X0 = dev(np.concatenate([sc.X0 for sc in races]))
+    U = dev(np.concatenate([sc.U0.reshape(-1) for sc in races]))
+    vs = dev(np.concatenate([sc.vref_scale for sc in races]))
+    out = b.plan(p, X0, U, vs, seed=4, mlp=net, K_prop=200)
+    torch.cuda.synchronize()
+    assert out["status"].item() == 0
+    xi_all, ks_all = out["xi"].cpu().numpy(), out["k_star"].cpu().numpy()
+    for r, sc in enumerate(races):
+        Ur = dev(sc.U0.copy())
+        single = P().ibr_plan(P().Track.from_data(sc.track), p, dev(sc.X0), Ur, dev(sc.vref_scale), 60, 512, 1, ego=0,
+                              seed=4, race=r, mlp=net, K_prop=200)
+        torch.cuda.synchronize()
+        nx, nk = 10 * 61 * 4, 2 * 10 + 1
+        np.testing.assert_array_equal(xi_all[r * nx:(r + 1) * nx], single["xi"].cpu().numpy().reshape(-1))
+        np.testing.assert_array_equal(ks_all[r * nk:(r + 1) * nk], single["k_star"].cpu().numpy())
