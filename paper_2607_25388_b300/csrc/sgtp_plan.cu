@@ -140,39 +140,41 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
 
 __device__ __forceinline__ int ld_status(const int *p) { return *(const volatile int *)p; }
 
-// Grid-wide barrier of a cooperative launch.  Every wait has a limit: a CTA
-// whose wait runs out records SGTP_E_TIMEOUT and returns false, and every
-// other waiter stops as soon as it sees a fatal status.
+// Grid-wide barrier of a cooperative launch: one arrival counter that only
+// grows (zeroed at launch).  Barrier e of the launch is passed once it reaches
+// e x gridDim.x; arrival is an acquire-release add by each CTA's thread 0
+// after the CTA's bar.sync, so the CTA's writes are visible to every CTA that
+// passes.  Every wait has a limit: a CTA whose wait runs out records
+// SGTP_E_TIMEOUT and returns false, and every other waiter stops as soon as
+// it sees a fatal status.
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__shared__ unsigned g_bar_epoch;      // barriers this CTA has entered (thread 0's count)
+
 __device__ bool grid_barrier(const PlanArgs &a, bool skip_arrival)
 {
     __shared__ int ok_sh;
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned *count = a.bar, *gen = a.bar + 1;
-        const unsigned g = ld_acquire(gen);
-        __threadfence();
-        bool released = false;
-        if (!skip_arrival) {
-            const unsigned prev = atomicAdd(count, 1u);
-            if (prev == gridDim.x - 1) {
-                atomicExch(count, 0u);
-                __threadfence();
-                atomicAdd(gen, 1u);
-                released = true;
-            }
-        }
-        if (!released) {
+        unsigned *count = a.bar;
+        const unsigned target = (g_bar_epoch += 1u) * gridDim.x;
+        bool passed = false;
+        if (!skip_arrival) passed = atom_add_acq_rel(count, 1u) + 1u == target;
+        if (!passed) {
             const unsigned long long t0 = global_ns();
-            while (ld_acquire(gen) == g) {
+            while ((int)(ld_acquire(count) - target) < 0) {
                 if (ld_status(a.status) & 0xff) break;
                 if (global_ns() - t0 > (unsigned long long)a.timeout_ns) {
                     atomicOr(a.status, SGTP_E_TIMEOUT);
                     break;
                 }
-                __nanosleep(64);
             }
         }
-        __threadfence();
         ok_sh = (ld_status(a.status) & 0xff) == 0;
     }
     __syncthreads();
@@ -402,7 +404,10 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
     int flag = 0;
     unsigned phase = 0;
     bool ok = true;
-    if (threadIdx.x == 0) mbar_init(Tl::bar(), 1);
+    if (threadIdx.x == 0) {
+        mbar_init(Tl::bar(), 1);
+        g_bar_epoch = 0u;
+    }
     stamp(a, 0);
 
     // ------------------------------------------------------------ setup (one CTA per vehicle)
