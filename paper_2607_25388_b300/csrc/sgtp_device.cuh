@@ -262,6 +262,29 @@ __device__ __forceinline__ int nearest_segment_warp(const TrackView &tv, float p
     return (int)(best & 0xffffffffu);
 }
 
+// The same search by every thread of the CTA (lowest index on ties); key_sh
+// is one shared 64-bit word.  All threads must call it; all get the result.
+__device__ __forceinline__ int nearest_segment_cta(const TrackView &tv, float px, float py, unsigned long long *key_sh)
+{
+    if (threadIdx.x == 0) *key_sh = ~0ull;
+    __syncthreads();
+    unsigned long long best = ~0ull;
+    for (int j = threadIdx.x; j < tv.N; j += blockDim.x) {
+        float t, cr;
+        const float d2 = seg_dist2(__ldg(tv.A + j), __ldg(tv.B + j), px, py, t, cr);
+        const unsigned long long key = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)j;
+        best = key < best ? key : best;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+        best = other < best ? other : best;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMin(key_sh, best);
+    __syncthreads();
+    return (int)(*key_sh & 0xffffffffu);
+}
+
 // Projection on a known segment j (global index).
 __device__ __forceinline__ FrenetPt frenet_at(const TrackView &tv, int j, float px, float py)
 {
@@ -294,28 +317,37 @@ __device__ __forceinline__ float wrap_angle(float a) { return __fmaf_rn(-kTwoPi,
 __device__ __forceinline__ void reference_traj(const TrackView &tv, const SegWindow &w, const float4 *Cw, int j0,
                                                float s0, float dt, float vscale, int T, float4 *ref)
 {
+    const int N = tv.N, Wn = w.Wn;
+    const float L = tv.L;
     float hi = s0, lo = 0.f;
-    int j = j0, lap = 0;                                      // segment j of lap `lap`
-    int rl = w.Wn > 0 ? wrap_index(j0 - w.w0, tv.N) : -1;    // its window-local index
+    int j = j0, lap = 0;                                     // segment j of lap `lap`
+    int rl = Wn > 0 ? wrap_index(j0 - w.w0, N) : -1;       // its window-local index
+    // data of segment j, reloaded only when the walk moves to another segment
+    float4 va, vb, c;
+    float sj;
+    auto load = [&]() {
+        if ((unsigned)rl < (unsigned)Wn) {
+            va = w.A[rl]; vb = w.B[rl]; sj = w.S[rl]; c = Cw[rl];
+        } else {
+            va = __ldg(tv.A + j); vb = __ldg(tv.B + j); sj = __ldg(tv.S + j); c = __ldg(tv.C + j);
+        }
+    };
+    load();
+    // x^r at the current progress (hi, lo): walk to the segment holding it
     auto locate = [&]() -> float4 {
-        float4 va, vb, c;
-        float sj;
-        for (int it = 0; it < 2 * tv.N + 2; ++it) {
-            if ((unsigned)rl < (unsigned)w.Wn) {
-                va = w.A[rl]; vb = w.B[rl]; sj = w.S[rl]; c = Cw[rl];
-            } else {
-                va = __ldg(tv.A + j); vb = __ldg(tv.B + j); sj = __ldg(tv.S + j); c = __ldg(tv.C + j);
-            }
-            const float hm = hi - (float)lap * tv.L;          // exact: within a factor 2 of lap L
-            const float sn = (j + 1 == tv.N) ? tv.L : sj + vb.w;
+        for (int it = 0; it < 2 * N + 2; ++it) {
+            const float hm = hi - (float)lap * L;            // exact: within a factor 2 of lap L
+            const float sn = (j + 1 == N) ? L : sj + vb.w;
             if (hm < sj) {
                 --j; --rl;
-                if (j < 0) { j = tv.N - 1; --lap; }
+                if (j < 0) { j = N - 1; --lap; }
+                load();
                 continue;
             }
             if (hm >= sn) {
                 ++j; ++rl;
-                if (j == tv.N) { j = 0; ++lap; }
+                if (j == N) { j = 0; ++lap; }
+                load();
                 continue;
             }
             const float u = ((hm - sj) + lo) / vb.w;

@@ -203,8 +203,9 @@ __device__ __forceinline__ void stage_vehicle_window(const PlanArgs &a, const Tr
 // Features of vehicle i before a best response (layout in sgtp_mlp.h):
 // Frenet-relative ego state, raceline curvature ahead, and the nine nearest
 // opponents by |Delta s| (ties by index after rounding |Delta s| to mm).
-// All threads of the CTA; thread 0 writes the ego terms, threads 1..4 one
-// curvature each, threads 32.. one opponent each (rank by counting).
+// All threads of the CTA (at least 64); thread 0 writes the ego terms,
+// threads 1..4 one curvature each, threads 32.. one opponent each (rank by
+// counting), and the slots of absent opponents are zeroed.
 // key_sh: SGTP_MAX_AGENTS floats of shared scratch.
 __device__ void compute_features(const PlanArgs &a, const RaceDev &R, int i, int bin, bool game_on, float *f,
                                  float *key_sh)
@@ -271,7 +272,8 @@ __device__ void compute_features(const PlanArgs &a, const RaceDev &R, int i, int
             o[5] = (prog - horizon_gain) / 40.f;
         }
     }
-    if (tid >= 64 && tid < 64 + 9 * 6 && (tid - 64) / 6 >= n_opp) f[8 + (tid - 64)] = 0.f;
+    for (int q = tid; q < 9 * 6; q += blockDim.x)
+        if (q / 6 >= n_opp) f[8 + q] = 0.f;
 }
 
 __device__ __forceinline__ void mma_bf16_16816(float c[4], const unsigned a[4], const unsigned b[2])
@@ -418,9 +420,9 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
         const TrackView tv = get_track(a, R.track_id);
         const float4 x0 = make_float4(a.X0[4 * ag], a.X0[4 * ag + 1], a.X0[4 * ag + 2], a.X0[4 * ag + 3]);
         __syncthreads();
-        if (warp == 0) {
-            const int j = nearest_segment_warp(tv, x0.x, x0.y);
-            if (lane == 0) j0_sh = j;
+        {
+            const int j = nearest_segment_cta(tv, x0.x, x0.y, &cta_key);
+            if (threadIdx.x == 0) j0_sh = j;
         }
         for (int q = threadIdx.x; q < R.T; q += blockDim.x) {
             // nominal controls, clipped: the zero-noise sample

@@ -325,3 +325,25 @@ def test_learned_batch_equals_learned_single_plans(net):
         nx, nk = 10 * 61 * 4, 2 * 10 + 1
         np.testing.assert_array_equal(xi_all[r * nx:(r + 1) * nx], single["xi"].cpu().numpy().reshape(-1))
         np.testing.assert_array_equal(ks_all[r * nk:(r + 1) * nk], single["k_star"].cpu().numpy())
+
+
+@pytest.mark.parametrize("block", [64, 128])
+def test_learned_plan_is_identical_for_every_block_size(net, block):
+    """Features (incl. the zeroed slots of absent opponents), proposals and
+    selections do not depend on the CTA size."""
+    p = S.params_fullscale()
+    sc = S.two_car_race(331, K=1024, T=60, L=2)
+    trk = P().Track.from_data(sc.track)
+
+    def run(opts):
+        U = dev(sc.U0.copy())
+        out = P().ibr_plan(trk, p, dev(sc.X0), U, dev(sc.vref_scale), sc.T, 1024, 2, ego=sc.ego, seed=2,
+                           want_hist=True, mlp=net, K_prop=300, want_features=True, want_prop=True, opts=opts)
+        torch.cuda.synchronize()
+        return {k: v.cpu().numpy() for k, v in out.items()}
+
+    a = run(None)
+    b = run(P().launch_opts(block=block, samples_per_thread=256 // block))
+    assert np.all(a["features"][:, :, 14:62] == 0.0)       # one opponent: slots 1..8 are zero
+    for k in ("features", "prop", "xi", "k_star", "u_hist"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
