@@ -466,6 +466,12 @@ __device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned coun
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// Plain arrival (release at CTA scope), no transaction bytes.
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
@@ -500,6 +506,7 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
 // lands in shared memory after the CTA has left.
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity, unsigned long long limit_ns)
 {
+    if (mbar_try_wait(bar, parity)) return true;         // the common case: no clock read
     const unsigned long long t0 = global_ns();
     while (!mbar_try_wait(bar, parity)) {
         const unsigned long long dt = global_ns() - t0;

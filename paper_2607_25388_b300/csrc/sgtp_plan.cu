@@ -36,9 +36,7 @@ struct RaceDev {
     int xi_off;      // float offset into xi_out (n_v * (T+1) * 4)
     int ks_off;      // offset into k_star_out ((L+1) * n_v + 1)
     int pos_off;     // float2 offset into each prediction buffer (n_v * (T+1))
-    int item_all;    // BR items before this race in a Jacobi round
-    int item_ego;    // BR items before this race in the extra ego round
-    int pad[3];
+    int pad[5];
 };
 
 struct AgentDev {
@@ -481,18 +479,16 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
         int cur = -1;                 // vehicle (global index) staged
         unsigned long long *cur_slot = nullptr;
         for (int item = i0; item < i1; ++item) {
-            int ri, i, t;
+            // item = vehicle (all vehicles of all races in a Jacobi round, the
+            // races' egos in the extra round) x tile of that vehicle's samples
+            int ri, i;
+            const int unit = item / a.tiles, t = item - unit * a.tiles;
             if (!extra) {
-                ri = find_race(a, item, [](const RaceDev &r) { return r.item_all; });
-                const RaceDev R0 = get_race(a, ri);
-                const int local = item - R0.item_all;
-                i = local / a.tiles;
-                t = local - i * a.tiles;
+                ri = find_race(a, unit, [](const RaceDev &r) { return r.agent_off; });
+                i = unit - get_race(a, ri).agent_off;
             } else {
-                ri = find_race(a, item, [](const RaceDev &r) { return r.item_ego; });
-                const RaceDev R0 = get_race(a, ri);
-                i = R0.ego;
-                t = item - R0.item_ego;
+                ri = unit;
+                i = get_race(a, ri).ego;
             }
             const RaceDev R = get_race(a, ri);
             const int ag = R.agent_off + i;
@@ -553,10 +549,10 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
                 __syncthreads();
                 if (abort_sh) { ok = false; break; }
             }
-            // a tile is 256 consecutive samples; 256 / blockDim.x per thread
+            // a tile of kTileSingle samples, kTileSingle / blockDim.x per thread
             unsigned long long best = ~0ull;
-            for (unsigned j = threadIdx.x; j < 256u; j += blockDim.x) {
-                const unsigned k = (unsigned)t * 256u + j;
+            for (unsigned j = threadIdx.x; j < (unsigned)kTileSingle; j += blockDim.x) {
+                const unsigned k = (unsigned)t * kTileSingle + j;
                 if (k < (unsigned)a.K) {
                     const SampleResult r = run_candidate<MAXO, false>(S, a.p, a.key, k, round > 0, flag, nullptr,
                                                                       nullptr, nullptr);
@@ -703,9 +699,10 @@ sgtp_status launch_plan_v(PlanArgs &a, int block, int ctas, cudaStream_t s)
     return SGTP_OK;
 }
 
-// Register budget: the 128-register build when at most two 256-thread CTAs
-// per SM are wanted -- explicitly, or by default when a Jacobi round has
-// fewer sample tiles than three CTAs per SM could take at once.
+// Work decomposition and register budget of one launch: tiles of
+// kTileSingle samples; the 128-register build when at most two 256-thread
+// CTAs per SM are wanted -- explicitly, or by default when a Jacobi round
+// has fewer tiles than three CTAs per SM could take at once.
 template <int MAXO>
 sgtp_status launch_plan_t(PlanArgs &a, const sgtp_launch_opts *opts, cudaStream_t s)
 {
@@ -714,9 +711,11 @@ sgtp_status launch_plan_t(PlanArgs &a, const sgtp_launch_opts *opts, cudaStream_
     int dev = 0, sms = 0;
     SGTP_CUDA(cudaGetDevice(&dev));
     SGTP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int threads_per_sm = (ctas > 0 ? ctas : 0) * block;
+    a.tiles = (a.K + kTileSingle - 1) / kTileSingle;
+    a.items_all = a.n_agents * a.tiles;
+    a.items_ego = a.n_races * a.tiles;
     bool wide;
-    if (ctas > 0) wide = threads_per_sm <= 512;
+    if (ctas > 0) wide = ctas * block <= 512;
     else wide = (long long)a.items_all < 3ll * sms;
     if (wide && ctas == 0) ctas = 512 / block;
     return wide ? launch_plan_v<MAXO, 2>(a, block, ctas, s) : launch_plan_v<MAXO, 3>(a, block, ctas, s);
@@ -749,7 +748,6 @@ void fill_common(PlanArgs &a, const sgtp_track *trk, const sgtp_params *p, int K
     a.A = trk->A; a.B = trk->B; a.W = trk->W; a.S = trk->S; a.C = trk->C;
     a.p = *p;
     a.K = K; a.L = L;
-    a.tiles = (K + 255) / 256;
     a.X0 = X0; a.U_io = U_io; a.vref = vref;
     a.key = make_uint2((unsigned)seed, (unsigned)(seed >> 32));
     a.xi_out = xi_out; a.k_star_out = k_star_out; a.xi_hist = xi_hist; a.u_hist = u_hist;
@@ -783,7 +781,7 @@ struct sgtp_batch {
     std::vector<RaceDev> races;
     RaceDev *races_dev = nullptr;
     long long agents = 0, u_elems = 0, xi_elems = 0, ks = 0, n_pos = 0;
-    int items_all = 0, items_ego = 0, maxT = 0, max_nv = 0;
+    int maxT = 0, max_nv = 0;
 };
 
 extern "C" size_t sgtp_plan_workspace_bytes(int32_t n_v, int32_t T, int32_t L)
@@ -822,8 +820,6 @@ static sgtp_status ibr_plan_impl(const sgtp_track *trk, int32_t track_id, const 
     a.races = nullptr;
     a.n_races = 1;
     a.n_agents = n_v;
-    a.items_all = n_v * a.tiles;
-    a.items_ego = a.tiles;
     a.maxT = T;
     a.xi_total = (long long)n_v * (T + 1) * 4;
     a.u_total = (long long)n_v * T * 2;
@@ -884,8 +880,8 @@ extern "C" sgtp_status sgtp_batch_create(const sgtp_track *trk, const sgtp_race 
     SGTP_CHECK(L >= 0 && L < 4096, "L out of range");
     sgtp_batch *b = new sgtp_batch();
     b->trk = trk; b->n_races = n_races; b->K = K; b->L = L;
-    const int tiles = (K + 255) / 256;
-    long long ag = 0, u = 0, xi = 0, ks = 0, pos = 0, it_all = 0, it_ego = 0;
+    const long long tiles = (K + kTileSingle - 1) / kTileSingle;
+    long long ag = 0, u = 0, xi = 0, ks = 0, pos = 0;
     for (int r = 0; r < n_races; ++r) {
         const sgtp_race &q = races[r];
         if (q.track_id < 0 || q.track_id >= trk->n_tracks || q.n_v < 1 || q.n_v > SGTP_MAX_AGENTS || q.T < 1 ||
@@ -897,20 +893,17 @@ extern "C" sgtp_status sgtp_batch_create(const sgtp_track *trk, const sgtp_race 
         R.track_id = q.track_id; R.n_v = q.n_v; R.T = q.T; R.ego = q.ego; R.race_tag = q.race_tag;
         R.n_tail = 0;   // filled per call from mu_tail
         R.agent_off = (int)ag; R.u_off = (int)u; R.xi_off = (int)xi; R.ks_off = (int)ks; R.pos_off = (int)pos;
-        R.item_all = (int)it_all; R.item_ego = (int)it_ego;
         b->races.push_back(R);
         ag += q.n_v; u += (long long)q.n_v * q.T * 2; xi += (long long)q.n_v * (q.T + 1) * 4;
         ks += (long long)(L + 1) * q.n_v + 1; pos += (long long)q.n_v * (q.T + 1);
-        it_all += (long long)q.n_v * tiles; it_ego += tiles;
         b->maxT = std::max(b->maxT, q.T);
         b->max_nv = std::max(b->max_nv, q.n_v);
     }
-    if (xi > (1ll << 31) || it_all > (1ll << 31) || u > (1ll << 31)) {
+    if (xi > (1ll << 31) || ag * tiles > (1ll << 31) || u > (1ll << 31)) {
         delete b;
         return set_error(SGTP_E_INVALID, "batch too large for 32-bit offsets");
     }
     b->agents = ag; b->u_elems = u; b->xi_elems = xi; b->ks = ks; b->n_pos = pos;
-    b->items_all = (int)it_all; b->items_ego = (int)it_ego;
     cudaError_t e = cudaMalloc(&b->races_dev, sizeof(RaceDev) * n_races);
     if (e != cudaSuccess) {
         delete b;
@@ -977,8 +970,6 @@ static sgtp_status batch_plan_impl(const sgtp_batch *b, const sgtp_params *p, co
     a.races = b->races_dev;
     a.n_races = b->n_races;
     a.n_agents = (int)b->agents;
-    a.items_all = b->items_all;
-    a.items_ego = b->items_ego;
     a.maxT = b->maxT;
     a.xi_total = b->xi_elems;
     a.u_total = b->u_elems;

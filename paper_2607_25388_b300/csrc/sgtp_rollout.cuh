@@ -20,6 +20,7 @@
 namespace sgtp {
 
 constexpr int kWinTile = 512;          // track window of a best-response tile (segments)
+constexpr int kTileSingle = 256;       // samples of a work item of the plan kernel
 constexpr float kFarAway = 1.0e15f;    // position of an absent opponent slot
 
 // Scalars of one best-response problem (shared memory).
@@ -156,7 +157,7 @@ struct SampleState {
     float pos, vel;   // continuous segment position and its last advance
     f2p cost;         // running c_track, two partial sums
     float rho_bd, d_tail;
-    float g2[2 * BRTile<MAXO>::NP];
+    float g2[MAXO];
 };
 
 template <int MAXO>
@@ -171,7 +172,73 @@ __device__ __forceinline__ void sample_init(SampleState<MAXO> &St, const BRScala
     St.rho_bd = __int_as_float(0x7f800000);
     St.d_tail = 0.f;
 #pragma unroll
-    for (int o = 0; o < 2 * BRTile<MAXO>::NP; ++o) St.g2[o] = __int_as_float(0x7f800000);
+    for (int o = 0; o < MAXO; ++o) St.g2[o] = __int_as_float(0x7f800000);
+}
+
+// Pieces of one rollout step.
+
+// control cost, tau = 0..H-1, and smoothness, tau = 1..H-1 (Eq. ctrack)
+__device__ __forceinline__ f2p step_control_cost(const sgtp_params &p, f2p cost, float &a_prev, float &d_prev,
+                                                 float2 u, int tau)
+{
+    const f2p uu = pk(u.x, u.y);
+    f2p acc = fma2(mul2(uu, uu), pk(p.R[0], p.R[1]), cost);
+    if (tau > 0) {
+        const f2p du = sub2(uu, pk(a_prev, d_prev));
+        acc = fma2(mul2(du, du), pk(p.S[0], p.S[1]), acc);
+    }
+    a_prev = u.x; d_prev = u.y;
+    return acc;
+}
+
+// tracking term at the new state, tau = 1..H (Eq. ctrack), heading error wrapped
+__device__ __forceinline__ f2p step_tracking_cost(const sgtp_params &p, f2p acc, float x, float y, float psi, float v,
+                                                  float4 r)
+{
+    const f2p exy = sub2(pk(x, y), pk(r.x, r.y));
+    acc = fma2(mul2(exy, exy), pk(p.Q[0], p.Q[1]), acc);
+    const f2p epv = pk(wrap_angle(psi - r.z), v - r.w);
+    return fma2(mul2(epv, epv), pk(p.Q[2], p.Q[3]), acc);
+}
+
+// time-aligned distances to opponents [2 Q0, 2 Q1) of one step (Eq. Dmin),
+// two at a time, and to the odd last one when ODD
+template <int Q0, int Q1, bool ODD, int MAXO>
+__device__ __forceinline__ void step_opponents(float *g2, float x, float y, const float4 *row)
+{
+    const f2p X = pk(x, x), Y = pk(y, y);
+#pragma unroll
+    for (int q = Q0; q < Q1; ++q) {
+        const float4 o = row[q];
+        const f2p dx = sub2(X, pk(o.x, o.y));
+        const f2p dy = sub2(Y, pk(o.z, o.w));
+        const float2 d2 = upk(fma2(dx, dx, mul2(dy, dy)));
+        g2[2 * q] = fminf(g2[2 * q], d2.x);
+        g2[2 * q + 1] = fminf(g2[2 * q + 1], d2.y);
+    }
+    if (ODD && (MAXO & 1)) {
+        // the odd last opponent alone: the same operations on one lane
+        const float4 o = row[MAXO / 2];
+        const float dx = __fsub_rn(x, o.x), dy = __fsub_rn(y, o.z);
+        const float d2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
+        g2[MAXO - 1] = fminf(g2[MAXO - 1], d2);
+    }
+}
+
+// Frenet of the new state (progress unwrapped along the rollout), boundary
+// clearance (Sec. III-B) with widths at the foot point, tail offsets
+struct GeoState {
+    float s, pos, vel, rho_bd, d_tail;
+    int r;
+};
+__device__ __forceinline__ FrenetPt step_geometry(GeoState &G, const BRScalars &S, const SegWindow &w, int st, float x,
+                                                  float y, int &flag)
+{
+    const FrenetPt f = frenet_step(S.tv, w, G.r, G.pos, G.vel, x, y, flag);
+    G.s = G.s + wrap_len(f.s - G.s, S.tv.L, S.invL);
+    G.rho_bd = fminf(G.rho_bd, fminf(f.wr + f.d, f.wl - f.d));
+    if (st > S.T - S.n_tail) G.d_tail = G.d_tail + f.d;
+    return f;
 }
 
 // Advance a candidate by one step tau with control u; optional outputs.
@@ -180,48 +247,14 @@ __device__ __forceinline__ void sample_step(SampleState<MAXO> &St, const BRScala
                                             int tau, float2 u, int &flag, float *st_out, float *fr_out)
 {
     using T = Tile<MAXO>;
-    // control cost, tau = 0..H-1, and smoothness, tau = 1..H-1 (Eq. ctrack)
-    const f2p uu = pk(u.x, u.y);
-    f2p acc = fma2(mul2(uu, uu), pk(p.R[0], p.R[1]), St.cost);
-    if (tau > 0) {
-        const f2p du = sub2(uu, pk(St.a_prev, St.d_prev));
-        acc = fma2(mul2(du, du), pk(p.S[0], p.S[1]), acc);
-    }
-    St.a_prev = u.x; St.d_prev = u.y;
-
+    f2p acc = step_control_cost(p, St.cost, St.a_prev, St.d_prev, u, tau);
     bicycle_step(p, St.x, St.y, St.psi, St.v, u.x, u.y);
     const int st = tau + 1;
-
-    // Frenet of the new state, progress unwrapped along the rollout
-    const FrenetPt f = frenet_step(S.tv, T::win(S.w0, S.Wn), St.r, St.pos, St.vel, St.x, St.y, flag);
-    St.s = St.s + wrap_len(f.s - St.s, S.tv.L, S.invL);
-
-    // tracking term, tau = 1..H (Eq. ctrack), heading error wrapped
-    const float4 r = T::ref()[st];
-    const f2p exy = sub2(pk(St.x, St.y), pk(r.x, r.y));
-    acc = fma2(mul2(exy, exy), pk(p.Q[0], p.Q[1]), acc);
-    const f2p epv = pk(wrap_angle(St.psi - r.z), St.v - r.w);
-    St.cost = fma2(mul2(epv, epv), pk(p.Q[2], p.Q[3]), acc);
-
-    // boundary clearance (Sec. III-B) with widths at the foot point
-    St.rho_bd = fminf(St.rho_bd, fminf(f.wr + f.d, f.wl - f.d));
-
-    // tail lateral offsets (blocking term)
-    if (st > S.T - S.n_tail) St.d_tail = St.d_tail + f.d;
-
-    // time-aligned distances to every opponent (Eq. Dmin), two at a time
-    constexpr int NP = BRTile<MAXO>::NP;
-    const float4 *row = T::opp() + tau * NP;
-    const f2p X = pk(St.x, St.x), Y = pk(St.y, St.y);
-#pragma unroll
-    for (int q = 0; q < NP; ++q) {
-        const float4 o = row[q];
-        const f2p dx = sub2(X, pk(o.x, o.y));
-        const f2p dy = sub2(Y, pk(o.z, o.w));
-        const float2 d2 = upk(fma2(dx, dx, mul2(dy, dy)));
-        St.g2[2 * q] = fminf(St.g2[2 * q], d2.x);
-        St.g2[2 * q + 1] = fminf(St.g2[2 * q + 1], d2.y);
-    }
+    GeoState G{St.s, St.pos, St.vel, St.rho_bd, St.d_tail, St.r};
+    const FrenetPt f = step_geometry(G, S, T::win(S.w0, S.Wn), st, St.x, St.y, flag);
+    St.s = G.s; St.pos = G.pos; St.vel = G.vel; St.rho_bd = G.rho_bd; St.d_tail = G.d_tail; St.r = G.r;
+    St.cost = step_tracking_cost(p, acc, St.x, St.y, St.psi, St.v, T::ref()[st]);
+    step_opponents<0, MAXO / 2, true, MAXO>(St.g2, St.x, St.y, T::opp() + tau * BRTile<MAXO>::NP);
     if (OUT) {
         if (st_out) {
             st_out[4 * st + 0] = St.x; st_out[4 * st + 1] = St.y; st_out[4 * st + 2] = St.psi;
@@ -239,14 +272,14 @@ struct SampleResult {
 // Terminal game cost per opponent (Eqs. c_contest, c_long, c_block,
 // c_safety), total cost (Eq. allc), feasibility and violation (Sec. III-B).
 template <int MAXO>
-__device__ __forceinline__ SampleResult sample_finish(const SampleState<MAXO> &St, const BRScalars &S,
-                                                      const sgtp_params &p, bool game_on)
+__device__ __forceinline__ SampleResult finish_terms(f2p cost, float s, float rho_bd, float d_tail, const float *g2,
+                                                     const BRScalars &S, const sgtp_params &p, bool game_on)
 {
     using T = Tile<MAXO>;
-    const float2 cp = upk(St.cost);
+    const float2 cp = upk(cost);
     const float c_track = cp.x + cp.y;
-    const float dbar_i = St.d_tail / (float)S.n_tail;
-    const float prog_i = St.s - S.s_t;
+    const float dbar_i = d_tail / (float)S.n_tail;
+    const float prog_i = s - S.s_t;
     float c_game = 0.f;
     float rho_obs = __int_as_float(0x7f800000);
 #pragma unroll
@@ -257,7 +290,7 @@ __device__ __forceinline__ SampleResult sample_finish(const SampleState<MAXO> &S
             const float c_contest = fabsf(ds_H) < p.s_contest ? -p.w_contest : 0.f;
             const float c_long = -p.w_long * os.y * ds_H;
             const float c_block = os.z != 0.f ? -os.z / (1.f + fabsf(dbar_i - T::odbar()[o])) : 0.f;
-            const float g = sqrtf(St.g2[o]);
+            const float g = sqrtf(g2[o]);
             const float sh = fmaxf(0.f, p.g_safe - g);
             const float c_safety = p.w_safety * sh * sh;
             c_game = c_game + (c_contest + c_long + c_block + c_safety);
@@ -266,11 +299,18 @@ __device__ __forceinline__ SampleResult sample_finish(const SampleState<MAXO> &S
     }
     SampleResult r;
     r.cost = game_on ? __fmaf_rn(p.w_game, c_game, c_track) : c_track;
-    const bool b = St.rho_bd >= p.m_bd;
+    const bool b = rho_bd >= p.m_bd;
     const bool ob = rho_obs >= p.d_col;
     r.feasible = b && ob;
-    r.viol = fmaxf(0.f, p.m_bd - St.rho_bd) + fmaxf(0.f, p.d_col - rho_obs);
+    r.viol = fmaxf(0.f, p.m_bd - rho_bd) + fmaxf(0.f, p.d_col - rho_obs);
     return r;
+}
+
+template <int MAXO>
+__device__ __forceinline__ SampleResult sample_finish(const SampleState<MAXO> &St, const BRScalars &S,
+                                                      const sgtp_params &p, bool game_on)
+{
+    return finish_terms<MAXO>(St.cost, St.s, St.rho_bd, St.d_tail, St.g2, S, p, game_on);
 }
 
 // Full candidate: noise, controls, rollout, finish.  Optional outputs are
