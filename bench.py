@@ -128,10 +128,12 @@ def run_reference(args):
         oracle_rate(per_step / 4)
     vals = [oracle_rate(per_step) for _ in range(args.steps)]
     v = statistics.mean(x["value"] for x in vals)
+    steps_per_plan = ((L + 1) * N_V + 1) * K * T
     line = {"metric": "rollout-steps/s", "value": v, "unit": "rollout-steps/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_v": N_V, "K": K, "T": T, "L": L}, "impl": "reference",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": steps_per_plan / v * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_v": N_V, "K": K, "T": T, "L": L,
+                       "ms_per_step_basis": "one full plan at the sampled rate"}, "impl": "reference",
             "cpu_baseline": {"value": v, "unit": "rollout-steps/s", "cores": vals[0]["cores"], "kind": "oracle",
                              "sample": vals[0]["sample"]},
             "e2e": {"value": v, "unit": "rollout-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
