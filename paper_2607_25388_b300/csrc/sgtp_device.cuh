@@ -109,6 +109,49 @@ __device__ __forceinline__ f2p fma2(f2p a, f2p b, f2p c)
 
 // Squared distance from p to segment (vertex a.xy, chord b); t is the
 // clamped parameter, cr the cross product e x (p - a) (sign of d).
+// ---------------------------------------------------------------- hardware approximations
+// The special-function unit's approximations with denormal inputs and
+// results flushed to zero (PTX .approx.ftz): no denormal handling around the
+// instruction.  Every argument in this engine is either zero or a normal
+// float (wrapped angles, steering angles, uniforms in [2^-24, 1), squared
+// distances clamped to >= 1e-30), so the flush never applies.
+__device__ __forceinline__ float sin_ftz(float x)
+{
+    float r;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float cos_ftz(float x)
+{
+    float r;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float lg2_ftz(float x)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float sqrt_ftz(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rcp_ftz(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 __device__ __forceinline__ float seg_dist2(const float4 &a, const float4 &b, float px, float py, float &t, float &cr)
 {
     const float dx = px - a.x, dy = py - a.y;
@@ -140,7 +183,7 @@ __device__ __forceinline__ SegData seg_at(const TrackView &tv, const SegWindow &
 
 __device__ __forceinline__ FrenetPt frenet_result(const SegData &g, int m, float t, float d2, float cr)
 {
-    const float dist = __fmul_rn(d2, rsqrtf(fmaxf(d2, 1e-30f)));
+    const float dist = __fmul_rn(d2, rsqrt_ftz(fmaxf(d2, 1e-30f)));
     FrenetPt f;
     f.s = __fmaf_rn(t, g.b.w, g.s);
     f.d = cr >= 0.0f ? dist : -dist;
@@ -406,16 +449,15 @@ __device__ __forceinline__ float uniform_open(unsigned w)
 
 // Box-Muller pair from two words: (sqrt(-2 ln u1) cos 2pi u2, ... sin ...).
 // The angle is evaluated as 2 pi u2 - pi in (-pi, pi) with the signs folded
-// back, keeping __sincosf inside its accurate range.
+// back, keeping the sine and cosine approximations inside their accurate range.
 __device__ __forceinline__ float2 box_muller(unsigned w0, unsigned w1)
 {
     const float u1 = uniform_open(w0), u2 = uniform_open(w1);
     // -2 ln u1 = (-2 ln 2) log2 u1; the approximate log2 may overshoot 0 as u1 -> 1
-    const float m = fmaxf(-1.38629436111989061883f * __log2f(u1), 0.f);
-    float r;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(m));
-    float sn, cs;
-    __sincosf(__fmaf_rn(kTwoPi, u2, -kPi), &sn, &cs);
+    const float m = fmaxf(-1.38629436111989061883f * lg2_ftz(u1), 0.f);
+    const float r = sqrt_ftz(m);
+    const float ang = __fmaf_rn(kTwoPi, u2, -kPi);
+    const float sn = sin_ftz(ang), cs = cos_ftz(ang);
     return make_float2(-r * cs, -r * sn);
 }
 

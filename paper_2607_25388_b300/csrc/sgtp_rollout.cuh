@@ -125,14 +125,13 @@ __device__ __forceinline__ unsigned stream_bit_of(unsigned k, int K_prop) { retu
 __device__ __forceinline__ void bicycle_step(const sgtp_params &p, float &x, float &y, float &psi, float &v, float a,
                                              float delta)
 {
-    float sn, cs;
-    __sincosf(wrap_angle(psi), &sn, &cs);
-    float sd, cd;
-    __sincosf(delta, &sd, &cd);
+    const float pw = wrap_angle(psi);
+    const float sn = sin_ftz(pw), cs = cos_ftz(pw);
+    const float sd = sin_ftz(delta), cd = cos_ftz(delta);
     const float dv = __fmul_rn(p.dt, v);
     const float x1 = __fmaf_rn(dv, cs, x);
     const float y1 = __fmaf_rn(dv, sn, y);
-    const float psi1 = psi + __fdividef(__fmul_rn(dv, sd), __fmul_rn(cd, p.wheelbase));
+    const float psi1 = psi + __fmul_rn(__fmul_rn(dv, sd), rcp_ftz(__fmul_rn(cd, p.wheelbase)));
     const float v1 = fminf(fmaxf(__fmaf_rn(p.dt, a, v), p.v_min), p.v_max);
     x = x1; y = y1; psi = psi1; v = v1;
 }
