@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import ctypes as C
 import json
+import math
 import time
 
 import numpy as np
@@ -167,9 +168,11 @@ def generate_dataset(seeds, plans_per_race: int, advance: int = 10, K=16384, T=6
     return torch.cat(xs).contiguous(), torch.cat(ys).contiguous()
 
 
-def train(mlp: Mlp, X: torch.Tensor, Y: torch.Tensor, epochs: int, batch=4096, lr=1e-3, seed=0, log=None):
+def train(mlp: Mlp, X: torch.Tensor, Y: torch.Tensor, epochs: int, batch=4096, lr=1e-3, seed=0, log=None,
+          cosine=False):
     """Adam on the Gaussian NLL over shuffled mini-batches; returns the mean
-    loss of each epoch."""
+    loss of each epoch.  With ``cosine`` the learning rate follows a cosine
+    decay from lr to 0 over the epochs."""
     g = torch.Generator(device=X.device)
     g.manual_seed(seed)
     n = X.shape[0]
@@ -180,9 +183,10 @@ def train(mlp: Mlp, X: torch.Tensor, Y: torch.Tensor, epochs: int, batch=4096, l
         perm = torch.randperm(n, device=X.device, generator=g)
         acc = torch.zeros(1, device=X.device)
         nb = 0
+        lr_e = lr * 0.5 * (1.0 + math.cos(math.pi * ep / epochs)) if cosine else lr
         for b0 in range(0, n - batch + 1, batch):
             idx = perm[b0:b0 + batch]
-            mlp.train_step(X[idx].contiguous(), Y[idx].contiguous(), lr, loss_out=loss)
+            mlp.train_step(X[idx].contiguous(), Y[idx].contiguous(), lr_e, loss_out=loss)
             acc += loss
             nb += 1
         losses.append(float(acc.item() / max(nb, 1)))

@@ -33,6 +33,7 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--batch", type=int, default=4096)
+    ap.add_argument("--cosine", action="store_true", help="cosine learning-rate decay to 0")
     ap.add_argument("--eval-seeds", type=str, default="200-209")
     ap.add_argument("--eval-states", type=int, default=4, help="closed-loop states per evaluation race")
     ap.add_argument("--k-prop", type=int, default=2048)
@@ -44,7 +45,8 @@ def main(argv=None):
     log = (lambda m: None) if args.quiet else (lambda m: print(m, file=sys.stderr, flush=True))
     params = S.params_fullscale()
     T, K, L = 60, 16384, 5
-    rec = dict(races=args.races, plans_per_race=args.plans, advance=args.advance, epochs=args.epochs)
+    rec = dict(races=args.races, plans_per_race=args.plans, advance=args.advance, epochs=args.epochs,
+               cosine=args.cosine)
     if args.load:
         mlp = LR.Mlp.load(args.load)
     else:
@@ -56,7 +58,7 @@ def main(argv=None):
         rec["datagen_s"] = time.time() - t0
         mlp = LR.Mlp(T, seed=1)
         t0 = time.time()
-        losses = LR.train(mlp, X, Y, args.epochs, args.batch, args.lr, log=log)
+        losses = LR.train(mlp, X, Y, args.epochs, args.batch, args.lr, log=log, cosine=args.cosine)
         torch.cuda.synchronize()
         rec["train_s"] = time.time() - t0
         rec["loss_first_epoch"], rec["loss_last_epoch"] = losses[0], losses[-1]
