@@ -314,6 +314,12 @@ void sgtp_graph_destroy(sgtp_graph *g);
 /* ------------------------------------------------------------------ */
 /* Misc                                                                 */
 /* ------------------------------------------------------------------ */
+/* Wait for `stream` and read a device status word written by a planning
+ * call (status_dev): *status_host receives 0 or the SGTP_E_* code of a
+ * device-side failure (low byte) with flag bits above it.  Returns
+ * SGTP_E_CUDA if the stream itself failed.  Blocks the calling thread. */
+sgtp_status sgtp_sync_status(const int32_t *status_dev, void *stream, int32_t *status_host);
+
 const char *sgtp_last_error(void);     /* thread-local text of the last failure */
 const char *sgtp_version(void);
 /* Number of kernel launches this library has enqueued since load (all

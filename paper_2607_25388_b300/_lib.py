@@ -83,6 +83,7 @@ def lib():
                                              u32, u32, i32, vp, vp, vp, vp, vp, sz, vp]
             L.sgtp_best_response_noalloc.argtypes = [vp, i32, C.POINTER(Params), vp, vp, f32, vp, i32, i32, i32,
                                                      u64, u32, u32, u32, i32, vp, vp, vp, vp, vp]
+            L.sgtp_sync_status.argtypes = [vp, vp, C.POINTER(i32)]
             L.sgtp_last_error.restype = C.c_char_p
             L.sgtp_version.restype = C.c_char_p
             L.sgtp_launch_count.restype = C.c_int64
@@ -147,7 +148,7 @@ EXPORTS = [
     "sgtp_plan_workspace_bytes", "sgtp_ibr_plan",
     "sgtp_graph_capture_plan", "sgtp_graph_capture_batch", "sgtp_graph_set_seed", "sgtp_graph_launch",
     "sgtp_graph_destroy",
-    "sgtp_last_error", "sgtp_version", "sgtp_launch_count",
+    "sgtp_sync_status", "sgtp_last_error", "sgtp_version", "sgtp_launch_count",
     "sgtp_mlp_param_count", "sgtp_mlp_create", "sgtp_mlp_destroy", "sgtp_mlp_reserve", "sgtp_mlp_forward",
     "sgtp_mlp_proposal", "sgtp_mlp_train_step", "sgtp_mlp_get_params", "sgtp_mlp_set_params", "sgtp_mlp_info",
     "sgtp_best_response_mixed", "sgtp_ibr_plan_learned", "sgtp_batch_plan_learned",

@@ -594,6 +594,14 @@ static sgtp_status br_launch(const BRArgs &a, int maxo, bool key_mode, const flo
     return SGTP_OK;
 }
 
+extern "C" sgtp_status sgtp_sync_status(const int32_t *status_dev, void *stream, int32_t *status_host)
+{
+    SGTP_CHECK(status_dev != nullptr && status_host != nullptr, "NULL argument");
+    SGTP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    SGTP_CUDA(cudaMemcpy(status_host, status_dev, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    return SGTP_OK;
+}
+
 extern "C" size_t sgtp_br_workspace_bytes(int32_t n_opp, int32_t T)
 {
     if (n_opp < 0 || T < 1) return 0;

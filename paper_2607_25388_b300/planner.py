@@ -14,8 +14,17 @@ import torch
 from . import _lib
 from ._lib import check, lib, make_params
 
-__all__ = ["Track", "rollout_costs", "best_response", "best_response_noalloc", "best_response_mixed", "PlanGraph", "ibr_plan", "Batch", "launch_opts",
+__all__ = ["sync_status", "Track", "rollout_costs", "best_response", "best_response_noalloc", "best_response_mixed", "PlanGraph", "ibr_plan", "Batch", "launch_opts",
            "stream_ptr", "br_workspace_bytes", "plan_workspace_bytes"]
+
+
+def sync_status(status: torch.Tensor, stream=None) -> int:
+    """Wait for the stream and return a planning call's device status word
+    (0, or SGTP_E_* in the low byte with flag bits above it)."""
+    _dev(status, "status", dtype=torch.int32, shape=(1,))
+    out = C.c_int32()
+    check(lib().sgtp_sync_status(status.data_ptr(), stream_ptr(stream), C.byref(out)), "sgtp_sync_status")
+    return int(out.value)
 
 
 def stream_ptr(stream=None) -> int:

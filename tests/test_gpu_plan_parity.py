@@ -187,3 +187,6 @@ def test_barrier_wait_times_out_instead_of_hanging():
     assert g["status"][0] & 0xFF == 4
     ok = gpu_plan(sc, p, 256, 1, seed=1)
     assert ok["status"][0] == 0
+    # the host-side status query reads the same word
+    st = torch.tensor([4 | (5 << 8)], dtype=torch.int32, device="cuda")
+    assert P.sync_status(st) == 4 | (5 << 8)
