@@ -181,20 +181,41 @@ __device__ bool grid_barrier(const PlanArgs &a, bool skip_arrival)
 
 // Stage the window of a vehicle's track around segment j0 (thread 0 issues
 // the bulk copies; the caller waits); fills the tile scalars' window fields.
+__shared__ const float4 *g_win_track;   // track (A array) of the staged window, NULL when none
+__shared__ int g_win_w0;                 // its first segment
+
+// Stage the window of a vehicle's track around segment j0 (thread 0 issues
+// the bulk copies; the caller waits when this returns true on thread 0) and
+// fill the tile scalars' window fields.  A window already in shared memory
+// is reused, without any copy, when it holds the same track and j0 lies
+// between half the usual look-back and the usual look-back plus an eighth
+// of the window: a rollout then still has at least 7/8 of the window ahead
+// of it (and leaves the window only to the global-memory path).  The C
+// array (setup only) is always copied.
 template <int MAXO>
-__device__ __forceinline__ void stage_vehicle_window(const PlanArgs &a, const TrackView &tv, int j0, bool with_c)
+__device__ __forceinline__ bool stage_vehicle_window(const PlanArgs &a, const TrackView &tv, int j0, bool with_c)
 {
     using T = Tile<MAXO>;
+    bool issued = false;
     if (threadIdx.x == 0) {
         BRScalars &S = T::sc();
         const int Wn = min(a.Wn, (tv.N + 3) & ~3);
         const int back = min(a.back, Wn / 4);
         S.tv = tv;
         S.Wn = Wn;
-        S.w0 = window_start(j0, back, tv.N);
         S.invL = 1.0f / tv.L;
-        T::stage_window(tv, S.w0, Wn, with_c);
+        const int r = g_win_track == tv.A ? wrap_index(j0 - g_win_w0, tv.N) : -1;
+        if (!with_c && r >= back / 2 && r <= back + Wn / 8) {
+            S.w0 = g_win_w0;
+        } else {
+            S.w0 = window_start(j0, back, tv.N);
+            T::stage_window(tv, S.w0, Wn, with_c);
+            g_win_track = tv.A;
+            g_win_w0 = S.w0;
+            issued = true;
+        }
     }
+    return issued;
 }
 
 // ---------------------------------------------------------------- learned proposal
@@ -354,6 +375,7 @@ __device__ void proposal_for(const PlanArgs &a, const RaceDev &R, int i, int bin
     __nv_bfloat16 *act0 = (__nv_bfloat16 *)(key_sh + SGTP_MAX_AGENTS);
     __nv_bfloat16 *act1 = act0 + SGTP_MLP_HIDDEN;
     const int ag = R.agent_off + i;
+    if (threadIdx.x == 0) g_win_track = nullptr;      // the scratch overlays the staged window
     compute_features(a, R, i, bin, game_on, x, key_sh);
     __syncthreads();
     if (a.feat_out && threadIdx.x < 64)
@@ -407,6 +429,7 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
     if (threadIdx.x == 0) {
         mbar_init(Tl::bar(), 1);
         g_bar_epoch = 0u;
+        g_win_track = nullptr;
     }
     stamp(a, 0);
 
@@ -429,11 +452,10 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
         }
         __syncthreads();
         const int j0 = j0_sh;
-        stage_vehicle_window<MAXO>(a, tv, j0, true);
-        if (threadIdx.x == 0) {
+        if (stage_vehicle_window<MAXO>(a, tv, j0, true)) {
             if (!mbar_wait_bounded(Tl::bar(), phase, (unsigned long long)a.timeout_ns)) atomicOr(a.status, SGTP_E_TIMEOUT);
+            phase ^= 1u;
         }
-        phase ^= 1u;
         __syncthreads();
         const FrenetPt f = frenet_at(tv, j0, x0.x, x0.y);
         AgentDev A;
@@ -499,7 +521,7 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
                 const TrackView tv = get_track(a, R.track_id);
                 const AgentDev A = load_agent(a.agents + ag);
                 const int T = R.T, n_opp = R.n_v - 1;
-                stage_vehicle_window<MAXO>(a, tv, A.j0, false);
+                const bool issued = stage_vehicle_window<MAXO>(a, tv, A.j0, false);
                 if (threadIdx.x == 0) {
                     cta_key = ~0ull;
                     S.x0 = A.x0; S.s_t = A.s_t; S.d_t = A.d_t;
@@ -541,11 +563,11 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
                 cur_slot = a.keys + R.ks_off + (extra ? (a.L + 1) * R.n_v : round * R.n_v + i);
                 __syncthreads();
                 if (threadIdx.x == 0) {
-                    if (!mbar_wait_bounded(Tl::bar(), phase, (unsigned long long)a.timeout_ns))
+                    if (issued && !mbar_wait_bounded(Tl::bar(), phase, (unsigned long long)a.timeout_ns))
                         atomicOr(a.status, SGTP_E_TIMEOUT);
                     abort_sh = (ld_status(a.status) & 0xff) != 0;
                 }
-                phase ^= 1u;
+                if (issued) phase ^= 1u;
                 __syncthreads();
                 if (abort_sh) { ok = false; break; }
             }
@@ -590,7 +612,7 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
             }
             const int slot = extra ? (a.L + 1) * R.n_v : round * R.n_v + i;
             const TrackView tv = get_track(a, R.track_id);
-            stage_vehicle_window<MAXO>(a, tv, A.j0, false);
+            const bool issued = stage_vehicle_window<MAXO>(a, tv, A.j0, false);
             if (threadIdx.x == 0) {
                 const unsigned long long key = __ldcg(a.keys + R.ks_off + slot);
                 ks_sh = (unsigned)(key & 0x7fffffffull);
@@ -618,10 +640,10 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
                     a.u_hist[(size_t)round * a.u_total + uo + 2 * q + 1] = u.y;
                 }
             }
-            if (threadIdx.x == 0) {
+            if (threadIdx.x == 0 && issued) {
                 if (!mbar_wait_bounded(Tl::bar(), phase, (unsigned long long)a.timeout_ns)) atomicOr(a.status, SGTP_E_TIMEOUT);
             }
-            phase ^= 1u;
+            if (issued) phase ^= 1u;
             __syncthreads();
             float *xi_final = (round == a.L || extra) ? a.xi_out + xo : nullptr;
             float *xi_h = a.xi_hist ? a.xi_hist + (size_t)round * a.xi_total + xo : nullptr;
