@@ -203,20 +203,45 @@ def compare(mlp: Mlp, seeds, states_per_race: int, advance=10, K=16384, K_eq=409
     each state, every game-on best response of the plain plan (rounds 1..L
     and the extra ego response) is re-solved three ways on its exact inputs:
     plain with K samples, plain with K_eq samples (equal budget), and learned
-    with K_prop proposal + (K_eq - K_prop) plain samples.  Returns the
-    selected costs and feasibility of each, per response."""
+    with K_prop proposal + (K_eq - K_prop) plain samples.  End to end, the
+    learned planner also plans from the same state and warm start, and the
+    ego's final trajectory of each plan is scored against its own plan's
+    round-L predictions.  Returns the selected costs and feasibility of
+    each, per response and per plan."""
     params = params or S.params_fullscale()
     sa, sd = float(np.float32(params["sigma_a"])), float(np.float32(params["sigma_delta"]))
     rec = {k: [] for k in ("plain", "plain_eq", "learned", "feas_plain", "feas_plain_eq", "feas_learned",
-                           "k_match")}
+                           "k_match", "e2e_plain", "e2e_learned", "e2e_feas_plain", "e2e_feas_learned")}
+
+    def ego_final(out_, X0_, ego_, n_v_, seed_, race_):
+        """Cost (violation if infeasible) and feasibility of the ego's final
+        trajectory of a plan against the round-L predictions of that plan:
+        its selected controls evaluated as the single, noise-free sample."""
+        u = out_["u_hist"][L + 1, ego_].contiguous()
+        opp = out_["xi_hist"][L, [j for j in range(n_v_) if j != ego_]].contiguous()
+        prop = torch.stack([u[:, 0], u[:, 1], torch.full_like(u[:, 0], 1e-30), torch.full_like(u[:, 0], 1e-30)],
+                           dim=1).contiguous()
+        r_ = best_response_mixed(race_.track, params, X0_[ego_].contiguous(), u, float(race_.vs[ego_]), opp, T, 1,
+                                 prop, 1, seed=seed_, agent=ego_, rnd=L + 1, game_on=True)
+        return r_["cost"], r_["any_feasible"]
+
     for seed in seeds:
         race = Race(S.ten_car_race(int(seed), K=K, T=T, L=L), device)
         ego, n_v = race.sc.ego, race.n_v
         for q in range(states_per_race):
             pseed = 1_000_003 * int(seed) + q
             X0 = race.X.clone()
+            U0 = race.U.clone()
+            # end to end: the learned planner from the same state and warm start
+            UL = U0.clone()
+            outl = ibr_plan(race.track, params, X0, UL, race.vs, T, K_eq, L, ego=ego, seed=pseed, want_hist=True,
+                            mlp=mlp, K_prop=K_prop)
             out = ibr_plan(race.track, params, race.X, race.U, race.vs, T, K, L, ego=ego, seed=pseed,
                            want_hist=True, want_features=True)
+            for key, o_ in (("plain", out), ("learned", outl)):
+                c_, f_ = ego_final(o_, X0, ego, n_v, pseed, race)
+                rec["e2e_" + key].append(c_)
+                rec["e2e_feas_" + key].append(f_)
             xh, uh, feat, ks = out["xi_hist"], out["u_hist"], out["features"], out["k_star"].cpu().numpy()
             jobs = [(r, i) for r in range(1, L + 2) for i in range(n_v) if r <= L or i == ego]
             F = torch.stack([feat[r, i] for r, i in jobs]).contiguous()
@@ -238,7 +263,8 @@ def compare(mlp: Mlp, seeds, states_per_race: int, advance=10, K=16384, K_eq=409
                 rec["k_match"].append((a["k_star"], int(ks[kpos])))
             race.advance(out["xi"], advance)   # U was warm-started in place by the plan
     res = {}
-    for k in ("plain", "plain_eq", "learned", "feas_plain", "feas_plain_eq", "feas_learned"):
+    for k in ("plain", "plain_eq", "learned", "feas_plain", "feas_plain_eq", "feas_learned", "e2e_plain",
+              "e2e_learned", "e2e_feas_plain", "e2e_feas_learned"):
         res[k] = torch.cat(rec[k]).float().cpu().numpy()
     km = [(int(a.item()), b) for a, b in rec["k_match"]]
     res["k_match"] = float(np.mean([a == b for a, b in km]))
@@ -253,6 +279,15 @@ def summarize(res: dict) -> dict:
     fp, fe, fl = (res[k].astype(bool) for k in ("feas_plain", "feas_plain_eq", "feas_learned"))
     out = dict(n_responses=int(fp.size), feasible_plain=float(fp.mean()), feasible_plain_eq=float(fe.mean()),
                feasible_learned=float(fl.mean()), k_match=res["k_match"])
+    if "e2e_plain" in res:
+        # end to end: the ego's final trajectory of each planner, in its own plan
+        gp, gl = res["e2e_feas_plain"].astype(bool), res["e2e_feas_learned"].astype(bool)
+        both = gp & gl
+        out.update(e2e_plans=int(gp.size), e2e_feasible_plain=float(gp.mean()), e2e_feasible_learned=float(gl.mean()))
+        if both.any():
+            mp, ml = float(res["e2e_plain"][both].mean()), float(res["e2e_learned"][both].mean())
+            out.update(e2e_mean_cost_plain=mp, e2e_mean_cost_learned=ml, e2e_cost_gap_abs=ml - mp,
+                       e2e_cost_gap=(ml - mp) / abs(mp))
     for name, f2, c2 in (("learned", fl, res["learned"]), ("plain_eq", fe, res["plain_eq"])):
         both = fp & f2
         mp = float(res["plain"][both].mean()) if both.any() else float("nan")

@@ -45,11 +45,12 @@ def main(argv=None):
     log = (lambda m: None) if args.quiet else (lambda m: print(m, file=sys.stderr, flush=True))
     params = S.params_fullscale()
     T, K, L = 60, 16384, 5
-    rec = dict(races=args.races, plans_per_race=args.plans, advance=args.advance, epochs=args.epochs,
-               cosine=args.cosine)
+    rec = dict(advance=args.advance)
     if args.load:
         mlp = LR.Mlp.load(args.load)
+        rec["weights"] = args.load
     else:
+        rec.update(races=args.races, plans_per_race=args.plans, epochs=args.epochs, cosine=args.cosine)
         t0 = time.time()
         X, Y = LR.generate_dataset(range(10000, 10000 + args.races), args.plans, args.advance, K, T, L, params,
                                    log=log)
