@@ -314,8 +314,8 @@ __global__ void __launch_bounds__(256) br_prep_kernel(TrackView tv, sgtp_params 
         const float *q0 = opp + (size_t)o * (T + 1) * 4;
         const float *pt = q0 + (size_t)(tau + 1) * 4;
         const int jo = j0_sh[o + 1];
-        const float ch = sqrtf((pt[0] - q0[0]) * (pt[0] - q0[0]) + (pt[1] - q0[1]) * (pt[1] - q0[1]));
-        const int guess = wrap_index(jo - w.w0, tv.N) + min((int)(ch / __ldg(tv.B + jo).w), 4 * kWinTile);
+        const int guess = wrap_index(jo - w.w0, tv.N) + chord_guess(pt[0] - q0[0], pt[1] - q0[1], __ldg(tv.B + jo),
+                                                                    4 * kWinTile);
         const FrenetPt f = frenet_search(tv, w, guess, pt[0], pt[1]);
         flag |= f.flag;
         ofr[q] = make_float2(f.s, f.d);

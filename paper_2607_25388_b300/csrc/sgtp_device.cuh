@@ -231,6 +231,20 @@ static __device__ __forceinline__ FrenetPt frenet_search(const TrackView tv, con
     return f;
 }
 
+// Start segment offset for frenet_search of a point displaced by (dx, dy)
+// from a state whose nearest segment has chord b = B[j]: the displacement's
+// length in units of |e_j|, capped at cap, negative when the displacement
+// points against the segment's direction (a vehicle that has turned around
+// moves back along the track, and an always-forward guess would overshoot by
+// twice its travel).  Within the track's reach the walk ends at the same
+// segment from any start; the guess only keeps the walk short.
+__device__ __forceinline__ int chord_guess(float dx, float dy, float4 b, int cap)
+{
+    const float ch = sqrtf(dx * dx + dy * dy);
+    const int n = min((int)(ch / b.w), cap);
+    return __fmaf_rn(dx, b.x, dy * b.y) < 0.0f ? -n : n;
+}
+
 // Frenet projection s(x; G), d(x; G) (Sec. II) of a rollout state.
 // Two consecutive segments j-1, j of the polyline are equidistant from p
 // exactly on the bisector of their angle at waypoint j (where both feet are

@@ -367,7 +367,7 @@ __device__ __forceinline__ void stage_opponents(int T, int n_opp, F src)
 // the bicycle recurrence (the same arithmetic as the sample loop, so the
 // states are bit-identical to the evaluated candidate's) into st(); then
 // every thread projects one state onto the track by the distance search of
-// frenet_search from a guess (the chord from x0 in segment lengths), which
+// frenet_search from a guess (chord_guess: the signed chord from x0 in segment lengths), which
 // reaches the same nearest segment as the sample loop's walk; then one
 // thread unwraps the progress in step order.  Outputs (any may be NULL):
 // positions (T+1), states twice (T+1)x4, and the prediction summary
@@ -393,11 +393,10 @@ __device__ void roll_cooperative(const sgtp_params &p, float4 x0, float s_t, int
     __syncthreads();
     const SegWindow w = Tl::win(S.w0, S.Wn);
     const int r0 = wrap_index(j0 - S.w0, S.tv.N);
-    const float inv_len0 = 1.0f / __ldg(S.tv.B + j0).w;
+    const float4 b0 = __ldg(S.tv.B + j0);
     for (int q = threadIdx.x; q < T; q += blockDim.x) {
         const float4 v = st[q + 1];
-        const float ch = sqrtf((v.x - x0.x) * (v.x - x0.x) + (v.y - x0.y) * (v.y - x0.y));
-        const int guess = r0 + min((int)(ch * inv_len0), 4 * kWinTile);
+        const int guess = r0 + chord_guess(v.x - x0.x, v.y - x0.y, b0, 4 * kWinTile);
         const FrenetPt f = frenet_search(S.tv, w, guess, v.x, v.y);
         flag |= f.flag;
         fr[q] = make_float2(f.s, f.d);

@@ -165,3 +165,25 @@ def test_full_size_ten_car_response_on_sampled_candidates():
     g, o, _ = run_both(sc.track, p, sc.X0[0], sc.U0[0], 1.0, opp, T, K, k_list=kl, seed=11, agent=0, rnd=3)
     assert_rel_close(g["states"], o["states"], STATE_RTOL, "states")
     check_candidates(g, o, "ten-car sample", pos_scale=float(np.abs(sc.track.xr[:, :2]).max()))
+
+
+def test_vehicles_driving_against_the_track_direction():
+    """Ego and opponents heading backwards along the track at 50 m/s: 150 m
+    of travel (about 95 segments) against the polyline's direction.  The
+    opponents' progress summaries and every candidate's Frenet coordinates
+    must still be the globally nearest projections of Sec. II."""
+    td = S.fourier_track(707)
+    p = S.params_fullscale()
+    T, K = 60, 200
+    x, y, psi = S.pose_at(td, 900.0, 1.0)
+    x0 = np.float32([x, y, psi + np.pi, 50.0])
+    rng = np.random.default_rng(707)
+    u_nom = np.float32(np.stack([rng.normal(0, 1, T), rng.normal(0, 0.01, T)], 1))
+    opp = []
+    for ds, d in ((-20.0, -3.0), (15.0, 2.5), (40.0, 0.0)):
+        ox, oy, op = S.pose_at(td, 900.0 + ds, d)
+        opp.append(S.constant_velocity_prediction([ox, oy, op + np.pi, 50.0], T, p["dt"]))
+    g, o, _ = run_both(td, p, x0, u_nom, 1.0, np.stack(opp), T, K, seed=11, rnd=2, game_on=True)
+    assert_rel_close(g["states"], o["states"], STATE_RTOL, "states")
+    assert_frenet_close(g["frenet"], o["frenet"], o["states"])
+    check_candidates(g, o, "reversed", pos_scale=float(np.abs(td.xr[:, :2]).max()))

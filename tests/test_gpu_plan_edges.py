@@ -33,3 +33,18 @@ def test_plan_edge_cases_teacher_forced(n_v, T, K, L, seed, n_check):
         assert (g["k_star"] == 0).all()
     teacher_forced_check(sc, p, g, K, L, seed=seed, n_check=n_check)
     np.testing.assert_array_equal(g["U"], g["u_hist"][L + 1])
+
+
+def test_plan_with_a_vehicle_facing_backwards():
+    """One vehicle of a three-car race faces against the track direction at
+    50 m/s, so its nominal and selected trajectories run about 95 segments
+    backwards: the plan must report a clean status and every response must
+    match the oracle's (teacher-forced)."""
+    T, K, L = 60, 256, 1
+    sc = S.grid_race(S.fourier_track(708), 3, T, K, L, 709)
+    sc.X0[1, 2] += np.float32(np.pi)
+    sc.X0[1, 3] = np.float32(50.0)
+    p = S.params_fullscale()
+    g = gpu_plan(sc, p, K, L, seed=4)
+    assert g["status"][0] == 0
+    teacher_forced_check(sc, p, g, K, L, seed=4)
