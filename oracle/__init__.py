@@ -14,6 +14,8 @@ ctypes.  Every entry point mirrors a step of the paper:
 * :func:`rollout_costs`      per-candidate cost (Eq. allc), flags (Eq. selection), violation
 * :func:`best_response`      one best response with selection and fallback (Sec. III-B)
 * :func:`ibr_plan`           the SGTP planning call (Alg. 1)
+* :func:`best_response_mppi` GA-IBR-MPPI best response: path-integral update (Sec. IV-A ablation)
+* :func:`ibr_plan_mppi`      the GA-IBR-MPPI planning call
 
 Parity status of each function is listed in the header of ``sgtp_oracle.c``'s
 tests (``tests/test_oracle_*.py``).
@@ -99,6 +101,13 @@ def lib():
         L.orc_ibr_plan.argtypes = [
             C.POINTER(OrcParams), dp, dp, dp, C.c_int, C.c_int, dp, dp, dp, C.c_int, C.c_int, C.c_int,
             C.c_int, C.c_uint64, C.c_uint32, dp, C.POINTER(C.c_int), dp, dp, C.c_int]
+        L.orc_best_response_mppi.argtypes = [
+            C.POINTER(OrcParams), dp, dp, dp, C.c_int, dp, dp, C.c_double, dp, C.c_int, C.c_int, C.c_int,
+            C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int, C.c_double, C.POINTER(C.c_int), dp, dp, dp,
+            C.c_int]
+        L.orc_ibr_plan_mppi.argtypes = [
+            C.POINTER(OrcParams), dp, dp, dp, C.c_int, C.c_int, dp, dp, dp, C.c_int, C.c_int, C.c_int,
+            C.c_int, C.c_uint64, C.c_uint32, C.c_double, dp, C.POINTER(C.c_int), dp, dp, C.c_int]
         L.orc_reference.argtypes = [C.POINTER(OrcParams), dp, dp, dp, C.c_int, dp, C.c_double, C.c_int, dp]
         L.orc_rollout.argtypes = [C.POINTER(OrcParams), dp, dp, C.c_int, dp]
         L.orc_std_normals_batch.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
@@ -302,6 +311,49 @@ def ibr_plan(params, track: Track, X0, U_nom, vref_scale, T, K, L, ego, seed=0, 
     rc = lib().orc_ibr_plan(C.byref(make_params(params)), *track.args(), n_v, _p(X0), _p(U), _p(vs), T, K, L, ego,
                             seed, race, _p(xi), ks.ctypes.data_as(C.POINTER(C.c_int)), _p(xh), _p(uh),
                             _nthreads(nthreads))
+    assert rc == 0
+    out = dict(xi=xi, u_nom=U, k_star=ks)
+    if want_hist:
+        out["xi_hist"] = xh
+        out["u_hist"] = uh
+    return out
+
+
+def best_response_mppi(params, track: Track, x0, u_nom, vref_scale, opp, T, K, lam, seed=0, race=0, agent=0, rnd=0,
+                       game_on=True, want_costs=False, nthreads=None):
+    """One GA-IBR-MPPI best response at temperature ``lam``: the
+    importance-weighted mean of the K sampled control sequences
+    (``u_new``), its rollout (``xi_new``) and the lowest-cost sample."""
+    opp = _d(opp).reshape(-1, T + 1, 4) if opp is not None and np.size(opp) else np.zeros((0, T + 1, 4))
+    km = C.c_int()
+    u_new = np.zeros((T, 2)); xi = np.zeros((T + 1, 4))
+    costs = np.zeros(K) if want_costs else None
+    rc = lib().orc_best_response_mppi(
+        C.byref(make_params(params)), *track.args(), _p(_d(x0)), _p(_d(u_nom)), float(np.float32(vref_scale)),
+        _p(opp) if opp.shape[0] else None, opp.shape[0], T, K, seed, race, agent, rnd, int(bool(game_on)),
+        float(lam), C.byref(km), _p(u_new), _p(xi), _p(costs), _nthreads(nthreads))
+    assert rc == 0
+    out = dict(k_min=km.value, u_new=u_new, xi_new=xi)
+    if want_costs:
+        out["costs"] = costs
+    return out
+
+
+def ibr_plan_mppi(params, track: Track, X0, U_nom, vref_scale, T, K, L, ego, lam, seed=0, race=0, nthreads=None,
+                  want_hist=False):
+    """The GA-IBR-MPPI planning call: :func:`ibr_plan` with the
+    path-integral update at temperature ``lam``."""
+    X0 = _d(X0).reshape(-1, 4)
+    n_v = X0.shape[0]
+    U = _d(U_nom).reshape(n_v, T, 2).copy()
+    vs = _d([float(np.float32(v)) for v in vref_scale])
+    xi = np.zeros((n_v, T + 1, 4))
+    ks = np.zeros((L + 1) * n_v + 1, dtype=np.int32)
+    xh = np.zeros((L + 2, n_v, T + 1, 4)) if want_hist else None
+    uh = np.zeros((L + 2, n_v, T, 2)) if want_hist else None
+    rc = lib().orc_ibr_plan_mppi(C.byref(make_params(params)), *track.args(), n_v, _p(X0), _p(U), _p(vs), T, K, L,
+                                 ego, seed, race, float(lam), _p(xi), ks.ctypes.data_as(C.POINTER(C.c_int)), _p(xh),
+                                 _p(uh), _nthreads(nthreads))
     assert rc == 0
     out = dict(xi=xi, u_nom=U, k_star=ks)
     if want_hist:

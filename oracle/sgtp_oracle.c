@@ -629,24 +629,83 @@ static void nominal_rollout(const orc_params *p, const double *x0, const double 
     }
 }
 
-/* The SGTP planning call (Alg. 1).
+/* GA-IBR-MPPI best response (Sec. IV-A, the second ablation): the same K
+ * samples, rollouts, tracking cost and game-aware cost as the SGTP best
+ * response, but no feasibility selection.  The nominal sequence becomes the
+ * path-integral (importance-weighted) mean of the sampled controls, the
+ * update of standard MPPI that the paper cites:
+ *     w_k = exp(-(c_k - c_min) / lambda),   U_new = sum_k w_k U^(k) / sum_k w_k.
+ * The paper gives no temperature; lambda is an input.  Readings: U^(k) are
+ * the clipped controls sample k was rolled out with, so U_new is admissible;
+ * a sample whose cost is not finite weighs nothing, and when no sample has a
+ * finite cost the clipped nominal is kept; the new trajectory xi_new
+ * ((T+1)x4) is the rollout of U_new; k_min is the lowest-cost sample (lowest
+ * index on ties), reported for inspection only.  cost_out (K, may be NULL)
+ * receives every sample's cost. */
+int orc_best_response_mppi(const orc_params *p, const double *xr, const double *wl, const double *wr, int N,
+                           const double *x0, const double *u_nom, double vref_scale, const double *opp, int n_opp,
+                           int T, int K, uint64_t seed, uint32_t race, uint32_t agent, uint32_t round, int game_on,
+                           double lambda, int *k_min, double *u_new, double *xi_new, double *cost_out, int nthreads)
+{
+    orc_problem P;
+    if (K < 1 || !(lambda > 0.0)) return -1;
+    if (setup_problem(&P, p, xr, wl, wr, N, x0, u_nom, vref_scale, opp, n_opp, T, seed, race, agent, round, 0,
+                      game_on, 0))
+        return -1;
+    double *cost = (double *)malloc(sizeof(double) * (size_t)K);
+    double *viol = (double *)malloc(sizeof(double) * (size_t)K);
+    unsigned char *feas = (unsigned char *)malloc((size_t)K);
+    double *u = (double *)malloc(sizeof(double) * (size_t)T * 2);
+    run_jobs(&P, NULL, K, nthreads, cost, feas, viol, NULL, NULL, NULL, NULL, NULL, NULL);
+    int kb = -1;
+    double c_min = INFINITY;
+    for (int k = 0; k < K; ++k)
+        if (isfinite(cost[k]) && cost[k] < c_min) { c_min = cost[k]; kb = k; }
+    *k_min = kb;
+    if (kb < 0) {
+        for (int tau = 0; tau < T; ++tau) {
+            u_new[2 * tau] = clampd(u_nom[2 * tau], p->a_min, p->a_max);
+            u_new[2 * tau + 1] = clampd(u_nom[2 * tau + 1], -p->delta_max, p->delta_max);
+        }
+    } else {
+        double w_sum = 0.0;
+        for (int q = 0; q < 2 * T; ++q) u_new[q] = 0.0;
+        for (int k = 0; k < K; ++k) {
+            if (!isfinite(cost[k])) continue;
+            const double w = exp(-(cost[k] - c_min) / lambda);
+            sample_controls(&P, (uint32_t)k, u);
+            for (int q = 0; q < 2 * T; ++q) u_new[q] += w * u[q];
+            w_sum += w;
+        }
+        for (int q = 0; q < 2 * T; ++q) u_new[q] /= w_sum;
+    }
+    eval_candidate(&P, u_new, xi_new, NULL);
+    if (cost_out) memcpy(cost_out, cost, sizeof(double) * (size_t)K);
+    free(u); free(cost); free(viol); free(feas);
+    teardown_problem(&P);
+    return 0;
+}
+
+/* The planning loop of Alg. 1, shared by both update rules.
  *   round 0: every vehicle best-responds, without the game term, to the
  *            others' nominal rollouts (Alg. 1 initialisation, read as the
  *            feasibility-selected tracking response);
  *   rounds 1..L: Jacobi iterative best response against the previous round;
  *   finally one extra ego response (round tag L+1) against round L.
  * After each best response the vehicle's nominal controls become the
- * selected ones (warm start).  xi_out holds round-L trajectories, except
- * the ego's, which is its extra response.  k_star_out has (L+1)*n_v+1
- * entries: round-major, then the extra ego response.  xi_hist (optional)
- * has (L+2) x n_v x (T+1) x 4 entries: slot r holds the round-r trajectory
- * of every vehicle; slot L+1 holds round L again except the ego's extra
- * response.  u_hist likewise with (L+2) x n_v x T x 2 nominal controls
- * after each round. */
-int orc_ibr_plan(const orc_params *p, const double *xr, const double *wl, const double *wr, int N, int n_v,
-                 const double *X0, double *U_io, const double *vref_scale, int T, int K, int L, int ego,
-                 uint64_t seed, uint32_t race, double *xi_out, int *k_star_out, double *xi_hist,
-                 double *u_hist, int nthreads)
+ * response's controls (warm start): the selected sample's (SGTP, lambda <= 0)
+ * or the path-integral mean (GA-IBR-MPPI, lambda > 0).  xi_out holds
+ * round-L trajectories, except the ego's, which is its extra response.
+ * k_star_out has (L+1)*n_v+1 entries: round-major, then the extra ego
+ * response (the selected sample; for GA-IBR-MPPI the lowest-cost one).
+ * xi_hist (optional) has (L+2) x n_v x (T+1) x 4 entries: slot r holds the
+ * round-r trajectory of every vehicle; slot L+1 holds round L again except
+ * the ego's extra response.  u_hist likewise with (L+2) x n_v x T x 2
+ * nominal controls after each round. */
+static int plan_loop(const orc_params *p, const double *xr, const double *wl, const double *wr, int N, int n_v,
+                     const double *X0, double *U_io, const double *vref_scale, int T, int K, int L, int ego,
+                     uint64_t seed, uint32_t race, double lambda, double *xi_out, int *k_star_out, double *xi_hist,
+                     double *u_hist, int nthreads)
 {
     if (n_v < 1 || n_v > 17 || ego < 0 || ego >= n_v || L < 0) return -1;
     const size_t traj = (size_t)(T + 1) * 4;
@@ -664,9 +723,15 @@ int orc_ibr_plan(const orc_params *p, const double *xr, const double *wl, const 
             for (int j = 0; j < n_v; ++j)
                 if (j != i) memcpy(opp + traj * (m++), xi + traj * j, sizeof(double) * traj);
             int ks, anyf;
-            rc = orc_best_response(p, xr, wl, wr, N, X0 + 4 * i, U_io + (size_t)i * T * 2, vref_scale[i], opp,
-                                   n_v - 1, T, K, seed, race, (uint32_t)i, (uint32_t)round, 0, round > 0, &ks,
-                                   u_new + (size_t)i * T * 2, xi_new + traj * i, &anyf, NULL, nthreads);
+            if (lambda > 0.0)
+                rc = orc_best_response_mppi(p, xr, wl, wr, N, X0 + 4 * i, U_io + (size_t)i * T * 2, vref_scale[i],
+                                            opp, n_v - 1, T, K, seed, race, (uint32_t)i, (uint32_t)round, round > 0,
+                                            lambda, &ks, u_new + (size_t)i * T * 2, xi_new + traj * i, NULL,
+                                            nthreads);
+            else
+                rc = orc_best_response(p, xr, wl, wr, N, X0 + 4 * i, U_io + (size_t)i * T * 2, vref_scale[i], opp,
+                                       n_v - 1, T, K, seed, race, (uint32_t)i, (uint32_t)round, 0, round > 0, &ks,
+                                       u_new + (size_t)i * T * 2, xi_new + traj * i, &anyf, NULL, nthreads);
             k_star_out[nk++] = ks;
         }
         /* Jacobi: all vehicles of the round updated together */
@@ -681,6 +746,28 @@ int orc_ibr_plan(const orc_params *p, const double *xr, const double *wl, const 
     memcpy(xi_out, xi, sizeof(double) * traj * (size_t)n_v);
     free(xi); free(xi_new); free(opp); free(u_new);
     return rc;
+}
+
+/* The SGTP planning call (Alg. 1): plan_loop with feasibility selection. */
+int orc_ibr_plan(const orc_params *p, const double *xr, const double *wl, const double *wr, int N, int n_v,
+                 const double *X0, double *U_io, const double *vref_scale, int T, int K, int L, int ego,
+                 uint64_t seed, uint32_t race, double *xi_out, int *k_star_out, double *xi_hist,
+                 double *u_hist, int nthreads)
+{
+    return plan_loop(p, xr, wl, wr, N, n_v, X0, U_io, vref_scale, T, K, L, ego, seed, race, 0.0, xi_out,
+                     k_star_out, xi_hist, u_hist, nthreads);
+}
+
+/* The GA-IBR-MPPI planning call (Sec. IV-A ablation): the same loop with the
+ * path-integral update of orc_best_response_mppi at temperature lambda > 0. */
+int orc_ibr_plan_mppi(const orc_params *p, const double *xr, const double *wl, const double *wr, int N, int n_v,
+                      const double *X0, double *U_io, const double *vref_scale, int T, int K, int L, int ego,
+                      uint64_t seed, uint32_t race, double lambda, double *xi_out, int *k_star_out,
+                      double *xi_hist, double *u_hist, int nthreads)
+{
+    if (!(lambda > 0.0)) return -1;
+    return plan_loop(p, xr, wl, wr, N, n_v, X0, U_io, vref_scale, T, K, L, ego, seed, race, lambda, xi_out,
+                     k_star_out, xi_hist, u_hist, nthreads);
 }
 
 /* Exposed pieces used by the oracle's own checks. */
