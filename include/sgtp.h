@@ -280,6 +280,48 @@ sgtp_status sgtp_ibr_plan(const sgtp_track *trk, int32_t track_id, const sgtp_pa
                           void *workspace, size_t workspace_bytes, void *stream);
 
 /* ------------------------------------------------------------------ */
+/* GA-IBR-MPPI: the paper's second ablation (Sec. IV-A)                 */
+/* ------------------------------------------------------------------ */
+/* The same planning loop, samples, rollouts and game-aware cost as
+ * sgtp_ibr_plan, but no feasibility selection: after each best response the
+ * vehicle's nominal controls become the path-integral mean of its samples'
+ * (clipped) controls, the update of standard MPPI,
+ *     w_k = exp(-(c_k - c_min) / lambda),  U_new = sum_k w_k U^(k) / sum_k w_k,
+ * with c_k the total cost (Eq. allc; round 0 without the game term), and
+ * the response's trajectory is the rollout of U_new.  The paper gives no
+ * temperature: lambda > 0 (in cost units) is an argument.  A sample whose
+ * cost is not finite weighs nothing; if no sample of a response has a finite
+ * cost, the clipped nominal is kept.  k_star_out receives each response's
+ * lowest-cost sample (lowest k on ties), for inspection only.
+ *   - Arrays, layouts, ownership, rounds and the status word are those of
+ *     sgtp_ibr_plan; the workspace is sgtp_plan_mppi_workspace_bytes (it
+ *     grows with K: one partial sum of 2T+2 floats per 256-sample tile).
+ *   - Sums are formed in a fixed order (32-sample groups by warp shuffles,
+ *     then groups, then tiles in index order, each tile's weights taken
+ *     relative to its own minimum and rescaled by exp(-(m_t - c_min)/lambda)),
+ *     so every launch shape gives bit-identical results.
+ *   - SGTP_E_INVALID (nothing launched) for lambda not > 0 or not finite,
+ *     and for the arguments sgtp_ibr_plan rejects. */
+size_t sgtp_plan_mppi_workspace_bytes(int32_t n_v, int32_t T, int32_t L, int32_t K);
+
+sgtp_status sgtp_ibr_plan_mppi(const sgtp_track *trk, int32_t track_id, const sgtp_params *p, int32_t n_v,
+                               const float *X0, float *U_io, const float *vref_scale, int32_t T, int32_t K,
+                               int32_t L, int32_t ego, uint64_t seed, uint32_t race, float lambda, float *xi_out,
+                               int32_t *k_star_out, float *xi_hist, float *u_hist, int32_t *status_dev,
+                               const sgtp_launch_opts *opts, void *workspace, size_t workspace_bytes,
+                               void *stream);
+
+/* The same for every race of a batch in one launch (sgtp_batch_plan's
+ * arrays); its workspace size comes from sgtp_batch_mppi_workspace_bytes. */
+sgtp_status sgtp_batch_mppi_workspace_bytes(const sgtp_batch *b, size_t *workspace_bytes);
+
+sgtp_status sgtp_batch_plan_mppi(const sgtp_batch *b, const sgtp_params *p, float lambda, const float *X0,
+                                 float *U_io, const float *vref_scale, uint64_t seed, float *xi_out,
+                                 int32_t *k_star_out, float *xi_hist, float *u_hist, int32_t *status_dev,
+                                 const sgtp_launch_opts *opts, void *workspace, size_t workspace_bytes,
+                                 void *stream);
+
+/* ------------------------------------------------------------------ */
 /* CUDA graphs of planning calls                                        */
 /* ------------------------------------------------------------------ */
 typedef struct sgtp_graph sgtp_graph;   /* opaque, library owned */

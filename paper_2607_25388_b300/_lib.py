@@ -99,6 +99,13 @@ def lib():
                                                C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(sz)]
                 L.sgtp_batch_plan.argtypes = [vp, C.POINTER(Params), vp, vp, vp, u64, vp, vp, vp, vp, vp,
                                               C.POINTER(LaunchOpts), vp, sz, vp]
+            L.sgtp_plan_mppi_workspace_bytes.argtypes = [i32, i32, i32, i32]
+            L.sgtp_plan_mppi_workspace_bytes.restype = sz
+            L.sgtp_ibr_plan_mppi.argtypes = [vp, i32, C.POINTER(Params), i32, vp, vp, vp, i32, i32, i32, i32, u64,
+                                             u32, f32, vp, vp, vp, vp, vp, C.POINTER(LaunchOpts), vp, sz, vp]
+            L.sgtp_batch_mppi_workspace_bytes.argtypes = [vp, C.POINTER(sz)]
+            L.sgtp_batch_plan_mppi.argtypes = [vp, C.POINTER(Params), f32, vp, vp, vp, u64, vp, vp, vp, vp, vp,
+                                               C.POINTER(LaunchOpts), vp, sz, vp]
             L.sgtp_graph_capture_plan.argtypes = [vp, i32, C.POINTER(Params), i32, vp, vp, vp, i32, i32, i32, i32,
                                                   u64, u32, vp, vp, vp, vp, vp, C.POINTER(LaunchOpts), vp, sz,
                                                   C.POINTER(vp)]
@@ -152,6 +159,8 @@ EXPORTS = [
     "sgtp_mlp_param_count", "sgtp_mlp_create", "sgtp_mlp_destroy", "sgtp_mlp_reserve", "sgtp_mlp_forward",
     "sgtp_mlp_proposal", "sgtp_mlp_train_step", "sgtp_mlp_get_params", "sgtp_mlp_set_params", "sgtp_mlp_info",
     "sgtp_best_response_mixed", "sgtp_ibr_plan_learned", "sgtp_batch_plan_learned",
+    "sgtp_plan_mppi_workspace_bytes", "sgtp_ibr_plan_mppi", "sgtp_batch_mppi_workspace_bytes",
+    "sgtp_batch_plan_mppi",
 ]
 
 

@@ -85,6 +85,9 @@ struct PlanArgs {
     float4 *prop;                  // per vehicle: maxT steps (mean a, mean delta, sigma a, sigma delta)
     float *feat_out;               // optional: (L+2) x n_agents x 64 features of each best response
     float4 *prop_out;              // optional: (L+2) x n_agents x maxT proposals of each best response
+    // GA-IBR-MPPI (mppi_il > 0): path-integral update instead of selection
+    float mppi_il;                 // 1 / lambda
+    float *mppi_part;              // per vehicle x tile: m_t, sum w u (2T), sum w; stride 2 maxT + 2
 };
 
 __device__ __forceinline__ void stamp(const PlanArgs &a, int i)
@@ -408,11 +411,148 @@ __device__ void proposal_for(const PlanArgs &a, const RaceDev &R, int i, int bin
     }
 }
 
+// ---------------------------------------------------------------- GA-IBR-MPPI
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Path-integral partial sums of one tile of kTileSingle samples (all threads
+// of the CTA; the tile's costs are in Tl::st() as floats, +inf for a
+// non-finite cost or k >= K).  With m_t the tile's minimum cost, every sample
+// weighs w = exp((m_t - c) / lambda) and its clipped controls are drawn again
+// from the same counter; w u is summed over each 32-sample group by a
+// shuffle butterfly over lanes (lane = k mod 32), then over the groups in
+// order, so the sums depend on k alone, not on the launch shape.  Output
+// row of mppi_part: [0] m_t, [1 + 2 tau + c] sum w u_tau,c, [1 + 2T] sum w.
+// Group sums are kept in the C window, which only the setup phase uses.
+template <int MAXO>
+__device__ void mppi_tile(const PlanArgs &a, int t, int ag, int T)
+{
+    using Tl = Tile<MAXO>;
+    constexpr int kGroups = kTileSingle / 32;
+    const BRScalars &S = Tl::sc();
+    float *mc = (float *)Tl::st();
+    float *gw = mc + kTileSingle;
+    float *grp = (float *)Tl::C();
+    __shared__ float m_sh;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (warp == 0) {
+        float m = __int_as_float(0x7f800000);
+        for (int q = lane; q < kTileSingle; q += 32) m = fminf(m, mc[q]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) m_sh = m;
+    }
+    __syncthreads();
+    const float m = m_sh;
+    const float4 *dist = Tl::dist();
+    for (unsigned j = threadIdx.x; j < (unsigned)kTileSingle; j += blockDim.x) {
+        const unsigned k = (unsigned)t * kTileSingle + j;
+        const float c = mc[j];
+        const float w = c <= 3.402823466e38f ? expf(__fmul_rn(m - c, a.mppi_il)) : 0.f;
+        float *gs = grp + (j >> 5) * (2 * T);
+        for (int mm = 0; 2 * mm < T; ++mm) {
+            float2 z0, z1;
+            noise_pair(S, a.key, k, S.stream_bit, mm, z0, z1);
+            const int t0 = 2 * mm;
+            const float2 u0 = sample_control_d(a.p, dist[t0], z0);
+            float v0 = __fmul_rn(w, u0.x), v1 = __fmul_rn(w, u0.y), v2 = 0.f, v3 = 0.f;
+            if (t0 + 1 < T) {
+                const float2 u1 = sample_control_d(a.p, dist[t0 + 1], z1);
+                v2 = __fmul_rn(w, u1.x);
+                v3 = __fmul_rn(w, u1.y);
+            }
+            v0 = warp_sum(v0); v1 = warp_sum(v1); v2 = warp_sum(v2); v3 = warp_sum(v3);
+            if (lane == 0) {
+                gs[2 * t0] = v0;
+                gs[2 * t0 + 1] = v1;
+                if (t0 + 1 < T) { gs[2 * t0 + 2] = v2; gs[2 * t0 + 3] = v3; }
+            }
+        }
+        const float ws = warp_sum(w);
+        if (lane == 0) gw[j >> 5] = ws;
+    }
+    __syncthreads();
+    float *out = a.mppi_part + ((size_t)ag * a.tiles + t) * (size_t)(2 * a.maxT + 2);
+    for (int v = threadIdx.x; v <= 2 * T; v += blockDim.x) {
+        float acc = 0.f;
+#pragma unroll
+        for (int g = 0; g < kGroups; ++g) acc += v < 2 * T ? grp[g * 2 * T + v] : gw[g];
+        out[1 + v] = acc;
+    }
+    if (threadIdx.x == 0) out[0] = m;
+    __syncthreads();
+}
+
+// The GA-IBR-MPPI update of vehicle ag (all threads of the CTA): c_min =
+// min_t m_t, then sum_t exp((c_min - m_t) / lambda) x row_t over the tiles in
+// index order (factors staged in the C window in chunks), and U-bar <-
+// sum w u / sum w, clipped (rounding may leave the box by an ulp).  With no
+// finite cost the clipped nominal is kept.  Writes Tl::ctl(), U_io, u_hist.
+template <int MAXO>
+__device__ void mppi_update(const PlanArgs &a, int ag, int T, size_t uo, int round)
+{
+    using Tl = Tile<MAXO>;
+    constexpr int kChunk = 4 * kWinTile;
+    const size_t stride = (size_t)(2 * a.maxT + 2);
+    const float *part = a.mppi_part + (size_t)ag * a.tiles * stride;
+    float *acc = (float *)Tl::st();
+    float *e = (float *)Tl::C();
+    __shared__ float red_sh[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    float ml = __int_as_float(0x7f800000);
+    for (int q = threadIdx.x; q < a.tiles; q += blockDim.x) ml = fminf(ml, __ldcg(part + (size_t)q * stride));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ml = fminf(ml, __shfl_xor_sync(0xffffffffu, ml, o));
+    if (lane == 0) red_sh[warp] = ml;
+    for (int v = threadIdx.x; v <= 2 * T; v += blockDim.x) acc[v] = 0.f;
+    __syncthreads();
+    float cmin = red_sh[0];
+    for (int w = 1; w < nwarps; ++w) cmin = fminf(cmin, red_sh[w]);
+    for (int base = 0; base < a.tiles; base += kChunk) {
+        const int n = min(kChunk, a.tiles - base);
+        __syncthreads();
+        for (int q = threadIdx.x; q < n; q += blockDim.x) {
+            const float mt = __ldcg(part + (size_t)(base + q) * stride);
+            e[q] = mt <= 3.402823466e38f ? expf(__fmul_rn(cmin - mt, a.mppi_il)) : 0.f;
+        }
+        __syncthreads();
+        for (int v = threadIdx.x; v <= 2 * T; v += blockDim.x) {
+            const float *pv = part + (size_t)base * stride + 1 + v;
+            float sum = acc[v];
+#pragma unroll 8
+            for (int q = 0; q < n; ++q) sum = __fmaf_rn(e[q], __ldcg(pv + (size_t)q * stride), sum);
+            acc[v] = sum;
+        }
+    }
+    __syncthreads();
+    const float W = acc[2 * T];
+    const bool ok = cmin <= 3.402823466e38f && W > 0.f;
+    for (int q = threadIdx.x; q < T; q += blockDim.x) {
+        const float2 ubar = ok ? make_float2(__fdiv_rn(acc[2 * q], W), __fdiv_rn(acc[2 * q + 1], W))
+                               : make_float2(__ldcg(a.U_io + uo + 2 * q), __ldcg(a.U_io + uo + 2 * q + 1));
+        const float2 u = sample_control(a.p, ubar, make_float2(0.f, 0.f));
+        Tl::ctl()[q] = u;
+        a.U_io[uo + 2 * q] = u.x;
+        a.U_io[uo + 2 * q + 1] = u.y;
+        if (a.u_hist) {
+            a.u_hist[(size_t)round * a.u_total + uo + 2 * q] = u.x;
+            a.u_hist[(size_t)round * a.u_total + uo + 2 * q + 1] = u.y;
+        }
+    }
+}
+
 // MINB is the number of resident CTAs of 256 threads per SM the build is
 // sized for: 3 (80 registers, for plans with many sample tiles per round) or
 // 2 (128 registers, no spills, for plans with few tiles, where the latency
 // of one rollout dominates).  Both compute every sample with the same code.
-template <int MAXO, int MINB>
+// MPPI selects the GA-IBR-MPPI update (a build of its own, so that the SGTP
+// builds carry none of its code).
+template <int MAXO, int MINB, bool MPPI>
 __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
 {
     using Tl = Tile<MAXO>;
@@ -571,19 +711,26 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
                 __syncthreads();
                 if (abort_sh) { ok = false; break; }
             }
-            // a tile of kTileSingle samples, kTileSingle / blockDim.x per thread
+            // a tile of kTileSingle samples, kTileSingle / blockDim.x per thread;
+            // GA-IBR-MPPI keys every sample as feasible (its k* is the lowest
+            // cost) and keeps the tile's costs for its partial sums
+            constexpr bool mppi = MPPI;
             unsigned long long best = ~0ull;
             for (unsigned j = threadIdx.x; j < (unsigned)kTileSingle; j += blockDim.x) {
                 const unsigned k = (unsigned)t * kTileSingle + j;
+                float c = __int_as_float(0x7f800000);
                 if (k < (unsigned)a.K) {
                     const SampleResult r = run_candidate<MAXO, false>(S, a.p, a.key, k, round > 0, flag, nullptr,
                                                                       nullptr, nullptr);
-                    const unsigned long long key = make_key(r.feasible, r.cost, r.viol, k);
+                    const unsigned long long key = make_key(r.feasible || mppi, r.cost, r.viol, k);
                     best = key < best ? key : best;
+                    if (fabsf(r.cost) <= 3.402823466e38f) c = r.cost;
                 }
+                if constexpr (MPPI) ((float *)Tl::st())[j] = c;
             }
             best = warp_min_u64(best);
             if (lane == 0) atomicMin(&cta_key, best);
+            if constexpr (MPPI) mppi_tile<MAXO>(a, t, ag, R.T);
         }
         if (!ok) break;
         __syncthreads();
@@ -620,11 +767,13 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
             }
             __syncthreads();
             // controls of the selected sample, one step per thread (same noise,
-            // same clipping as its evaluation): warm start U-bar <- U^(k*)
+            // same clipping as its evaluation): warm start U-bar <- U^(k*);
+            // GA-IBR-MPPI: U-bar <- the path-integral mean
             const unsigned ks = ks_sh;
             const unsigned ar = (unsigned)i | ((unsigned)round << 16);
             const bool from_prop = a.mlp_wb && ks < (unsigned)a.K_prop;
-            for (int q = threadIdx.x; q < T; q += blockDim.x) {
+            if constexpr (MPPI) mppi_update<MAXO>(a, ag, T, uo, round);
+            else for (int q = threadIdx.x; q < T; q += blockDim.x) {
                 const unsigned sbit = from_prop ? 0x80000000u : 0u;
                 const uint4 wv = philox4x32_10(make_uint4(ks, (unsigned)(q >> 1) | sbit, ar, R.race_tag), a.key);
                 const float2 z = (q & 1) ? box_muller(wv.z, wv.w) : box_muller(wv.x, wv.y);
@@ -659,8 +808,9 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
 
 // ================================================================ host side
 struct Layout {
-    size_t bar, keys, agents, ref, pos0, pos1, summ0, summ1, prop, total;
-    Layout(long long n_keys, long long n_agents, long long n_pos, int maxT)
+    size_t bar, keys, agents, ref, pos0, pos1, summ0, summ1, prop, part, total;
+    // part_floats: GA-IBR-MPPI partial sums (0 for the SGTP calls)
+    Layout(long long n_keys, long long n_agents, long long n_pos, int maxT, long long part_floats = 0)
     {
         auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
         bar = 0;
@@ -672,18 +822,19 @@ struct Layout {
         summ0 = up(pos1 + sizeof(float2) * n_pos);
         summ1 = up(summ0 + sizeof(float2) * n_agents);
         prop = up(summ1 + sizeof(float2) * n_agents);
-        total = up(prop + sizeof(float4) * n_agents * maxT);
+        part = up(prop + sizeof(float4) * n_agents * maxT);
+        total = up(part + sizeof(float) * part_floats);
     }
 };
 
 int maxo_bucket(int n) { return n <= 1 ? 1 : n <= 3 ? 3 : n <= 9 ? 9 : 15; }
 
-template <int MAXO, int MINB>
+template <int MAXO, int MINB, bool MPPI>
 sgtp_status configure_plan_t()
 {
     static std::atomic<int> configured{0};
     if (!configured.load()) {
-        SGTP_CUDA(cudaFuncSetAttribute(plan_kernel<MAXO, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        SGTP_CUDA(cudaFuncSetAttribute(plan_kernel<MAXO, MINB, MPPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024));
         configured.store(1);
     }
@@ -693,30 +844,31 @@ sgtp_status configure_plan_t()
 sgtp_status configure_plan_kernels()
 {
     sgtp_status st;
-    if ((st = configure_plan_t<1, 2>()) || (st = configure_plan_t<3, 2>()) || (st = configure_plan_t<9, 2>()) ||
-        (st = configure_plan_t<15, 2>()) || (st = configure_plan_t<1, 3>()) || (st = configure_plan_t<3, 3>()) ||
-        (st = configure_plan_t<9, 3>()) || (st = configure_plan_t<15, 3>()))
+    if ((st = configure_plan_t<1, 2, false>()) || (st = configure_plan_t<3, 2, false>()) ||
+        (st = configure_plan_t<9, 2, false>()) || (st = configure_plan_t<15, 2, false>()) ||
+        (st = configure_plan_t<1, 3, false>()) || (st = configure_plan_t<3, 3, false>()) ||
+        (st = configure_plan_t<9, 3, false>()) || (st = configure_plan_t<15, 3, false>()))
         return st;
     return SGTP_OK;
 }
 
-template <int MAXO, int MINB>
+template <int MAXO, int MINB, bool MPPI>
 sgtp_status launch_plan_v(PlanArgs &a, int block, int ctas, cudaStream_t s)
 {
     const size_t smem = BRTile<MAXO>::kBytes;
-    sgtp_status cst = configure_plan_t<MAXO, MINB>();
+    sgtp_status cst = configure_plan_t<MAXO, MINB, MPPI>();
     if (cst) return cst;
     int dev = 0, sms = 0, per_sm = 0;
     SGTP_CUDA(cudaGetDevice(&dev));
     SGTP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    SGTP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_kernel<MAXO, MINB>, block, smem));
+    SGTP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_kernel<MAXO, MINB, MPPI>, block, smem));
     SGTP_CHECK(per_sm >= 1, "plan kernel does not fit on an SM (smem %zu)", smem);
     if (ctas > 0 && ctas < per_sm) per_sm = ctas;
     const int grid = sms * per_sm;
     void *args[] = {&a};
     SGTP_CUDA(cudaMemsetAsync(a.bar, 0, 256, s));
     SGTP_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), s));
-    SGTP_CUDA(cudaLaunchCooperativeKernel((const void *)plan_kernel<MAXO, MINB>, grid, block, args, smem, s));
+    SGTP_CUDA(cudaLaunchCooperativeKernel((const void *)plan_kernel<MAXO, MINB, MPPI>, grid, block, args, smem, s));
     count_launch();
     return SGTP_OK;
 }
@@ -740,7 +892,9 @@ sgtp_status launch_plan_t(PlanArgs &a, const sgtp_launch_opts *opts, cudaStream_
     if (ctas > 0) wide = ctas * block <= 512;
     else wide = (long long)a.items_all < 3ll * sms;
     if (wide && ctas == 0) ctas = 512 / block;
-    return wide ? launch_plan_v<MAXO, 2>(a, block, ctas, s) : launch_plan_v<MAXO, 3>(a, block, ctas, s);
+    if (a.mppi_il > 0.f)
+        return wide ? launch_plan_v<MAXO, 2, true>(a, block, ctas, s) : launch_plan_v<MAXO, 3, true>(a, block, ctas, s);
+    return wide ? launch_plan_v<MAXO, 2, false>(a, block, ctas, s) : launch_plan_v<MAXO, 3, false>(a, block, ctas, s);
 }
 
 sgtp_status launch_plan(PlanArgs &a, int max_opp, const sgtp_launch_opts *opts, cudaStream_t s)
@@ -793,6 +947,20 @@ void attach_workspace(PlanArgs &a, const Layout &lay, void *ws)
     a.summ[0] = (float2 *)(w + lay.summ0);
     a.summ[1] = (float2 *)(w + lay.summ1);
     a.prop = (float4 *)(w + lay.prop);
+    a.mppi_part = (float *)(w + lay.part);
+}
+
+long long mppi_part_floats(long long n_agents, int K, int maxT)
+{
+    return n_agents * (long long)((K + kTileSingle - 1) / kTileSingle) * (2ll * maxT + 2);
+}
+
+// 1 / lambda of a GA-IBR-MPPI call, or -1 when lambda is not finite and > 0
+float mppi_inverse(float lambda)
+{
+    if (!(lambda > 0.f) || !(lambda <= 3.402823466e38f)) return -1.f;
+    const double il = 1.0 / (double)lambda;
+    return (float)(il < 3.402823466e38 ? il : 3.402823466e38);
 }
 
 }  // namespace
@@ -817,7 +985,7 @@ static sgtp_status ibr_plan_impl(const sgtp_track *trk, int32_t track_id, const 
                                  int32_t ego, uint64_t seed, uint32_t race, float *xi_out, int32_t *k_star_out,
                                  float *xi_hist, float *u_hist, int32_t *status_dev, const sgtp_launch_opts *opts,
                                  const sgtp_mlp *mlp, int32_t K_prop, float *feat_out, float *prop_out,
-                                 void *workspace, size_t workspace_bytes, void *stream)
+                                 void *workspace, size_t workspace_bytes, void *stream, float mppi_lambda = 0.f)
 {
     SGTP_CHECK(trk != nullptr, "track is NULL");
     SGTP_CHECK(track_id >= 0 && track_id < trk->n_tracks, "track_id out of range");
@@ -830,11 +998,17 @@ static sgtp_status ibr_plan_impl(const sgtp_track *trk, int32_t track_id, const 
     SGTP_CHECK(ego >= 0 && ego < n_v, "ego out of range");
     SGTP_CHECK(race < (1u << 31), "race tag out of range");
     SGTP_CHECK(X0 && U_io && vref_scale && xi_out && k_star_out && status_dev, "NULL array");
-    const Layout lay((long long)(L + 1) * n_v + 1, n_v, (long long)n_v * (T + 1), T);
+    const bool mppi = mppi_lambda != 0.f;
+    const float il = mppi ? mppi_inverse(mppi_lambda) : 0.f;
+    SGTP_CHECK(!mppi || il > 0.f, "lambda must be finite and > 0");
+    SGTP_CHECK(!(mppi && mlp), "GA-IBR-MPPI takes the plain sampler only");
+    const Layout lay((long long)(L + 1) * n_v + 1, n_v, (long long)n_v * (T + 1), T,
+                     mppi ? mppi_part_floats(n_v, K, T) : 0);
     SGTP_CHECK(workspace && workspace_bytes >= lay.total, "workspace too small: need %zu bytes", lay.total);
     SGTP_CHECK(((uintptr_t)workspace & 255u) == 0, "workspace must be 256-byte aligned");
     PlanArgs a{};
     fill_common(a, trk, p, K, L, X0, U_io, vref_scale, seed, xi_out, k_star_out, xi_hist, u_hist, status_dev, opts);
+    a.mppi_il = il;
     RaceDev &R = a.one;
     R = RaceDev{};
     R.track_id = track_id; R.n_v = n_v; R.T = T; R.ego = ego; R.race_tag = race;
@@ -890,6 +1064,25 @@ extern "C" sgtp_status sgtp_ibr_plan_learned(const sgtp_track *trk, int32_t trac
 }
 
 
+
+extern "C" size_t sgtp_plan_mppi_workspace_bytes(int32_t n_v, int32_t T, int32_t L, int32_t K)
+{
+    if (n_v < 1 || T < 1 || L < 0 || K < 1) return 0;
+    return Layout((long long)(L + 1) * n_v + 1, n_v, (long long)n_v * (T + 1), T, mppi_part_floats(n_v, K, T)).total;
+}
+
+extern "C" sgtp_status sgtp_ibr_plan_mppi(const sgtp_track *trk, int32_t track_id, const sgtp_params *p, int32_t n_v,
+                                          const float *X0, float *U_io, const float *vref_scale, int32_t T, int32_t K,
+                                          int32_t L, int32_t ego, uint64_t seed, uint32_t race, float lambda,
+                                          float *xi_out, int32_t *k_star_out, float *xi_hist, float *u_hist,
+                                          int32_t *status_dev, const sgtp_launch_opts *opts, void *workspace,
+                                          size_t workspace_bytes, void *stream)
+{
+    SGTP_CHECK(mppi_inverse(lambda) > 0.f, "lambda must be finite and > 0");
+    return ibr_plan_impl(trk, track_id, p, n_v, X0, U_io, vref_scale, T, K, L, ego, seed, race, xi_out, k_star_out,
+                         xi_hist, u_hist, status_dev, opts, nullptr, 0, nullptr, nullptr, workspace, workspace_bytes,
+                         stream, lambda);
+}
 
 extern "C" sgtp_status sgtp_batch_create(const sgtp_track *trk, const sgtp_race *races, int32_t n_races, int32_t K,
                                          int32_t L, sgtp_batch **out)
@@ -974,13 +1167,17 @@ static sgtp_status batch_plan_impl(const sgtp_batch *b, const sgtp_params *p, co
                                    const float *vref_scale, uint64_t seed, float *xi_out, int32_t *k_star_out,
                                    float *xi_hist, float *u_hist, int32_t *status_dev, const sgtp_launch_opts *opts,
                                    const sgtp_mlp *mlp, int32_t K_prop, float *feat_out, float *prop_out,
-                                   void *workspace, size_t workspace_bytes, void *stream)
+                                   void *workspace, size_t workspace_bytes, void *stream, float mppi_lambda = 0.f)
 {
     SGTP_CHECK(b != nullptr, "batch is NULL");
     sgtp_status st = check_params(p);
     if (st) return st;
     SGTP_CHECK(X0 && U_io && vref_scale && xi_out && k_star_out && status_dev, "NULL array");
-    const Layout lay(b->ks, b->agents, b->n_pos, b->maxT);
+    const bool mppi = mppi_lambda != 0.f;
+    const float il = mppi ? mppi_inverse(mppi_lambda) : 0.f;
+    SGTP_CHECK(!mppi || il > 0.f, "lambda must be finite and > 0");
+    SGTP_CHECK(!(mppi && mlp), "GA-IBR-MPPI takes the plain sampler only");
+    const Layout lay(b->ks, b->agents, b->n_pos, b->maxT, mppi ? mppi_part_floats(b->agents, b->K, b->maxT) : 0);
     SGTP_CHECK(workspace && workspace_bytes >= lay.total, "workspace too small: need %zu bytes", lay.total);
     SGTP_CHECK(((uintptr_t)workspace & 255u) == 0, "workspace must be 256-byte aligned");
     st = refresh_tail_counts(b, p);
@@ -989,6 +1186,7 @@ static sgtp_status batch_plan_impl(const sgtp_batch *b, const sgtp_params *p, co
     PlanArgs a{};
     fill_common(a, b->trk, p, b->K, b->L, X0, U_io, vref_scale, seed, xi_out, k_star_out, xi_hist, u_hist,
                 status_dev, opts);
+    a.mppi_il = il;
     a.races = b->races_dev;
     a.n_races = b->n_races;
     a.n_agents = (int)b->agents;
@@ -1031,6 +1229,24 @@ extern "C" sgtp_status sgtp_batch_plan_learned(const sgtp_batch *b, const sgtp_p
 {
     return batch_plan_impl(b, p, X0, U_io, vref_scale, seed, xi_out, k_star_out, xi_hist, u_hist, status_dev, opts,
                            mlp, K_prop, feat_out, prop_out, workspace, workspace_bytes, stream);
+}
+
+extern "C" sgtp_status sgtp_batch_mppi_workspace_bytes(const sgtp_batch *b, size_t *workspace_bytes)
+{
+    SGTP_CHECK(b != nullptr && workspace_bytes != nullptr, "NULL argument");
+    *workspace_bytes = Layout(b->ks, b->agents, b->n_pos, b->maxT, mppi_part_floats(b->agents, b->K, b->maxT)).total;
+    return SGTP_OK;
+}
+
+extern "C" sgtp_status sgtp_batch_plan_mppi(const sgtp_batch *b, const sgtp_params *p, float lambda, const float *X0,
+                                            float *U_io, const float *vref_scale, uint64_t seed, float *xi_out,
+                                            int32_t *k_star_out, float *xi_hist, float *u_hist, int32_t *status_dev,
+                                            const sgtp_launch_opts *opts, void *workspace, size_t workspace_bytes,
+                                            void *stream)
+{
+    SGTP_CHECK(mppi_inverse(lambda) > 0.f, "lambda must be finite and > 0");
+    return batch_plan_impl(b, p, X0, U_io, vref_scale, seed, xi_out, k_star_out, xi_hist, u_hist, status_dev, opts,
+                           nullptr, 0, nullptr, nullptr, workspace, workspace_bytes, stream, lambda);
 }
 
 // ================================================================ CUDA graphs

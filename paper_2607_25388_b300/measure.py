@@ -8,7 +8,9 @@
 4. 256 independent races in one launch (n_v ~ U{2..10}, T ~ U{30..80}, K = 4096, L = 3), direct and graph;
 5. plan latency of the ten-car race: plain K = 16384, plain K = 4096, and the learned sampler with
    2048 proposal + 2048 plain samples (network weights do not change the work);
-5b. the same three samplers with 32 ten-car races per launch (per-plan time when the GPU is full).
+5b. the same three samplers with 32 ten-car races per launch (per-plan time when the GPU is full);
+6. the GA-IBR-MPPI ablation (path-integral update, lambda = 1e4) of the ten-car plan next to SGTP at the
+   same K, direct launch.
 
 Times are CUDA-event medians over `reps` calls after warm-up, inputs resident on the device.
 """
@@ -187,12 +189,35 @@ def config5_batched(reps, n_races=32):
     return res
 
 
+def config6(reps, lam=1.0e4):
+    """Ten-car plan (K = 16384, T = 60, L = 5): SGTP and GA-IBR-MPPI."""
+    p = S.params_fullscale()
+    sc = S.ten_car_race(200)
+    trk = Track.from_data(sc.track)
+    n_v, T, K, L = 10, 60, 16384, 5
+    X0, vs = torch.as_tensor(sc.X0).cuda(), torch.as_tensor(sc.vref_scale).cuda()
+    U0 = torch.as_tensor(sc.U0).cuda()
+    U = U0.clone()
+    res = {}
+    for name, lam_i in (("SGTP", None), (f"GA-IBR-MPPI lambda={lam:g}", lam)):
+        holder = {}
+
+        def run():
+            U.copy_(U0)
+            holder["o"] = ibr_plan(trk, p, X0, U, vs, T, K, L, ego=0, seed=3, out=holder.get("o"), mppi_lambda=lam_i)
+
+        res[name] = _line(f"6: ten-car plan, {name}", _median_ms(run, reps), R.rollout_steps_plan(n_v, K, T, L),
+                          R.flops_plan(n_v, K, T, L))
+    return res
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--reps", type=int, default=50)
-    ap.add_argument("--configs", type=str, default="1,2,3,4,5,5b")
+    ap.add_argument("--configs", type=str, default="1,2,3,4,5,5b,6")
     args = ap.parse_args(argv)
-    fns = {"1": config1, "2": config2, "3": config3, "4": config4, "5": config5, "5b": config5_batched}
+    fns = {"1": config1, "2": config2, "3": config3, "4": config4, "5": config5, "5b": config5_batched,
+           "6": config6}
     for c in args.configs.split(","):
         fns[c.strip()](args.reps)
 

@@ -114,6 +114,10 @@ def plan_workspace_bytes(n_v: int, T: int, L: int) -> int:
     return int(lib().sgtp_plan_workspace_bytes(n_v, T, L))
 
 
+def plan_mppi_workspace_bytes(n_v: int, T: int, L: int, K: int) -> int:
+    return int(lib().sgtp_plan_mppi_workspace_bytes(n_v, T, L, K))
+
+
 def _br_inputs(x0, u_nom, opp, T):
     dev = x0.device
     _dev(x0, "x0", shape=(4,))
@@ -225,13 +229,16 @@ def best_response_mixed(track: Track, params: dict, x0, u_nom, vref_scale, opp, 
 
 def ibr_plan(track: Track, params: dict, X0, U_io, vref_scale, T, K, L, ego=0, seed=0, race=0, track_id=0,
              want_hist=False, opts=None, workspace=None, out=None, stream=None, mlp=None, K_prop=0,
-             want_features=False, want_prop=False):
+             want_features=False, want_prop=False, mppi_lambda=None):
     """The SGTP planning call (Alg. 1) for one race; U_io is updated in place
     (warm start).  Returns device tensors xi (n_v, T+1, 4), k_star, status.
     With ``mlp`` (a :class:`learned.Mlp`) K_prop samples of every best
     response come from the network's proposal; ``want_features`` returns
     the features of every best response ((L+2, n_v, 64)), ``want_prop`` the
-    proposals ((L+2, n_v, T, 4))."""
+    proposals ((L+2, n_v, T, 4)).  With ``mppi_lambda`` the call is the
+    GA-IBR-MPPI ablation (sgtp_ibr_plan_mppi): every response's controls
+    become the path-integral mean at that temperature, and k_star holds the
+    lowest-cost samples."""
     n_v = X0.shape[0]
     dev = X0.device
     _dev(X0, "X0", shape=(n_v, 4))
@@ -244,7 +251,9 @@ def ibr_plan(track: Track, params: dict, X0, U_io, vref_scale, T, K, L, ego=0, s
         if want_hist:
             out["xi_hist"] = torch.empty((L + 2, n_v, T + 1, 4), dtype=torch.float32, device=dev)
             out["u_hist"] = torch.empty((L + 2, n_v, T, 2), dtype=torch.float32, device=dev)
-    nb = plan_workspace_bytes(n_v, T, L)
+    if mppi_lambda is not None and (mlp is not None or want_features or want_prop):
+        raise ValueError("GA-IBR-MPPI takes the plain sampler only")
+    nb = plan_workspace_bytes(n_v, T, L) if mppi_lambda is None else plan_mppi_workspace_bytes(n_v, T, L, K)
     ws = workspace if workspace is not None else _ws(nb, dev)
     P = make_params(params)
     if isinstance(opts, str):
@@ -267,6 +276,16 @@ def ibr_plan(track: Track, params: dict, X0, U_io, vref_scale, T, K, L, ego=0, s
             out["prop"].data_ptr() if "prop" in out else None,
             out["status"].data_ptr(), C.byref(o), ws.data_ptr(), ws.numel(), stream_ptr(stream))
         check(st, "sgtp_ibr_plan_learned")
+        return out
+    if mppi_lambda is not None:
+        st = lib().sgtp_ibr_plan_mppi(track.handle, track_id, C.byref(P), n_v, X0.data_ptr(), U_io.data_ptr(),
+                                      vref_scale.data_ptr(), T, K, L, ego, int(seed), race, float(mppi_lambda),
+                                      out["xi"].data_ptr(), out["k_star"].data_ptr(),
+                                      out["xi_hist"].data_ptr() if "xi_hist" in out else None,
+                                      out["u_hist"].data_ptr() if "u_hist" in out else None,
+                                      out["status"].data_ptr(), C.byref(o), ws.data_ptr(), ws.numel(),
+                                      stream_ptr(stream))
+        check(st, "sgtp_ibr_plan_mppi")
         return out
     st = lib().sgtp_ibr_plan(track.handle, track_id, C.byref(P), n_v, X0.data_ptr(), U_io.data_ptr(),
                              vref_scale.data_ptr(), T, K, L, ego, int(seed), race, out["xi"].data_ptr(),
@@ -386,19 +405,39 @@ class Batch:
             out["u_hist"] = torch.empty((self.L + 2) * self.u_elems, dtype=torch.float32, device=dev)
         return out
 
+    @property
+    def mppi_workspace_bytes(self):
+        w = C.c_size_t()
+        check(lib().sgtp_batch_mppi_workspace_bytes(self._h, C.byref(w)), "sgtp_batch_mppi_workspace_bytes")
+        return w.value
+
     def plan(self, params, X0, U_io, vref_scale, seed=0, want_hist=False, opts=None, workspace=None, out=None,
-             stream=None, mlp=None, K_prop=0):
+             stream=None, mlp=None, K_prop=0, mppi_lambda=None):
         """Plan every race in one launch; with ``mlp`` (a learned.Mlp) K_prop
-        samples of every best response come from the network's proposal."""
+        samples of every best response come from the network's proposal; with
+        ``mppi_lambda`` every race runs the GA-IBR-MPPI ablation."""
         dev = X0.device
         _dev(X0, "X0", shape=(self.agents, 4))
         _dev(U_io, "U_io", shape=(self.u_elems,))
         _dev(vref_scale, "vref_scale", shape=(self.agents,))
         if out is None:
             out = self._outputs(dev, want_hist)
-        ws = workspace if workspace is not None else _ws(self.workspace_bytes, dev)
+        if mppi_lambda is not None and mlp is not None:
+            raise ValueError("GA-IBR-MPPI takes the plain sampler only")
+        ws = workspace if workspace is not None else _ws(
+            self.workspace_bytes if mppi_lambda is None else self.mppi_workspace_bytes, dev)
         P = make_params(params)
         o = opts if opts is not None else launch_opts()
+        if mppi_lambda is not None:
+            st = lib().sgtp_batch_plan_mppi(self._h, C.byref(P), float(mppi_lambda), X0.data_ptr(), U_io.data_ptr(),
+                                            vref_scale.data_ptr(), int(seed), out["xi"].data_ptr(),
+                                            out["k_star"].data_ptr(),
+                                            out["xi_hist"].data_ptr() if "xi_hist" in out else None,
+                                            out["u_hist"].data_ptr() if "u_hist" in out else None,
+                                            out["status"].data_ptr(), C.byref(o), ws.data_ptr(), ws.numel(),
+                                            stream_ptr(stream))
+            check(st, "sgtp_batch_plan_mppi")
+            return out
         if mlp is not None:
             st = lib().sgtp_batch_plan_learned(
                 self._h, C.byref(P), mlp.handle, int(K_prop), X0.data_ptr(), U_io.data_ptr(), vref_scale.data_ptr(),

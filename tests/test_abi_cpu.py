@@ -48,6 +48,10 @@ def test_workspace_sizes():
     assert L.sgtp_br_workspace_bytes(-1, 60) == 0
     assert L.sgtp_plan_workspace_bytes(10, 60, 5) > L.sgtp_plan_workspace_bytes(2, 60, 5)
     assert L.sgtp_plan_workspace_bytes(0, 60, 5) == 0
+    # GA-IBR-MPPI adds one row of 2T+2 floats per 256-sample tile per vehicle
+    base = L.sgtp_plan_workspace_bytes(10, 60, 5)
+    assert L.sgtp_plan_mppi_workspace_bytes(10, 60, 5, 16384) >= base + 10 * 64 * 122 * 4
+    assert L.sgtp_plan_mppi_workspace_bytes(10, 60, 5, 0) == 0
 
 
 def _params():
@@ -82,6 +86,16 @@ def test_invalid_arguments_are_rejected_without_launch():
     assert L.sgtp_mlp_forward(None, vp(16), 4, vp(16), None) == 1
     assert L.sgtp_ibr_plan_learned(None, 0, C.byref(P), 2, vp(16), vp(16), vp(16), 10, 10, 1, 0, 0, 0, None, 0,
                                    vp(16), vp(16), None, None, None, None, vp(16), None, vp(256), 1 << 20, None) == 1
+    # GA-IBR-MPPI: the temperature must be finite and > 0
+    for lam in (0.0, -2.0, float("inf"), float("nan")):
+        st = L.sgtp_ibr_plan_mppi(None, 0, C.byref(P), 2, vp(16), vp(16), vp(16), 10, 10, 1, 0, 0, 0, lam, vp(16),
+                                  vp(16), None, None, vp(16), None, vp(256), 1 << 20, None)
+        assert st == 1 and b"lambda" in L.sgtp_last_error()
+        assert L.sgtp_batch_plan_mppi(None, C.byref(P), lam, None, None, None, 0, None, None, None, None, None,
+                                      None, None, 0, None) == 1
+    assert L.sgtp_ibr_plan_mppi(None, 0, C.byref(P), 2, vp(16), vp(16), vp(16), 10, 10, 1, 0, 0, 0, 1.0, vp(16),
+                                vp(16), None, None, vp(16), None, vp(256), 1 << 20, None) == 1
+    assert b"track" in L.sgtp_last_error()
     # bad params
     bad = _params(); bad.dt = -1.0
     assert L.sgtp_batch_plan(None, C.byref(bad), None, None, None, 0, None, None, None, None, None, None, None, 0,
