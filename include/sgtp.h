@@ -322,6 +322,82 @@ sgtp_status sgtp_batch_plan_mppi(const sgtp_batch *b, const sgtp_params *p, floa
                                  void *stream);
 
 /* ------------------------------------------------------------------ */
+/* Closed-loop race simulation (receding horizon)                       */
+/* ------------------------------------------------------------------ */
+/* The evaluation setting of Sec. IV-A (trials of several vehicles that
+ * re-plan every control period; metrics of the Evaluation Metrics
+ * subsection), on the batch layout: every race of an sgtp_batch is one
+ * trial.  A closed loop alternates sgtp_batch_plan (or _mppi) with
+ * sgtp_sim_step on the same arrays; both only enqueue work, so the loop can
+ * run on one stream and be captured in a CUDA graph.  Readings (the paper
+ * races in a simulator with its own vehicle model and a cited pure-pursuit
+ * tracker whose parameters it does not give):
+ *   - the plant is the planner's kinematic bicycle (Sec. II) with the same
+ *     float arithmetic, so replaying a plan's controls reproduces its
+ *     trajectory exactly;
+ *   - pure pursuit steers toward the planned position pp_preview steps
+ *     ahead of the current substep (a time-based look-ahead):
+ *     delta = clip(atan(2 wheelbase sin(alpha) / l_d)), alpha the bearing of
+ *     the target relative to the heading, l_d its distance; the acceleration
+ *     tracks the next planned speed, a = clip((v_plan - v) / dt);
+ *   - the ego is in contact with an opponent when their reference points are
+ *     closer than contact_dist, and with a wall when its boundary clearance
+ *     min(w^R(s) + d, w^L(s) - d) drops below wall_margin; a trial ends at
+ *     the ego's first contact or after max_steps control steps;
+ *   - an opponent is in close interaction while |Delta s| < close_ds and
+ *     |Delta d| < close_dd in Frenet coordinates (Delta s wrapped to the
+ *     half lap); a segment is a maximal run of such steps. */
+typedef struct sgtp_sim_params {
+    int32_t n_apply;          /* control steps of each plan applied before re-planning, 1 .. min T */
+    int32_t max_steps;        /* trial length in control steps                             */
+    int32_t tracker;          /* SGTP_TRACK_CONTROLS or SGTP_TRACK_PURE_PURSUIT            */
+    int32_t pp_preview;       /* pure pursuit: planned position this many steps ahead, >= 1 */
+    float contact_dist;       /* vehicle contact distance between reference points (m)     */
+    float wall_margin;        /* wall contact below this boundary clearance (m)            */
+    float close_ds, close_dd; /* close-interaction box in Frenet coordinates (m)           */
+} sgtp_sim_params;
+
+#define SGTP_TRACK_CONTROLS 0        /* apply the plan's controls U_io[0 .. n_apply)       */
+#define SGTP_TRACK_PURE_PURSUIT 1    /* track the planned trajectory xi by pure pursuit   */
+
+/* Per-trial state and result, one per race, in DEVICE memory owned by the
+ * caller (n_races x sizeof(sgtp_sim_race), 16-byte aligned); written by
+ * sgtp_sim_reset and sgtp_sim_step, read by the caller after a stream sync.
+ * Fields marked internal carry the loop's state between steps. */
+typedef struct sgtp_sim_race {
+    int32_t alive;             /* 1 while the trial runs                                  */
+    int32_t steps;             /* control steps simulated (the trial duration / dt)      */
+    int32_t ego_collision;     /* 0 none, 1 vehicle contact, 2 wall contact               */
+    int32_t close_segments;    /* completed close-interaction segments, all opponents    */
+    int32_t close_steps;       /* their total length in control steps                    */
+    float ego_speed_sum;       /* sum of the ego's speed after every step                */
+    float ego_du2_sum;         /* sum of ||u_k - u_{k-1}||^2 of the ego's applied controls */
+    int32_t pad0;
+    float progress[SGTP_MAX_AGENTS];   /* unwrapped Frenet progress gain s_t - s_0            */
+    float rel0[SGTP_MAX_AGENTS];       /* s_{j,0} - s_{ego,0} wrapped to the half lap         */
+    float d[SGTP_MAX_AGENTS];          /* Frenet offset after the last step                    */
+    float s_raw[SGTP_MAX_AGENTS];      /* internal: last projection s in [0, L)               */
+    int32_t close_run[SGTP_MAX_AGENTS]; /* internal: current close-interaction run            */
+    float u_prev[2];                    /* internal: the ego's last applied control           */
+    int32_t pad1[2];
+} sgtp_sim_race;
+
+/* Start every trial of the batch from the states X [agents x 4] (device):
+ * projections of every vehicle, zero progress, alive = 1. */
+sgtp_status sgtp_sim_reset(const sgtp_batch *b, const float *X, sgtp_sim_race *state, void *stream);
+
+/* Advance every live trial by sp->n_apply control steps (fewer if the ego
+ * makes contact): controls from U_io or by pure pursuit on xi (the plan's
+ * xi_out layout), bicycle steps of all vehicles in lock step, projection of
+ * every vehicle on the globally nearest segment after each step, contact and
+ * close-interaction checks, metric sums.  X_io [agents x 4] receives the new
+ * states and U_io [u_elems] the warm start shifted by the steps applied (the
+ * last control repeated).  Trials that have ended are left untouched.
+ * SGTP_E_INVALID (nothing launched) for sizes or parameters out of range. */
+sgtp_status sgtp_sim_step(const sgtp_batch *b, const sgtp_params *p, const sgtp_sim_params *sp, float *X_io,
+                          float *U_io, const float *xi, sgtp_sim_race *state, void *stream);
+
+/* ------------------------------------------------------------------ */
 /* CUDA graphs of planning calls                                        */
 /* ------------------------------------------------------------------ */
 typedef struct sgtp_graph sgtp_graph;   /* opaque, library owned */

@@ -99,9 +99,12 @@ def pure_pursuit(params: dict, plan, m: int, preview: int, x):
     return np.array([acc, delta])
 
 
-def step(params: dict, track: Track, sp: dict, X, U, xi, ego: int, state: dict):
+def step(params: dict, track: Track, sp: dict, X, U, xi, ego: int, state: dict, margins=None):
     """One sgtp_sim_step of one trial: returns (X', U', state').  X (n, 4),
-    U (n, T, 2), xi (n, T+1, 4) as float64 copies of the device values."""
+    U (n, T, 2), xi (n, T+1, 4) as float64 copies of the device values.
+    margins (a list, optional) receives, per substep, the smallest distance
+    of any decision argument to its threshold: (contact, wall, close-box
+    longitudinal, close-box lateral)."""
     X = np.array(X, np.float64)
     U = np.array(U, np.float64)
     st = copy.deepcopy(state)
@@ -132,18 +135,25 @@ def step(params: dict, track: Track, sp: dict, X, U, xi, ego: int, state: dict):
             st["d"][i] = pr[i][1]
         st["steps"] += 1
         coll = 0
+        mg = [math.inf] * 4
         for j in range(n):
-            if j != ego and math.hypot(X[j, 0] - X[ego, 0], X[j, 1] - X[ego, 1]) < contact:
+            if j == ego:
+                continue
+            dist = math.hypot(X[j, 0] - X[ego, 0], X[j, 1] - X[ego, 1])
+            mg[0] = min(mg[0], abs(dist - contact))
+            if dist < contact:
                 coll = 1
-        if not coll:
-            _, de, wl, wr = pr[ego]
-            if min(wr + de, wl - de) < wall:
-                coll = 2
+        _, de, wl, wr = pr[ego]
+        mg[1] = abs(min(wr + de, wl - de) - wall)
+        if not coll and min(wr + de, wl - de) < wall:
+            coll = 2
         for j in range(n):
             if j == ego:
                 continue
             ds = _wrap(pr[ego][0] - pr[j][0], L)
             dd = pr[ego][1] - pr[j][1]
+            mg[2] = min(mg[2], abs(abs(ds) - cds))
+            mg[3] = min(mg[3], abs(abs(dd) - cdd))
             if abs(ds) < cds and abs(dd) < cdd:
                 st["close_run"][j] += 1
             elif st["close_run"][j] > 0:
@@ -159,6 +169,8 @@ def step(params: dict, track: Track, sp: dict, X, U, xi, ego: int, state: dict):
                     st["close_segments"] += 1
                     st["close_steps"] += int(st["close_run"][j])
                     st["close_run"][j] = 0
+        if margins is not None:
+            margins.append(mg)
         applied = m + 1
     Un = U.copy()
     for tau in range(T):

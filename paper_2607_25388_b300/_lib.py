@@ -48,6 +48,25 @@ class Race(C.Structure):
                 ("race_tag", C.c_uint32)]
 
 
+class SimParams(C.Structure):
+    _fields_ = [("n_apply", C.c_int32), ("max_steps", C.c_int32), ("tracker", C.c_int32), ("pp_preview", C.c_int32),
+                ("contact_dist", C.c_float), ("wall_margin", C.c_float), ("close_ds", C.c_float),
+                ("close_dd", C.c_float)]
+
+
+MAX_AGENTS = 16
+
+
+class SimRace(C.Structure):
+    """Mirror of sgtp_sim_race (include/sgtp.h)."""
+    _fields_ = [("alive", C.c_int32), ("steps", C.c_int32), ("ego_collision", C.c_int32),
+                ("close_segments", C.c_int32), ("close_steps", C.c_int32), ("ego_speed_sum", C.c_float),
+                ("ego_du2_sum", C.c_float), ("pad0", C.c_int32),
+                ("progress", C.c_float * MAX_AGENTS), ("rel0", C.c_float * MAX_AGENTS), ("d", C.c_float * MAX_AGENTS),
+                ("s_raw", C.c_float * MAX_AGENTS), ("close_run", C.c_int32 * MAX_AGENTS),
+                ("u_prev", C.c_float * 2), ("pad1", C.c_int32 * 2)]
+
+
 def make_params(d: dict) -> Params:
     P = Params()
     for f in PARAM_FIELDS:
@@ -106,6 +125,8 @@ def lib():
             L.sgtp_batch_mppi_workspace_bytes.argtypes = [vp, C.POINTER(sz)]
             L.sgtp_batch_plan_mppi.argtypes = [vp, C.POINTER(Params), f32, vp, vp, vp, u64, vp, vp, vp, vp, vp,
                                                C.POINTER(LaunchOpts), vp, sz, vp]
+            L.sgtp_sim_reset.argtypes = [vp, vp, vp, vp]
+            L.sgtp_sim_step.argtypes = [vp, C.POINTER(Params), C.POINTER(SimParams), vp, vp, vp, vp, vp]
             L.sgtp_graph_capture_plan.argtypes = [vp, i32, C.POINTER(Params), i32, vp, vp, vp, i32, i32, i32, i32,
                                                   u64, u32, vp, vp, vp, vp, vp, C.POINTER(LaunchOpts), vp, sz,
                                                   C.POINTER(vp)]
@@ -160,7 +181,7 @@ EXPORTS = [
     "sgtp_mlp_proposal", "sgtp_mlp_train_step", "sgtp_mlp_get_params", "sgtp_mlp_set_params", "sgtp_mlp_info",
     "sgtp_best_response_mixed", "sgtp_ibr_plan_learned", "sgtp_batch_plan_learned",
     "sgtp_plan_mppi_workspace_bytes", "sgtp_ibr_plan_mppi", "sgtp_batch_mppi_workspace_bytes",
-    "sgtp_batch_plan_mppi",
+    "sgtp_batch_plan_mppi", "sgtp_sim_reset", "sgtp_sim_step",
 ]
 
 

@@ -19,6 +19,7 @@
 
 #include <atomic>
 
+#include "sgtp_batch.hpp"
 #include "sgtp_host.hpp"
 #include "sgtp_mlp.h"
 #include "sgtp_rollout.cuh"
@@ -26,18 +27,6 @@
 using namespace sgtp;
 
 namespace {
-
-struct RaceDev {
-    int track_id, n_v, T, ego;
-    unsigned race_tag;
-    int n_tail;
-    int agent_off;   // first vehicle of the race in the batch arrays
-    int u_off;       // float offset into U_io (n_v * T * 2 per race)
-    int xi_off;      // float offset into xi_out (n_v * (T+1) * 4)
-    int ks_off;      // offset into k_star_out ((L+1) * n_v + 1)
-    int pos_off;     // float2 offset into each prediction buffer (n_v * (T+1))
-    int pad[5];
-};
 
 struct AgentDev {
     float4 x0;
@@ -965,15 +954,6 @@ float mppi_inverse(float lambda)
 
 }  // namespace
 
-struct sgtp_batch {
-    const sgtp_track *trk = nullptr;
-    int n_races = 0, K = 0, L = 0;
-    std::vector<RaceDev> races;
-    RaceDev *races_dev = nullptr;
-    long long agents = 0, u_elems = 0, xi_elems = 0, ks = 0, n_pos = 0;
-    int maxT = 0, max_nv = 0;
-};
-
 extern "C" size_t sgtp_plan_workspace_bytes(int32_t n_v, int32_t T, int32_t L)
 {
     if (n_v < 1 || T < 1 || L < 0) return 0;
@@ -1112,6 +1092,7 @@ extern "C" sgtp_status sgtp_batch_create(const sgtp_track *trk, const sgtp_race 
         ag += q.n_v; u += (long long)q.n_v * q.T * 2; xi += (long long)q.n_v * (q.T + 1) * 4;
         ks += (long long)(L + 1) * q.n_v + 1; pos += (long long)q.n_v * (q.T + 1);
         b->maxT = std::max(b->maxT, q.T);
+        b->minT = r == 0 ? q.T : std::min(b->minT, q.T);
         b->max_nv = std::max(b->max_nv, q.n_v);
     }
     if (xi > (1ll << 31) || ag * tiles > (1ll << 31) || u > (1ll << 31)) {
@@ -1123,6 +1104,14 @@ extern "C" sgtp_status sgtp_batch_create(const sgtp_track *trk, const sgtp_race 
     if (e != cudaSuccess) {
         delete b;
         return set_error(SGTP_E_NOMEM, "batch table allocation failed: %s", cudaGetErrorString(e));
+    }
+    // the table is valid on the device from here on (the simulation entry
+    // points read it before any planning call; tail counts follow per call)
+    e = cudaMemcpy(b->races_dev, b->races.data(), sizeof(RaceDev) * n_races, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(b->races_dev);
+        delete b;
+        return set_error(SGTP_E_CUDA, "batch table upload failed: %s", cudaGetErrorString(e));
     }
     *out = b;
     return SGTP_OK;

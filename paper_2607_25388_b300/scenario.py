@@ -223,6 +223,39 @@ def grid_race(track: TrackData, n_v: int, T: int, K: int, L: int, seed: int, s0=
                     name=f"{track.name}-grid{n_v}")
 
 
+def trial_race(track: TrackData, n_v: int, T: int, K: int, L: int, seed: int, s0: float, gap_lo=8.0, gap_hi=20.0,
+               v_lo=40.0, v_hi=55.0) -> Scenario:
+    """One closed-loop trial (Sec. IV-A): the ego (vehicle 0) starts behind
+    every opponent; opponent j starts gap_lo..gap_hi m ahead of the previous
+    car, d ~ U(-3, 3) m; speeds U(v_lo, v_hi); headings along the raceline;
+    reference speed scale 1 for the ego and 0.9 for the opponents."""
+    rng = np.random.default_rng(seed)
+    X0 = np.zeros((n_v, 4), F32)
+    s = s0
+    for i in range(n_v):
+        if i > 0:
+            s += float(rng.uniform(gap_lo, gap_hi))
+        x, y, psi = pose_at(track, s, float(rng.uniform(-3.0, 3.0)) if i > 0 else 0.0)
+        X0[i] = (x, y, psi, rng.uniform(v_lo, v_hi))
+    vs = np.full(n_v, 0.9, F32)
+    vs[0] = 1.0
+    return Scenario(track=track, X0=X0, U0=np.zeros((n_v, T, 2), F32), vref_scale=vs, ego=0, T=T, K=K, L=L,
+                    name=f"{track.name}-trial{n_v}")
+
+
+def trial_set(n_tracks=7, starts=6, n_v=3, T=60, K=4096, L=2, seed0=400):
+    """n_tracks seeded Fourier tracks x `starts` evenly spaced starting points
+    (the paper's 7 tracks x 6 starts; its MapZoo tracks are replaced by
+    synthetic ones)."""
+    out = []
+    for t in range(n_tracks):
+        tr = fourier_track(seed0 + t)
+        Lt = track_length(tr)
+        for k in range(starts):
+            out.append(trial_race(tr, n_v, T, K, L, seed0 * 100 + t * starts + k, s0=k * Lt / starts))
+    return out
+
+
 def two_car_race(seed: int, K=8192, T=50, L=3) -> Scenario:
     """Two cars 5-15 m apart on a seeded Fourier track, d ~ U(-2, 2),
     v ~ U(40, 60); the rear car is the ego."""

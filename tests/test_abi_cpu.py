@@ -96,6 +96,10 @@ def test_invalid_arguments_are_rejected_without_launch():
     assert L.sgtp_ibr_plan_mppi(None, 0, C.byref(P), 2, vp(16), vp(16), vp(16), 10, 10, 1, 0, 0, 0, 1.0, vp(16),
                                 vp(16), None, None, vp(16), None, vp(256), 1 << 20, None) == 1
     assert b"track" in L.sgtp_last_error()
+    # closed-loop simulation: NULL batch
+    sp = _lib.SimParams(1, 10, 0, 5, 4.5, 0.0, 5.0, 2.5)
+    assert L.sgtp_sim_reset(None, vp(16), vp(256), None) == 1 and b"batch" in L.sgtp_last_error()
+    assert L.sgtp_sim_step(None, C.byref(P), C.byref(sp), vp(16), vp(16), vp(16), vp(256), None) == 1
     # bad params
     bad = _params(); bad.dt = -1.0
     assert L.sgtp_batch_plan(None, C.byref(bad), None, None, None, 0, None, None, None, None, None, None, None, 0,
@@ -111,3 +115,21 @@ def test_tail_count_rule_matches_oracle():
             v = float(np.float32(mu)) * H - 1e-4
             n = min(H, max(1, int(np.ceil(v))))
             assert O.tail_count(mu, H) == n
+
+
+def test_sim_structs_match_the_header(tmp_path):
+    """Sizes and offsets of sgtp_sim_params / sgtp_sim_race as a C compiler
+    lays them out from include/sgtp.h equal the binding's mirrors."""
+    import os
+    import subprocess
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    src = tmp_path / "probe.c"
+    fields = [f for f, _ in _lib.SimRace._fields_]
+    body = "".join(f'printf("%zu ", offsetof(sgtp_sim_race, {f}));' for f in fields)
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "sgtp.h"\nint main(void){'
+                   'printf("%zu %zu ", sizeof(sgtp_sim_params), sizeof(sgtp_sim_race));' + body + 'return 0;}\n')
+    exe = tmp_path / "probe"
+    subprocess.check_call(["gcc", "-std=c11", "-I", inc, str(src), "-o", str(exe)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    assert got[0] == C.sizeof(_lib.SimParams) and got[1] == C.sizeof(_lib.SimRace)
+    assert got[2:] == [getattr(_lib.SimRace, f).offset for f in fields]
