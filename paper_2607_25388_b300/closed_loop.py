@@ -58,13 +58,16 @@ def main(argv=None):
     ap.add_argument("--L", type=int, default=2)
     ap.add_argument("--n-apply", type=int, default=1)
     ap.add_argument("--tracker", choices=["controls", "pure_pursuit"], default="pure_pursuit")
+    ap.add_argument("--pp-preview", type=int, default=3, help="pure pursuit look-ahead in plan steps")
+    ap.add_argument("--contact", type=float, default=2.5, help="vehicle contact distance (m)")
     ap.add_argument("--lam", type=float, default=1.0e4, help="GA-IBR-MPPI temperature")
     ap.add_argument("--variants", type=str, default="sgtp,no_game_cost,ga_ibr_mppi")
     args = ap.parse_args(argv)
     params = S.params_fullscale()
     scs = S.trial_set(args.tracks, args.starts, args.n_v, args.T, args.K, args.L)
     sp = SM.sim_params(n_apply=args.n_apply, max_steps=int(round(args.seconds / params["dt"])),
-                       tracker=SM.TRACK_PURE_PURSUIT if args.tracker == "pure_pursuit" else SM.TRACK_CONTROLS)
+                       tracker=SM.TRACK_PURE_PURSUIT if args.tracker == "pure_pursuit" else SM.TRACK_CONTROLS,
+                       pp_preview=args.pp_preview, contact_dist=args.contact)
     for v in args.variants.split(","):
         p, lam = params, None
         if v == "no_game_cost":
@@ -75,7 +78,8 @@ def main(argv=None):
             raise SystemExit(f"unknown planner {v}")
         m = run_variant(v, scs, p, args.K, args.L, sp, lam)
         m.update(config=dict(trials=len(scs), n_v=args.n_v, seconds=args.seconds, K=args.K, T=args.T, L=args.L,
-                             n_apply=args.n_apply, tracker=args.tracker, lam=lam))
+                             n_apply=args.n_apply, tracker=args.tracker, pp_preview=args.pp_preview,
+                             contact=args.contact, lam=lam))
         print(json.dumps(m), flush=True)
 
 

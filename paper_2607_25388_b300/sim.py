@@ -38,12 +38,14 @@ TRACK_CONTROLS, TRACK_PURE_PURSUIT = 0, 1
 _INTS_PER_RACE = C.sizeof(SimRace) // 4
 
 
-def sim_params(n_apply=1, max_steps=1000, tracker=TRACK_CONTROLS, pp_preview=5, contact_dist=4.5, wall_margin=0.0,
+def sim_params(n_apply=1, max_steps=1000, tracker=TRACK_CONTROLS, pp_preview=3, contact_dist=2.5, wall_margin=0.0,
                close_ds=5.0, close_dd=2.5) -> SimParams:
-    """Defaults at the full scale of these scenarios: contact below 4.5 m
-    between reference points (the planner's d_col), wall contact when the
-    reference point leaves the track, and the paper's close-interaction box
-    (1.0 m x 0.5 m at 1/10 scale) scaled by 5."""
+    """Defaults at the full scale of these scenarios: physical contact below
+    2.5 m between reference points (the planner's collision threshold d_col =
+    4.5 m keeps a margin over it, as the paper's 0.9 m does over its
+    1/10-scale cars' contact distance, a ratio of about 1.8), wall contact
+    when the reference point leaves the track, and the paper's
+    close-interaction box (1.0 m x 0.5 m at 1/10 scale) scaled by 5."""
     return SimParams(int(n_apply), int(max_steps), int(tracker), int(pp_preview), float(contact_dist),
                      float(wall_margin), float(close_ds), float(close_dd))
 
