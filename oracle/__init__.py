@@ -16,6 +16,8 @@ ctypes.  Every entry point mirrors a step of the paper:
 * :func:`ibr_plan`           the SGTP planning call (Alg. 1)
 * :func:`best_response_mppi` GA-IBR-MPPI best response: path-integral update (Sec. IV-A ablation)
 * :func:`ibr_plan_mppi`      the GA-IBR-MPPI planning call
+* :func:`perturb_prediction` a perturbed opponent prediction (Table II robustness study)
+* :func:`ibr_plan_perturbed` the SGTP planning call with perturbed predictions
 
 Parity status of each function is listed in the header of ``sgtp_oracle.c``'s
 tests (``tests/test_oracle_*.py``).
@@ -108,6 +110,11 @@ def lib():
         L.orc_ibr_plan_mppi.argtypes = [
             C.POINTER(OrcParams), dp, dp, dp, C.c_int, C.c_int, dp, dp, dp, C.c_int, C.c_int, C.c_int,
             C.c_int, C.c_uint64, C.c_uint32, C.c_double, dp, C.POINTER(C.c_int), dp, dp, C.c_int]
+        L.orc_perturb_prediction.argtypes = [dp, dp, dp, C.c_int, dp, C.c_int, C.c_uint64, C.c_uint32, C.c_uint32,
+                                             C.c_uint32, C.c_uint32, C.c_double, C.c_double, C.c_int, dp, dp]
+        L.orc_ibr_plan_perturbed.argtypes = [
+            C.POINTER(OrcParams), dp, dp, dp, C.c_int, C.c_int, dp, dp, dp, C.c_int, C.c_int, C.c_int,
+            C.c_int, C.c_uint64, C.c_uint32, C.c_double, C.c_double, dp, C.POINTER(C.c_int), dp, dp, C.c_int]
         L.orc_reference.argtypes = [C.POINTER(OrcParams), dp, dp, dp, C.c_int, dp, C.c_double, C.c_int, dp]
         L.orc_rollout.argtypes = [C.POINTER(OrcParams), dp, dp, C.c_int, dp]
         L.orc_std_normals_batch.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
@@ -354,6 +361,41 @@ def ibr_plan_mppi(params, track: Track, X0, U_nom, vref_scale, T, K, L, ego, lam
     rc = lib().orc_ibr_plan_mppi(C.byref(make_params(params)), *track.args(), n_v, _p(X0), _p(U), _p(vs), T, K, L,
                                  ego, seed, race, float(lam), _p(xi), ks.ctypes.data_as(C.POINTER(C.c_int)), _p(xh),
                                  _p(uh), _nthreads(nthreads))
+    assert rc == 0
+    out = dict(xi=xi, u_nom=U, k_star=ks)
+    if want_hist:
+        out["xi_hist"] = xh
+        out["u_hist"] = uh
+    return out
+
+
+def perturb_prediction(track: Track, states, T, seed, race, observer, rnd, jv, sigma_lon, sigma_lat, n_tail):
+    """Opponent jv's prediction (T+1 x 4 states) as perturbed for vehicle
+    ``observer`` in round ``rnd``; returns (states', (d gain, d tail mean))."""
+    st = _d(states).reshape(T + 1, 4)
+    out = np.zeros_like(st)
+    delta = np.zeros(2)
+    rc = lib().orc_perturb_prediction(*track.args(), _p(st), T, seed, race, observer, rnd, jv, float(sigma_lon),
+                                      float(sigma_lat), int(n_tail), _p(out), _p(delta))
+    assert rc == 0
+    return out, delta
+
+
+def ibr_plan_perturbed(params, track: Track, X0, U_nom, vref_scale, T, K, L, ego, sigma_lon, sigma_lat, seed=0, race=0,
+                       nthreads=None, want_hist=False):
+    """:func:`ibr_plan` with every opponent prediction perturbed before each
+    best response (:func:`perturb_prediction`)."""
+    X0 = _d(X0).reshape(-1, 4)
+    n_v = X0.shape[0]
+    U = _d(U_nom).reshape(n_v, T, 2).copy()
+    vs = _d([float(np.float32(v)) for v in vref_scale])
+    xi = np.zeros((n_v, T + 1, 4))
+    ks = np.zeros((L + 1) * n_v + 1, dtype=np.int32)
+    xh = np.zeros((L + 2, n_v, T + 1, 4)) if want_hist else None
+    uh = np.zeros((L + 2, n_v, T, 2)) if want_hist else None
+    rc = lib().orc_ibr_plan_perturbed(C.byref(make_params(params)), *track.args(), n_v, _p(X0), _p(U), _p(vs), T, K,
+                                      L, ego, seed, race, float(sigma_lon), float(sigma_lat), _p(xi),
+                                      ks.ctypes.data_as(C.POINTER(C.c_int)), _p(xh), _p(uh), _nthreads(nthreads))
     assert rc == 0
     out = dict(xi=xi, u_nom=U, k_star=ks)
     if want_hist:

@@ -255,6 +255,7 @@ typedef struct {
     const double *u_nom;     /* T x 2 */
     double vref_scale;
     const double *opp;       /* n_opp x (T+1) x 4 */
+    const double *opp_pos;   /* states whose positions enter the distance terms (NULL: opp) */
     int n_opp, T;
     uint64_t seed;
     uint32_t race, agent, round, stream;
@@ -381,7 +382,7 @@ static orc_sample_result eval_candidate(const orc_problem *P, const double *u, d
 
         /* time-aligned distances to each opponent (Eq. Dmin) */
         for (int j = 0; j < P->n_opp; ++j) {
-            const double *q = P->opp + ((size_t)j * (T + 1) + st) * 4;
+            const double *q = (P->opp_pos ? P->opp_pos : P->opp) + ((size_t)j * (T + 1) + st) * 4;
             const double dx = x[0] - q[0], dy = x[1] - q[1];
             const double g2 = dx * dx + dy * dy;
             if (g2 < gmin2[j]) gmin2[j] = g2;
@@ -571,18 +572,24 @@ int orc_eval_controls(const orc_params *p, const double *xr, const double *wl, c
  * prop (T x 4, may be NULL) and K_prop add the proposal of sample_controls;
  * cost_out (K, may be NULL) receives every candidate's cost and viol_out (K,
  * may be NULL) every violation. */
-int orc_best_response_mixed(const orc_params *p, const double *xr, const double *wl, const double *wr, int N,
-                            const double *x0, const double *u_nom, double vref_scale, const double *opp, int n_opp,
-                            int T, int K, uint64_t seed, uint32_t race, uint32_t agent, uint32_t round,
-                            uint32_t stream, int game_on, const double *prop, int K_prop, int *k_star,
-                            double *u_star, double *xi_star, int *any_feasible, double *cost_out,
-                            double *viol_out, int nthreads)
+static int br_core(const orc_params *p, const double *xr, const double *wl, const double *wr, int N,
+                   const double *x0, const double *u_nom, double vref_scale, const double *opp, int n_opp, int T,
+                   int K, uint64_t seed, uint32_t race, uint32_t agent, uint32_t round, uint32_t stream,
+                   int game_on, const double *prop, int K_prop, const double *opp_pos, const double *sum_delta,
+                   int *k_star, double *u_star, double *xi_star, int *any_feasible, double *cost_out,
+                   double *viol_out, int nthreads)
 {
     orc_problem P;
     if (K < 1 || K_prop < 0 || K_prop > K) return -1;
     if (setup_problem(&P, p, xr, wl, wr, N, x0, u_nom, vref_scale, opp, n_opp, T, seed, race, agent, round,
                       stream, game_on, 0))
         return -1;
+    P.opp_pos = opp_pos;
+    if (sum_delta)
+        for (int j = 0; j < n_opp; ++j) {
+            P.opp_sum[j].sH += sum_delta[2 * j];
+            P.opp_sum[j].dbar += sum_delta[2 * j + 1];
+        }
     P.prop = prop;
     P.K_prop = prop ? K_prop : 0;
     double *cost = (double *)malloc(sizeof(double) * (size_t)K);
@@ -599,6 +606,59 @@ int orc_best_response_mixed(const orc_params *p, const double *xr, const double 
     if (viol_out) memcpy(viol_out, viol, sizeof(double) * (size_t)K);
     free(u); free(cost); free(viol); free(feas);
     teardown_problem(&P);
+    return 0;
+}
+
+int orc_best_response_mixed(const orc_params *p, const double *xr, const double *wl, const double *wr, int N,
+                            const double *x0, const double *u_nom, double vref_scale, const double *opp, int n_opp,
+                            int T, int K, uint64_t seed, uint32_t race, uint32_t agent, uint32_t round,
+                            uint32_t stream, int game_on, const double *prop, int K_prop, int *k_star,
+                            double *u_star, double *xi_star, int *any_feasible, double *cost_out,
+                            double *viol_out, int nthreads)
+{
+    return br_core(p, xr, wl, wr, N, x0, u_nom, vref_scale, opp, n_opp, T, K, seed, race, agent, round, stream,
+                   game_on, prop, K_prop, NULL, NULL, k_star, u_star, xi_star, any_feasible, cost_out, viol_out,
+                   nthreads);
+}
+
+/* Perturbed prediction of opponent jv as seen by vehicle `observer` in
+ * round `round` (robustness study of Sec. IV, Table II; the paper's
+ * perturbation model is a cited one that is not available, so this is plain
+ * Gaussian noise in Frenet coordinates, first order): every predicted
+ * position p_tau, tau = 1..T, moves by sigma_lon z_1 along the unit direction
+ * of its nearest raceline segment and by sigma_lat z_2 along that segment's
+ * left normal, (z_1, z_2) the Box-Muller pair of counter
+ * (2^30 | jv, (tau-1) >> 1, observer | round << 16, race), a counter no
+ * sample uses (samples have k < 2^30).  The prediction's progress gain moves
+ * by sigma_lon z_1 at tau = T and its tail-mean offset by the mean of
+ * sigma_lat z_2 over the tail steps: delta_out = (d gain, d tail mean).
+ * The current state (tau = 0), headings and speeds are unchanged. */
+int orc_perturb_prediction(const double *xr, const double *wl, const double *wr, int N, const double *states, int T,
+                           uint64_t seed, uint32_t race, uint32_t observer, uint32_t round, uint32_t jv,
+                           double sigma_lon, double sigma_lat, int n_tail, double *out_states, double *delta_out)
+{
+    orc_track trk;
+    if (track_init(&trk, xr, wl, wr, N)) return -1;
+    memcpy(out_states, states, sizeof(double) * (size_t)(T + 1) * 4);
+    double dgain = 0.0, dsum = 0.0;
+    for (int tau = 1; tau <= T; ++tau) {
+        double z1, z2, s, d;
+        int j;
+        orc_std_normals(seed, race, observer, round, 0, (1u << 30) | jv, tau - 1, &z1, &z2);
+        const double *q = states + 4 * tau;
+        orc_frenet_raw(&trk, q[0], q[1], &s, &d, &j);
+        const int jn = (j + 1) % N;
+        const double ex = xr[4 * jn] - xr[4 * j], ey = xr[4 * jn + 1] - xr[4 * j + 1];
+        const double len = sqrt(ex * ex + ey * ey);
+        const double tx = ex / len, ty = ey / len;
+        out_states[4 * tau] = q[0] + sigma_lon * z1 * tx - sigma_lat * z2 * ty;
+        out_states[4 * tau + 1] = q[1] + sigma_lon * z1 * ty + sigma_lat * z2 * tx;
+        if (tau == T) dgain = sigma_lon * z1;
+        if (tau > T - n_tail) dsum += sigma_lat * z2;
+    }
+    delta_out[0] = dgain;
+    delta_out[1] = dsum / (double)n_tail;
+    track_free(&trk);
     return 0;
 }
 
@@ -704,15 +764,20 @@ int orc_best_response_mppi(const orc_params *p, const double *xr, const double *
  * nominal controls after each round. */
 static int plan_loop(const orc_params *p, const double *xr, const double *wl, const double *wr, int N, int n_v,
                      const double *X0, double *U_io, const double *vref_scale, int T, int K, int L, int ego,
-                     uint64_t seed, uint32_t race, double lambda, double *xi_out, int *k_star_out, double *xi_hist,
-                     double *u_hist, int nthreads)
+                     uint64_t seed, uint32_t race, double lambda, double sigma_lon, double sigma_lat,
+                     double *xi_out, int *k_star_out, double *xi_hist, double *u_hist, int nthreads)
 {
     if (n_v < 1 || n_v > 17 || ego < 0 || ego >= n_v || L < 0) return -1;
+    const int perturb = sigma_lon != 0.0 || sigma_lat != 0.0;
+    if (perturb && lambda > 0.0) return -1;
+    const int n_tail = orc_tail_count(p->mu_tail, T);
     const size_t traj = (size_t)(T + 1) * 4;
     double *xi = (double *)malloc(sizeof(double) * traj * (size_t)n_v);
     double *xi_new = (double *)malloc(sizeof(double) * traj * (size_t)n_v);
     double *opp = (double *)malloc(sizeof(double) * traj * (size_t)(n_v > 1 ? n_v - 1 : 1));
     double *u_new = (double *)malloc(sizeof(double) * (size_t)T * 2 * (size_t)n_v);
+    double *opp_pos = (double *)malloc(sizeof(double) * traj * (size_t)(n_v > 1 ? n_v - 1 : 1));
+    double *delta = (double *)malloc(sizeof(double) * 2 * (size_t)(n_v > 1 ? n_v - 1 : 1));
     for (int i = 0; i < n_v; ++i) nominal_rollout(p, X0 + 4 * i, U_io + (size_t)i * T * 2, T, xi + traj * i);
     int nk = 0, rc = 0;
     for (int round = 0; round <= L + 1 && rc == 0; ++round) {
@@ -720,8 +785,15 @@ static int plan_loop(const orc_params *p, const double *xr, const double *wl, co
         for (int i = 0; i < n_v && rc == 0; ++i) {
             if (extra && i != ego) continue;
             int m = 0;
-            for (int j = 0; j < n_v; ++j)
-                if (j != i) memcpy(opp + traj * (m++), xi + traj * j, sizeof(double) * traj);
+            for (int j = 0; j < n_v; ++j) {
+                if (j == i) continue;
+                memcpy(opp + traj * m, xi + traj * j, sizeof(double) * traj);
+                if (perturb)
+                    orc_perturb_prediction(xr, wl, wr, N, xi + traj * j, T, seed, race, (uint32_t)i, (uint32_t)round,
+                                           (uint32_t)j, sigma_lon, sigma_lat, n_tail, opp_pos + traj * m,
+                                           delta + 2 * m);
+                ++m;
+            }
             int ks, anyf;
             if (lambda > 0.0)
                 rc = orc_best_response_mppi(p, xr, wl, wr, N, X0 + 4 * i, U_io + (size_t)i * T * 2, vref_scale[i],
@@ -729,9 +801,10 @@ static int plan_loop(const orc_params *p, const double *xr, const double *wl, co
                                             lambda, &ks, u_new + (size_t)i * T * 2, xi_new + traj * i, NULL,
                                             nthreads);
             else
-                rc = orc_best_response(p, xr, wl, wr, N, X0 + 4 * i, U_io + (size_t)i * T * 2, vref_scale[i], opp,
-                                       n_v - 1, T, K, seed, race, (uint32_t)i, (uint32_t)round, 0, round > 0, &ks,
-                                       u_new + (size_t)i * T * 2, xi_new + traj * i, &anyf, NULL, nthreads);
+                rc = br_core(p, xr, wl, wr, N, X0 + 4 * i, U_io + (size_t)i * T * 2, vref_scale[i], opp, n_v - 1, T,
+                             K, seed, race, (uint32_t)i, (uint32_t)round, 0, round > 0, NULL, 0,
+                             perturb ? opp_pos : NULL, perturb ? delta : NULL, &ks, u_new + (size_t)i * T * 2,
+                             xi_new + traj * i, &anyf, NULL, NULL, nthreads);
             k_star_out[nk++] = ks;
         }
         /* Jacobi: all vehicles of the round updated together */
@@ -744,7 +817,7 @@ static int plan_loop(const orc_params *p, const double *xr, const double *wl, co
         if (u_hist) memcpy(u_hist + (size_t)T * 2 * n_v * round, U_io, sizeof(double) * (size_t)T * 2 * n_v);
     }
     memcpy(xi_out, xi, sizeof(double) * traj * (size_t)n_v);
-    free(xi); free(xi_new); free(opp); free(u_new);
+    free(xi); free(xi_new); free(opp); free(u_new); free(opp_pos); free(delta);
     return rc;
 }
 
@@ -754,8 +827,19 @@ int orc_ibr_plan(const orc_params *p, const double *xr, const double *wl, const 
                  uint64_t seed, uint32_t race, double *xi_out, int *k_star_out, double *xi_hist,
                  double *u_hist, int nthreads)
 {
-    return plan_loop(p, xr, wl, wr, N, n_v, X0, U_io, vref_scale, T, K, L, ego, seed, race, 0.0, xi_out,
+    return plan_loop(p, xr, wl, wr, N, n_v, X0, U_io, vref_scale, T, K, L, ego, seed, race, 0.0, 0.0, 0.0, xi_out,
                      k_star_out, xi_hist, u_hist, nthreads);
+}
+
+/* The SGTP planning call with every opponent prediction perturbed before
+ * each best response (orc_perturb_prediction, per observer and round). */
+int orc_ibr_plan_perturbed(const orc_params *p, const double *xr, const double *wl, const double *wr, int N, int n_v,
+                           const double *X0, double *U_io, const double *vref_scale, int T, int K, int L, int ego,
+                           uint64_t seed, uint32_t race, double sigma_lon, double sigma_lat, double *xi_out,
+                           int *k_star_out, double *xi_hist, double *u_hist, int nthreads)
+{
+    return plan_loop(p, xr, wl, wr, N, n_v, X0, U_io, vref_scale, T, K, L, ego, seed, race, 0.0, sigma_lon, sigma_lat,
+                     xi_out, k_star_out, xi_hist, u_hist, nthreads);
 }
 
 /* The GA-IBR-MPPI planning call (Sec. IV-A ablation): the same loop with the
@@ -766,8 +850,8 @@ int orc_ibr_plan_mppi(const orc_params *p, const double *xr, const double *wl, c
                       double *xi_hist, double *u_hist, int nthreads)
 {
     if (!(lambda > 0.0)) return -1;
-    return plan_loop(p, xr, wl, wr, N, n_v, X0, U_io, vref_scale, T, K, L, ego, seed, race, lambda, xi_out,
-                     k_star_out, xi_hist, u_hist, nthreads);
+    return plan_loop(p, xr, wl, wr, N, n_v, X0, U_io, vref_scale, T, K, L, ego, seed, race, lambda, 0.0, 0.0,
+                     xi_out, k_star_out, xi_hist, u_hist, nthreads);
 }
 
 /* Exposed pieces used by the oracle's own checks. */
