@@ -322,6 +322,38 @@ sgtp_status sgtp_batch_plan_mppi(const sgtp_batch *b, const sgtp_params *p, floa
                                  void *stream);
 
 /* ------------------------------------------------------------------ */
+/* Perturbed opponent predictions (robustness study, Table II)          */
+/* ------------------------------------------------------------------ */
+/* sgtp_ibr_plan / sgtp_batch_plan with every opponent prediction perturbed
+ * before each best response uses it.  The paper's perturbation model is a
+ * cited one that is not available; the perturbation here is Gaussian noise
+ * in Frenet coordinates, to first order: predicted position p_tau (tau =
+ * 1..T) of opponent j, as seen by vehicle i in round r, moves by
+ * sigma_lon z_1 along the unit direction of p_tau's nearest raceline segment
+ * and by sigma_lat z_2 along that direction's left normal, (z_1, z_2) the
+ * Box-Muller pair of Philox counter (2^30 | j, (tau-1) >> 1, i | r << 16,
+ * race) -- a counter no sample uses, since samples have k < 2^30.  The
+ * prediction's progress gain moves by sigma_lon z_1 of tau = T and its
+ * tail-mean offset by the mean of sigma_lat z_2 over the tail steps; the
+ * opponent's current state is observed exactly.  With both sigmas 0 the
+ * call equals the unperturbed one bit for bit.
+ *   - Arguments, outputs, workspace (sgtp_plan_workspace_bytes /
+ *     sgtp_batch_sizes) and errors as for sgtp_ibr_plan / sgtp_batch_plan.
+ *   - SGTP_E_INVALID for a sigma that is negative or not finite. */
+sgtp_status sgtp_ibr_plan_perturbed(const sgtp_track *trk, int32_t track_id, const sgtp_params *p, int32_t n_v,
+                                    const float *X0, float *U_io, const float *vref_scale, int32_t T, int32_t K,
+                                    int32_t L, int32_t ego, uint64_t seed, uint32_t race, float sigma_lon,
+                                    float sigma_lat, float *xi_out, int32_t *k_star_out, float *xi_hist,
+                                    float *u_hist, int32_t *status_dev, const sgtp_launch_opts *opts,
+                                    void *workspace, size_t workspace_bytes, void *stream);
+
+sgtp_status sgtp_batch_plan_perturbed(const sgtp_batch *b, const sgtp_params *p, float sigma_lon, float sigma_lat,
+                                      const float *X0, float *U_io, const float *vref_scale, uint64_t seed,
+                                      float *xi_out, int32_t *k_star_out, float *xi_hist, float *u_hist,
+                                      int32_t *status_dev, const sgtp_launch_opts *opts, void *workspace,
+                                      size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------ */
 /* Closed-loop race simulation (receding horizon)                       */
 /* ------------------------------------------------------------------ */
 /* The evaluation setting of Sec. IV-A (trials of several vehicles that

@@ -112,6 +112,10 @@ def lib():
             C.c_int, C.c_uint64, C.c_uint32, C.c_double, dp, C.POINTER(C.c_int), dp, dp, C.c_int]
         L.orc_perturb_prediction.argtypes = [dp, dp, dp, C.c_int, dp, C.c_int, C.c_uint64, C.c_uint32, C.c_uint32,
                                              C.c_uint32, C.c_uint32, C.c_double, C.c_double, C.c_int, dp, dp]
+        L.orc_rollout_costs_perturbed.argtypes = [
+            C.POINTER(OrcParams), dp, dp, dp, C.c_int, dp, dp, C.c_double, dp, dp, dp, C.c_int, C.c_int,
+            C.POINTER(C.c_int32), C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int, dp,
+            C.POINTER(C.c_ubyte), dp, dp, dp, dp, C.c_int]
         L.orc_ibr_plan_perturbed.argtypes = [
             C.POINTER(OrcParams), dp, dp, dp, C.c_int, C.c_int, dp, dp, dp, C.c_int, C.c_int, C.c_int,
             C.c_int, C.c_uint64, C.c_uint32, C.c_double, C.c_double, dp, C.POINTER(C.c_int), dp, dp, C.c_int]
@@ -401,4 +405,37 @@ def ibr_plan_perturbed(params, track: Track, X0, U_nom, vref_scale, T, K, L, ego
     if want_hist:
         out["xi_hist"] = xh
         out["u_hist"] = uh
+    return out
+
+
+def rollout_costs_perturbed(params, track: Track, x0, u_nom, vref_scale, opp, opp_pos, sum_delta, T, K=None,
+                            k_list=None, seed=0, race=0, agent=0, rnd=0, game_on=True, want_states=False,
+                            want_controls=False, nthreads=None):
+    """:func:`rollout_costs` with perturbed opponent data: positions of the
+    distance terms from ``opp_pos``, summaries of ``opp`` shifted by
+    ``sum_delta`` (n_opp x 2), as :func:`perturb_prediction` returns them."""
+    opp = _d(opp).reshape(-1, T + 1, 4)
+    opp_pos = _d(opp_pos).reshape(-1, T + 1, 4)
+    sd = _d(sum_delta).reshape(-1, 2)
+    n_opp = opp.shape[0]
+    if k_list is not None:
+        kl = np.ascontiguousarray(np.asarray(k_list, dtype=np.int32))
+        n = kl.shape[0]
+        klp = kl.ctypes.data_as(C.POINTER(C.c_int32))
+    else:
+        n = int(K)
+        klp = None
+    cost = np.zeros(n); viol = np.zeros(n); feas = np.zeros(n, dtype=np.uint8); mg = np.zeros((n, 3))
+    states = np.zeros((n, T + 1, 4)) if want_states else None
+    ctl = np.zeros((n, T, 2)) if want_controls else None
+    rc = lib().orc_rollout_costs_perturbed(
+        C.byref(make_params(params)), *track.args(), _p(_d(x0)), _p(_d(u_nom)), float(np.float32(vref_scale)),
+        _p(opp), _p(opp_pos), _p(sd), n_opp, T, klp, n, seed, race, agent, rnd, int(bool(game_on)), _p(cost),
+        feas.ctypes.data_as(C.POINTER(C.c_ubyte)), _p(viol), _p(states), _p(ctl), _p(mg), _nthreads(nthreads))
+    assert rc == 0
+    out = dict(cost=cost, feasible=feas, violation=viol, margins=mg)
+    if want_states:
+        out["states"] = states
+    if want_controls:
+        out["controls"] = ctl
     return out

@@ -528,6 +528,31 @@ static void teardown_problem(orc_problem *P) { problem_free(P); track_free(&P->t
  * feasibility steps).  k_list (n entries) selects which k to evaluate; when it
  * is NULL, k = 0..n-1.  Optional per-candidate outputs may be NULL; prop
  * (T x 4, may be NULL) and K_prop add the proposal of sample_controls. */
+/* The same with perturbed opponent data (orc_perturb_prediction): opp_pos
+ * (n_opp x (T+1) x 4) gives the positions of the distance terms and
+ * sum_delta (n_opp x 2) the shifts of each prediction's progress gain and
+ * tail-mean offset; the summaries themselves come from opp. */
+int orc_rollout_costs_perturbed(const orc_params *p, const double *xr, const double *wl, const double *wr, int N,
+                                const double *x0, const double *u_nom, double vref_scale, const double *opp,
+                                const double *opp_pos, const double *sum_delta, int n_opp, int T,
+                                const int32_t *k_list, int n, uint64_t seed, uint32_t race, uint32_t agent,
+                                uint32_t round, int game_on, double *cost, unsigned char *feas, double *viol,
+                                double *states, double *controls, double *margins, int nthreads)
+{
+    orc_problem P;
+    if (setup_problem(&P, p, xr, wl, wr, N, x0, u_nom, vref_scale, opp, n_opp, T, seed, race, agent, round, 0,
+                      game_on, 0))
+        return -1;
+    P.opp_pos = opp_pos;
+    for (int j = 0; j < n_opp; ++j) {
+        P.opp_sum[j].sH += sum_delta[2 * j];
+        P.opp_sum[j].dbar += sum_delta[2 * j + 1];
+    }
+    run_jobs(&P, k_list, n, nthreads, cost, feas, viol, states, NULL, controls, NULL, NULL, margins);
+    teardown_problem(&P);
+    return 0;
+}
+
 int orc_rollout_costs(const orc_params *p, const double *xr, const double *wl, const double *wr, int N,
                       const double *x0, const double *u_nom, double vref_scale, const double *opp, int n_opp,
                       int T, const int32_t *k_list, int n, uint64_t seed, uint32_t race, uint32_t agent,

@@ -125,6 +125,11 @@ def lib():
             L.sgtp_batch_mppi_workspace_bytes.argtypes = [vp, C.POINTER(sz)]
             L.sgtp_batch_plan_mppi.argtypes = [vp, C.POINTER(Params), f32, vp, vp, vp, u64, vp, vp, vp, vp, vp,
                                                C.POINTER(LaunchOpts), vp, sz, vp]
+            L.sgtp_ibr_plan_perturbed.argtypes = [vp, i32, C.POINTER(Params), i32, vp, vp, vp, i32, i32, i32, i32,
+                                                  u64, u32, f32, f32, vp, vp, vp, vp, vp, C.POINTER(LaunchOpts), vp,
+                                                  sz, vp]
+            L.sgtp_batch_plan_perturbed.argtypes = [vp, C.POINTER(Params), f32, f32, vp, vp, vp, u64, vp, vp, vp, vp,
+                                                    vp, C.POINTER(LaunchOpts), vp, sz, vp]
             L.sgtp_sim_reset.argtypes = [vp, vp, vp, vp]
             L.sgtp_sim_step.argtypes = [vp, C.POINTER(Params), C.POINTER(SimParams), vp, vp, vp, vp, vp]
             L.sgtp_graph_capture_plan.argtypes = [vp, i32, C.POINTER(Params), i32, vp, vp, vp, i32, i32, i32, i32,
@@ -181,7 +186,7 @@ EXPORTS = [
     "sgtp_mlp_proposal", "sgtp_mlp_train_step", "sgtp_mlp_get_params", "sgtp_mlp_set_params", "sgtp_mlp_info",
     "sgtp_best_response_mixed", "sgtp_ibr_plan_learned", "sgtp_batch_plan_learned",
     "sgtp_plan_mppi_workspace_bytes", "sgtp_ibr_plan_mppi", "sgtp_batch_mppi_workspace_bytes",
-    "sgtp_batch_plan_mppi", "sgtp_sim_reset", "sgtp_sim_step",
+    "sgtp_batch_plan_mppi", "sgtp_sim_reset", "sgtp_sim_step", "sgtp_ibr_plan_perturbed", "sgtp_batch_plan_perturbed",
 ]
 
 

@@ -10,7 +10,9 @@ re-plan every control period (receding horizon); the trial ends at the
 ego's first contact or at the time limit.  All trials of a planner run
 together: each control period is one batched planning call and one
 simulation step.  Planners: SGTP, SGTP without the game-aware cost
-(w_game = 0, the paper's first ablation) and GA-IBR-MPPI (the second).
+(w_game = 0, the paper's first ablation), GA-IBR-MPPI (the second), and
+SGTP with perturbed opponent predictions (Table II: mild and severe noise,
+the paper's (0.03, 0.015) and (0.08, 0.04) at 1/10 scale, x5 here).
 The paper's MapZoo tracks, its simulator and its 1/10-scale parameters are
 replaced by synthetic full-scale tracks and the planner's own bicycle model.
 """
@@ -27,8 +29,8 @@ from . import scenario as S
 from . import sim as SM
 
 
-def run_variant(name, scs, params, K, L, sp, lam=None):
-    tr = SM.Trials(scs, params, K, L, sp, mppi_lambda=lam)
+def run_variant(name, scs, params, K, L, sp, lam=None, pred_sigma=None):
+    tr = SM.Trials(scs, params, K, L, sp, mppi_lambda=lam, pred_sigma=pred_sigma)
     tr.reset()
     # warm-up of the launch path, then the timed trial set from a fresh reset
     tr.plan()
@@ -61,25 +63,28 @@ def main(argv=None):
     ap.add_argument("--pp-preview", type=int, default=3, help="pure pursuit look-ahead in plan steps")
     ap.add_argument("--contact", type=float, default=2.5, help="vehicle contact distance (m)")
     ap.add_argument("--lam", type=float, default=1.0e4, help="GA-IBR-MPPI temperature")
-    ap.add_argument("--variants", type=str, default="sgtp,no_game_cost,ga_ibr_mppi")
+    ap.add_argument("--variants", type=str, default="sgtp,no_game_cost,ga_ibr_mppi,sgtp_mild_noise,sgtp_severe_noise")
     args = ap.parse_args(argv)
     params = S.params_fullscale()
     scs = S.trial_set(args.tracks, args.starts, args.n_v, args.T, args.K, args.L)
     sp = SM.sim_params(n_apply=args.n_apply, max_steps=int(round(args.seconds / params["dt"])),
                        tracker=SM.TRACK_PURE_PURSUIT if args.tracker == "pure_pursuit" else SM.TRACK_CONTROLS,
                        pp_preview=args.pp_preview, contact_dist=args.contact)
+    noise = {"sgtp_mild_noise": (0.15, 0.075), "sgtp_severe_noise": (0.40, 0.20)}
     for v in args.variants.split(","):
-        p, lam = params, None
+        p, lam, sig = params, None, None
         if v == "no_game_cost":
             p = dict(params, w_game=0.0)
         elif v == "ga_ibr_mppi":
             lam = args.lam
+        elif v in noise:
+            sig = noise[v]
         elif v != "sgtp":
             raise SystemExit(f"unknown planner {v}")
-        m = run_variant(v, scs, p, args.K, args.L, sp, lam)
+        m = run_variant(v, scs, p, args.K, args.L, sp, lam, sig)
         m.update(config=dict(trials=len(scs), n_v=args.n_v, seconds=args.seconds, K=args.K, T=args.T, L=args.L,
                              n_apply=args.n_apply, tracker=args.tracker, pp_preview=args.pp_preview,
-                             contact=args.contact, lam=lam))
+                             contact=args.contact, lam=lam, pred_sigma=sig))
         print(json.dumps(m), flush=True)
 
 

@@ -77,6 +77,9 @@ struct PlanArgs {
     // GA-IBR-MPPI (mppi_il > 0): path-integral update instead of selection
     float mppi_il;                 // 1 / lambda
     float *mppi_part;              // per vehicle x tile: m_t, sum w u (2T), sum w; stride 2 maxT + 2
+    // perturbed opponent predictions (sig_lon or sig_lat > 0)
+    float sig_lon, sig_lat;
+    float2 *ptan[2];               // per vehicle: T+1 unit directions of the predictions' nearest segments
 };
 
 __device__ __forceinline__ void stamp(const PlanArgs &a, int i)
@@ -400,6 +403,26 @@ __device__ void proposal_for(const PlanArgs &a, const RaceDev &R, int i, int bin
     }
 }
 
+// ---------------------------------------------------------------- perturbed predictions
+// Gaussian pair of step tau (1..T) of opponent jv's prediction as seen by
+// the best response with counter word ar = observer | round << 16: counter
+// (2^30 | jv, (tau-1) >> 1, ar, race), a word no sample uses (k < 2^30).
+__device__ __forceinline__ float2 pred_noise(uint2 key, unsigned jv, int tau, unsigned ar, unsigned race)
+{
+    const uint4 w = philox4x32_10(make_uint4((1u << 30) | jv, (unsigned)((tau - 1) >> 1), ar, race), key);
+    return ((tau - 1) & 1) ? box_muller(w.z, w.w) : box_muller(w.x, w.y);
+}
+
+// Predicted position p of step tau moved by sig_lon z_1 along the unit
+// direction t of its nearest segment and sig_lat z_2 along t's left normal.
+__device__ __forceinline__ float2 perturb_point(const PlanArgs &a, float2 p, float2 t, unsigned jv, int tau,
+                                                unsigned ar, unsigned race)
+{
+    const float2 z = pred_noise(a.key, jv, tau, ar, race);
+    const float ds = a.sig_lon * z.x, dd = a.sig_lat * z.y;
+    return make_float2(p.x + ds * t.x - dd * t.y, p.y + ds * t.y + dd * t.x);
+}
+
 // ---------------------------------------------------------------- GA-IBR-MPPI
 __device__ __forceinline__ float warp_sum(float v)
 {
@@ -596,7 +619,8 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
                            a.ref + (size_t)R.pos_off + (size_t)i * (R.T + 1));
         }
         roll_cooperative<MAXO>(a.p, x0, f.s, j0, R.T, R.n_tail, a.pos[0] + R.pos_off + (size_t)i * (R.T + 1), nullptr,
-                               nullptr, a.summ[0] + ag, flag);
+                               nullptr, a.summ[0] + ag, flag,
+                               a.ptan[0] ? a.ptan[0] + R.pos_off + (size_t)i * (R.T + 1) : nullptr);
     }
     {
         // fresh selection keys for every best response of the plan
@@ -673,15 +697,28 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
                 const float4 *gref = a.ref + (size_t)R.pos_off + (size_t)i * (T + 1);
                 for (int q = threadIdx.x; q <= T; q += blockDim.x) Tl::ref()[q] = __ldcg(gref + q);
                 const float2 *pin = a.pos[bin] + R.pos_off;
+                const float2 *tin = a.ptan[bin] ? a.ptan[bin] + R.pos_off : nullptr;
+                const unsigned ar = (unsigned)i | ((unsigned)round << 16);
                 stage_opponents<MAXO>(T, n_opp, [&](int tau, int o) {
                     const int jv = o < i ? o : o + 1;
-                    return __ldcg(pin + (size_t)jv * (T + 1) + tau);
+                    const float2 q = __ldcg(pin + (size_t)jv * (T + 1) + tau);
+                    if (!tin) return q;
+                    return perturb_point(a, q, __ldcg(tin + (size_t)jv * (T + 1) + tau), (unsigned)jv, tau, ar,
+                                         R.race_tag);
                 });
                 if (threadIdx.x < n_opp) {
                     const int o = threadIdx.x;
                     const int jv = o < i ? o : o + 1;
                     const AgentDev B = load_agent(a.agents + R.agent_off + jv);
-                    const float2 sm = __ldcg(a.summ[bin] + R.agent_off + jv);
+                    float2 sm = __ldcg(a.summ[bin] + R.agent_off + jv);
+                    if (tin) {
+                        // the perturbed prediction's progress gain and tail-mean offset
+                        sm.x += a.sig_lon * pred_noise(a.key, (unsigned)jv, T, ar, R.race_tag).x;
+                        float dsum = 0.f;
+                        for (int tau = T - R.n_tail + 1; tau <= T; ++tau)
+                            dsum += a.sig_lat * pred_noise(a.key, (unsigned)jv, tau, ar, R.race_tag).y;
+                        sm.y += dsum / (float)R.n_tail;
+                    }
                     const float ds_t = wrap_len(A.s_t - B.s_t, tv.L, 1.0f / tv.L);
                     const float alpha = 1.0f / (1.0f + fabsf(ds_t) / (a.p.s_contest + a.p.eps_alpha));
                     const float gamma = (ds_t > a.p.s_role && ds_t < a.p.s_contest) ? a.p.w_block : 0.f;
@@ -787,7 +824,8 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
             float *xi_h = a.xi_hist ? a.xi_hist + (size_t)round * a.xi_total + xo : nullptr;
             roll_cooperative<MAXO>(a.p, A.x0, A.s_t, A.j0, T, R.n_tail,
                                    extra ? nullptr : a.pos[bout] + R.pos_off + (size_t)i * (T + 1), xi_final, xi_h,
-                                   extra ? nullptr : a.summ[bout] + ag, flag);
+                                   extra ? nullptr : a.summ[bout] + ag, flag,
+                                   (extra || !a.ptan[bout]) ? nullptr : a.ptan[bout] + R.pos_off + (size_t)i * (T + 1));
         }
         if (round <= a.L) ok = grid_barrier(a, skip);
         stamp(a, 4 + 3 * round);
@@ -797,7 +835,7 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
 
 // ================================================================ host side
 struct Layout {
-    size_t bar, keys, agents, ref, pos0, pos1, summ0, summ1, prop, part, total;
+    size_t bar, keys, agents, ref, pos0, pos1, summ0, summ1, prop, part, tan0, tan1, total;
     // part_floats: GA-IBR-MPPI partial sums (0 for the SGTP calls)
     Layout(long long n_keys, long long n_agents, long long n_pos, int maxT, long long part_floats = 0)
     {
@@ -812,7 +850,9 @@ struct Layout {
         summ1 = up(summ0 + sizeof(float2) * n_agents);
         prop = up(summ1 + sizeof(float2) * n_agents);
         part = up(prop + sizeof(float4) * n_agents * maxT);
-        total = up(part + sizeof(float) * part_floats);
+        tan0 = up(part + sizeof(float) * part_floats);
+        tan1 = up(tan0 + sizeof(float2) * n_pos);
+        total = up(tan1 + sizeof(float2) * n_pos);
     }
 };
 
@@ -937,6 +977,10 @@ void attach_workspace(PlanArgs &a, const Layout &lay, void *ws)
     a.summ[1] = (float2 *)(w + lay.summ1);
     a.prop = (float4 *)(w + lay.prop);
     a.mppi_part = (float *)(w + lay.part);
+    if (a.sig_lon != 0.f || a.sig_lat != 0.f) {
+        a.ptan[0] = (float2 *)(w + lay.tan0);
+        a.ptan[1] = (float2 *)(w + lay.tan1);
+    }
 }
 
 long long mppi_part_floats(long long n_agents, int K, int maxT)
@@ -965,7 +1009,8 @@ static sgtp_status ibr_plan_impl(const sgtp_track *trk, int32_t track_id, const 
                                  int32_t ego, uint64_t seed, uint32_t race, float *xi_out, int32_t *k_star_out,
                                  float *xi_hist, float *u_hist, int32_t *status_dev, const sgtp_launch_opts *opts,
                                  const sgtp_mlp *mlp, int32_t K_prop, float *feat_out, float *prop_out,
-                                 void *workspace, size_t workspace_bytes, void *stream, float mppi_lambda = 0.f)
+                                 void *workspace, size_t workspace_bytes, void *stream, float mppi_lambda = 0.f,
+                                 float sig_lon = 0.f, float sig_lat = 0.f)
 {
     SGTP_CHECK(trk != nullptr, "track is NULL");
     SGTP_CHECK(track_id >= 0 && track_id < trk->n_tracks, "track_id out of range");
@@ -986,9 +1031,14 @@ static sgtp_status ibr_plan_impl(const sgtp_track *trk, int32_t track_id, const 
                      mppi ? mppi_part_floats(n_v, K, T) : 0);
     SGTP_CHECK(workspace && workspace_bytes >= lay.total, "workspace too small: need %zu bytes", lay.total);
     SGTP_CHECK(((uintptr_t)workspace & 255u) == 0, "workspace must be 256-byte aligned");
+    SGTP_CHECK(std::isfinite(sig_lon) && std::isfinite(sig_lat) && sig_lon >= 0.f && sig_lat >= 0.f,
+               "prediction sigmas must be finite and >= 0");
+    SGTP_CHECK(!(mppi && (sig_lon > 0.f || sig_lat > 0.f)), "perturbed predictions take the SGTP update only");
     PlanArgs a{};
     fill_common(a, trk, p, K, L, X0, U_io, vref_scale, seed, xi_out, k_star_out, xi_hist, u_hist, status_dev, opts);
     a.mppi_il = il;
+    a.sig_lon = sig_lon;
+    a.sig_lat = sig_lat;
     RaceDev &R = a.one;
     R = RaceDev{};
     R.track_id = track_id; R.n_v = n_v; R.T = T; R.ego = ego; R.race_tag = race;
@@ -1062,6 +1112,19 @@ extern "C" sgtp_status sgtp_ibr_plan_mppi(const sgtp_track *trk, int32_t track_i
     return ibr_plan_impl(trk, track_id, p, n_v, X0, U_io, vref_scale, T, K, L, ego, seed, race, xi_out, k_star_out,
                          xi_hist, u_hist, status_dev, opts, nullptr, 0, nullptr, nullptr, workspace, workspace_bytes,
                          stream, lambda);
+}
+
+extern "C" sgtp_status sgtp_ibr_plan_perturbed(const sgtp_track *trk, int32_t track_id, const sgtp_params *p,
+                                               int32_t n_v, const float *X0, float *U_io, const float *vref_scale,
+                                               int32_t T, int32_t K, int32_t L, int32_t ego, uint64_t seed,
+                                               uint32_t race, float sigma_lon, float sigma_lat, float *xi_out,
+                                               int32_t *k_star_out, float *xi_hist, float *u_hist,
+                                               int32_t *status_dev, const sgtp_launch_opts *opts, void *workspace,
+                                               size_t workspace_bytes, void *stream)
+{
+    return ibr_plan_impl(trk, track_id, p, n_v, X0, U_io, vref_scale, T, K, L, ego, seed, race, xi_out, k_star_out,
+                         xi_hist, u_hist, status_dev, opts, nullptr, 0, nullptr, nullptr, workspace, workspace_bytes,
+                         stream, 0.f, sigma_lon, sigma_lat);
 }
 
 extern "C" sgtp_status sgtp_batch_create(const sgtp_track *trk, const sgtp_race *races, int32_t n_races, int32_t K,
@@ -1156,7 +1219,8 @@ static sgtp_status batch_plan_impl(const sgtp_batch *b, const sgtp_params *p, co
                                    const float *vref_scale, uint64_t seed, float *xi_out, int32_t *k_star_out,
                                    float *xi_hist, float *u_hist, int32_t *status_dev, const sgtp_launch_opts *opts,
                                    const sgtp_mlp *mlp, int32_t K_prop, float *feat_out, float *prop_out,
-                                   void *workspace, size_t workspace_bytes, void *stream, float mppi_lambda = 0.f)
+                                   void *workspace, size_t workspace_bytes, void *stream, float mppi_lambda = 0.f,
+                                   float sig_lon = 0.f, float sig_lat = 0.f)
 {
     SGTP_CHECK(b != nullptr, "batch is NULL");
     sgtp_status st = check_params(p);
@@ -1173,9 +1237,14 @@ static sgtp_status batch_plan_impl(const sgtp_batch *b, const sgtp_params *p, co
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
     PlanArgs a{};
+    SGTP_CHECK(std::isfinite(sig_lon) && std::isfinite(sig_lat) && sig_lon >= 0.f && sig_lat >= 0.f,
+               "prediction sigmas must be finite and >= 0");
+    SGTP_CHECK(!(mppi && (sig_lon > 0.f || sig_lat > 0.f)), "perturbed predictions take the SGTP update only");
     fill_common(a, b->trk, p, b->K, b->L, X0, U_io, vref_scale, seed, xi_out, k_star_out, xi_hist, u_hist,
                 status_dev, opts);
     a.mppi_il = il;
+    a.sig_lon = sig_lon;
+    a.sig_lat = sig_lat;
     a.races = b->races_dev;
     a.n_races = b->n_races;
     a.n_agents = (int)b->agents;
@@ -1236,6 +1305,18 @@ extern "C" sgtp_status sgtp_batch_plan_mppi(const sgtp_batch *b, const sgtp_para
     SGTP_CHECK(mppi_inverse(lambda) > 0.f, "lambda must be finite and > 0");
     return batch_plan_impl(b, p, X0, U_io, vref_scale, seed, xi_out, k_star_out, xi_hist, u_hist, status_dev, opts,
                            nullptr, 0, nullptr, nullptr, workspace, workspace_bytes, stream, lambda);
+}
+
+extern "C" sgtp_status sgtp_batch_plan_perturbed(const sgtp_batch *b, const sgtp_params *p, float sigma_lon,
+                                                 float sigma_lat, const float *X0, float *U_io,
+                                                 const float *vref_scale, uint64_t seed, float *xi_out,
+                                                 int32_t *k_star_out, float *xi_hist, float *u_hist,
+                                                 int32_t *status_dev, const sgtp_launch_opts *opts, void *workspace,
+                                                 size_t workspace_bytes, void *stream)
+{
+    return batch_plan_impl(b, p, X0, U_io, vref_scale, seed, xi_out, k_star_out, xi_hist, u_hist, status_dev, opts,
+                           nullptr, 0, nullptr, nullptr, workspace, workspace_bytes, stream, 0.f, sigma_lon,
+                           sigma_lat);
 }
 
 // ================================================================ CUDA graphs

@@ -371,11 +371,14 @@ __device__ __forceinline__ void stage_opponents(int T, int n_opp, F src)
 // reaches the same nearest segment as the sample loop's walk; then one
 // thread unwraps the progress in step order.  Outputs (any may be NULL):
 // positions (T+1), states twice (T+1)x4, and the prediction summary
-// (progress gain s_H - s_t, tail-mean offset).  Uses the tile's window,
+// (progress gain s_H - s_t, tail-mean offset); tan_out (T+1, entry 0
+// unused) receives the unit direction of each state's nearest segment, the
+// longitudinal axis of a perturbed prediction.  Uses the tile's window,
 // which must be staged.  All threads of the CTA must call it.
 template <int MAXO>
 __device__ void roll_cooperative(const sgtp_params &p, float4 x0, float s_t, int j0, int T, int n_tail,
-                                 float2 *pos_out, float *xi_a, float *xi_b, float2 *summ_out, int &flag)
+                                 float2 *pos_out, float *xi_a, float *xi_b, float2 *summ_out, int &flag,
+                                 float2 *tan_out = nullptr)
 {
     using Tl = Tile<MAXO>;
     const BRScalars &S = Tl::sc();
@@ -399,6 +402,11 @@ __device__ void roll_cooperative(const sgtp_params &p, float4 x0, float s_t, int
         const int guess = r0 + chord_guess(v.x - x0.x, v.y - x0.y, b0, 4 * kWinTile);
         const FrenetPt f = frenet_search(S.tv, w, guess, v.x, v.y);
         flag |= f.flag;
+        if (tan_out) {
+            const float4 b = seg_at(S.tv, w, f.m).b;
+            const float il = b.w * b.z;                // 1 / |e_j|
+            tan_out[q + 1] = make_float2(b.x * il, b.y * il);
+        }
         fr[q] = make_float2(f.s, f.d);
     }
     __syncthreads();

@@ -229,7 +229,7 @@ def best_response_mixed(track: Track, params: dict, x0, u_nom, vref_scale, opp, 
 
 def ibr_plan(track: Track, params: dict, X0, U_io, vref_scale, T, K, L, ego=0, seed=0, race=0, track_id=0,
              want_hist=False, opts=None, workspace=None, out=None, stream=None, mlp=None, K_prop=0,
-             want_features=False, want_prop=False, mppi_lambda=None):
+             want_features=False, want_prop=False, mppi_lambda=None, pred_sigma=None):
     """The SGTP planning call (Alg. 1) for one race; U_io is updated in place
     (warm start).  Returns device tensors xi (n_v, T+1, 4), k_star, status.
     With ``mlp`` (a :class:`learned.Mlp`) K_prop samples of every best
@@ -238,7 +238,8 @@ def ibr_plan(track: Track, params: dict, X0, U_io, vref_scale, T, K, L, ego=0, s
     proposals ((L+2, n_v, T, 4)).  With ``mppi_lambda`` the call is the
     GA-IBR-MPPI ablation (sgtp_ibr_plan_mppi): every response's controls
     become the path-integral mean at that temperature, and k_star holds the
-    lowest-cost samples."""
+    lowest-cost samples.  With ``pred_sigma = (sigma_lon, sigma_lat)`` every
+    opponent prediction is perturbed before use (sgtp_ibr_plan_perturbed)."""
     n_v = X0.shape[0]
     dev = X0.device
     _dev(X0, "X0", shape=(n_v, 4))
@@ -253,6 +254,8 @@ def ibr_plan(track: Track, params: dict, X0, U_io, vref_scale, T, K, L, ego=0, s
             out["u_hist"] = torch.empty((L + 2, n_v, T, 2), dtype=torch.float32, device=dev)
     if mppi_lambda is not None and (mlp is not None or want_features or want_prop):
         raise ValueError("GA-IBR-MPPI takes the plain sampler only")
+    if pred_sigma is not None and (mppi_lambda is not None or mlp is not None or want_features or want_prop):
+        raise ValueError("perturbed predictions take the plain SGTP call only")
     nb = plan_workspace_bytes(n_v, T, L) if mppi_lambda is None else plan_mppi_workspace_bytes(n_v, T, L, K)
     ws = workspace if workspace is not None else _ws(nb, dev)
     P = make_params(params)
@@ -276,6 +279,17 @@ def ibr_plan(track: Track, params: dict, X0, U_io, vref_scale, T, K, L, ego=0, s
             out["prop"].data_ptr() if "prop" in out else None,
             out["status"].data_ptr(), C.byref(o), ws.data_ptr(), ws.numel(), stream_ptr(stream))
         check(st, "sgtp_ibr_plan_learned")
+        return out
+    if pred_sigma is not None:
+        st = lib().sgtp_ibr_plan_perturbed(track.handle, track_id, C.byref(P), n_v, X0.data_ptr(), U_io.data_ptr(),
+                                           vref_scale.data_ptr(), T, K, L, ego, int(seed), race,
+                                           float(pred_sigma[0]), float(pred_sigma[1]), out["xi"].data_ptr(),
+                                           out["k_star"].data_ptr(),
+                                           out["xi_hist"].data_ptr() if "xi_hist" in out else None,
+                                           out["u_hist"].data_ptr() if "u_hist" in out else None,
+                                           out["status"].data_ptr(), C.byref(o), ws.data_ptr(), ws.numel(),
+                                           stream_ptr(stream))
+        check(st, "sgtp_ibr_plan_perturbed")
         return out
     if mppi_lambda is not None:
         st = lib().sgtp_ibr_plan_mppi(track.handle, track_id, C.byref(P), n_v, X0.data_ptr(), U_io.data_ptr(),
@@ -412,10 +426,12 @@ class Batch:
         return w.value
 
     def plan(self, params, X0, U_io, vref_scale, seed=0, want_hist=False, opts=None, workspace=None, out=None,
-             stream=None, mlp=None, K_prop=0, mppi_lambda=None):
+             stream=None, mlp=None, K_prop=0, mppi_lambda=None, pred_sigma=None):
         """Plan every race in one launch; with ``mlp`` (a learned.Mlp) K_prop
         samples of every best response come from the network's proposal; with
-        ``mppi_lambda`` every race runs the GA-IBR-MPPI ablation."""
+        ``mppi_lambda`` every race runs the GA-IBR-MPPI ablation; with
+        ``pred_sigma = (sigma_lon, sigma_lat)`` the opponent predictions are
+        perturbed (sgtp_batch_plan_perturbed)."""
         dev = X0.device
         _dev(X0, "X0", shape=(self.agents, 4))
         _dev(U_io, "U_io", shape=(self.u_elems,))
@@ -428,6 +444,18 @@ class Batch:
             self.workspace_bytes if mppi_lambda is None else self.mppi_workspace_bytes, dev)
         P = make_params(params)
         o = opts if opts is not None else launch_opts()
+        if pred_sigma is not None:
+            if mlp is not None or mppi_lambda is not None:
+                raise ValueError("perturbed predictions take the plain SGTP call only")
+            st = lib().sgtp_batch_plan_perturbed(self._h, C.byref(P), float(pred_sigma[0]), float(pred_sigma[1]),
+                                                 X0.data_ptr(), U_io.data_ptr(), vref_scale.data_ptr(), int(seed),
+                                                 out["xi"].data_ptr(), out["k_star"].data_ptr(),
+                                                 out["xi_hist"].data_ptr() if "xi_hist" in out else None,
+                                                 out["u_hist"].data_ptr() if "u_hist" in out else None,
+                                                 out["status"].data_ptr(), C.byref(o), ws.data_ptr(), ws.numel(),
+                                                 stream_ptr(stream))
+            check(st, "sgtp_batch_plan_perturbed")
+            return out
         if mppi_lambda is not None:
             st = lib().sgtp_batch_plan_mppi(self._h, C.byref(P), float(mppi_lambda), X0.data_ptr(), U_io.data_ptr(),
                                             vref_scale.data_ptr(), int(seed), out["xi"].data_ptr(),

@@ -54,11 +54,12 @@ class Trials:
     """A set of closed-loop trials run together (one batch)."""
 
     def __init__(self, scenarios, params: dict, K: int, L: int, sp: SimParams, mppi_lambda=None, opts=None,
-                 device="cuda"):
+                 device="cuda", pred_sigma=None):
         self.scenarios = scenarios
         self.params = params
         self.sp = sp
         self.mppi_lambda = mppi_lambda
+        self.pred_sigma = pred_sigma
         self.track = Track.from_many([sc.track for sc in scenarios])
         self.batch = Batch(self.track, [dict(track_id=r, n_v=sc.X0.shape[0], T=sc.T, ego=sc.ego, race_tag=r)
                                         for r, sc in enumerate(scenarios)], K=K, L=L)
@@ -85,7 +86,7 @@ class Trials:
 
     def plan(self):
         self.batch.plan(self.params, self.X, self.U, self.vs, seed=self.k, opts=self.opts, workspace=self.ws,
-                        out=self.out, mppi_lambda=self.mppi_lambda)
+                        out=self.out, mppi_lambda=self.mppi_lambda, pred_sigma=self.pred_sigma)
 
     def sim_step(self):
         check(lib().sgtp_sim_step(self.batch.handle, C.byref(self.P), C.byref(self.sp), self.X.data_ptr(),

@@ -105,3 +105,16 @@ def test_zero_sigma_plan_is_the_sgtp_plan():
         np.testing.assert_array_equal(a[k], b[k])
     c = O.ibr_plan_perturbed(p, ot, sc.X0, sc.U0, sc.vref_scale, T, K, L, sc.ego, 0.4, 0.2, seed=4, want_hist=True)
     assert not np.array_equal(a["k_star"], c["k_star"])     # the noise reaches the responses
+
+
+def test_perturbed_candidate_costs_reduce_to_the_plain_ones_at_zero_sigma():
+    """The perturbed evaluation with unperturbed positions and zero shifts is
+    the plain evaluation, candidate by candidate."""
+    sc = S.single_br_oval(K=64, T=30)
+    p = S.params_fullscale()
+    ot = O.Track(sc.track.xr, sc.track.wl, sc.track.wr)
+    a = O.rollout_costs(p, ot, sc.X0[0], sc.U0[0], 1.0, sc.opp, sc.T, K=64, seed=2, rnd=1)
+    b = O.rollout_costs_perturbed(p, ot, sc.X0[0], sc.U0[0], 1.0, sc.opp, sc.opp, np.zeros((1, 2)), sc.T, K=64,
+                                  seed=2, rnd=1)
+    for k in ("cost", "feasible", "violation", "margins"):
+        np.testing.assert_array_equal(a[k], b[k])
