@@ -297,14 +297,16 @@ __global__ void __launch_bounds__(256) br_prep_kernel(TrackView tv, sgtp_params 
     __syncthreads();
     const BRScalars &S = Tl::sc();
     const SegWindow w = Tl::win(S.w0, S.Wn);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         const FrenetPt f = frenet_at(tv, j0, xs.x, xs.y);
-        h->key = ~0ull;
-        h->x0 = xs;
-        h->s_t = f.s;
-        h->d_t = f.d;
-        h->t0 = f.t;
-        h->j0 = j0;
+        if (threadIdx.x == 0) {
+            h->key = ~0ull;
+            h->x0 = xs;
+            h->s_t = f.s;
+            h->d_t = f.d;
+            h->t0 = f.t;
+            h->j0 = j0;
+        }
         reference_traj(tv, w, Tl::C(), j0, f.s, p.dt, vscale, T, ref);
     }
     // every (opponent, step) projection in parallel

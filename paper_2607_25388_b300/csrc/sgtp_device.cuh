@@ -368,56 +368,73 @@ __device__ __forceinline__ float wrap_angle(float a) { return __fmaf_rn(-kTwoPi,
 // accumulated as an unevaluated float pair (hi + lo, Knuth's two-sum); the
 // position inside a segment is ((hi - lap L) - s_j) + lo with an exact lap
 // subtraction, so the reference stays within a few float ulps of the exact
-// recursion however long the track.  One thread.  Segment data comes from
-// the shared-memory window (A, B, S and C) when it holds the segment, else
-// from global memory.  j0 is the global segment of s0 (s0 in [0, L)).
+// recursion however long the track.
+//
+// One warp (all 32 lanes call it; lane 0 writes ref).  The recursion is
+// sequential, so every lane carries the same (hi, lo); the lanes hold 32
+// consecutive segments (from the shared-memory window, A, B, S and C, when it
+// has them, else from global memory), and each step finds the segment
+// holding the progress, s_j <= hm < s_j + |e_j| (the lap's last segment ends
+// at L), with one ballot -- the lowest such lane -- instead of a walk of
+// dependent loads.  The block moves forward when the progress passes its
+// middle.  j0 is the global segment of s0 (s0 in [0, L)).
 __device__ __forceinline__ void reference_traj(const TrackView &tv, const SegWindow &w, const float4 *Cw, int j0,
                                                float s0, float dt, float vscale, int T, float4 *ref)
 {
+    const int lane = threadIdx.x & 31;
     const int N = tv.N, Wn = w.Wn;
     const float L = tv.L;
     float hi = s0, lo = 0.f;
-    int j = j0, lap = 0;                                     // segment j of lap `lap`
-    int rl = Wn > 0 ? wrap_index(j0 - w.w0, N) : -1;       // its window-local index
-    // data of segment j, reloaded only when the walk moves to another segment
+    int jb = j0, lapb = 0;                 // first segment of the lanes' block and its lap
     float4 va, vb, c;
     float sj;
-    auto load = [&]() {
+    int lapl;
+    bool last;
+    auto load_block = [&]() {
+        int g = jb + lane, lp = lapb;
+        while (g >= N) { g -= N; ++lp; }
+        while (g < 0) { g += N; --lp; }
+        const int rl = Wn > 0 ? wrap_index(g - w.w0, N) : -1;
         if ((unsigned)rl < (unsigned)Wn) {
             va = w.A[rl]; vb = w.B[rl]; sj = w.S[rl]; c = Cw[rl];
         } else {
-            va = __ldg(tv.A + j); vb = __ldg(tv.B + j); sj = __ldg(tv.S + j); c = __ldg(tv.C + j);
+            va = __ldg(tv.A + g); vb = __ldg(tv.B + g); sj = __ldg(tv.S + g); c = __ldg(tv.C + g);
         }
+        lapl = lp;
+        last = g == N - 1;
     };
-    load();
-    // x^r at the current progress (hi, lo): walk to the segment holding it
+    load_block();
     auto locate = [&]() -> float4 {
-        for (int it = 0; it < 2 * N + 2; ++it) {
-            const float hm = hi - (float)lap * L;            // exact: within a factor 2 of lap L
-            const float sn = (j + 1 == N) ? L : sj + vb.w;
-            if (hm < sj) {
-                --j; --rl;
-                if (j < 0) { j = N - 1; --lap; }
-                load();
-                continue;
+        for (int it = 0; it < 2 * (N / 32) + 8; ++it) {
+            const float hm = hi - (float)lapl * L;            // exact: within a factor 2 of lap L
+            const float sn = last ? L : sj + vb.w;
+            const unsigned bal = __ballot_sync(0xffffffffu, hm >= sj && hm < sn);
+            if (bal) {
+                const int src = __ffs(bal) - 1;
+                const float u = ((hm - sj) + lo) * (vb.w * vb.z);      // / |e_j|, as |e_j| * (1 / |e_j|^2)
+                float4 o;
+                o.x = __shfl_sync(0xffffffffu, __fmaf_rn(u, vb.x, va.x), src);
+                o.y = __shfl_sync(0xffffffffu, __fmaf_rn(u, vb.y, va.y), src);
+                o.z = __shfl_sync(0xffffffffu, __fmaf_rn(u, c.y, c.x), src);
+                o.w = __shfl_sync(0xffffffffu, __fmaf_rn(u, c.w, c.z), src);
+                if (src >= 16) {                               // keep at least 16 segments ahead
+                    jb += src;
+                    while (jb >= N) { jb -= N; ++lapb; }
+                    load_block();
+                }
+                return o;
             }
-            if (hm >= sn) {
-                ++j; ++rl;
-                if (j == N) { j = 0; ++lap; }
-                load();
-                continue;
-            }
-            const float u = ((hm - sj) + lo) / vb.w;
-            float4 o;
-            o.x = __fmaf_rn(u, vb.x, va.x);
-            o.y = __fmaf_rn(u, vb.y, va.y);
-            o.z = __fmaf_rn(u, c.y, c.x);
-            o.w = __fmaf_rn(u, c.w, c.z);
-            return o;
+            // no lane holds it: move the block by 32 segments toward it
+            const bool ahead = __shfl_sync(0xffffffffu, hm >= sn, 31);
+            jb += ahead ? 32 : -32;
+            while (jb >= N) { jb -= N; ++lapb; }
+            while (jb < 0) { jb += N; --lapb; }
+            load_block();
         }
-        return make_float4(va.x, va.y, c.x, c.z);
+        return make_float4(__shfl_sync(0xffffffffu, va.x, 0), __shfl_sync(0xffffffffu, va.y, 0),
+                           __shfl_sync(0xffffffffu, c.x, 0), __shfl_sync(0xffffffffu, c.z, 0));
     };
-    ref[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lane == 0) ref[0] = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 r_cur = locate();
     for (int tau = 0; tau < T; ++tau) {
         const float ds = __fmul_rn(dt, __fmul_rn(vscale, r_cur.w));
@@ -432,7 +449,7 @@ __device__ __forceinline__ void reference_traj(const TrackView &tv, const SegWin
         float4 r1 = locate();
         r_cur = r1;
         r1.w = __fmul_rn(r1.w, vscale);
-        ref[tau + 1] = r1;
+        if (lane == 0) ref[tau + 1] = r1;
     }
 }
 

@@ -612,9 +612,9 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
         const FrenetPt f = frenet_at(tv, j0, x0.x, x0.y);
         AgentDev A;
         A.x0 = x0; A.s_t = f.s; A.d_t = f.d; A.j0 = j0; A.race = ri; A.t0 = f.t;
-        if (threadIdx.x == 32) {
+        if ((threadIdx.x >> 5) == 1) {
             // reference recursion (warp 1) alongside the nominal rollout's dynamics (warp 0)
-            a.agents[ag] = A;
+            if (threadIdx.x == 32) a.agents[ag] = A;
             reference_traj(tv, Tl::win(S.w0, S.Wn), Tl::C(), j0, f.s, a.p.dt, a.vref[ag], R.T,
                            a.ref + (size_t)R.pos_off + (size_t)i * (R.T + 1));
         }

@@ -136,6 +136,28 @@ __device__ __forceinline__ void bicycle_step(const sgtp_params &p, float &x, flo
     x = x1; y = y1; psi = psi1; v = v1;
 }
 
+// bicycle_step with the steering terms sin(delta) and 1/(cos(delta) L)
+// computed beforehand (same instructions, so the same bits): the
+// sequential rollout of a fixed control sequence then carries only the
+// state recursion.
+__device__ __forceinline__ void bicycle_step_pre(const sgtp_params &p, float &x, float &y, float &psi, float &v, float a,
+                                                 float2 steer)
+{
+    const float pw = wrap_angle(psi);
+    const float sn = sin_ftz(pw), cs = cos_ftz(pw);
+    const float dv = __fmul_rn(p.dt, v);
+    const float x1 = __fmaf_rn(dv, cs, x);
+    const float y1 = __fmaf_rn(dv, sn, y);
+    const float psi1 = psi + __fmul_rn(__fmul_rn(dv, steer.x), steer.y);
+    const float v1 = fminf(fmaxf(__fmaf_rn(p.dt, a, v), p.v_min), p.v_max);
+    x = x1; y = y1; psi = psi1; v = v1;
+}
+
+__device__ __forceinline__ float2 steer_terms(const sgtp_params &p, float delta)
+{
+    return make_float2(sin_ftz(delta), rcp_ftz(__fmul_rn(cos_ftz(delta), p.wheelbase)));
+}
+
 // Normal pairs of candidate k at steps 2m and 2m+1 (one Philox block).
 // The key comes from a kernel parameter, so that the round keys of the
 // Weyl schedule stay in the uniform datapath.
@@ -363,9 +385,11 @@ __device__ __forceinline__ void stage_opponents(int T, int n_opp, F src)
     }
 }
 
-// Roll out the controls ctl()[0..T) from x0 cooperatively: one thread runs
-// the bicycle recurrence (the same arithmetic as the sample loop, so the
-// states are bit-identical to the evaluated candidate's) into st(); then
+// Roll out the controls ctl()[0..T) from x0 cooperatively: warp 0 prepares
+// the steering terms of every step (in the opponent area, which only the
+// sample phase uses), then its thread 0 runs the bicycle recurrence
+// (the same arithmetic as the sample loop, so the states are bit-identical
+// to the evaluated candidate's) into st(); then
 // every thread projects one state onto the track by the distance search of
 // frenet_search from a guess (chord_guess: the signed chord from x0 in segment lengths), which
 // reaches the same nearest segment as the sample loop's walk; then one
@@ -384,13 +408,18 @@ __device__ void roll_cooperative(const sgtp_params &p, float4 x0, float s_t, int
     const BRScalars &S = Tl::sc();
     float4 *st = Tl::st();
     float2 *fr = Tl::fr();
-    if (threadIdx.x == 0) {
-        float x = x0.x, y = x0.y, psi = x0.z, v = x0.w;
-        st[0] = x0;
-        for (int tau = 0; tau < T; ++tau) {
-            const float2 u = Tl::ctl()[tau];
-            bicycle_step(p, x, y, psi, v, u.x, u.y);
-            st[tau + 1] = make_float4(x, y, psi, v);
+    float2 *steer = (float2 *)Tl::opp();
+    if (threadIdx.x < 32) {
+        for (int q = threadIdx.x; q < T; q += 32) steer[q] = steer_terms(p, Tl::ctl()[q].y);
+        __syncwarp();
+        if (threadIdx.x == 0) {
+            float x = x0.x, y = x0.y, psi = x0.z, v = x0.w;
+            st[0] = x0;
+#pragma unroll 4
+            for (int tau = 0; tau < T; ++tau) {
+                bicycle_step_pre(p, x, y, psi, v, Tl::ctl()[tau].x, steer[tau]);
+                st[tau + 1] = make_float4(x, y, psi, v);
+            }
         }
     }
     __syncthreads();
