@@ -4,7 +4,8 @@
 
 1. single best response on the oval (K = 1024, T = 40, one opponent);
 2. two-car plan (K = 8192, T = 50, L = 3);
-3. ten-car plan (K = 16384, T = 60, L = 5), direct launch and CUDA-graph replay;
+3. ten-car plan (K = 16384, T = 60, L = 5), direct launch and CUDA-graph replay (median and p99 over at
+   least 200 replays);
 4. 256 independent races in one launch (n_v ~ U{2..10}, T ~ U{30..80}, K = 4096, L = 3), direct and graph;
 5. plan latency of the ten-car race: plain K = 16384, plain K = 4096, and the learned sampler with
    2048 proposal + 2048 plain samples (network weights do not change the work);
@@ -27,7 +28,7 @@ from . import scenario as S
 from .planner import Batch, PlanGraph, Track, best_response, ibr_plan, launch_opts
 
 
-def _median_ms(fn, reps, warmup=5):
+def _times_ms(fn, reps, warmup=5):
     for _ in range(warmup):
         fn()
     torch.cuda.synchronize()
@@ -40,7 +41,11 @@ def _median_ms(fn, reps, warmup=5):
         b.record(s)
         ev.append((a, b))
     torch.cuda.synchronize()
-    return float(np.median([a.elapsed_time(b) for a, b in ev]))
+    return np.array([a.elapsed_time(b) for a, b in ev])
+
+
+def _median_ms(fn, reps, warmup=5):
+    return float(np.median(_times_ms(fn, reps, warmup)))
 
 
 def _line(config, ms, steps, flops, **extra):
@@ -63,7 +68,7 @@ def config1(reps):
                  R.flops_best_response(sc.K, sc.T, 1), launches_per_call=3)
 
 
-def _plan_lines(name, sc, reps, graph=True):
+def _plan_lines(name, sc, reps, graph=True, min_graph_reps=0):
     p = S.params_fullscale()
     trk = Track.from_data(sc.track)
     n_v, T, K, L = sc.X0.shape[0], sc.T, sc.K, sc.L
@@ -86,7 +91,9 @@ def _plan_lines(name, sc, reps, graph=True):
             U.copy_(U0)
             g.launch()
 
-        out["graph"] = _line(name + " (CUDA graph replay)", _median_ms(replay, reps), steps, flops)
+        t = _times_ms(replay, max(reps, min_graph_reps), warmup=10)
+        out["graph"] = _line(name + " (CUDA graph replay)", float(np.median(t)), steps, flops, plans=int(t.size),
+                             p99_ms=float(np.percentile(t, 99)))
     return out
 
 
@@ -95,7 +102,8 @@ def config2(reps):
 
 
 def config3(reps):
-    return _plan_lines("3: ten-car plan, K=16384, T=60, L=5", S.ten_car_race(200), reps)
+    # median and p99 of at least 200 graph replays after 10 warm-up plans
+    return _plan_lines("3: ten-car plan, K=16384, T=60, L=5", S.ten_car_race(200), reps, min_graph_reps=200)
 
 
 def config4(reps):
