@@ -64,44 +64,53 @@ def test_zero_temperature_equals_sgtp_when_every_sample_is_feasible():
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
 
 
+def check_mppi_response(sc, params, g, K, L, seed, lam, race, rnd, i, trk, ot, nominal):
+    """Recompute response (rnd, i) of a GPU GA-IBR-MPPI plan with the oracle
+    from the GPU's own inputs and compare (tolerance in the module doc)."""
+    P = planner()
+    n_v, T = sc.X0.shape[0], sc.T
+    prev_xi = nominal if rnd == 0 else g["xi_hist"][rnd - 1]
+    u_nom = sc.U0[i] if rnd == 0 else g["u_hist"][rnd - 1][i]
+    opp = np.stack([prev_xi[j] for j in range(n_v) if j != i]) if n_v > 1 else None
+    slot = (L + 1) * n_v if rnd == L + 1 else rnd * n_v + i
+    what = f"round {rnd} agent {i}"
+    o = O.best_response_mppi(params, ot, sc.X0[i], u_nom, sc.vref_scale[i], opp, T, K, lam, seed=seed, race=race,
+                             agent=i, rnd=rnd, game_on=rnd > 0, want_costs=True)
+    smp = O.rollout_costs(params, ot, sc.X0[i], u_nom, sc.vref_scale[i], opp, T, K=K, seed=seed, race=race,
+                          agent=i, rnd=rnd, game_on=rnd > 0, want_controls=True)
+    gc = P.rollout_costs(trk, params, dev(np.float32(sc.X0[i])), dev(np.float32(u_nom)), sc.vref_scale[i],
+                         None if opp is None else dev(np.float32(opp)), T, K, seed=seed, race=race, agent=i,
+                         rnd=rnd, game_on=rnd > 0)["cost"].cpu().numpy().astype(np.float64)
+    c = o["costs"]
+    dc = float(np.abs(gc - c).max())
+    eps = dc / lam
+    spread = np.abs(smp["controls"] - o["u_new"][None]).max(axis=0)           # (T, 2)
+    tol = 2.0 * 2.0 * eps * spread + 1e-4 * np.maximum(1.0, np.abs(smp["controls"]).max(axis=0))
+    err = np.abs(g["u_hist"][rnd][i] - o["u_new"])
+    assert (err <= tol).all(), f"{what}: U error {err.max():.3e} above bound (dc {dc:.3e})"
+    # the trajectory is the rollout of the GPU's own U_new
+    assert_rel_close(g["xi_hist"][rnd][i], O.rollout(params, sc.X0[i], g["u_hist"][rnd][i], T), STATE_RTOL,
+                     f"{what} xi")
+    kg, ko = int(g["k_star"][slot]), o["k_min"]
+    assert kg == ko or abs(c[kg] - c[ko]) <= SELECT_RTOL * max(1.0, abs(c[ko])), \
+        f"{what}: lowest-cost sample gpu {kg} oracle {ko}"
+
+
+def nominal_predictions(sc, params):
+    lo = np.float32([params["a_min"], -params["delta_max"]])
+    hi = np.float32([params["a_max"], params["delta_max"]])
+    return np.stack([O.rollout(params, sc.X0[i], np.clip(sc.U0[i], lo, hi), sc.T) for i in range(sc.X0.shape[0])])
+
+
 def teacher_forced_mppi(sc, params, g, K, L, seed, lam, race=0):
     """Recompute every response with the oracle from the GPU's own inputs."""
     P = planner()
     trk = P.Track.from_data(sc.track)
     ot = O.Track(sc.track.xr, sc.track.wl, sc.track.wr)
-    n_v, T = sc.X0.shape[0], sc.T
-    lo = np.float32([params["a_min"], -params["delta_max"]])
-    hi = np.float32([params["a_max"], params["delta_max"]])
-    nominal = np.stack([O.rollout(params, sc.X0[i], np.clip(sc.U0[i], lo, hi), T) for i in range(n_v)])
-    ks = g["k_star"]
+    nominal = nominal_predictions(sc, params)
     for rnd in range(L + 2):
-        agents = [sc.ego] if rnd == L + 1 else range(n_v)
-        for i in agents:
-            prev_xi = nominal if rnd == 0 else g["xi_hist"][rnd - 1]
-            u_nom = sc.U0[i] if rnd == 0 else g["u_hist"][rnd - 1][i]
-            opp = np.stack([prev_xi[j] for j in range(n_v) if j != i]) if n_v > 1 else None
-            slot = (L + 1) * n_v if rnd == L + 1 else rnd * n_v + i
-            what = f"round {rnd} agent {i}"
-            o = O.best_response_mppi(params, ot, sc.X0[i], u_nom, sc.vref_scale[i], opp, T, K, lam, seed=seed,
-                                     race=race, agent=i, rnd=rnd, game_on=rnd > 0, want_costs=True)
-            smp = O.rollout_costs(params, ot, sc.X0[i], u_nom, sc.vref_scale[i], opp, T, K=K, seed=seed, race=race,
-                                  agent=i, rnd=rnd, game_on=rnd > 0, want_controls=True)
-            gc = P.rollout_costs(trk, params, dev(np.float32(sc.X0[i])), dev(np.float32(u_nom)), sc.vref_scale[i],
-                                 None if opp is None else dev(np.float32(opp)), T, K, seed=seed, race=race, agent=i,
-                                 rnd=rnd, game_on=rnd > 0)["cost"].cpu().numpy().astype(np.float64)
-            c = o["costs"]
-            dc = float(np.abs(gc - c).max())
-            eps = dc / lam
-            spread = np.abs(smp["controls"] - o["u_new"][None]).max(axis=0)           # (T, 2)
-            tol = 2.0 * 2.0 * eps * spread + 1e-4 * np.maximum(1.0, np.abs(smp["controls"]).max(axis=0))
-            err = np.abs(g["u_hist"][rnd][i] - o["u_new"])
-            assert (err <= tol).all(), f"{what}: U error {err.max():.3e} above bound (dc {dc:.3e})"
-            # the trajectory is the rollout of the GPU's own U_new
-            assert_rel_close(g["xi_hist"][rnd][i], O.rollout(params, sc.X0[i], g["u_hist"][rnd][i], T), STATE_RTOL,
-                             f"{what} xi")
-            kg, ko = int(ks[slot]), o["k_min"]
-            assert kg == ko or abs(c[kg] - c[ko]) <= SELECT_RTOL * max(1.0, abs(c[ko])), \
-                f"{what}: lowest-cost sample gpu {kg} oracle {ko}"
+        for i in ([sc.ego] if rnd == L + 1 else range(sc.X0.shape[0])):
+            check_mppi_response(sc, params, g, K, L, seed, lam, race, rnd, i, trk, ot, nominal)
 
 
 @pytest.mark.parametrize("n_v,T,K,L,lam,seed", [
