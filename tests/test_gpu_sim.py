@@ -85,15 +85,40 @@ def test_reset_matches_oracle():
         _frenet_close(rec.rel0[:n_v], o["rel0"], max(scale, OS.track_len(ot)), "rel0")
 
 
-@pytest.mark.parametrize("tracker,n_apply", [(0, 3), (1, 2)])
-def test_sim_step_teacher_forced(tracker, n_apply):
-    tr, scs, p, sp = _trials(tracker, n_apply)
-    tr.reset()
+def check_trial_step(p, ot, spd, sc, sl, X0, U0, xi, rec0, rec1, X1, U1, what):
+    """Compare one trial's GPU step (rec0 -> rec1, X0/U0 -> X1/U1) with the
+    oracle's step from the same inputs; returns whether the continuous
+    fields were compared (not after a contact decided within the guard)."""
+    n_v, T = sc.X0.shape[0], sc.T
+    a, u, x = sl
+    mg = []
+    Xo, Uo, so = OS.step(p, ot, spd, X0[a:a + n_v], U0[u:u + n_v * T * 2].reshape(n_v, T, 2),
+                         xi[x:x + n_v * (T + 1) * 4].reshape(n_v, T + 1, 4), sc.ego, _as_oracle(rec0, n_v), margins=mg)
+    near = any(m[0] <= GUARD_DIST or m[1] <= GUARD_DIST or m[2] <= GUARD_PROG or m[3] <= GUARD_DIST for m in mg)
+    g = rec1
+    if not near:
+        assert (g.alive, g.steps, g.ego_collision) == (so["alive"], so["steps"], so["ego_collision"]), what
+        assert (g.close_segments, g.close_steps) == (so["close_segments"], so["close_steps"]), what
+        assert list(g.close_run[:n_v]) == [int(v) for v in so["close_run"]], what
+    if g.steps != so["steps"]:
+        return False                 # a contact decided differently within the guard band
+    assert_rel_close(X1[a:a + n_v], Xo, STATE_RTOL, what + " X")
+    np.testing.assert_array_equal(U1[u:u + n_v * T * 2].reshape(n_v, T, 2), Uo.astype(np.float32), err_msg=what + " U")
+    scale = max(float(np.abs(sc.track.xr[:, :2]).max()), OS.track_len(ot))
+    _frenet_close(g.progress[:n_v], so["progress"], scale, what + " progress")
+    _frenet_close(g.s_raw[:n_v], so["s_raw"], scale, what + " s")
+    _frenet_close(g.d[:n_v], so["d"], scale, what + " d")
+    assert abs(g.ego_speed_sum - so["ego_speed_sum"]) <= 1e-4 * max(1.0, abs(so["ego_speed_sum"])), what
+    assert abs(g.ego_du2_sum - so["ego_du2_sum"]) <= 1e-4 * abs(so["ego_du2_sum"]) + 1e-5, what
+    return True
+
+
+def _run_checked(tr, scs, p, sp, periods, trials):
     spd = _sp_dict(sp)
     sl = _slices(scs)
-    tracks = [O.Track(sc.track.xr, sc.track.wl, sc.track.wr) for sc in scs]
+    tracks = {r: O.Track(scs[r].track.xr, scs[r].track.wl, scs[r].track.wr) for r in trials}
     checked = 0
-    for period in range(10):
+    for period in range(periods):
         tr.plan()
         torch.cuda.synchronize()
         X0, U0, xi = tr.X.cpu().numpy(), tr.U.cpu().numpy(), tr.out["xi"].cpu().numpy()
@@ -103,37 +128,35 @@ def test_sim_step_teacher_forced(tracker, n_apply):
         torch.cuda.synchronize()
         X1, U1 = tr.X.cpu().numpy(), tr.U.cpu().numpy()
         after = _records(tr)
-        for r, sc in enumerate(scs):
-            n_v, T = sc.X0.shape[0], sc.T
-            a, u, x = sl[r]
+        for r in trials:
             if not before[r].alive:
                 assert after[r].steps == before[r].steps
                 continue
-            mg = []
-            Xo, Uo, so = OS.step(p, tracks[r], spd, X0[a:a + n_v], U0[u:u + n_v * T * 2].reshape(n_v, T, 2),
-                                 xi[x:x + n_v * (T + 1) * 4].reshape(n_v, T + 1, 4), sc.ego,
-                                 _as_oracle(before[r], n_v), margins=mg)
-            what = f"period {period} trial {r}"
-            near = any(m[0] <= GUARD_DIST or m[1] <= GUARD_DIST or m[2] <= GUARD_PROG or m[3] <= GUARD_DIST
-                       for m in mg)
-            g = after[r]
-            if not near:
-                assert (g.alive, g.steps, g.ego_collision) == (so["alive"], so["steps"], so["ego_collision"]), what
-                assert (g.close_segments, g.close_steps) == (so["close_segments"], so["close_steps"]), what
-                assert list(g.close_run[:n_v]) == [int(v) for v in so["close_run"]], what
-            if g.steps != so["steps"]:
-                continue             # a contact decided differently within the guard band
-            assert_rel_close(X1[a:a + n_v], Xo, STATE_RTOL, what + " X")
-            np.testing.assert_array_equal(U1[u:u + n_v * T * 2].reshape(n_v, T, 2), Uo.astype(np.float32),
-                                          err_msg=what + " U")
-            scale = max(float(np.abs(sc.track.xr[:, :2]).max()), OS.track_len(tracks[r]))
-            _frenet_close(g.progress[:n_v], so["progress"], scale, what + " progress")
-            _frenet_close(g.s_raw[:n_v], so["s_raw"], scale, what + " s")
-            _frenet_close(g.d[:n_v], so["d"], scale, what + " d")
-            assert abs(g.ego_speed_sum - so["ego_speed_sum"]) <= 1e-4 * max(1.0, abs(so["ego_speed_sum"])), what
-            assert abs(g.ego_du2_sum - so["ego_du2_sum"]) <= 1e-4 * abs(so["ego_du2_sum"]) + 1e-5, what
-            checked += 1
-    assert checked >= 20
+            checked += check_trial_step(p, tracks[r], spd, scs[r], sl[r], X0, U0, xi, before[r], after[r], X1, U1,
+                                        f"period {period} trial {r}")
+    return checked
+
+
+@pytest.mark.parametrize("tracker,n_apply", [(0, 3), (1, 2)])
+def test_sim_step_teacher_forced(tracker, n_apply):
+    tr, scs, p, sp = _trials(tracker, n_apply)
+    tr.reset()
+    assert _run_checked(tr, scs, p, sp, 10, range(len(scs))) >= 20
+
+
+def test_full_trial_set_sampled_trials():
+    """The 42-trial set of the closed-loop results (7 tracks x 6 starts, the
+    ego behind two opponents, K = 4096, T = 60, L = 2, pure pursuit, one
+    control step per plan): eight sampled trials teacher-forced over the
+    first 12 control periods."""
+    from paper_2607_25388_b300 import sim as SM
+    p = S.params_fullscale()
+    scs = S.trial_set(7, 6, 3, 60, 4096, 2)
+    sp = SM.sim_params(n_apply=1, max_steps=1000, tracker=SM.TRACK_PURE_PURSUIT)
+    tr = SM.Trials(scs, p, 4096, 2, sp)
+    tr.reset()
+    trials = sorted(np.random.default_rng(5).choice(len(scs), 8, replace=False).tolist())
+    assert _run_checked(tr, scs, p, sp, 12, trials) >= 60
 
 
 def test_replaying_the_plan_controls_reproduces_its_trajectory():
