@@ -19,7 +19,11 @@ struct RaceDev {
     int xi_off;      // float offset into xi_out (n_v * (T+1) * 4)
     int ks_off;      // offset into k_star_out ((L+1) * n_v + 1)
     int pos_off;     // float2 offset into each prediction buffer (n_v * (T+1))
-    int pad[5];
+    int pad0;
+    // work before this race in a round, in units of rollout steps per sample
+    // (each sample tile of a race weighs its horizon T): Jacobi rounds
+    // (every vehicle) and the extra round (egos only)
+    long long wcum_all, wcum_ego;
 };
 
 }  // namespace sgtp
@@ -32,5 +36,6 @@ struct sgtp_batch {
     long long agents = 0, u_elems = 0, xi_elems = 0, ks = 0, n_pos = 0;
     int maxT = 0, max_nv = 0;
     int minT = 0;   // shortest horizon of the batch's races
+    long long w_all = 0, w_ego = 0;   // total work of a Jacobi round / the extra round (see RaceDev)
 };
 

@@ -46,6 +46,7 @@ struct PlanArgs {
     int n_races, n_agents;
     int K, L, tiles;          // tiles of blockDim samples per best response
     int items_all, items_ego; // BR items of a Jacobi round / the extra round
+    long long w_all, w_ego;   // their total work (batches: items weighted by T; see RaceDev)
     int maxT;
     const float *X0;
     float *U_io;
@@ -122,6 +123,27 @@ __device__ __forceinline__ int find_race(const PlanArgs &a, int x, F field)
         if (field(a.races[mid]) <= x) lo = mid; else hi = mid - 1;
     }
     return lo;
+}
+
+// First item of a round whose work starts at or after x (batches): the race
+// holding x by its work prefix, then ceil((x - prefix) / T) items into it.
+// Every item of a race weighs its horizon T, so that the CTAs' shares of a
+// round, cut at equal work, take about equal time across races of
+// different horizons.
+__device__ __forceinline__ int first_item_at(const PlanArgs &a, long long x, bool extra)
+{
+    int lo = 0, hi = a.n_races - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const long long w = extra ? a.races[mid].wcum_ego : a.races[mid].wcum_all;
+        if (w <= x) lo = mid; else hi = mid - 1;
+    }
+    const RaceDev R = a.races[lo];
+    const long long w0 = extra ? R.wcum_ego : R.wcum_all;
+    const long long n = (long long)(extra ? 1 : R.n_v) * a.tiles;
+    const long long k = (x - w0 + R.T - 1) / R.T;
+    const long long first = (long long)(extra ? lo : R.agent_off) * a.tiles;
+    return (int)(first + (k < n ? k : n));
 }
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
@@ -648,9 +670,18 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
             if (!grid_barrier(a, skip)) break;
         }
         stamp(a, 2 + 3 * round);
-        const int n_items = extra ? a.items_ego : a.items_all;
-        const int i0 = (int)((long long)n_items * blockIdx.x / gridDim.x);
-        const int i1 = (int)((long long)n_items * (blockIdx.x + 1) / gridDim.x);
+        // this CTA's share of the round: equal item counts for one race, equal
+        // work (items weighted by their race's horizon) for a batch
+        int i0, i1;
+        if (!a.races) {
+            const int n_items = extra ? a.items_ego : a.items_all;
+            i0 = (int)((long long)n_items * blockIdx.x / gridDim.x);
+            i1 = (int)((long long)n_items * (blockIdx.x + 1) / gridDim.x);
+        } else {
+            const long long W = extra ? a.w_ego : a.w_all;
+            i0 = first_item_at(a, W * blockIdx.x / gridDim.x, extra);
+            i1 = first_item_at(a, W * (blockIdx.x + 1) / gridDim.x, extra);
+        }
         int cur = -1;                 // vehicle (global index) staged
         unsigned long long *cur_slot = nullptr;
         for (int item = i0; item < i1; ++item) {
@@ -1151,6 +1182,10 @@ extern "C" sgtp_status sgtp_batch_create(const sgtp_track *trk, const sgtp_race 
         R.track_id = q.track_id; R.n_v = q.n_v; R.T = q.T; R.ego = q.ego; R.race_tag = q.race_tag;
         R.n_tail = 0;   // filled per call from mu_tail
         R.agent_off = (int)ag; R.u_off = (int)u; R.xi_off = (int)xi; R.ks_off = (int)ks; R.pos_off = (int)pos;
+        R.wcum_all = b->w_all;
+        R.wcum_ego = b->w_ego;
+        b->w_all += (long long)q.n_v * tiles * q.T;
+        b->w_ego += tiles * q.T;
         b->races.push_back(R);
         ag += q.n_v; u += (long long)q.n_v * q.T * 2; xi += (long long)q.n_v * (q.T + 1) * 4;
         ks += (long long)(L + 1) * q.n_v + 1; pos += (long long)q.n_v * (q.T + 1);
@@ -1247,6 +1282,8 @@ static sgtp_status batch_plan_impl(const sgtp_batch *b, const sgtp_params *p, co
     a.sig_lat = sig_lat;
     a.races = b->races_dev;
     a.n_races = b->n_races;
+    a.w_all = b->w_all;
+    a.w_ego = b->w_ego;
     a.n_agents = (int)b->agents;
     a.maxT = b->maxT;
     a.xi_total = b->xi_elems;
