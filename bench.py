@@ -14,7 +14,7 @@ the timed events.  `e2e` repeats the measurement through the public API with
 pinned host buffers: host->device copy of the state and warm start,
 the plan, device->host copy of the trajectories and selections.
 
---impl reference times the FP64 CPU oracle (the reference of this build) on
+--impl reference times the FP64 CPU oracle (the reference arm: the plain CPU restatement) on
 the host cores on a bounded sample of the same workload.
 """
 from __future__ import annotations

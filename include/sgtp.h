@@ -63,7 +63,7 @@ enum {
     SGTP_E_UNSUPPORTED = 6
 };
 
-/* Limits of this build. */
+/* Limits of the library. */
 #define SGTP_MAX_AGENTS 16        /* vehicles per race (so <= 15 opponents)         */
 #define SGTP_MAX_T 128            /* horizon steps                                  */
 #define SGTP_MAX_K (1 << 30)      /* samples per best response                      */
