@@ -63,7 +63,8 @@ extern "C" int64_t sgtp_launch_count(void) { return (int64_t)g_launches.load(); 
 // compensated (Kahan) running sum of the segment lengths gives s_j in float32
 // to about one ulp of L.
 __global__ void track_prep_kernel(const float *xr, const float *wl, const float *wr, const int *src_off,
-                                  TrackDesc *desc, float4 *A, float4 *B, float4 *W, float *S, float4 *C)
+                                  TrackDesc *desc, float4 *A, float4 *B, float4 *W, float *S, float4 *C, float4 *G0,
+                                  float4 *G1, float4 *G2, float2 *G3)
 {
     const TrackDesc d = desc[blockIdx.x];
     const int so = src_off[blockIdx.x];
@@ -83,6 +84,17 @@ __global__ void track_prep_kernel(const float *xr, const float *wl, const float 
         B[o] = make_float4(ex, ey, 1.0f / l2, len);
         W[o] = make_float4(wl[so + g], wl[so + gn] - wl[so + g], wr[so + g], wr[so + gn] - wr[so + g]);
         C[o] = make_float4(p0[2], wrap_angle(p1[2] - p0[2]), p0[3], p1[3] - p0[3]);
+        // projection records (plane offsets in double, then rounded)
+        const float ux = ex / len, uy = ey / len;
+        const float bx = ux + fx / lp, by = uy + fy / lp;
+        const double px = p0[0], py = p0[1];
+        G0[o] = make_float4(bx, by, (float)((double)bx * px + (double)by * py), len);
+        G1[o] = make_float4(ux, uy, (float)((double)ux * px + (double)uy * py),
+                            (float)((double)ux * py - (double)uy * px));
+        const float l0 = wl[so + g], r0 = wr[so + g], l1 = wl[so + gn], r1 = wr[so + gn];
+        const float h0 = 0.5f * (l0 + r0), h1 = 0.5f * (l1 + r1), c0 = 0.5f * (l0 - r0), c1 = 0.5f * (l1 - r1);
+        G2[o] = make_float4(1.0f / len, h0, h1 - h0, c0);
+        G3[o] = make_float2(c1 - c0, 0.f);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -99,6 +111,8 @@ __global__ void track_prep_kernel(const float *xr, const float *wl, const float 
     }
     __syncthreads();
     for (int j = d.N + threadIdx.x; j < next; j += blockDim.x) S[d.offset + j] = S[d.offset + j % d.N];
+    __syncthreads();
+    for (int j = threadIdx.x; j < next; j += blockDim.x) G3[d.offset + j].y = S[d.offset + j];
 }
 
 static sgtp_status track_create_impl(const float *xr, const float *wl, const float *wr, const int32_t *offsets,
@@ -147,7 +161,9 @@ static sgtp_status track_create_impl(const float *xr, const float *wl, const flo
     cudaError_t e = cudaSuccess;
     if ((e = cudaMalloc(&T->A, sizeof(float4) * total)) || (e = cudaMalloc(&T->B, sizeof(float4) * total)) ||
         (e = cudaMalloc(&T->W, sizeof(float4) * total)) || (e = cudaMalloc(&T->C, sizeof(float4) * total)) ||
-        (e = cudaMalloc(&T->S, sizeof(float) * total)) ||
+        (e = cudaMalloc(&T->S, sizeof(float) * total)) || (e = cudaMalloc(&T->G0, sizeof(float4) * total)) ||
+        (e = cudaMalloc(&T->G1, sizeof(float4) * total)) || (e = cudaMalloc(&T->G2, sizeof(float4) * total)) ||
+        (e = cudaMalloc(&T->G3, sizeof(float2) * total)) ||
         (e = cudaMalloc(&T->desc_dev, sizeof(TrackDesc) * n_tracks)) ||
         (e = cudaMalloc(&d_xr, sizeof(float) * 4 * total_src)) || (e = cudaMalloc(&d_wl, sizeof(float) * total_src)) ||
         (e = cudaMalloc(&d_wr, sizeof(float) * total_src)) || (e = cudaMalloc(&d_off, sizeof(int) * n_tracks))) {
@@ -164,7 +180,8 @@ static sgtp_status track_create_impl(const float *xr, const float *wl, const flo
         sgtp_track_destroy(T);
         return set_error(SGTP_E_CUDA, "track upload failed: %s", cudaGetErrorString(e));
     }
-    track_prep_kernel<<<n_tracks, 256, 0, s>>>(d_xr, d_wl, d_wr, d_off, T->desc_dev, T->A, T->B, T->W, T->S, T->C);
+    track_prep_kernel<<<n_tracks, 256, 0, s>>>(d_xr, d_wl, d_wr, d_off, T->desc_dev, T->A, T->B, T->W, T->S, T->C,
+                                               T->G0, T->G1, T->G2, T->G3);
     count_launch();
     if ((e = cudaGetLastError()) ||
         (e = cudaMemcpyAsync(T->desc.data(), T->desc_dev, sizeof(TrackDesc) * n_tracks, cudaMemcpyDeviceToHost, s)) ||
@@ -196,6 +213,7 @@ extern "C" void sgtp_track_destroy(sgtp_track *T)
 {
     if (!T) return;
     cudaFree(T->A); cudaFree(T->B); cudaFree(T->W); cudaFree(T->S); cudaFree(T->C); cudaFree(T->desc_dev);
+    cudaFree(T->G0); cudaFree(T->G1); cudaFree(T->G2); cudaFree(T->G3);
     delete T;
 }
 
@@ -246,15 +264,14 @@ struct BRLayout {
 __global__ void __launch_bounds__(256) br_prep_kernel(TrackView tv, sgtp_params p, const float *x0, const float *opp,
                                                       int n_opp, int T, float vscale, int n_tail, unsigned char *ws,
                                                       size_t off_ref, size_t off_opp, size_t off_osum,
-                                                      size_t off_odbar, int Wn, int back, long long timeout_ns)
+                                                      size_t off_odbar)
 {
-    using Tl = Tile<1>;
     BRHeader *h = (BRHeader *)ws;
     float4 *ref = (float4 *)(ws + off_ref);
     float2 *opos = (float2 *)(ws + off_opp);
     float4 *osum = (float4 *)(ws + off_osum);
     float *odbar = (float *)(ws + off_odbar);
-    float2 *ofr = (float2 *)(g_smem + BRTile<1>::kBytes);          // [T][n_opp] raw (s, d)
+    float2 *ofr = (float2 *)g_smem;                                 // [T][n_opp] raw (s, d)
     __shared__ float s0_sh[SGTP_MAX_AGENTS], t0_sh[SGTP_MAX_AGENTS], sH_sh[SGTP_MAX_AGENTS];
     __shared__ int j0_sh[SGTP_MAX_AGENTS + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
@@ -269,15 +286,6 @@ __global__ void __launch_bounds__(256) br_prep_kernel(TrackView tv, sgtp_params 
     __syncthreads();
     const int j0 = j0_sh[0];
     const float4 xs = make_float4(x0[0], x0[1], x0[2], x0[3]);
-    if (threadIdx.x == 0) {
-        BRScalars &S = Tl::sc();
-        mbar_init(Tl::bar(), 1);
-        S.tv = tv;
-        S.Wn = Wn;
-        S.w0 = window_start(j0, back, tv.N);
-        S.invL = invL;
-        Tl::stage_window(tv, S.w0, Wn, true);
-    }
     if (threadIdx.x < n_opp) {
         const int o = threadIdx.x;
         const float *q = opp + (size_t)o * (T + 1) * 4;
@@ -291,12 +299,8 @@ __global__ void __launch_bounds__(256) br_prep_kernel(TrackView tv, sgtp_params 
         opos[q] = make_float2(pt[0], pt[1]);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        if (!mbar_wait_bounded(Tl::bar(), 0, (unsigned long long)timeout_ns)) atomicOr(&h->flag, SGTP_E_TIMEOUT);
-    }
-    __syncthreads();
-    const BRScalars &S = Tl::sc();
-    const SegWindow w = Tl::win(S.w0, S.Wn);
+    // projections of this one-CTA preparation read the track from global memory
+    const SegWindow w{nullptr, nullptr, nullptr, nullptr, 0, 0};
     if (threadIdx.x < 32) {
         const FrenetPt f = frenet_at(tv, j0, xs.x, xs.y);
         if (threadIdx.x == 0) {
@@ -307,7 +311,7 @@ __global__ void __launch_bounds__(256) br_prep_kernel(TrackView tv, sgtp_params 
             h->t0 = f.t;
             h->j0 = j0;
         }
-        reference_traj(tv, w, Tl::C(), j0, f.s, p.dt, vscale, T, ref);
+        reference_traj(tv, w, nullptr, j0, f.s, p.dt, vscale, T, ref);
     }
     // every (opponent, step) projection in parallel
     int flag = 0;
@@ -316,8 +320,7 @@ __global__ void __launch_bounds__(256) br_prep_kernel(TrackView tv, sgtp_params 
         const float *q0 = opp + (size_t)o * (T + 1) * 4;
         const float *pt = q0 + (size_t)(tau + 1) * 4;
         const int jo = j0_sh[o + 1];
-        const int guess = wrap_index(jo - w.w0, tv.N) + chord_guess(pt[0] - q0[0], pt[1] - q0[1], __ldg(tv.B + jo),
-                                                                    4 * kWinTile);
+        const int guess = jo + chord_guess(pt[0] - q0[0], pt[1] - q0[1], __ldg(tv.B + jo), 4 * kWinTile);
         const FrenetPt f = frenet_search(tv, w, guess, pt[0], pt[1]);
         flag |= f.flag;
         ofr[q] = make_float2(f.s, f.d);
@@ -350,6 +353,7 @@ struct BRArgs {
     const float *u_nom;
     int T, n_opp, K, n_tail, Wn, back;
     uint2 key;
+    RoundKeys rk;                // the key's Weyl schedule
     unsigned agent_round, race;
     int game_on;
     // outputs (costs mode)
@@ -361,9 +365,10 @@ struct BRArgs {
     int K_prop;
 };
 
-// Stage one best response's tile: scalars, track window (TMA), reference,
-// nominal controls, opponent pairs and pair terms.  Ends with the window
-// copies complete and a __syncthreads.  Returns false if the wait timed out.
+// Stage one best response's tile: scalars, track window (TMA) with its lap
+// correction, reference, nominal controls, opponent pairs and pair terms.
+// Ends with the window ready and a __syncthreads.  Returns false if the
+// wait timed out.
 template <int MAXO>
 __device__ bool br_stage(const BRArgs &a)
 {
@@ -379,13 +384,14 @@ __device__ bool br_stage(const BRArgs &a)
         S.Wn = a.Wn;
         S.w0 = window_start(j0, a.back, a.tv.N);
         S.r0 = wrap_index(j0 - S.w0, a.tv.N);
+        S.lap0 = S.w0 + S.r0 >= a.tv.N ? 1 : 0;
         S.pos0 = (float)S.r0 + h->t0;
-        S.vel0 = __fdiv_rn(__fmul_rn(a.p.dt, h->x0.w), __ldg(a.tv.B + j0).w);
+        S.ppred0 = S.pos0 + __fdiv_rn(__fmul_rn(a.p.dt, h->x0.w), __ldg(a.tv.B + j0).w) - 0.5f;
         S.T = a.T; S.n_opp = a.n_opp; S.n_tail = a.n_tail;
         S.invL = 1.0f / a.tv.L;
         S.key = a.key; S.ctr_agent_round = a.agent_round; S.ctr_race = a.race; S.stream_bit = 0u;
         S.K_prop = a.prop ? a.K_prop : 0;
-        T::stage_window(a.tv, S.w0, S.Wn, false);
+        T::stage_window(a.tv, S.w0, S.Wn);
     }
     const float4 *gref = (const float4 *)(a.ws + a.off_ref);
     for (int i = threadIdx.x; i <= a.T; i += blockDim.x) T::ref()[i] = gref[i];
@@ -402,6 +408,10 @@ __device__ bool br_stage(const BRArgs &a)
     __syncthreads();
     if (threadIdx.x == 0) ok_sh = mbar_wait_bounded(T::bar(), 0, (unsigned long long)a.timeout_ns) ? 1 : 0;
     __syncthreads();
+    if (ok_sh && window_wraps(T::sc())) {
+        T::fix_laps(T::sc());
+        __syncthreads();
+    }
     return ok_sh != 0;
 }
 
@@ -419,7 +429,7 @@ __global__ void __launch_bounds__(256, 3) br_rollout_kernel(BRArgs a)
     const unsigned k = blockIdx.x * blockDim.x + threadIdx.x;
     if (ok && k < (unsigned)a.K) {
         if (KEY_MODE) {
-            const SampleResult r = run_candidate<MAXO, false>(S, a.p, a.key, k, a.game_on != 0, flag, nullptr, nullptr,
+            const SampleResult r = run_candidate<MAXO, false>(S, a.p, a.rk, k, a.game_on != 0, flag, nullptr, nullptr,
                                                               nullptr);
             best = make_key(r.feasible, r.cost, r.viol, k);
         } else {
@@ -428,9 +438,9 @@ __global__ void __launch_bounds__(256, 3) br_rollout_kernel(BRArgs a)
             float *uo = a.controls ? a.controls + (size_t)k * a.T * 2 : nullptr;
             SampleResult r;
             if (st || fr || uo)
-                r = run_candidate<MAXO, true>(S, a.p, a.key, k, a.game_on != 0, flag, st, fr, uo);
+                r = run_candidate<MAXO, true>(S, a.p, a.rk, k, a.game_on != 0, flag, st, fr, uo);
             else
-                r = run_candidate<MAXO, false>(S, a.p, a.key, k, a.game_on != 0, flag, nullptr, nullptr, nullptr);
+                r = run_candidate<MAXO, false>(S, a.p, a.rk, k, a.game_on != 0, flag, nullptr, nullptr, nullptr);
             a.cost[k] = r.cost;
             a.viol[k] = r.viol;
             a.feas[k] = r.feasible ? 1 : 0;
@@ -512,16 +522,18 @@ static size_t br_smem(const BRArgs &) { return BRTile<MAXO>::kBytes; }
 template <int MAXO>
 static sgtp_status launch_rollout(const BRArgs &a, bool key_mode, cudaStream_t s, int grid)
 {
-    static bool configured = false;
-    if (!configured) {
+    // the shared-memory opt-in applies to the current device only
+    static PerDeviceFlag configured;
+    const sgtp_status cst = once_per_device(configured, []() -> sgtp_status {
         SGTP_CUDA(cudaFuncSetAttribute(br_rollout_kernel<MAXO, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024));
         SGTP_CUDA(cudaFuncSetAttribute(br_rollout_kernel<MAXO, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024));
         SGTP_CUDA(cudaFuncSetAttribute(br_finalize_kernel<MAXO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024));
-        configured = true;
-    }
+        return SGTP_OK;
+    });
+    if (cst) return cst;
     if (key_mode)
         br_rollout_kernel<MAXO, true><<<grid, 256, br_smem<MAXO>(a), s>>>(a);
     else
@@ -562,6 +574,7 @@ static sgtp_status br_common(const sgtp_track *trk, int32_t track_id, const sgtp
     a.Wn = window_len(a.tv.N, kWinTile);
     a.back = a.Wn >= 256 ? 64 : a.Wn / 4;
     a.key = make_uint2((unsigned)seed, (unsigned)(seed >> 32));
+    a.rk = make_round_keys(a.key);
     a.agent_round = agent | (round << 16);
     a.race = race;
     a.game_on = game_on;
@@ -574,15 +587,15 @@ static sgtp_status br_launch(const BRArgs &a, int maxo, bool key_mode, const flo
                              float vref_scale, cudaStream_t s)
 {
     const int grid = (a.K + 255) / 256;
-    static bool prep_configured = false;
-    if (!prep_configured) {
+    static PerDeviceFlag prep_configured;
+    const sgtp_status cst = once_per_device(prep_configured, []() -> sgtp_status {
         SGTP_CUDA(cudaFuncSetAttribute(br_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        prep_configured = true;
-    }
-    const size_t prep_smem = BRTile<1>::kBytes + sizeof(float2) * (size_t)a.T * (a.n_opp > 0 ? a.n_opp : 1);
+        return SGTP_OK;
+    });
+    if (cst) return cst;
+    const size_t prep_smem = sizeof(float2) * (size_t)a.T * (a.n_opp > 0 ? a.n_opp : 1);
     br_prep_kernel<<<1, 256, prep_smem, s>>>(a.tv, a.p, x0, opp, a.n_opp, a.T, vref_scale, a.n_tail,
-                                             (unsigned char *)a.ws, a.off_ref, a.off_opp, a.off_osum, a.off_odbar,
-                                             a.Wn, a.back, a.timeout_ns);
+                                             (unsigned char *)a.ws, a.off_ref, a.off_opp, a.off_osum, a.off_odbar);
     sgtp_status st;
     switch (maxo) {
         case 1: st = launch_rollout<1>(a, key_mode, s, grid); break;
@@ -697,9 +710,8 @@ extern "C" sgtp_status sgtp_best_response_mixed(const sgtp_track *trk, int32_t t
 static __device__ __align__(256) unsigned char g_br_scratch[SGTP_NOALLOC_SCRATCH_BYTES];
 
 namespace {
-constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
-void *g_scratch_addr[kMaxDevices] = {};
+void *g_scratch_addr[sgtp::kMaxDevices] = {};
 }  // namespace
 
 extern "C" sgtp_status sgtp_best_response_noalloc(const sgtp_track *trk, int32_t track_id, const sgtp_params *p,

@@ -31,12 +31,22 @@ constexpr int kMaxMoves = 64;
 //   W[j] = (wL_j, wL_{j+1} - wL_j, wR_j, wR_{j+1} - wR_j)
 //   S[j] = s_j                      cumulative arc length
 //   C[j] = (psi_j, wrap(psi_{j+1} - psi_j), v_j, v_{j+1} - v_j)
+//
+// and the per-segment records of the sample-loop projection (frenet_fast in
+// sgtp_rollout.cuh), with u_j = e_j / |e_j| and b_j = u_{j-1} + u_j:
+//   G0[j] = (bx_j, by_j, b_j . P_j, |e_j|)   plane of waypoint j's bisector
+//   G1[j] = (ux_j, uy_j, u_j . P_j, u_j x P_j)  the segment's line
+//   G2[j] = (1/|e_j|, h_j, h_{j+1} - h_j, c_j)  half width h = (wL + wR)/2,
+//                                               centre offset c = (wL - wR)/2
+//   G3[j] = (c_{j+1} - c_j, s_j)
 struct TrackView {
     const float4 *A;
     const float4 *B;
     const float4 *W;
     const float *S;
     const float4 *C;
+    const float4 *G0, *G1, *G2;
+    const float2 *G3;
     int N;
     float L;
 };
@@ -245,60 +255,6 @@ __device__ __forceinline__ int chord_guess(float dx, float dy, float4 b, int cap
     return __fmaf_rn(dx, b.x, dy * b.y) < 0.0f ? -n : n;
 }
 
-// Frenet projection s(x; G), d(x; G) (Sec. II) of a rollout state.
-// Two consecutive segments j-1, j of the polyline are equidistant from p
-// exactly on the bisector of their angle at waypoint j (where both feet are
-// interior) or inside the wedge where both feet are the waypoint itself; so,
-// within the track's reach (closer than any non-adjacent segment), p's
-// nearest segment is j when p lies strictly past waypoint j's bisector
-// line and not past waypoint j+1's, a side test against the direction
-// u_{j-1} + u_j (one dot product; ties go to the lower index, as in the
-// definition).  The sample carries a continuous segment position pos
-// (window-local index plus parameter) and its last advance vel; the
-// bisectors at c, c+1, c+2 around the predicted position decide between c
-// and c+1; if neither, the distance search above takes over.
-__device__ __forceinline__ FrenetPt frenet_step(const TrackView &tv, const SegWindow &w, int &r, float &pos,
-                                                float &vel, float px, float py, int &flag)
-{
-    const int c = __float2int_rd(pos + vel - 0.5f);
-    FrenetPt f;
-    bool done = false;
-    if (c >= 0 && c + 2 < w.Wn) {
-        const f2p pp = pk(px, py);
-        const float4 v0 = w.A[c], v1 = w.A[c + 1], v2 = w.A[c + 2];
-        const float2 d0 = upk(sub2(pp, pk(v0.x, v0.y)));
-        const float2 d1 = upk(sub2(pp, pk(v1.x, v1.y)));
-        const float2 d2 = upk(sub2(pp, pk(v2.x, v2.y)));
-        const bool p0 = __fmaf_rn(d0.x, v0.z, __fmul_rn(d0.y, v0.w)) > 0.f;
-        const bool p1 = __fmaf_rn(d1.x, v1.z, __fmul_rn(d1.y, v1.w)) > 0.f;
-        const bool p2 = __fmaf_rn(d2.x, v2.z, __fmul_rn(d2.y, v2.w)) > 0.f;
-        if (p0 && !p2) {
-            const int m = p1 ? c + 1 : c;
-            const float2 dm = p1 ? d1 : d0;
-            const float4 b = w.B[m];
-            float t = __fmul_rn(__fmaf_rn(dm.x, b.x, __fmul_rn(dm.y, b.y)), b.z);
-            t = fminf(fmaxf(t, 0.0f), 1.0f);
-            const float2 e = upk(fma2(pk(-t, -t), pk(b.x, b.y), pk(dm.x, dm.y)));
-            const float q2 = __fmaf_rn(e.x, e.x, __fmul_rn(e.y, e.y));
-            const float cr = __fmaf_rn(b.x, dm.y, -__fmul_rn(b.y, dm.x));
-            SegData g;
-            g.b = b; g.w = w.W[m]; g.s = w.S[m];
-            f = frenet_result(g, m, t, q2, cr);
-            done = true;
-        }
-    }
-    if (!done) {
-        const int start = (c < r - kMaxMoves || c > r + kMaxMoves) ? r : c;
-        f = frenet_search(tv, w, start, px, py);
-        flag |= f.flag;
-    }
-    const float np = (float)f.m + f.t;
-    vel = np - pos;
-    pos = np;
-    r = f.m;
-    return f;
-}
-
 // Global nearest segment by brute force over all N segments, cooperatively by
 // one warp (lowest index on ties).  Used once per vehicle state x_{i,t}.
 __device__ __forceinline__ int nearest_segment_warp(const TrackView &tv, float px, float py)
@@ -469,6 +425,37 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
     return c;
 }
 
+// The ten round keys of the Weyl schedule, computed once per launch on the
+// host: a kernel parameter, so every round's key is a constant-bank operand
+// of the sample loop instead of two additions per round.
+struct RoundKeys {
+    uint2 k[10];
+};
+
+__host__ __device__ inline RoundKeys make_round_keys(uint2 key)
+{
+    RoundKeys rk;
+    for (int r = 0; r < 10; ++r) {
+        rk.k[r] = key;
+        key.x += 0x9E3779B9u;
+        key.y += 0xBB67AE85u;
+    }
+    return rk;
+}
+
+// philox4x32_10 with precomputed round keys (the same bits).
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const RoundKeys &rk)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long p0 = (unsigned long long)c.x * 0xD2511F53ull;
+        const unsigned long long p1 = (unsigned long long)c.z * 0xCD9E8D57ull;
+        c = make_uint4((unsigned)(p1 >> 32) ^ c.y ^ rk.k[r].x, (unsigned)p1, (unsigned)(p0 >> 32) ^ c.w ^ rk.k[r].y,
+                       (unsigned)p0);
+    }
+    return c;
+}
+
 // Uniform in (0,1) from the top 23 bits: ((w >> 9) + 1/2) 2^-23, exact in
 // float32.  One funnel shift builds the float 1 + (w >> 9) 2^-23 in [1, 2)
 // (exponent bits 0x3f8 above the 23 mantissa bits); subtracting 1 - 2^-24 is
@@ -592,50 +579,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsig
     return true;
 }
 
-// Shared-memory layout of a track window (16-byte aligned pieces).
-struct WindowSmem {
-    unsigned A, B, W, S, end;
-    __host__ __device__ WindowSmem(unsigned base, int Wn)
-    {
-        A = base;
-        B = A + 16u * Wn;
-        W = B + 16u * Wn;
-        S = W + 16u * Wn;
-        end = S + 4u * Wn;
-    }
-};
-
 // Window start for a segment j0: `back` segments behind it, rounded down to a
 // multiple of 4 so that every array's copy starts 16-byte aligned.
 __device__ __forceinline__ int window_start(int j0, int back, int N)
 {
     int w0 = wrap_index(j0 - back, N);
     return w0 & ~3;
-}
-
-// Issue the bulk copies of window [w0, w0+Wn) (Wn a multiple of 4) of track
-// tv into shared memory at smem + layout (one thread; completes on bar), plus
-// the C array into cdst when it is given.
-__device__ __forceinline__ SegWindow stage_window_issue(const TrackView &tv, int w0, int Wn, unsigned char *smem,
-                                                       const WindowSmem &ly, unsigned long long *bar, bool issue,
-                                                       void *cdst = nullptr)
-{
-    SegWindow w;
-    w.A = (const float4 *)(smem + ly.A);
-    w.B = (const float4 *)(smem + ly.B);
-    w.W = (const float4 *)(smem + ly.W);
-    w.S = (const float *)(smem + ly.S);
-    w.w0 = w0;
-    w.Wn = Wn;
-    if (issue) {
-        mbar_expect_tx(bar, (unsigned)Wn * (cdst ? 68u : 52u));
-        bulk_g2s(smem + ly.A, tv.A + w0, (unsigned)Wn * 16u, bar);
-        bulk_g2s(smem + ly.B, tv.B + w0, (unsigned)Wn * 16u, bar);
-        bulk_g2s(smem + ly.W, tv.W + w0, (unsigned)Wn * 16u, bar);
-        bulk_g2s(smem + ly.S, tv.S + w0, (unsigned)Wn * 4u, bar);
-        if (cdst) bulk_g2s(cdst, tv.C + w0, (unsigned)Wn * 16u, bar);
-    }
-    return w;
 }
 
 }  // namespace sgtp

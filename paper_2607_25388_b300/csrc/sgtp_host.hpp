@@ -2,6 +2,7 @@
 // the track object, error text, launch counting and argument checks.
 #pragma once
 
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <string>
@@ -24,6 +25,8 @@ struct sgtp_track {
     long long total = 0;                   // elements over all (ring-extended) tracks
     float4 *A = nullptr, *B = nullptr, *W = nullptr, *C = nullptr;
     float *S = nullptr;
+    float4 *G0 = nullptr, *G1 = nullptr, *G2 = nullptr;   // sample-loop projection records
+    float2 *G3 = nullptr;
     sgtp::TrackDesc *desc_dev = nullptr;
     std::vector<sgtp::TrackDesc> desc;     // host copy (L filled after prep)
     int device = 0;
@@ -40,6 +43,7 @@ inline TrackView track_view(const sgtp_track *t, int id)
     TrackView v;
     v.A = t->A + d.offset; v.B = t->B + d.offset; v.W = t->W + d.offset; v.S = t->S + d.offset;
     v.C = t->C + d.offset;
+    v.G0 = t->G0 + d.offset; v.G1 = t->G1 + d.offset; v.G2 = t->G2 + d.offset; v.G3 = t->G3 + d.offset;
     v.N = d.N; v.L = d.L;
     return v;
 }
@@ -76,6 +80,16 @@ inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 sgtp_status check_params(const sgtp_params *p);
 
+// Devices whose one-time set-up is tracked per device index.
+constexpr int kMaxDevices = 64;
+
+// A flag per device for set-up that applies only to the device current when
+// it runs (cudaFuncSetAttribute, cudaGetSymbolAddress): zero-initialised in
+// static storage.
+struct PerDeviceFlag {
+    std::atomic<bool> on[kMaxDevices];
+};
+
 }  // namespace sgtp
 
 #define SGTP_CUDA(x)                                                                                  \
@@ -88,3 +102,23 @@ sgtp_status check_params(const sgtp_params *p);
     do {                                                                 \
         if (!(cond)) return sgtp::set_error(SGTP_E_INVALID, __VA_ARGS__); \
     } while (0)
+
+namespace sgtp {
+
+// Run `step` (which returns sgtp_status) once on the current device: later
+// calls on the same device skip it.  Several host threads may run it at
+// once on one device, which is harmless because every step used here is
+// idempotent.  Devices beyond kMaxDevices run it on every call.
+template <typename F>
+sgtp_status once_per_device(PerDeviceFlag &flag, F step)
+{
+    int dev = 0;
+    SGTP_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return step();
+    if (flag.on[dev].load(std::memory_order_acquire)) return SGTP_OK;
+    const sgtp_status st = step();
+    if (st == SGTP_OK) flag.on[dev].store(true, std::memory_order_release);
+    return st;
+}
+
+}  // namespace sgtp

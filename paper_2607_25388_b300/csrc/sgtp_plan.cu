@@ -40,6 +40,8 @@ struct PlanArgs {
     const TrackDesc *tdesc;
     const float4 *A, *B, *W, *C;
     const float *S;
+    const float4 *G0, *G1, *G2;
+    const float2 *G3;
     sgtp_params p;
     const RaceDev *races;     // NULL: single race `one`
     RaceDev one;
@@ -52,6 +54,7 @@ struct PlanArgs {
     float *U_io;
     const float *vref;
     uint2 key;
+    RoundKeys rk;             // the key's Weyl schedule
     float *xi_out;
     int *k_star_out;
     float *xi_hist, *u_hist;
@@ -108,6 +111,7 @@ __device__ __forceinline__ TrackView get_track(const PlanArgs &a, int id)
     TrackView v;
     v.A = a.A + d.offset; v.B = a.B + d.offset; v.W = a.W + d.offset; v.S = a.S + d.offset;
     v.C = a.C + d.offset;
+    v.G0 = a.G0 + d.offset; v.G1 = a.G1 + d.offset; v.G2 = a.G2 + d.offset; v.G3 = a.G3 + d.offset;
     v.N = d.N; v.L = d.L;
     return v;
 }
@@ -196,21 +200,21 @@ __device__ bool grid_barrier(const PlanArgs &a, bool skip_arrival)
     return ok_sh != 0;
 }
 
-// Stage the window of a vehicle's track around segment j0 (thread 0 issues
-// the bulk copies; the caller waits); fills the tile scalars' window fields.
-__shared__ const float4 *g_win_track;   // track (A array) of the staged window, NULL when none
-__shared__ int g_win_w0;                 // its first segment
+// The window in shared memory: its track (A array), first segment and the
+// lap of the vehicle it was corrected for; g_win_fix asks the threads to run
+// the lap correction once the copies have landed.
+__shared__ const float4 *g_win_track;
+__shared__ int g_win_w0, g_win_lap0, g_win_fix;
 
-// Stage the window of a vehicle's track around segment j0 (thread 0 issues
-// the bulk copies; the caller waits when this returns true on thread 0) and
-// fill the tile scalars' window fields.  A window already in shared memory
-// is reused, without any copy, when it holds the same track and j0 lies
-// between half the usual look-back and the usual look-back plus an eighth
-// of the window: a rollout then still has at least 7/8 of the window ahead
-// of it (and leaves the window only to the global-memory path).  The C
-// array (setup only) is always copied.
+// Stage the sample window of a vehicle whose state lies on segment j0
+// (thread 0 issues the bulk copies and returns true; every thread then
+// calls window_ready) and fill the tile scalars' window fields.  The window
+// starts `back` segments behind j0 (rounded down to a multiple of 4), a
+// function of j0 alone, so every CTA and every launch shape sees the same
+// window for a vehicle; a window already in shared memory for the same
+// track, start and lap is reused without a copy.
 template <int MAXO>
-__device__ __forceinline__ bool stage_vehicle_window(const PlanArgs &a, const TrackView &tv, int j0, bool with_c)
+__device__ __forceinline__ bool stage_vehicle_window(const PlanArgs &a, const TrackView &tv, int j0)
 {
     using T = Tile<MAXO>;
     bool issued = false;
@@ -221,18 +225,47 @@ __device__ __forceinline__ bool stage_vehicle_window(const PlanArgs &a, const Tr
         S.tv = tv;
         S.Wn = Wn;
         S.invL = 1.0f / tv.L;
-        const int r = g_win_track == tv.A ? wrap_index(j0 - g_win_w0, tv.N) : -1;
-        if (!with_c && r >= back / 2 && r <= back + Wn / 8) {
-            S.w0 = g_win_w0;
-        } else {
-            S.w0 = window_start(j0, back, tv.N);
-            T::stage_window(tv, S.w0, Wn, with_c);
+        S.w0 = window_start(j0, back, tv.N);
+        S.r0 = wrap_index(j0 - S.w0, tv.N);
+        S.lap0 = S.w0 + S.r0 >= tv.N ? 1 : 0;
+        if (!(g_win_track == tv.A && g_win_w0 == S.w0 && g_win_lap0 == S.lap0)) {
+            T::stage_window(tv, S.w0, Wn);
             g_win_track = tv.A;
             g_win_w0 = S.w0;
+            g_win_lap0 = S.lap0;
+            g_win_fix = window_wraps(S) ? 1 : 0;
             issued = true;
         }
     }
     return issued;
+}
+
+// Completes a staging: thread 0 waits (bounded) for the copies it issued,
+// then every thread takes part in the lap correction when one is due.
+// Returns false (on every thread) when the wait ran out.
+template <int MAXO>
+__device__ __forceinline__ bool window_ready(const PlanArgs &a, bool issued, unsigned &phase)
+{
+    using T = Tile<MAXO>;
+    __shared__ int wok_sh;
+    if (threadIdx.x == 0) {
+        wok_sh = 1;
+        if (issued) {
+            if (!mbar_wait_bounded(T::bar(), phase, (unsigned long long)a.timeout_ns)) {
+                atomicOr(a.status, SGTP_E_TIMEOUT);
+                wok_sh = 0;
+            }
+            phase ^= 1u;
+        }
+    }
+    __syncthreads();
+    const bool ok = wok_sh != 0;
+    if (g_win_fix) {
+        if (ok) T::fix_laps(T::sc());
+        __syncthreads();
+        if (threadIdx.x == 0) g_win_fix = 0;
+    }
+    return ok;
 }
 
 // ---------------------------------------------------------------- learned proposal
@@ -392,7 +425,6 @@ __device__ void proposal_for(const PlanArgs &a, const RaceDev &R, int i, int bin
     __nv_bfloat16 *act0 = (__nv_bfloat16 *)(key_sh + SGTP_MAX_AGENTS);
     __nv_bfloat16 *act1 = act0 + SGTP_MLP_HIDDEN;
     const int ag = R.agent_off + i;
-    if (threadIdx.x == 0) g_win_track = nullptr;      // the scratch overlays the staged window
     compute_features(a, R, i, bin, game_on, x, key_sh);
     __syncthreads();
     if (a.feat_out && threadIdx.x < 64)
@@ -461,7 +493,7 @@ __device__ __forceinline__ float warp_sum(float v)
 // shuffle butterfly over lanes (lane = k mod 32), then over the groups in
 // order, so the sums depend on k alone, not on the launch shape.  Output
 // row of mppi_part: [0] m_t, [1 + 2 tau + c] sum w u_tau,c, [1 + 2T] sum w.
-// Group sums are kept in the C window, which only the setup phase uses.
+// Group sums are kept in the tile's scratch area.
 template <int MAXO>
 __device__ void mppi_tile(const PlanArgs &a, int t, int ag, int T)
 {
@@ -470,7 +502,7 @@ __device__ void mppi_tile(const PlanArgs &a, int t, int ag, int T)
     const BRScalars &S = Tl::sc();
     float *mc = (float *)Tl::st();
     float *gw = mc + kTileSingle;
-    float *grp = (float *)Tl::C();
+    float *grp = (float *)Tl::scratch();
     __shared__ float m_sh;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __syncthreads();
@@ -491,7 +523,7 @@ __device__ void mppi_tile(const PlanArgs &a, int t, int ag, int T)
         float *gs = grp + (j >> 5) * (2 * T);
         for (int mm = 0; 2 * mm < T; ++mm) {
             float2 z0, z1;
-            noise_pair(S, a.key, k, S.stream_bit, mm, z0, z1);
+            noise_pair(S, a.rk, k, S.stream_bit, mm, z0, z1);
             const int t0 = 2 * mm;
             const float2 u0 = sample_control_d(a.p, dist[t0], z0);
             float v0 = __fmul_rn(w, u0.x), v1 = __fmul_rn(w, u0.y), v2 = 0.f, v3 = 0.f;
@@ -524,18 +556,18 @@ __device__ void mppi_tile(const PlanArgs &a, int t, int ag, int T)
 
 // The GA-IBR-MPPI update of vehicle ag (all threads of the CTA): c_min =
 // min_t m_t, then sum_t exp((c_min - m_t) / lambda) x row_t over the tiles in
-// index order (factors staged in the C window in chunks), and U-bar <-
+// index order (factors staged in the scratch area in chunks), and U-bar <-
 // sum w u / sum w, clipped (rounding may leave the box by an ulp).  With no
 // finite cost the clipped nominal is kept.  Writes Tl::ctl(), U_io, u_hist.
 template <int MAXO>
 __device__ void mppi_update(const PlanArgs &a, int ag, int T, size_t uo, int round)
 {
     using Tl = Tile<MAXO>;
-    constexpr int kChunk = 4 * kWinTile;
+    constexpr int kChunk = BRTile<MAXO>::kScrBytes / 4;
     const size_t stride = (size_t)(2 * a.maxT + 2);
     const float *part = a.mppi_part + (size_t)ag * a.tiles * stride;
     float *acc = (float *)Tl::st();
-    float *e = (float *)Tl::C();
+    float *e = (float *)Tl::scratch();
     __shared__ float red_sh[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     float ml = __int_as_float(0x7f800000);
@@ -604,6 +636,7 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
         mbar_init(Tl::bar(), 1);
         g_bar_epoch = 0u;
         g_win_track = nullptr;
+        g_win_fix = 0;
     }
     stamp(a, 0);
 
@@ -626,18 +659,16 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
         }
         __syncthreads();
         const int j0 = j0_sh;
-        if (stage_vehicle_window<MAXO>(a, tv, j0, true)) {
-            if (!mbar_wait_bounded(Tl::bar(), phase, (unsigned long long)a.timeout_ns)) atomicOr(a.status, SGTP_E_TIMEOUT);
-            phase ^= 1u;
-        }
-        __syncthreads();
+        window_ready<MAXO>(a, stage_vehicle_window<MAXO>(a, tv, j0), phase);
         const FrenetPt f = frenet_at(tv, j0, x0.x, x0.y);
         AgentDev A;
         A.x0 = x0; A.s_t = f.s; A.d_t = f.d; A.j0 = j0; A.race = ri; A.t0 = f.t;
         if ((threadIdx.x >> 5) == 1) {
-            // reference recursion (warp 1) alongside the nominal rollout's dynamics (warp 0)
+            // reference recursion (warp 1, track from global memory) alongside
+            // the nominal rollout's dynamics (warp 0)
             if (threadIdx.x == 32) a.agents[ag] = A;
-            reference_traj(tv, Tl::win(S.w0, S.Wn), Tl::C(), j0, f.s, a.p.dt, a.vref[ag], R.T,
+            const SegWindow none{nullptr, nullptr, nullptr, nullptr, 0, 0};
+            reference_traj(tv, none, nullptr, j0, f.s, a.p.dt, a.vref[ag], R.T,
                            a.ref + (size_t)R.pos_off + (size_t)i * (R.T + 1));
         }
         roll_cooperative<MAXO>(a.p, x0, f.s, j0, R.T, R.n_tail, a.pos[0] + R.pos_off + (size_t)i * (R.T + 1), nullptr,
@@ -665,7 +696,7 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
                 const int i = ag - R.agent_off;
                 if (extra && i != R.ego) continue;
                 __syncthreads();
-                proposal_for(a, R, i, bin, round > 0, round, g_smem + Tl::L::kA);
+                proposal_for(a, R, i, bin, round > 0, round, Tl::scratch());
             }
             if (!grid_barrier(a, skip)) break;
         }
@@ -705,13 +736,12 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
                 const TrackView tv = get_track(a, R.track_id);
                 const AgentDev A = load_agent(a.agents + ag);
                 const int T = R.T, n_opp = R.n_v - 1;
-                const bool issued = stage_vehicle_window<MAXO>(a, tv, A.j0, false);
+                const bool issued = stage_vehicle_window<MAXO>(a, tv, A.j0);
                 if (threadIdx.x == 0) {
                     cta_key = ~0ull;
                     S.x0 = A.x0; S.s_t = A.s_t; S.d_t = A.d_t;
-                    S.r0 = wrap_index(A.j0 - S.w0, tv.N);
                     S.pos0 = (float)S.r0 + A.t0;
-                    S.vel0 = __fdiv_rn(__fmul_rn(a.p.dt, A.x0.w), __ldg(tv.B + A.j0).w);
+                    S.ppred0 = S.pos0 + __fdiv_rn(__fmul_rn(a.p.dt, A.x0.w), __ldg(tv.B + A.j0).w) - 0.5f;
                     S.T = T; S.n_opp = n_opp; S.n_tail = R.n_tail;
                     S.key = a.key;
                     S.ctr_agent_round = (unsigned)i | ((unsigned)round << 16);
@@ -759,12 +789,8 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
                 cur = ag;
                 cur_slot = a.keys + R.ks_off + (extra ? (a.L + 1) * R.n_v : round * R.n_v + i);
                 __syncthreads();
-                if (threadIdx.x == 0) {
-                    if (issued && !mbar_wait_bounded(Tl::bar(), phase, (unsigned long long)a.timeout_ns))
-                        atomicOr(a.status, SGTP_E_TIMEOUT);
-                    abort_sh = (ld_status(a.status) & 0xff) != 0;
-                }
-                if (issued) phase ^= 1u;
+                window_ready<MAXO>(a, issued, phase);
+                if (threadIdx.x == 0) abort_sh = (ld_status(a.status) & 0xff) != 0;
                 __syncthreads();
                 if (abort_sh) { ok = false; break; }
             }
@@ -777,7 +803,7 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
                 const unsigned k = (unsigned)t * kTileSingle + j;
                 float c = __int_as_float(0x7f800000);
                 if (k < (unsigned)a.K) {
-                    const SampleResult r = run_candidate<MAXO, false>(S, a.p, a.key, k, round > 0, flag, nullptr,
+                    const SampleResult r = run_candidate<MAXO, false>(S, a.p, a.rk, k, round > 0, flag, nullptr,
                                                                       nullptr, nullptr);
                     const unsigned long long key = make_key(r.feasible || mppi, r.cost, r.viol, k);
                     best = key < best ? key : best;
@@ -816,7 +842,7 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
             }
             const int slot = extra ? (a.L + 1) * R.n_v : round * R.n_v + i;
             const TrackView tv = get_track(a, R.track_id);
-            const bool issued = stage_vehicle_window<MAXO>(a, tv, A.j0, false);
+            const bool issued = stage_vehicle_window<MAXO>(a, tv, A.j0);
             if (threadIdx.x == 0) {
                 const unsigned long long key = __ldcg(a.keys + R.ks_off + slot);
                 ks_sh = (unsigned)(key & 0x7fffffffull);
@@ -846,11 +872,7 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
                     a.u_hist[(size_t)round * a.u_total + uo + 2 * q + 1] = u.y;
                 }
             }
-            if (threadIdx.x == 0 && issued) {
-                if (!mbar_wait_bounded(Tl::bar(), phase, (unsigned long long)a.timeout_ns)) atomicOr(a.status, SGTP_E_TIMEOUT);
-            }
-            if (issued) phase ^= 1u;
-            __syncthreads();
+            window_ready<MAXO>(a, issued, phase);
             float *xi_final = (round == a.L || extra) ? a.xi_out + xo : nullptr;
             float *xi_h = a.xi_hist ? a.xi_hist + (size_t)round * a.xi_total + xo : nullptr;
             roll_cooperative<MAXO>(a.p, A.x0, A.s_t, A.j0, T, R.n_tail,
@@ -892,13 +914,13 @@ int maxo_bucket(int n) { return n <= 1 ? 1 : n <= 3 ? 3 : n <= 9 ? 9 : 15; }
 template <int MAXO, int MINB, bool MPPI>
 sgtp_status configure_plan_t()
 {
-    static std::atomic<int> configured{0};
-    if (!configured.load()) {
+    // the shared-memory opt-in applies to the current device only
+    static PerDeviceFlag configured;
+    return once_per_device(configured, []() -> sgtp_status {
         SGTP_CUDA(cudaFuncSetAttribute(plan_kernel<MAXO, MINB, MPPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024));
-        configured.store(1);
-    }
-    return SGTP_OK;
+        return SGTP_OK;
+    });
 }
 
 sgtp_status configure_plan_kernels()
@@ -982,10 +1004,12 @@ void fill_common(PlanArgs &a, const sgtp_track *trk, const sgtp_params *p, int K
 {
     a.tdesc = trk->desc_dev;
     a.A = trk->A; a.B = trk->B; a.W = trk->W; a.S = trk->S; a.C = trk->C;
+    a.G0 = trk->G0; a.G1 = trk->G1; a.G2 = trk->G2; a.G3 = trk->G3;
     a.p = *p;
     a.K = K; a.L = L;
     a.X0 = X0; a.U_io = U_io; a.vref = vref;
     a.key = make_uint2((unsigned)seed, (unsigned)(seed >> 32));
+    a.rk = make_round_keys(a.key);
     a.xi_out = xi_out; a.k_star_out = k_star_out; a.xi_hist = xi_hist; a.u_hist = u_hist;
     a.status = status;
     a.Wn = window_len(kWinTile, opts ? opts->window : 0);
@@ -1459,6 +1483,7 @@ extern "C" sgtp_status sgtp_graph_set_seed(sgtp_graph *G, uint64_t seed)
 {
     SGTP_CHECK(G != nullptr, "graph is NULL");
     G->args.key = make_uint2((unsigned)seed, (unsigned)(seed >> 32));
+    G->args.rk = make_round_keys(G->args.key);
     void *params[] = {&G->args};
     cudaKernelNodeParams kp = G->kp;
     kp.kernelParams = params;

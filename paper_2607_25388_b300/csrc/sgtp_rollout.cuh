@@ -25,40 +25,46 @@ constexpr float kFarAway = 1.0e15f;    // position of an absent opponent slot
 
 // Scalars of one best-response problem (shared memory).
 struct BRScalars {
-    TrackView tv;         // global track (slow path only)
+    TrackView tv;         // global track (out-of-window segments)
     float4 x0;
     float s_t, d_t;
-    float pos0, vel0;     // continuous segment position of x0 (window-local) and its predicted advance
+    float pos0;           // continuous segment position of x0 (window-local segment + parameter)
+    float ppred0;         // first predicted position: pos0 + advance at v0 - 1/2
     int r0;               // window-local segment of x0
-    int w0, Wn;           // window
+    int w0, Wn;           // window: segments w0 .. w0 + Wn - 1 of the ring-extended arrays
+    int lap0;             // 1 when x0's segment sits past the ring's end (w0 + r0 >= N)
     int T, n_opp, n_tail;
     float invL;
     uint2 key;            // noise counter words
     unsigned ctr_agent_round, ctr_race, stream_bit;
     int K_prop;           // samples k < K_prop come from the proposal distribution
-    int pad[2];
+    int pad[3];
 };
 
 // Shared-memory tile of one best response: fixed offsets for a given MAXO.
+// The track window holds the sample-loop projection records G0..G3 of
+// kWinTile segments; the scratch area serves the proposal network and the
+// GA-IBR-MPPI sums.
 template <int MAXO>
 struct BRTile {
     static constexpr int NP = (MAXO + 1) / 2;           // opponent pairs per step
     static constexpr unsigned kBar = 0;                 // TMA mbarrier (8 B)
     static constexpr unsigned kScal = 16;
-    static constexpr unsigned kA = (kScal + sizeof(BRScalars) + 15) & ~15u;
-    static constexpr unsigned kB = kA + 16u * kWinTile;
-    static constexpr unsigned kW = kB + 16u * kWinTile;
-    static constexpr unsigned kS = kW + 16u * kWinTile;
-    static constexpr unsigned kC = kS + 4u * kWinTile;   // heading/speed window (setup only)
-    static constexpr unsigned kRef = kC + 16u * kWinTile;
+    static constexpr unsigned kF0 = (kScal + sizeof(BRScalars) + 15) & ~15u;
+    static constexpr unsigned kF1 = kF0 + 16u * kWinTile;
+    static constexpr unsigned kF2 = kF1 + 16u * kWinTile;
+    static constexpr unsigned kF3 = kF2 + 16u * kWinTile;
+    static constexpr unsigned kRef = kF3 + 8u * kWinTile;
     static constexpr unsigned kUbar = kRef + 16u * (SGTP_MAX_T + 1);   // float4 [2][T]: plain, proposal
     static constexpr unsigned kOpp = kUbar + 32u * SGTP_MAX_T;
     static constexpr unsigned kOsum = kOpp + 16u * SGTP_MAX_T * NP;
     static constexpr unsigned kOdbar = kOsum + 16u * SGTP_MAX_AGENTS;
     static constexpr unsigned kCtl = kOdbar + 4u * SGTP_MAX_AGENTS;
     static constexpr unsigned kSt = kCtl + 8u * SGTP_MAX_T;          // states of one rollout (T+1)
-    static constexpr unsigned kFr = kSt + 16u * (SGTP_MAX_T + 1);     // their raw Frenet (s, d)
-    static constexpr unsigned kBytes = kFr + 8u * SGTP_MAX_T;
+    static constexpr unsigned kFr = kSt + 16u * (SGTP_MAX_T + 1);     // their (s, d)
+    static constexpr unsigned kScr = kFr + 8u * SGTP_MAX_T;           // scratch
+    static constexpr unsigned kScrBytes = 8192u;
+    static constexpr unsigned kBytes = kScr + kScrBytes;
 };
 
 extern __shared__ __align__(16) unsigned char g_smem[];
@@ -68,11 +74,10 @@ struct Tile {
     using L = BRTile<MAXO>;
     static __device__ __forceinline__ unsigned long long *bar() { return (unsigned long long *)(g_smem + L::kBar); }
     static __device__ __forceinline__ BRScalars &sc() { return *(BRScalars *)(g_smem + L::kScal); }
-    static __device__ __forceinline__ float4 *A() { return (float4 *)(g_smem + L::kA); }
-    static __device__ __forceinline__ float4 *B() { return (float4 *)(g_smem + L::kB); }
-    static __device__ __forceinline__ float4 *W() { return (float4 *)(g_smem + L::kW); }
-    static __device__ __forceinline__ float *S() { return (float *)(g_smem + L::kS); }
-    static __device__ __forceinline__ float4 *C() { return (float4 *)(g_smem + L::kC); }
+    static __device__ __forceinline__ float4 *F0() { return (float4 *)(g_smem + L::kF0); }
+    static __device__ __forceinline__ float4 *F1() { return (float4 *)(g_smem + L::kF1); }
+    static __device__ __forceinline__ float4 *F2() { return (float4 *)(g_smem + L::kF2); }
+    static __device__ __forceinline__ float2 *F3() { return (float2 *)(g_smem + L::kF3); }
     static __device__ __forceinline__ float4 *ref() { return (float4 *)(g_smem + L::kRef); }
     // per-step sampling distribution (mean a, mean delta, sigma a, sigma delta):
     // dist()[tau] for the plain sampler, dist()[SGTP_MAX_T + tau] for the proposal
@@ -83,21 +88,165 @@ struct Tile {
     static __device__ __forceinline__ float2 *ctl() { return (float2 *)(g_smem + L::kCtl); }
     static __device__ __forceinline__ float4 *st() { return (float4 *)(g_smem + L::kSt); }
     static __device__ __forceinline__ float2 *fr() { return (float2 *)(g_smem + L::kFr); }
-    static __device__ __forceinline__ SegWindow win(int w0, int Wn)
-    {
-        return SegWindow{A(), B(), W(), S(), w0, Wn};
-    }
+    static __device__ __forceinline__ unsigned char *scratch() { return g_smem + L::kScr; }
     // Issue the window's bulk copies (one thread; completes on bar()).
-    static __device__ __forceinline__ void stage_window(const TrackView &tv, int w0, int Wn, bool with_c)
+    static __device__ __forceinline__ void stage_window(const TrackView &tv, int w0, int Wn)
     {
-        mbar_expect_tx(bar(), (unsigned)Wn * (with_c ? 68u : 52u));
-        bulk_g2s(A(), tv.A + w0, (unsigned)Wn * 16u, bar());
-        bulk_g2s(B(), tv.B + w0, (unsigned)Wn * 16u, bar());
-        bulk_g2s(W(), tv.W + w0, (unsigned)Wn * 16u, bar());
-        bulk_g2s(S(), tv.S + w0, (unsigned)Wn * 4u, bar());
-        if (with_c) bulk_g2s(C(), tv.C + w0, (unsigned)Wn * 16u, bar());
+        mbar_expect_tx(bar(), (unsigned)Wn * 56u);
+        bulk_g2s(F0(), tv.G0 + w0, (unsigned)Wn * 16u, bar());
+        bulk_g2s(F1(), tv.G1 + w0, (unsigned)Wn * 16u, bar());
+        bulk_g2s(F2(), tv.G2 + w0, (unsigned)Wn * 16u, bar());
+        bulk_g2s(F3(), tv.G3 + w0, (unsigned)Wn * 8u, bar());
+    }
+    // Once the copies have landed (all threads; the caller synchronises
+    // after): the arc lengths of window segments on another lap of the ring
+    // than x0's segment move by that lap's multiple of L, so that progress
+    // read from the window is unwrapped relative to s_t.
+    static __device__ __forceinline__ void fix_laps(const BRScalars &S)
+    {
+        const int N = S.tv.N;
+        for (int r = threadIdx.x; r < S.Wn; r += blockDim.x) {
+            const int dl = (S.w0 + r >= N ? 1 : 0) - S.lap0;
+            if (dl != 0) F3()[r].y = F3()[r].y + (float)dl * S.tv.L;
+        }
     }
 };
+
+// True when a window fill needs fix_laps: it reaches past the ring's end.
+__device__ __forceinline__ bool window_wraps(const BRScalars &S) { return S.w0 + S.Wn > S.tv.N; }
+
+// ---------------------------------------------------------------- Frenet of rollout states
+// Frenet projection s(x; G), d(x; G) (Sec. II) of a state p on segment j of
+// the polyline, from the records G0..G3 (see TrackView):
+//   along = u_j . (p - P_j), perp = u_j x (p - P_j) (> 0 left of travel),
+//   t = clamp(along / |e_j|, 0, 1), foot P_j + t e_j,
+//   |p - foot|^2 = (along - t |e_j|)^2 + perp^2, d = sign(perp) |p - foot|,
+//   s = s_j + t |e_j|, widths at the foot by linear interpolation in t,
+//   boundary clearance min(wR + d, wL - d) = h - |d - c|.
+struct GeoPt {
+    float s, d, tc, rho;
+};
+
+__device__ __forceinline__ GeoPt frenet_eval(float4 g1, float4 g2, float2 g3, float len, float px, float py)
+{
+    GeoPt f;
+    const float along = __fmaf_rn(px, g1.x, __fmaf_rn(py, g1.y, -g1.z));
+    const float perp = __fmaf_rn(py, g1.x, __fmaf_rn(-px, g1.y, -g1.w));
+    const float tc = __saturatef(__fmul_rn(along, g2.x));
+    const float ex = __fmaf_rn(-tc, len, along);
+    const float q2 = __fmaf_rn(ex, ex, __fmul_rn(perp, perp));
+    f.d = copysignf(sqrt_ftz(q2), perp);
+    f.s = __fmaf_rn(tc, len, g3.y);
+    f.tc = tc;
+    const float h = __fmaf_rn(tc, g2.z, g2.y), c = __fmaf_rn(tc, g3.x, g2.w);
+    f.rho = h - fabsf(f.d - c);
+    return f;
+}
+
+// p lies strictly past the bisector of waypoint j (record q = G0[j]): then
+// segment j is nearer than segment j-1 (ties go to the lower index).
+__device__ __forceinline__ bool past_bisector(float4 q, float px, float py)
+{
+    return __fmaf_rn(px, q.x, __fmaf_rn(py, q.y, -q.z)) > 0.f;
+}
+
+// Global segment of window-local index r (any r) and its lap relative to
+// the window's first lap.
+__device__ __forceinline__ int lap_of(int g, int N) { return g >= 0 ? g / N : -((N - 1 - g) / N); }
+
+template <int MAXO>
+__device__ __forceinline__ float4 bisector_at(const BRScalars &S, int r)
+{
+    if ((unsigned)r < (unsigned)S.Wn) return Tile<MAXO>::F0()[r];
+    const int g = S.w0 + r;
+    const int j = g - lap_of(g, S.tv.N) * S.tv.N;
+    return __ldg(S.tv.G0 + j);
+}
+
+// Records of window-local segment r: from the window, or from global
+// memory with the same lap correction of the arc length as fix_laps.
+template <int MAXO>
+__device__ __forceinline__ void segment_at(const BRScalars &S, int r, float4 &g1, float4 &g2, float2 &g3, float &len)
+{
+    using T = Tile<MAXO>;
+    if ((unsigned)r < (unsigned)S.Wn) {
+        g1 = T::F1()[r]; g2 = T::F2()[r]; g3 = T::F3()[r]; len = T::F0()[r].w;
+    } else {
+        const int g = S.w0 + r, N = S.tv.N;
+        const int lap = lap_of(g, N);
+        const int j = g - lap * N;
+        g1 = __ldg(S.tv.G1 + j); g2 = __ldg(S.tv.G2 + j); g3 = __ldg(S.tv.G3 + j); len = __ldg(S.tv.G0 + j).w;
+        const int dl = lap - S.lap0;
+        if (dl != 0) g3.y = g3.y + (float)dl * S.tv.L;
+    }
+}
+
+// Segment of p by a walk over the bisectors from window-local segment r:
+// forward while p is past the next bisector, else backward while it is not
+// past the current one.  The result m has p past bisector m and not past
+// bisector m+1, i.e. segment m is nearer than both neighbours: a local
+// minimum of the distance over the segment index, which for points within
+// the track's reach is the global nearest segment of the projection (ties
+// to the lower index).  A walk longer than kMaxMoves stops and sets flag.
+template <int MAXO>
+__device__ __noinline__ int bisector_walk(const BRScalars &S, int r, float px, float py, int &flag)
+{
+    bool moved = false;
+    for (int it = 0; it < kMaxMoves; ++it) {
+        if (!past_bisector(bisector_at<MAXO>(S, r + 1), px, py)) break;
+        r += 1;
+        moved = true;
+        if (it == kMaxMoves - 1) flag = 1;
+    }
+    if (!moved) {
+        for (int it = 0; it < kMaxMoves; ++it) {
+            if (past_bisector(bisector_at<MAXO>(S, r), px, py)) break;
+            r -= 1;
+            if (it == kMaxMoves - 1) flag = 1;
+        }
+    }
+    return r;
+}
+
+// Frenet of the next rollout state.  The sample carries a continuous segment
+// position pos (window-local segment + parameter) and the predicted position
+// of the next state, ppred = pos + last advance - 1/2.  The bisectors of
+// c = floor(ppred), c+1, c+2 certify segment c or c+1 when p is past the
+// first and not past the third (three plane tests against shared memory);
+// otherwise the bisector walk takes over.
+template <int MAXO>
+__device__ __forceinline__ GeoPt frenet_fast(const BRScalars &S, float px, float py, float &pos, float &ppred, int &flag)
+{
+    using T = Tile<MAXO>;
+    const int c = __float2int_rd(ppred);
+    int m = 0;
+    float len = 0.f;
+    bool ok = false;
+    if ((unsigned)c < (unsigned)(S.Wn - 2)) {
+        const float4 q0 = T::F0()[c], q1 = T::F0()[c + 1], q2 = T::F0()[c + 2];
+        const bool b0 = past_bisector(q0, px, py), b1 = past_bisector(q1, px, py), b2 = past_bisector(q2, px, py);
+        if (b0 && !b2) {
+            m = b1 ? c + 1 : c;
+            len = b1 ? q1.w : q0.w;
+            ok = true;
+        }
+    }
+    float4 g1, g2;
+    float2 g3;
+    if (ok) {
+        g1 = T::F1()[m]; g2 = T::F2()[m]; g3 = T::F3()[m];
+    } else {
+        const int r = __float2int_rd(pos);
+        const int start = (c < r - kMaxMoves || c > r + kMaxMoves) ? r : c;
+        m = bisector_walk<MAXO>(S, start, px, py, flag);
+        segment_at<MAXO>(S, m, g1, g2, g3, len);
+    }
+    const GeoPt f = frenet_eval(g1, g2, g3, len, px, py);
+    const float np = (float)m + f.tc;
+    ppred = __fmaf_rn(2.f, np, -(pos + 0.5f));
+    pos = np;
+    return f;
+}
 
 // Clipped control from a nominal control and a normal pair z (Pi_U).
 __device__ __forceinline__ float2 sample_control(const sgtp_params &p, float2 ubar, float2 z)
@@ -159,12 +308,11 @@ __device__ __forceinline__ float2 steer_terms(const sgtp_params &p, float delta)
 }
 
 // Normal pairs of candidate k at steps 2m and 2m+1 (one Philox block).
-// The key comes from a kernel parameter, so that the round keys of the
-// Weyl schedule stay in the uniform datapath.
-__device__ __forceinline__ void noise_pair(const BRScalars &S, uint2 key, unsigned k, unsigned sbit, int m, float2 &z0,
-                                           float2 &z1)
+// The round keys are a kernel parameter (constant-bank operands).
+__device__ __forceinline__ void noise_pair(const BRScalars &S, const RoundKeys &rk, unsigned k, unsigned sbit, int m,
+                                           float2 &z0, float2 &z1)
 {
-    const uint4 w = philox4x32_10(make_uint4(k, (unsigned)m | sbit, S.ctr_agent_round, S.ctr_race), key);
+    const uint4 w = philox4x32_10_rk(make_uint4(k, (unsigned)m | sbit, S.ctr_agent_round, S.ctr_race), rk);
     z0 = box_muller(w.x, w.y);
     z1 = box_muller(w.z, w.w);
 }
@@ -173,9 +321,8 @@ template <int MAXO>
 struct SampleState {
     float x, y, psi, v;
     float a_prev, d_prev;
-    float s;          // unwrapped progress
-    int r;            // nearest segment (window-local)
-    float pos, vel;   // continuous segment position and its last advance
+    float s;          // progress, unwrapped relative to s_t
+    float pos, ppred; // continuous segment position and the next step's prediction
     f2p cost;         // running c_track, two partial sums
     float rho_bd, d_tail;
     float g2[MAXO];
@@ -187,8 +334,7 @@ __device__ __forceinline__ void sample_init(SampleState<MAXO> &St, const BRScala
     St.x = S.x0.x; St.y = S.x0.y; St.psi = S.x0.z; St.v = S.x0.w;
     St.a_prev = 0.f; St.d_prev = 0.f;
     St.s = S.s_t;
-    St.r = S.r0;
-    St.pos = S.pos0; St.vel = S.vel0;
+    St.pos = S.pos0; St.ppred = S.ppred0;
     St.cost = pk(0.f, 0.f);
     St.rho_bd = __int_as_float(0x7f800000);
     St.d_tail = 0.f;
@@ -246,23 +392,10 @@ __device__ __forceinline__ void step_opponents(float *g2, float x, float y, cons
     }
 }
 
-// Frenet of the new state (progress unwrapped along the rollout), boundary
-// clearance (Sec. III-B) with widths at the foot point, tail offsets
-struct GeoState {
-    float s, pos, vel, rho_bd, d_tail;
-    int r;
-};
-__device__ __forceinline__ FrenetPt step_geometry(GeoState &G, const BRScalars &S, const SegWindow &w, int st, float x,
-                                                  float y, int &flag)
-{
-    const FrenetPt f = frenet_step(S.tv, w, G.r, G.pos, G.vel, x, y, flag);
-    G.s = G.s + wrap_len(f.s - G.s, S.tv.L, S.invL);
-    G.rho_bd = fminf(G.rho_bd, fminf(f.wr + f.d, f.wl - f.d));
-    if (st > S.T - S.n_tail) G.d_tail = G.d_tail + f.d;
-    return f;
-}
-
-// Advance a candidate by one step tau with control u; optional outputs.
+// Advance a candidate by one step tau with control u: control costs, the
+// bicycle step, Frenet of the new state with its boundary clearance (Sec.
+// III-B, widths at the foot point) and tail offset, tracking cost,
+// opponent distances; optional outputs.
 template <int MAXO, bool OUT>
 __device__ __forceinline__ void sample_step(SampleState<MAXO> &St, const BRScalars &S, const sgtp_params &p,
                                             int tau, float2 u, int &flag, float *st_out, float *fr_out)
@@ -271,9 +404,10 @@ __device__ __forceinline__ void sample_step(SampleState<MAXO> &St, const BRScala
     f2p acc = step_control_cost(p, St.cost, St.a_prev, St.d_prev, u, tau);
     bicycle_step(p, St.x, St.y, St.psi, St.v, u.x, u.y);
     const int st = tau + 1;
-    GeoState G{St.s, St.pos, St.vel, St.rho_bd, St.d_tail, St.r};
-    const FrenetPt f = step_geometry(G, S, T::win(S.w0, S.Wn), st, St.x, St.y, flag);
-    St.s = G.s; St.pos = G.pos; St.vel = G.vel; St.rho_bd = G.rho_bd; St.d_tail = G.d_tail; St.r = G.r;
+    const GeoPt f = frenet_fast<MAXO>(S, St.x, St.y, St.pos, St.ppred, flag);
+    St.s = f.s;
+    St.rho_bd = fminf(St.rho_bd, f.rho);
+    if (st > S.T - S.n_tail) St.d_tail = St.d_tail + f.d;
     St.cost = step_tracking_cost(p, acc, St.x, St.y, St.psi, St.v, T::ref()[st]);
     step_opponents<0, MAXO / 2, true, MAXO>(St.g2, St.x, St.y, T::opp() + tau * BRTile<MAXO>::NP);
     if (OUT) {
@@ -337,9 +471,9 @@ __device__ __forceinline__ SampleResult sample_finish(const SampleState<MAXO> &S
 // Full candidate: noise, controls, rollout, finish.  Optional outputs are
 // written when OUT (states (T+1)x4, frenet (T+1)x2, controls Tx2).
 template <int MAXO, bool OUT>
-__device__ __forceinline__ SampleResult run_candidate(const BRScalars &S, const sgtp_params &p, uint2 key,
-                                                      unsigned k, bool game_on, int &flag, float *st_out,
-                                                      float *fr_out, float *u_out)
+__device__ __forceinline__ SampleResult run_candidate(const BRScalars &S, const sgtp_params &p,
+                                                      const RoundKeys &rk, unsigned k, bool game_on, int &flag,
+                                                      float *st_out, float *fr_out, float *u_out)
 {
     using T = Tile<MAXO>;
     SampleState<MAXO> St;
@@ -354,7 +488,7 @@ __device__ __forceinline__ SampleResult run_candidate(const BRScalars &S, const 
     const float4 *dist = T::dist() + (prop ? SGTP_MAX_T : 0);
     for (int m = 0; 2 * m < Tn; ++m) {
         float2 z0, z1;
-        noise_pair(S, key, k, sbit, m, z0, z1);
+        noise_pair(S, rk, k, sbit, m, z0, z1);
         const int t0 = 2 * m;
         const float2 u0 = sample_control_d(p, dist[t0], z0);
         if (OUT && u_out) { u_out[2 * t0] = u0.x; u_out[2 * t0 + 1] = u0.y; }
@@ -387,18 +521,18 @@ __device__ __forceinline__ void stage_opponents(int T, int n_opp, F src)
 
 // Roll out the controls ctl()[0..T) from x0 cooperatively: warp 0 prepares
 // the steering terms of every step (in the opponent area, which only the
-// sample phase uses), then its thread 0 runs the bicycle recurrence
-// (the same arithmetic as the sample loop, so the states are bit-identical
-// to the evaluated candidate's) into st(); then
-// every thread projects one state onto the track by the distance search of
-// frenet_search from a guess (chord_guess: the signed chord from x0 in segment lengths), which
-// reaches the same nearest segment as the sample loop's walk; then one
-// thread unwraps the progress in step order.  Outputs (any may be NULL):
+// sample phase uses), then its thread 0 runs the bicycle recurrence (the
+// same arithmetic as the sample loop, so the states are bit-identical to the
+// evaluated candidate's) into st(); then every thread projects one state
+// onto the track by the bisector walk from a guess (the signed chord from
+// x0 in segment lengths), which reaches the sample loop's segment; progress
+// comes out unwrapped relative to s_t.  Outputs (any may be NULL):
 // positions (T+1), states twice (T+1)x4, and the prediction summary
 // (progress gain s_H - s_t, tail-mean offset); tan_out (T+1, entry 0
-// unused) receives the unit direction of each state's nearest segment, the
+// unused) receives the unit direction of each state's segment, the
 // longitudinal axis of a perturbed prediction.  Uses the tile's window,
-// which must be staged.  All threads of the CTA must call it.
+// which must be staged for x0's segment j0.  All threads of the CTA must
+// call it.
 template <int MAXO>
 __device__ void roll_cooperative(const sgtp_params &p, float4 x0, float s_t, int j0, int T, int n_tail,
                                  float2 *pos_out, float *xi_a, float *xi_b, float2 *summ_out, int &flag,
@@ -423,30 +557,25 @@ __device__ void roll_cooperative(const sgtp_params &p, float4 x0, float s_t, int
         }
     }
     __syncthreads();
-    const SegWindow w = Tl::win(S.w0, S.Wn);
     const int r0 = wrap_index(j0 - S.w0, S.tv.N);
     const float4 b0 = __ldg(S.tv.B + j0);
     for (int q = threadIdx.x; q < T; q += blockDim.x) {
         const float4 v = st[q + 1];
         const int guess = r0 + chord_guess(v.x - x0.x, v.y - x0.y, b0, 4 * kWinTile);
-        const FrenetPt f = frenet_search(S.tv, w, guess, v.x, v.y);
-        flag |= f.flag;
-        if (tan_out) {
-            const float4 b = seg_at(S.tv, w, f.m).b;
-            const float il = b.w * b.z;                // 1 / |e_j|
-            tan_out[q + 1] = make_float2(b.x * il, b.y * il);
-        }
+        const int m = bisector_walk<MAXO>(S, guess, v.x, v.y, flag);
+        float4 g1, g2;
+        float2 g3;
+        float len;
+        segment_at<MAXO>(S, m, g1, g2, g3, len);
+        const GeoPt f = frenet_eval(g1, g2, g3, len, v.x, v.y);
+        if (tan_out) tan_out[q + 1] = make_float2(g1.x, g1.y);
         fr[q] = make_float2(f.s, f.d);
     }
     __syncthreads();
     if (threadIdx.x == 0 && summ_out) {
-        float s = s_t, dsum = 0.f;
-        for (int tau = 0; tau < T; ++tau) {
-            const float2 f = fr[tau];
-            s = s + wrap_len(f.x - s, S.tv.L, S.invL);
-            if (tau + 1 > T - n_tail) dsum = dsum + f.y;
-        }
-        *summ_out = make_float2(s - s_t, dsum / (float)n_tail);
+        float dsum = 0.f;
+        for (int tau = T - n_tail; tau < T; ++tau) dsum = dsum + fr[tau].y;
+        *summ_out = make_float2(fr[T - 1].x - s_t, dsum / (float)n_tail);
     }
     for (int q = threadIdx.x; q <= T; q += blockDim.x) {
         const float4 v = st[q];
