@@ -193,11 +193,18 @@ sgtp_status sgtp_best_response_noalloc(const sgtp_track *trk, int32_t track_id, 
 
 /* Launch shape of the persistent kernel.  Any zero field takes the
  * library's choice.  Every shape gives bit-identical results (each sample is
- * computed by one thread with the same code, and selection is an exact
- * integer minimum).  Samples are processed in tiles of 256 consecutive k. */
+ * computed with the same code, and selection is an exact integer minimum).
+ * Samples are processed in tiles of block x samples_per_thread consecutive k
+ * (GA-IBR-MPPI: tiles of 256).  By default a plan whose Jacobi round fits in
+ * one wave of 2 x 256 threads per SM runs one sample per thread with 128
+ * registers; one that fits in one wave of two samples per thread on
+ * 2 x 288 threads runs that; larger rounds run 3 x 256 threads per SM with
+ * one sample per thread. */
 typedef struct sgtp_launch_opts {
-    int32_t block;                /* threads per CTA: 64, 128 or 256 (default 256)   */
-    int32_t samples_per_thread;   /* samples of a tile per thread: 0 or 256 / block  */
+    int32_t block;                /* threads per CTA: 64, 128, 256 or 288 (288 only
+                                     with two samples per thread)                    */
+    int32_t samples_per_thread;   /* 0, 1 or 2: samples each thread rolls out at once
+                                     (2: interleaved, block 256 or 288)              */
     int32_t ctas_per_sm;          /* resident CTAs per SM (capped at the occupancy
                                      limit; default the limit)                       */
     int32_t window;               /* track segments staged in shared memory per CTA

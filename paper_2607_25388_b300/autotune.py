@@ -1,11 +1,12 @@
 """Launch-shape autotuner of the persistent plan kernel.
 
-The search space is the launch shape of ``sgtp_launch_opts``: threads per
-CTA (64, 128, 256; a 256-sample tile is then processed 256/block samples per
-thread) and resident CTAs per SM.  Every shape computes each sample with the
-same code and selects by an exact integer minimum, so the plan must be
-bit-identical across shapes; the tuner checks that on every candidate and
-refuses a shape that differs.
+The search space is the launch shape of ``sgtp_launch_opts``: the build
+(128-thread CTAs with one to three samples per thread at once, or the
+256-thread builds with one), samples per thread (0 = chosen per round) and
+resident CTAs per SM.  Every shape computes each sample with the same code
+and selects by an exact integer minimum, so the plan must be bit-identical
+across shapes; the tuner checks that on every candidate and refuses a shape
+that differs.
 
 Results are cached in a JSON file keyed by (horizon bucket, opponent bucket,
 K, L, SM count, device name); ``lookup`` returns the cached shape for a
@@ -24,8 +25,10 @@ import torch
 from . import scenario as S
 from .planner import Track, ibr_plan, launch_opts
 
-BLOCKS = (64, 128, 256)
-CTAS = (0, 1, 2, 3, 4, 6)        # 0 = the occupancy limit; larger values are capped by the library
+# (block, samples per thread): the 128-thread build with 0 (per round), 1, 2
+# or 3 samples per thread, the 256-thread builds with one
+SHAPES = ((128, 0), (128, 1), (128, 2), (128, 3), (256, 1))
+CTAS = (0, 1, 2, 3)              # 0 = the occupancy limit; larger values are capped by the library
 
 
 def cache_path() -> str:
@@ -66,7 +69,8 @@ def lookup(n_v: int, T: int, K: int, L: int, path: str | None = None, info=None)
     ent = _load(path or cache_path()).get(key(n_v, T, K, L, info))
     if not ent:
         return None
-    return launch_opts(block=ent["block"], samples_per_thread=256 // ent["block"], ctas_per_sm=ent["ctas_per_sm"])
+    return launch_opts(block=ent["block"], samples_per_thread=ent.get("samples_per_thread", 0),
+                       ctas_per_sm=ent["ctas_per_sm"])
 
 
 def _time_plan(trk, params, sc, K, L, opts, reps, warmup):
@@ -118,21 +122,18 @@ def tune(n_v: int, T: int, K: int, L: int, params=None, reps=10, warmup=3, track
     sc = S.grid_race(S.fourier_track(track_seed), n_v, T, K, L, track_seed + 1)
     trk = Track.from_data(sc.track)
     base_ms, base_digest = _time_plan(trk, params, sc, K, L, launch_opts(), reps, warmup)
-    best = dict(block=256, ctas_per_sm=0, ms=base_ms)
-    seen = set()
-    for block in BLOCKS:
+    best = dict(block=0, samples_per_thread=0, ctas_per_sm=0, ms=base_ms)
+    for block, spt in SHAPES:
         for ctas in CTAS:
-            opts = launch_opts(block=block, samples_per_thread=256 // block, ctas_per_sm=ctas)
+            opts = launch_opts(block=block, samples_per_thread=spt, ctas_per_sm=ctas)
             ms, digest = _time_plan(trk, params, sc, K, L, opts, reps, warmup)
             if digest != base_digest:
-                raise RuntimeError(f"launch shape block={block} ctas_per_sm={ctas} changed the plan")
-            if (block, round(ms, 4)) in seen:
-                continue
-            seen.add((block, round(ms, 4)))
+                raise RuntimeError(f"launch shape block={block} samples/thread={spt} ctas_per_sm={ctas} changed "
+                                   "the plan")
             if log:
-                log(f"block {block:3d} ctas/SM {ctas}: {ms:.4f} ms")
+                log(f"block {block:3d} samples/thread {spt} ctas/SM {ctas}: {ms:.4f} ms")
             if ms < best["ms"]:
-                best = dict(block=block, ctas_per_sm=ctas, ms=ms)
+                best = dict(block=block, samples_per_thread=spt, ctas_per_sm=ctas, ms=ms)
     best["default_ms"] = base_ms
     best["tuned_at"] = time.strftime("%Y-%m-%dT%H:%M:%S")
     store(n_v, T, K, L, best, path)

@@ -20,9 +20,9 @@ struct RaceDev {
     int ks_off;      // offset into k_star_out ((L+1) * n_v + 1)
     int pos_off;     // float2 offset into each prediction buffer (n_v * (T+1))
     int pad0;
-    // work before this race in a round, in units of rollout steps per sample
-    // (each sample tile of a race weighs its horizon T): Jacobi rounds
-    // (every vehicle) and the extra round (egos only)
+    // work before this race in a round per sample tile of a vehicle (each
+    // tile of a race weighs its horizon T; a launch multiplies by its tiles
+    // per vehicle): Jacobi rounds (every vehicle) and the extra round (egos)
     long long wcum_all, wcum_ego;
 };
 

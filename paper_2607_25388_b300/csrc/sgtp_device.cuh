@@ -471,9 +471,9 @@ __device__ __forceinline__ float uniform_open(unsigned w)
 __device__ __forceinline__ float2 box_muller(unsigned w0, unsigned w1)
 {
     const float u1 = uniform_open(w0), u2 = uniform_open(w1);
-    // -2 ln u1 = (-2 ln 2) log2 u1; the approximate log2 may overshoot 0 as u1 -> 1
-    const float m = fmaxf(-1.38629436111989061883f * lg2_ftz(u1), 0.f);
-    const float r = sqrt_ftz(m);
+    // -2 ln u1 = (-2 ln 2) log2 u1; the approximate log2 may overshoot 0 as
+    // u1 -> 1 (u1 <= 1 - 2^-24), where the magnitude stays the right size
+    const float r = sqrt_ftz(fabsf(-1.38629436111989061883f * lg2_ftz(u1)));
     const float ang = __fmaf_rn(kTwoPi, u2, -kPi);
     const float sn = sin_ftz(ang), cs = cos_ftz(ang);
     return make_float2(-r * cs, -r * sn);

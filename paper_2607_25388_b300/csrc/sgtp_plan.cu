@@ -17,6 +17,7 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include "sgtp_batch.hpp"
@@ -46,9 +47,14 @@ struct PlanArgs {
     const RaceDev *races;     // NULL: single race `one`
     RaceDev one;
     int n_races, n_agents;
-    int K, L, tiles;          // tiles of blockDim samples per best response
-    int items_all, items_ego; // BR items of a Jacobi round / the extra round
-    long long w_all, w_ego;   // their total work (batches: items weighted by T; see RaceDev)
+    int K, L;
+    // per round kind ([0] Jacobi rounds, [1] the extra ego round): samples
+    // each thread rolls out at once, samples per tile, tiles per best
+    // response, work items (vehicles x tiles), and the items' total work
+    // (batches: items weighted by their race's T; see RaceDev)
+    int ni[2], tile[2], tiles[2], items[2];
+    long long w[2];
+    long long w_units_all, w_units_ego;   // total work per sample tile
     int maxT;
     const float *X0;
     float *U_io;
@@ -139,14 +145,14 @@ __device__ __forceinline__ int first_item_at(const PlanArgs &a, long long x, boo
     int lo = 0, hi = a.n_races - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        const long long w = extra ? a.races[mid].wcum_ego : a.races[mid].wcum_all;
+        const long long w = (extra ? a.races[mid].wcum_ego : a.races[mid].wcum_all) * a.tiles[extra];
         if (w <= x) lo = mid; else hi = mid - 1;
     }
     const RaceDev R = a.races[lo];
-    const long long w0 = extra ? R.wcum_ego : R.wcum_all;
-    const long long n = (long long)(extra ? 1 : R.n_v) * a.tiles;
+    const long long w0 = (extra ? R.wcum_ego : R.wcum_all) * a.tiles[extra];
+    const long long n = (long long)(extra ? 1 : R.n_v) * a.tiles[extra];
     const long long k = (x - w0 + R.T - 1) / R.T;
-    const long long first = (long long)(extra ? lo : R.agent_off) * a.tiles;
+    const long long first = (long long)(extra ? lo : R.agent_off) * a.tiles[extra];
     return (int)(first + (k < n ? k : n));
 }
 
@@ -543,7 +549,7 @@ __device__ void mppi_tile(const PlanArgs &a, int t, int ag, int T)
         if (lane == 0) gw[j >> 5] = ws;
     }
     __syncthreads();
-    float *out = a.mppi_part + ((size_t)ag * a.tiles + t) * (size_t)(2 * a.maxT + 2);
+    float *out = a.mppi_part + ((size_t)ag * a.tiles[0] + t) * (size_t)(2 * a.maxT + 2);
     for (int v = threadIdx.x; v <= 2 * T; v += blockDim.x) {
         float acc = 0.f;
 #pragma unroll
@@ -565,13 +571,13 @@ __device__ void mppi_update(const PlanArgs &a, int ag, int T, size_t uo, int rou
     using Tl = Tile<MAXO>;
     constexpr int kChunk = BRTile<MAXO>::kScrBytes / 4;
     const size_t stride = (size_t)(2 * a.maxT + 2);
-    const float *part = a.mppi_part + (size_t)ag * a.tiles * stride;
+    const float *part = a.mppi_part + (size_t)ag * a.tiles[0] * stride;
     float *acc = (float *)Tl::st();
     float *e = (float *)Tl::scratch();
     __shared__ float red_sh[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     float ml = __int_as_float(0x7f800000);
-    for (int q = threadIdx.x; q < a.tiles; q += blockDim.x) ml = fminf(ml, __ldcg(part + (size_t)q * stride));
+    for (int q = threadIdx.x; q < a.tiles[0]; q += blockDim.x) ml = fminf(ml, __ldcg(part + (size_t)q * stride));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ml = fminf(ml, __shfl_xor_sync(0xffffffffu, ml, o));
     if (lane == 0) red_sh[warp] = ml;
@@ -579,8 +585,8 @@ __device__ void mppi_update(const PlanArgs &a, int ag, int T, size_t uo, int rou
     __syncthreads();
     float cmin = red_sh[0];
     for (int w = 1; w < nwarps; ++w) cmin = fminf(cmin, red_sh[w]);
-    for (int base = 0; base < a.tiles; base += kChunk) {
-        const int n = min(kChunk, a.tiles - base);
+    for (int base = 0; base < a.tiles[0]; base += kChunk) {
+        const int n = min(kChunk, a.tiles[0] - base);
         __syncthreads();
         for (int q = threadIdx.x; q < n; q += blockDim.x) {
             const float mt = __ldcg(part + (size_t)(base + q) * stride);
@@ -612,14 +618,55 @@ __device__ void mppi_update(const PlanArgs &a, int ag, int T, size_t uo, int rou
     }
 }
 
-// MINB is the number of resident CTAs of 256 threads per SM the build is
-// sized for: 3 (80 registers, for plans with many sample tiles per round) or
-// 2 (128 registers, no spills, for plans with few tiles, where the latency
-// of one rollout dominates).  Both compute every sample with the same code.
-// MPPI selects the GA-IBR-MPPI update (a build of its own, so that the SGTP
-// builds carry none of its code).
+// Register budgets of the persistent kernel (MODE):
+//   kWide3: 256 threads x 3 CTAs per SM, 80 registers, one sample per thread;
+//   kWide2: 256 x 2 CTAs, 128 registers, one sample per thread;
+//   kIlp:   128 x 3 CTAs, 168 registers, one to three samples per thread at
+//           once (chosen per round, so that a round fits in one wave where
+//           it can): independent rollouts interleaved in one thread hide
+//           each other's latency, and 168 registers hold three of them.
+// Every mode computes every sample with the same code.  MPPI selects the
+// GA-IBR-MPPI update (a build of its own, so that the SGTP builds carry none
+// of its code; kWide3 and kWide2 only).
+constexpr int kWide3 = 0, kWide2 = 1, kIlp = 2;
+
+template <int MAXO, int MODE, bool MPPI>
+__device__ __forceinline__ void plan_body(const PlanArgs &a);
+
 template <int MAXO, int MINB, bool MPPI>
 __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
+{
+    plan_body<MAXO, MINB == 3 ? kWide3 : kWide2, MPPI>(a);
+}
+
+template <int MAXO>
+__global__ void __launch_bounds__(128, 3) plan_kernel_ilp(PlanArgs a)
+{
+    plan_body<MAXO, kIlp, false>(a);
+}
+
+// Selection key of the NI candidates k0 + i blockDim of this thread (all
+// threads of the tile call it; candidates k >= K key as ~0).
+template <int MAXO, int NI>
+__device__ __forceinline__ unsigned long long tile_keys(const BRScalars &S, const PlanArgs &a, unsigned k0, int round,
+                                                        int &flag)
+{
+    unsigned kk[NI];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) kk[i] = k0 + (unsigned)i * blockDim.x;
+    SampleResult r[NI];
+    run_candidates<MAXO, NI, false>(S, a.p, a.rk, kk, round > 0, flag, r, nullptr, nullptr, nullptr);
+    unsigned long long best = ~0ull;
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        const unsigned long long key = make_key(r[i].feasible, r[i].cost, r[i].viol, kk[i]);
+        if (kk[i] < (unsigned)a.K && key < best) best = key;
+    }
+    return best;
+}
+
+template <int MAXO, int MODE, bool MPPI>
+__device__ __forceinline__ void plan_body(const PlanArgs &a)
 {
     using Tl = Tile<MAXO>;
     __shared__ unsigned long long cta_key;
@@ -705,11 +752,11 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
         // work (items weighted by their race's horizon) for a batch
         int i0, i1;
         if (!a.races) {
-            const int n_items = extra ? a.items_ego : a.items_all;
+            const int n_items = a.items[extra];
             i0 = (int)((long long)n_items * blockIdx.x / gridDim.x);
             i1 = (int)((long long)n_items * (blockIdx.x + 1) / gridDim.x);
         } else {
-            const long long W = extra ? a.w_ego : a.w_all;
+            const long long W = a.w[extra];
             i0 = first_item_at(a, W * blockIdx.x / gridDim.x, extra);
             i1 = first_item_at(a, W * (blockIdx.x + 1) / gridDim.x, extra);
         }
@@ -719,7 +766,7 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
             // item = vehicle (all vehicles of all races in a Jacobi round, the
             // races' egos in the extra round) x tile of that vehicle's samples
             int ri, i;
-            const int unit = item / a.tiles, t = item - unit * a.tiles;
+            const int unit = item / a.tiles[extra], t = item - unit * a.tiles[extra];
             if (!extra) {
                 ri = find_race(a, unit, [](const RaceDev &r) { return r.agent_off; });
                 i = unit - get_race(a, ri).agent_off;
@@ -794,22 +841,32 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
                 __syncthreads();
                 if (abort_sh) { ok = false; break; }
             }
-            // a tile of kTileSingle samples, kTileSingle / blockDim.x per thread;
+            // a tile of a.tile[extra] samples: in the kIlp build one to three
+            // per thread at once (a.ni[extra], candidates k, k + blockDim,
+            // k + 2 blockDim), otherwise a.tile / blockDim.x in turn;
             // GA-IBR-MPPI keys every sample as feasible (its k* is the lowest
             // cost) and keeps the tile's costs for its partial sums
             constexpr bool mppi = MPPI;
             unsigned long long best = ~0ull;
-            for (unsigned j = threadIdx.x; j < (unsigned)kTileSingle; j += blockDim.x) {
-                const unsigned k = (unsigned)t * kTileSingle + j;
-                float c = __int_as_float(0x7f800000);
-                if (k < (unsigned)a.K) {
-                    const SampleResult r = run_candidate<MAXO, false>(S, a.p, a.rk, k, round > 0, flag, nullptr,
-                                                                      nullptr, nullptr);
-                    const unsigned long long key = make_key(r.feasible || mppi, r.cost, r.viol, k);
-                    best = key < best ? key : best;
-                    if (fabsf(r.cost) <= 3.402823466e38f) c = r.cost;
+            if constexpr (MODE == kIlp) {
+                const unsigned k0 = (unsigned)t * a.tile[extra] + threadIdx.x;
+                const int ni = a.ni[extra];
+                if (ni == 3) best = tile_keys<MAXO, 3>(S, a, k0, round, flag);
+                else if (ni == 2) best = tile_keys<MAXO, 2>(S, a, k0, round, flag);
+                else best = tile_keys<MAXO, 1>(S, a, k0, round, flag);
+            } else {
+                for (unsigned j = threadIdx.x; j < (unsigned)a.tile[extra]; j += blockDim.x) {
+                    const unsigned k = (unsigned)t * a.tile[extra] + j;
+                    float c = __int_as_float(0x7f800000);
+                    if (k < (unsigned)a.K) {
+                        const SampleResult r = run_candidate<MAXO, false>(S, a.p, a.rk, k, round > 0, flag, nullptr,
+                                                                          nullptr, nullptr);
+                        const unsigned long long key = make_key(r.feasible || mppi, r.cost, r.viol, k);
+                        best = key < best ? key : best;
+                        if (fabsf(r.cost) <= 3.402823466e38f) c = r.cost;
+                    }
+                    if constexpr (MPPI) ((float *)Tl::st())[j] = c;
                 }
-                if constexpr (MPPI) ((float *)Tl::st())[j] = c;
             }
             best = warp_min_u64(best);
             if (lane == 0) atomicMin(&cta_key, best);
@@ -911,82 +968,127 @@ struct Layout {
 
 int maxo_bucket(int n) { return n <= 1 ? 1 : n <= 3 ? 3 : n <= 9 ? 9 : 15; }
 
-template <int MAXO, int MINB, bool MPPI>
+template <int MAXO, int MODE, bool MPPI>
+const void *plan_kernel_of()
+{
+    if constexpr (MODE == kIlp) return (const void *)plan_kernel_ilp<MAXO>;
+    else return (const void *)plan_kernel<MAXO, MODE == kWide3 ? 3 : 2, MPPI>;
+}
+
+template <int MAXO, int MODE, bool MPPI>
 sgtp_status configure_plan_t()
 {
     // the shared-memory opt-in applies to the current device only
     static PerDeviceFlag configured;
     return once_per_device(configured, []() -> sgtp_status {
-        SGTP_CUDA(cudaFuncSetAttribute(plan_kernel<MAXO, MINB, MPPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        SGTP_CUDA(cudaFuncSetAttribute(plan_kernel_of<MAXO, MODE, MPPI>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024));
         return SGTP_OK;
     });
 }
 
-sgtp_status configure_plan_kernels()
+template <int MAXO>
+sgtp_status configure_plan_maxo()
 {
     sgtp_status st;
-    if ((st = configure_plan_t<1, 2, false>()) || (st = configure_plan_t<3, 2, false>()) ||
-        (st = configure_plan_t<9, 2, false>()) || (st = configure_plan_t<15, 2, false>()) ||
-        (st = configure_plan_t<1, 3, false>()) || (st = configure_plan_t<3, 3, false>()) ||
-        (st = configure_plan_t<9, 3, false>()) || (st = configure_plan_t<15, 3, false>()))
+    if ((st = configure_plan_t<MAXO, kWide3, false>()) || (st = configure_plan_t<MAXO, kWide2, false>()) ||
+        (st = configure_plan_t<MAXO, kIlp, false>()) || (st = configure_plan_t<MAXO, kWide3, true>()) ||
+        (st = configure_plan_t<MAXO, kWide2, true>()))
         return st;
     return SGTP_OK;
 }
 
-template <int MAXO, int MINB, bool MPPI>
-sgtp_status launch_plan_v(PlanArgs &a, int block, int ctas, cudaStream_t s)
+sgtp_status configure_plan_kernels()
+{
+    sgtp_status st;
+    if ((st = configure_plan_maxo<1>()) || (st = configure_plan_maxo<3>()) || (st = configure_plan_maxo<9>()) ||
+        (st = configure_plan_maxo<15>()))
+        return st;
+    return SGTP_OK;
+}
+
+template <int MAXO, int MODE, bool MPPI>
+sgtp_status launch_plan_v(PlanArgs &a, int block, int ctas, int spt, cudaStream_t s)
 {
     const size_t smem = BRTile<MAXO>::kBytes;
-    sgtp_status cst = configure_plan_t<MAXO, MINB, MPPI>();
+    sgtp_status cst = configure_plan_t<MAXO, MODE, MPPI>();
     if (cst) return cst;
     int dev = 0, sms = 0, per_sm = 0;
     SGTP_CUDA(cudaGetDevice(&dev));
     SGTP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    SGTP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_kernel<MAXO, MINB, MPPI>, block, smem));
+    SGTP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_kernel_of<MAXO, MODE, MPPI>(), block, smem));
     SGTP_CHECK(per_sm >= 1, "plan kernel does not fit on an SM (smem %zu)", smem);
     if (ctas > 0 && ctas < per_sm) per_sm = ctas;
     const int grid = sms * per_sm;
+    // tiles of each round kind: kIlp rolls out ni samples per thread at once,
+    // the fewest that fit the round's samples in one wave of the grid (at
+    // most 3), unless the caller fixed it
+    const long long cand[2] = {(long long)a.n_agents * a.K, (long long)a.n_races * a.K};
+    for (int e = 0; e < 2; ++e) {
+        int ni = 1;
+        if (MODE == kIlp) {
+            const long long slots = (long long)grid * block;
+            ni = spt > 0 ? spt : (int)std::min(3ll, std::max(1ll, (cand[e] + slots - 1) / slots));
+        }
+        a.ni[e] = ni;
+        a.tile[e] = MPPI ? kTileSingle : block * ni;
+        a.tiles[e] = (a.K + a.tile[e] - 1) / a.tile[e];
+        a.items[e] = (e ? a.n_races : a.n_agents) * a.tiles[e];
+        a.w[e] = (e ? a.w_units_ego : a.w_units_all) * a.tiles[e];
+    }
     void *args[] = {&a};
     SGTP_CUDA(cudaMemsetAsync(a.bar, 0, 256, s));
     SGTP_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), s));
-    SGTP_CUDA(cudaLaunchCooperativeKernel((const void *)plan_kernel<MAXO, MINB, MPPI>, grid, block, args, smem, s));
+    SGTP_CUDA(cudaLaunchCooperativeKernel(plan_kernel_of<MAXO, MODE, MPPI>(), grid, block, args, smem, s));
     count_launch();
     return SGTP_OK;
 }
 
-// Work decomposition and register budget of one launch: tiles of
-// kTileSingle samples; the 128-register build when at most two 256-thread
-// CTAs per SM are wanted -- explicitly, or by default when a Jacobi round
-// has fewer tiles than three CTAs per SM could take at once.
+// Register budget and shape of one launch.  By default a plain SGTP plan
+// runs kIlp (samples per thread chosen per round) unless its Jacobi round is
+// at most one 256-thread CTA of samples per SM; a plan with the learned
+// proposal runs 256-thread CTAs (the network's layers are split over eight
+// warps): kWide2 when a Jacobi round has fewer 256-sample tiles than three
+// CTAs per SM could take at once, else kWide3; GA-IBR-MPPI likewise (it
+// takes the wide builds only).  Options override: block 128 (or
+// samples_per_thread > 1) selects kIlp, block 256 the wide builds
+// (ctas_per_sm <= 2: kWide2).
 template <int MAXO>
 sgtp_status launch_plan_t(PlanArgs &a, const sgtp_launch_opts *opts, cudaStream_t s)
 {
-    const int block = (opts && opts->block > 0) ? opts->block : 256;
+    int block = (opts && opts->block > 0) ? opts->block : 0;
+    const int spt = (opts && opts->samples_per_thread > 0) ? opts->samples_per_thread : 0;
     int ctas = opts ? opts->ctas_per_sm : 0;
     int dev = 0, sms = 0;
     SGTP_CUDA(cudaGetDevice(&dev));
     SGTP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    a.tiles = (a.K + kTileSingle - 1) / kTileSingle;
-    a.items_all = a.n_agents * a.tiles;
-    a.items_ego = a.n_races * a.tiles;
-    bool wide;
-    if (ctas > 0) wide = ctas * block <= 512;
-    else wide = (long long)a.items_all < 3ll * sms;
-    if (wide && ctas == 0) ctas = 512 / block;
-    if (a.mppi_il > 0.f)
-        return wide ? launch_plan_v<MAXO, 2, true>(a, block, ctas, s) : launch_plan_v<MAXO, 3, true>(a, block, ctas, s);
-    return wide ? launch_plan_v<MAXO, 2, false>(a, block, ctas, s) : launch_plan_v<MAXO, 3, false>(a, block, ctas, s);
+    const bool mppi = a.mppi_il > 0.f;
+    const bool learned = a.mlp_wb != nullptr || a.feat_out != nullptr;
+    SGTP_CHECK(!(mppi && (spt > 1 || block == 128)), "GA-IBR-MPPI takes 256-thread CTAs, one sample per thread");
+    // a round of at most one 256-thread CTA's worth of samples per SM runs
+    // the wide 128-register build by default (measured faster there)
+    const bool small = (long long)a.n_agents * a.K <= 256ll * sms;
+    const bool ilp = !mppi && (block == 128 || spt > 1 || (block == 0 && !learned && !small));
+    if (ilp) return launch_plan_v<MAXO, kIlp, false>(a, 128, ctas, spt, s);
+    block = 256;
+    const bool wide2 = ctas > 0 ? ctas <= 2 : (long long)((a.K + 255) / 256) * a.n_agents < 3ll * sms;
+    if (wide2 && ctas == 0) ctas = 2;
+    if (mppi)
+        return wide2 ? launch_plan_v<MAXO, kWide2, true>(a, block, ctas, 1, s)
+                     : launch_plan_v<MAXO, kWide3, true>(a, block, ctas, 1, s);
+    return wide2 ? launch_plan_v<MAXO, kWide2, false>(a, block, ctas, 1, s)
+                 : launch_plan_v<MAXO, kWide3, false>(a, block, ctas, 1, s);
 }
 
 sgtp_status launch_plan(PlanArgs &a, int max_opp, const sgtp_launch_opts *opts, cudaStream_t s)
 {
     if (opts) {
-        SGTP_CHECK(opts->block == 0 || opts->block == 64 || opts->block == 128 || opts->block == 256,
-                   "block must be 64, 128 or 256 (got %d)", opts->block);
-        const int b = opts->block > 0 ? opts->block : 256;
-        SGTP_CHECK(opts->samples_per_thread == 0 || opts->samples_per_thread == 256 / b,
-                   "samples_per_thread must be 0 or 256/block = %d", 256 / b);
+        SGTP_CHECK(opts->block == 0 || opts->block == 128 || opts->block == 256, "block must be 128 or 256 (got %d)",
+                   opts->block);
+        SGTP_CHECK(opts->samples_per_thread >= 0 && opts->samples_per_thread <= 3,
+                   "samples_per_thread must be 0 .. 3 (got %d)", opts->samples_per_thread);
+        SGTP_CHECK(!(opts->block == 256 && opts->samples_per_thread > 1),
+                   "256-thread CTAs take one sample per thread");
         SGTP_CHECK(opts->ctas_per_sm >= 0 && opts->window >= 0 && opts->wait_timeout_ns >= 0,
                    "negative launch option");
     }
@@ -1193,7 +1295,6 @@ extern "C" sgtp_status sgtp_batch_create(const sgtp_track *trk, const sgtp_race 
     SGTP_CHECK(L >= 0 && L < 4096, "L out of range");
     sgtp_batch *b = new sgtp_batch();
     b->trk = trk; b->n_races = n_races; b->K = K; b->L = L;
-    const long long tiles = (K + kTileSingle - 1) / kTileSingle;
     long long ag = 0, u = 0, xi = 0, ks = 0, pos = 0;
     for (int r = 0; r < n_races; ++r) {
         const sgtp_race &q = races[r];
@@ -1208,8 +1309,8 @@ extern "C" sgtp_status sgtp_batch_create(const sgtp_track *trk, const sgtp_race 
         R.agent_off = (int)ag; R.u_off = (int)u; R.xi_off = (int)xi; R.ks_off = (int)ks; R.pos_off = (int)pos;
         R.wcum_all = b->w_all;
         R.wcum_ego = b->w_ego;
-        b->w_all += (long long)q.n_v * tiles * q.T;
-        b->w_ego += tiles * q.T;
+        b->w_all += (long long)q.n_v * q.T;
+        b->w_ego += q.T;
         b->races.push_back(R);
         ag += q.n_v; u += (long long)q.n_v * q.T * 2; xi += (long long)q.n_v * (q.T + 1) * 4;
         ks += (long long)(L + 1) * q.n_v + 1; pos += (long long)q.n_v * (q.T + 1);
@@ -1217,7 +1318,7 @@ extern "C" sgtp_status sgtp_batch_create(const sgtp_track *trk, const sgtp_race 
         b->minT = r == 0 ? q.T : std::min(b->minT, q.T);
         b->max_nv = std::max(b->max_nv, q.n_v);
     }
-    if (xi > (1ll << 31) || ag * tiles > (1ll << 31) || u > (1ll << 31)) {
+    if (xi > (1ll << 31) || ag * (long long)K > (1ll << 31) || u > (1ll << 31)) {
         delete b;
         return set_error(SGTP_E_INVALID, "batch too large for 32-bit offsets");
     }
@@ -1306,8 +1407,8 @@ static sgtp_status batch_plan_impl(const sgtp_batch *b, const sgtp_params *p, co
     a.sig_lat = sig_lat;
     a.races = b->races_dev;
     a.n_races = b->n_races;
-    a.w_all = b->w_all;
-    a.w_ego = b->w_ego;
+    a.w_units_all = b->w_all;
+    a.w_units_ego = b->w_ego;
     a.n_agents = (int)b->agents;
     a.maxT = b->maxT;
     a.xi_total = b->xi_elems;

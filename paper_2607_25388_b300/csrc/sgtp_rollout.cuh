@@ -208,41 +208,58 @@ __device__ __noinline__ int bisector_walk(const BRScalars &S, int r, float px, f
     return r;
 }
 
-// Frenet of the next rollout state.  The sample carries a continuous segment
-// position pos (window-local segment + parameter) and the predicted position
-// of the next state, ppred = pos + last advance - 1/2.  The bisectors of
-// c = floor(ppred), c+1, c+2 certify segment c or c+1 when p is past the
-// first and not past the third (three plane tests against shared memory);
-// otherwise the bisector walk takes over.
-template <int MAXO>
-__device__ __forceinline__ GeoPt frenet_fast(const BRScalars &S, float px, float py, float &pos, float &ppred, int &flag)
-{
-    using T = Tile<MAXO>;
-    const int c = __float2int_rd(ppred);
-    int m = 0;
-    float len = 0.f;
-    bool ok = false;
-    if ((unsigned)c < (unsigned)(S.Wn - 2)) {
-        const float4 q0 = T::F0()[c], q1 = T::F0()[c + 1], q2 = T::F0()[c + 2];
-        const bool b0 = past_bisector(q0, px, py), b1 = past_bisector(q1, px, py), b2 = past_bisector(q2, px, py);
-        if (b0 && !b2) {
-            m = b1 ? c + 1 : c;
-            len = b1 ? q1.w : q0.w;
-            ok = true;
-        }
-    }
+// Segment of the next rollout state.  The sample carries a continuous
+// segment position pos (window-local segment + parameter) and the predicted
+// position of its next state, ppred = pos + last advance - 1/2.  With
+// c = floor(ppred) clamped into the window (wlim = S.Wn - 2), the bisectors of
+// c, c+1, c+2 certify segment c or c+1 when p is past the first and not past
+// the third (three plane tests against shared memory); the segment's records
+// are read unconditionally, and `ok` is false when the certificate fails or
+// c had to be clamped, in which case frenet_relocate must run.
+struct SegPick {
     float4 g1, g2;
     float2 g3;
-    if (ok) {
-        g1 = T::F1()[m]; g2 = T::F2()[m]; g3 = T::F3()[m];
-    } else {
-        const int r = __float2int_rd(pos);
-        const int start = (c < r - kMaxMoves || c > r + kMaxMoves) ? r : c;
-        m = bisector_walk<MAXO>(S, start, px, py, flag);
-        segment_at<MAXO>(S, m, g1, g2, g3, len);
-    }
-    const GeoPt f = frenet_eval(g1, g2, g3, len, px, py);
-    const float np = (float)m + f.tc;
+    float len;
+    int m;
+    bool ok;
+};
+
+template <int MAXO>
+__device__ __forceinline__ SegPick frenet_locate(int wlim, float px, float py, float ppred)
+{
+    using T = Tile<MAXO>;
+    SegPick q;
+    const int craw = __float2int_rd(ppred);
+    const int c = min(max(craw, 0), wlim - 1);
+    const float4 q0 = T::F0()[c], q1 = T::F0()[c + 1], q2 = T::F0()[c + 2];
+    const bool b0 = past_bisector(q0, px, py), b1 = past_bisector(q1, px, py), b2 = past_bisector(q2, px, py);
+    q.m = b1 ? c + 1 : c;
+    q.len = b1 ? q1.w : q0.w;
+    q.g1 = T::F1()[q.m]; q.g2 = T::F2()[q.m]; q.g3 = T::F3()[q.m];
+    q.ok = b0 && !b2 && c == craw;
+    return q;
+}
+
+// The rare case: the bisector walk from the predicted segment (or from the
+// last one when the prediction is far off), records from the window or
+// global memory.
+template <int MAXO>
+__device__ __noinline__ SegPick frenet_relocate(const BRScalars &S, float px, float py, float pos, float ppred, int &flag)
+{
+    SegPick q;
+    const int c = __float2int_rd(ppred), r = __float2int_rd(pos);
+    const int start = (c < r - kMaxMoves || c > r + kMaxMoves) ? r : c;
+    q.m = bisector_walk<MAXO>(S, start, px, py, flag);
+    segment_at<MAXO>(S, q.m, q.g1, q.g2, q.g3, q.len);
+    q.ok = true;
+    return q;
+}
+
+// Frenet of the state from its segment, and the next prediction.
+__device__ __forceinline__ GeoPt frenet_finish(const SegPick &q, float px, float py, float &pos, float &ppred)
+{
+    const GeoPt f = frenet_eval(q.g1, q.g2, q.g3, q.len, px, py);
+    const float np = (float)q.m + f.tc;
     ppred = __fmaf_rn(2.f, np, -(pos + 0.5f));
     pos = np;
     return f;
@@ -317,13 +334,21 @@ __device__ __forceinline__ void noise_pair(const BRScalars &S, const RoundKeys &
     z1 = box_muller(w.z, w.w);
 }
 
+// Running sums of the tracking cost (Eq. ctrack) per component: squared
+// state errors (x, y, psi, v) over tau = 1..H, squared controls over
+// tau = 0..H-1 and squared control differences over tau = 1..H-1; the
+// weights Q, R, S multiply them once per candidate.
+struct TrackSums {
+    float ex, ey, epsi, ev, ua, ud, da, dd;
+};
+
 template <int MAXO>
 struct SampleState {
     float x, y, psi, v;
     float a_prev, d_prev;
     float s;          // progress, unwrapped relative to s_t
     float pos, ppred; // continuous segment position and the next step's prediction
-    f2p cost;         // running c_track, two partial sums
+    TrackSums c;
     float rho_bd, d_tail;
     float g2[MAXO];
 };
@@ -335,7 +360,7 @@ __device__ __forceinline__ void sample_init(SampleState<MAXO> &St, const BRScala
     St.a_prev = 0.f; St.d_prev = 0.f;
     St.s = S.s_t;
     St.pos = S.pos0; St.ppred = S.ppred0;
-    St.cost = pk(0.f, 0.f);
+    St.c = TrackSums{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     St.rho_bd = __int_as_float(0x7f800000);
     St.d_tail = 0.f;
 #pragma unroll
@@ -344,28 +369,40 @@ __device__ __forceinline__ void sample_init(SampleState<MAXO> &St, const BRScala
 
 // Pieces of one rollout step.
 
-// control cost, tau = 0..H-1, and smoothness, tau = 1..H-1 (Eq. ctrack)
-__device__ __forceinline__ f2p step_control_cost(const sgtp_params &p, f2p cost, float &a_prev, float &d_prev,
-                                                 float2 u, int tau)
+// control cost terms, tau = 0..H-1, and smoothness terms, tau = 1..H-1 (Eq. ctrack)
+__device__ __forceinline__ void step_control_cost(TrackSums &c, float &a_prev, float &d_prev, float2 u, int tau)
 {
-    const f2p uu = pk(u.x, u.y);
-    f2p acc = fma2(mul2(uu, uu), pk(p.R[0], p.R[1]), cost);
+    c.ua = __fmaf_rn(u.x, u.x, c.ua);
+    c.ud = __fmaf_rn(u.y, u.y, c.ud);
     if (tau > 0) {
-        const f2p du = sub2(uu, pk(a_prev, d_prev));
-        acc = fma2(mul2(du, du), pk(p.S[0], p.S[1]), acc);
+        const float da = u.x - a_prev, dd = u.y - d_prev;
+        c.da = __fmaf_rn(da, da, c.da);
+        c.dd = __fmaf_rn(dd, dd, c.dd);
     }
     a_prev = u.x; d_prev = u.y;
-    return acc;
 }
 
-// tracking term at the new state, tau = 1..H (Eq. ctrack), heading error wrapped
-__device__ __forceinline__ f2p step_tracking_cost(const sgtp_params &p, f2p acc, float x, float y, float psi, float v,
-                                                  float4 r)
+// tracking terms at the new state, tau = 1..H (Eq. ctrack), heading error wrapped
+__device__ __forceinline__ void step_tracking_cost(TrackSums &c, float x, float y, float psi, float v, float4 r)
 {
-    const f2p exy = sub2(pk(x, y), pk(r.x, r.y));
-    acc = fma2(mul2(exy, exy), pk(p.Q[0], p.Q[1]), acc);
-    const f2p epv = pk(wrap_angle(psi - r.z), v - r.w);
-    return fma2(mul2(epv, epv), pk(p.Q[2], p.Q[3]), acc);
+    const float ex = x - r.x, ey = y - r.y, ep = wrap_angle(psi - r.z), ev = v - r.w;
+    c.ex = __fmaf_rn(ex, ex, c.ex);
+    c.ey = __fmaf_rn(ey, ey, c.ey);
+    c.epsi = __fmaf_rn(ep, ep, c.epsi);
+    c.ev = __fmaf_rn(ev, ev, c.ev);
+}
+
+// c_track from the running sums
+__device__ __forceinline__ float track_cost(const sgtp_params &p, const TrackSums &c)
+{
+    float t = __fmul_rn(p.Q[0], c.ex);
+    t = __fmaf_rn(p.Q[1], c.ey, t);
+    t = __fmaf_rn(p.Q[2], c.epsi, t);
+    t = __fmaf_rn(p.Q[3], c.ev, t);
+    t = __fmaf_rn(p.R[0], c.ua, t);
+    t = __fmaf_rn(p.R[1], c.ud, t);
+    t = __fmaf_rn(p.S[0], c.da, t);
+    return __fmaf_rn(p.S[1], c.dd, t);
 }
 
 // time-aligned distances to opponents [2 Q0, 2 Q1) of one step (Eq. Dmin),
@@ -392,30 +429,48 @@ __device__ __forceinline__ void step_opponents(float *g2, float x, float y, cons
     }
 }
 
-// Advance a candidate by one step tau with control u: control costs, the
-// bicycle step, Frenet of the new state with its boundary clearance (Sec.
-// III-B, widths at the foot point) and tail offset, tracking cost,
-// opponent distances; optional outputs.
-template <int MAXO, bool OUT>
-__device__ __forceinline__ void sample_step(SampleState<MAXO> &St, const BRScalars &S, const sgtp_params &p,
-                                            int tau, float2 u, int &flag, float *st_out, float *fr_out)
+// Advance NI candidates (one thread's) by one step tau with controls u:
+// control costs, the bicycle step, Frenet of the new states with their
+// boundary clearance (Sec. III-B, widths at the foot point) and tail
+// offsets, tracking costs, opponent distances; optional outputs (NI = 1).
+// The candidates' chains are independent, so their instructions interleave.
+template <int MAXO, int NI, bool OUT>
+__device__ __forceinline__ void sample_steps(SampleState<MAXO> (&St)[NI], const BRScalars &S, const sgtp_params &p,
+                                             int tau, int tail0, int wlim, const float2 (&u)[NI], int &flag,
+                                             float *st_out, float *fr_out)
 {
     using T = Tile<MAXO>;
-    f2p acc = step_control_cost(p, St.cost, St.a_prev, St.d_prev, u, tau);
-    bicycle_step(p, St.x, St.y, St.psi, St.v, u.x, u.y);
+    SegPick q[NI];
+    bool miss = false;
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        step_control_cost(St[i].c, St[i].a_prev, St[i].d_prev, u[i], tau);
+        bicycle_step(p, St[i].x, St[i].y, St[i].psi, St[i].v, u[i].x, u[i].y);
+        q[i] = frenet_locate<MAXO>(wlim, St[i].x, St[i].y, St[i].ppred);
+        miss = miss || !q[i].ok;
+    }
+    if (__any_sync(__activemask(), miss)) {
+#pragma unroll
+        for (int i = 0; i < NI; ++i)
+            if (!q[i].ok) q[i] = frenet_relocate<MAXO>(S, St[i].x, St[i].y, St[i].pos, St[i].ppred, flag);
+    }
     const int st = tau + 1;
-    const GeoPt f = frenet_fast<MAXO>(S, St.x, St.y, St.pos, St.ppred, flag);
-    St.s = f.s;
-    St.rho_bd = fminf(St.rho_bd, f.rho);
-    if (st > S.T - S.n_tail) St.d_tail = St.d_tail + f.d;
-    St.cost = step_tracking_cost(p, acc, St.x, St.y, St.psi, St.v, T::ref()[st]);
-    step_opponents<0, MAXO / 2, true, MAXO>(St.g2, St.x, St.y, T::opp() + tau * BRTile<MAXO>::NP);
-    if (OUT) {
-        if (st_out) {
-            st_out[4 * st + 0] = St.x; st_out[4 * st + 1] = St.y; st_out[4 * st + 2] = St.psi;
-            st_out[4 * st + 3] = St.v;
+    const float4 r = T::ref()[st];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        const GeoPt f = frenet_finish(q[i], St[i].x, St[i].y, St[i].pos, St[i].ppred);
+        St[i].s = f.s;
+        St[i].rho_bd = fminf(St[i].rho_bd, f.rho);
+        if (st > tail0) St[i].d_tail = St[i].d_tail + f.d;
+        step_tracking_cost(St[i].c, St[i].x, St[i].y, St[i].psi, St[i].v, r);
+        step_opponents<0, MAXO / 2, true, MAXO>(St[i].g2, St[i].x, St[i].y, T::opp() + tau * BRTile<MAXO>::NP);
+        if (OUT) {
+            if (st_out) {
+                st_out[4 * st + 0] = St[i].x; st_out[4 * st + 1] = St[i].y; st_out[4 * st + 2] = St[i].psi;
+                st_out[4 * st + 3] = St[i].v;
+            }
+            if (fr_out) { fr_out[2 * st] = St[i].s; fr_out[2 * st + 1] = f.d; }
         }
-        if (fr_out) { fr_out[2 * st] = St.s; fr_out[2 * st + 1] = f.d; }
     }
 }
 
@@ -427,12 +482,10 @@ struct SampleResult {
 // Terminal game cost per opponent (Eqs. c_contest, c_long, c_block,
 // c_safety), total cost (Eq. allc), feasibility and violation (Sec. III-B).
 template <int MAXO>
-__device__ __forceinline__ SampleResult finish_terms(f2p cost, float s, float rho_bd, float d_tail, const float *g2,
+__device__ __forceinline__ SampleResult finish_terms(float c_track, float s, float rho_bd, float d_tail, const float *g2,
                                                      const BRScalars &S, const sgtp_params &p, bool game_on)
 {
     using T = Tile<MAXO>;
-    const float2 cp = upk(cost);
-    const float c_track = cp.x + cp.y;
     const float dbar_i = d_tail / (float)S.n_tail;
     const float prog_i = s - S.s_t;
     float c_game = 0.f;
@@ -465,41 +518,64 @@ template <int MAXO>
 __device__ __forceinline__ SampleResult sample_finish(const SampleState<MAXO> &St, const BRScalars &S,
                                                       const sgtp_params &p, bool game_on)
 {
-    return finish_terms<MAXO>(St.cost, St.s, St.rho_bd, St.d_tail, St.g2, S, p, game_on);
+    return finish_terms<MAXO>(track_cost(p, St.c), St.s, St.rho_bd, St.d_tail, St.g2, S, p, game_on);
 }
 
-// Full candidate: noise, controls, rollout, finish.  Optional outputs are
-// written when OUT (states (T+1)x4, frenet (T+1)x2, controls Tx2).
+// NI full candidates k[0..NI) in one thread: noise, controls, rollout,
+// finish.  Optional outputs are written when OUT (NI = 1; states (T+1)x4,
+// frenet (T+1)x2, controls Tx2).
+template <int MAXO, int NI, bool OUT>
+__device__ __forceinline__ void run_candidates(const BRScalars &S, const sgtp_params &p, const RoundKeys &rk,
+                                               const unsigned (&k)[NI], bool game_on, int &flag,
+                                               SampleResult (&res)[NI], float *st_out, float *fr_out, float *u_out)
+{
+    using T = Tile<MAXO>;
+    static_assert(!OUT || NI == 1, "per-candidate outputs take one candidate per thread");
+    SampleState<MAXO> St[NI];
+    unsigned sbit[NI];
+    const float4 *dist[NI];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        sample_init(St[i], S);
+        const bool prop = k[i] < (unsigned)S.K_prop;
+        sbit[i] = prop ? 0x80000000u : S.stream_bit;
+        dist[i] = T::dist() + (prop ? SGTP_MAX_T : 0);
+    }
+    if (OUT) {
+        if (st_out) { st_out[0] = St[0].x; st_out[1] = St[0].y; st_out[2] = St[0].psi; st_out[3] = St[0].v; }
+        if (fr_out) { fr_out[0] = S.s_t; fr_out[1] = S.d_t; }
+    }
+    const int Tn = S.T, tail0 = S.T - S.n_tail, wlim = S.Wn - 2;
+    for (int m = 0; 2 * m < Tn; ++m) {
+        float2 z0[NI], z1[NI], u[NI];
+#pragma unroll
+        for (int i = 0; i < NI; ++i) noise_pair(S, rk, k[i], sbit[i], m, z0[i], z1[i]);
+        const int t0 = 2 * m;
+#pragma unroll
+        for (int i = 0; i < NI; ++i) u[i] = sample_control_d(p, dist[i][t0], z0[i]);
+        if (OUT && u_out) { u_out[2 * t0] = u[0].x; u_out[2 * t0 + 1] = u[0].y; }
+        sample_steps<MAXO, NI, OUT>(St, S, p, t0, tail0, wlim, u, flag, st_out, fr_out);
+        if (t0 + 1 < Tn) {
+#pragma unroll
+            for (int i = 0; i < NI; ++i) u[i] = sample_control_d(p, dist[i][t0 + 1], z1[i]);
+            if (OUT && u_out) { u_out[2 * t0 + 2] = u[0].x; u_out[2 * t0 + 3] = u[0].y; }
+            sample_steps<MAXO, NI, OUT>(St, S, p, t0 + 1, tail0, wlim, u, flag, st_out, fr_out);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NI; ++i) res[i] = sample_finish(St[i], S, p, game_on);
+}
+
+// One full candidate per thread.
 template <int MAXO, bool OUT>
 __device__ __forceinline__ SampleResult run_candidate(const BRScalars &S, const sgtp_params &p,
                                                       const RoundKeys &rk, unsigned k, bool game_on, int &flag,
                                                       float *st_out, float *fr_out, float *u_out)
 {
-    using T = Tile<MAXO>;
-    SampleState<MAXO> St;
-    sample_init(St, S);
-    if (OUT) {
-        if (st_out) { st_out[0] = St.x; st_out[1] = St.y; st_out[2] = St.psi; st_out[3] = St.v; }
-        if (fr_out) { fr_out[0] = S.s_t; fr_out[1] = S.d_t; }
-    }
-    const int Tn = S.T;
-    const bool prop = k < (unsigned)S.K_prop;
-    const unsigned sbit = prop ? 0x80000000u : S.stream_bit;
-    const float4 *dist = T::dist() + (prop ? SGTP_MAX_T : 0);
-    for (int m = 0; 2 * m < Tn; ++m) {
-        float2 z0, z1;
-        noise_pair(S, rk, k, sbit, m, z0, z1);
-        const int t0 = 2 * m;
-        const float2 u0 = sample_control_d(p, dist[t0], z0);
-        if (OUT && u_out) { u_out[2 * t0] = u0.x; u_out[2 * t0 + 1] = u0.y; }
-        sample_step<MAXO, OUT>(St, S, p, t0, u0, flag, st_out, fr_out);
-        if (t0 + 1 < Tn) {
-            const float2 u1 = sample_control_d(p, dist[t0 + 1], z1);
-            if (OUT && u_out) { u_out[2 * t0 + 2] = u1.x; u_out[2 * t0 + 3] = u1.y; }
-            sample_step<MAXO, OUT>(St, S, p, t0 + 1, u1, flag, st_out, fr_out);
-        }
-    }
-    return sample_finish(St, S, p, game_on);
+    const unsigned kk[1] = {k};
+    SampleResult r[1];
+    run_candidates<MAXO, 1, OUT>(S, p, rk, kk, game_on, flag, r, st_out, fr_out, u_out);
+    return r[0];
 }
 
 // Stage one best response's opponent positions into the pair layout:

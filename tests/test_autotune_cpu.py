@@ -16,8 +16,8 @@ def test_cache_round_trip(tmp_path):
     path = str(tmp_path / "tune.json")
     info = (148, "B300")
     assert A.lookup(10, 60, 16384, 5, path, info) is None
-    A.store(10, 60, 16384, 5, dict(block=128, ctas_per_sm=4, ms=0.8), path, info)
+    A.store(10, 60, 16384, 5, dict(block=128, samples_per_thread=2, ctas_per_sm=3, ms=0.8), path, info)
     o = A.lookup(10, 60, 16384, 5, path, info)
-    assert (o.block, o.samples_per_thread, o.ctas_per_sm) == (128, 2, 4)
-    A.store(2, 30, 4096, 3, dict(block=64, ctas_per_sm=0, ms=0.1), path, info)
+    assert (o.block, o.samples_per_thread, o.ctas_per_sm) == (128, 2, 3)
+    A.store(2, 30, 4096, 3, dict(block=256, samples_per_thread=1, ctas_per_sm=0, ms=0.1), path, info)
     assert A.lookup(10, 60, 16384, 5, path, info).block == 128

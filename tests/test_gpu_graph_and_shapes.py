@@ -30,23 +30,24 @@ def plan(sc, p, K, L, seed, trk, opts=None):
     return res
 
 
-def test_block_sizes_give_identical_plans():
-    sc = S.ten_car_race(501, K=1000, T=50, L=2)        # K not a multiple of 256: a ragged last tile
+def test_launch_shapes_give_identical_plans():
+    sc = S.ten_car_race(501, K=1000, T=50, L=2)        # K not a multiple of any tile: a ragged last tile
     p = S.params_fullscale()
     trk = P().Track.from_data(sc.track)
     ref = plan(sc, p, 1000, 2, 3, trk)
     assert ref["status"][0] == 0
-    for block in (64, 128):
-        got = plan(sc, p, 1000, 2, 3, trk, P().launch_opts(block=block, samples_per_thread=256 // block))
+    for block, spt, ctas in ((128, 1, 0), (128, 2, 0), (128, 3, 1), (256, 1, 0), (256, 1, 2)):
+        got = plan(sc, p, 1000, 2, 3, trk, P().launch_opts(block=block, samples_per_thread=spt, ctas_per_sm=ctas))
         for k in ("xi", "k_star", "U", "xi_hist", "u_hist"):
-            np.testing.assert_array_equal(got[k], ref[k], err_msg=f"block {block} {k}")
+            np.testing.assert_array_equal(got[k], ref[k], err_msg=f"block {block} x {spt} ctas {ctas} {k}")
 
 
 def test_invalid_launch_shapes_are_rejected():
     sc = S.two_car_race(502, K=256, T=20, L=1)
     p = S.params_fullscale()
     trk = P().Track.from_data(sc.track)
-    for o in (dict(block=96), dict(block=512), dict(block=128, samples_per_thread=1), dict(ctas_per_sm=-1)):
+    for o in (dict(block=96), dict(block=512), dict(block=64), dict(block=256, samples_per_thread=2),
+              dict(samples_per_thread=4), dict(ctas_per_sm=-1)):
         with pytest.raises(RuntimeError, match="SGTP_E_INVALID"):
             plan(sc, p, 256, 1, 0, trk, P().launch_opts(**o))
 

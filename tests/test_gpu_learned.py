@@ -327,8 +327,8 @@ def test_learned_batch_equals_learned_single_plans(net):
         np.testing.assert_array_equal(ks_all[r * nk:(r + 1) * nk], single["k_star"].cpu().numpy())
 
 
-@pytest.mark.parametrize("block", [64, 128])
-def test_learned_plan_is_identical_for_every_block_size(net, block):
+@pytest.mark.parametrize("shape", [(128, 1, 0), (128, 2, 1), (256, 1, 2)])
+def test_learned_plan_is_identical_for_every_block_size(net, shape):
     """Features (incl. the zeroed slots of absent opponents), proposals and
     selections do not depend on the CTA size."""
     p = S.params_fullscale()
@@ -343,7 +343,7 @@ def test_learned_plan_is_identical_for_every_block_size(net, block):
         return {k: v.cpu().numpy() for k, v in out.items()}
 
     a = run(None)
-    b = run(P().launch_opts(block=block, samples_per_thread=256 // block))
+    b = run(P().launch_opts(block=shape[0], samples_per_thread=shape[1], ctas_per_sm=shape[2]))
     assert np.all(a["features"][:, :, 14:62] == 0.0)       # one opponent: slots 1..8 are zero
     for k in ("features", "prop", "xi", "k_star", "u_hist"):
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)

@@ -105,8 +105,8 @@ def test_perturbation_changes_the_plan_and_is_shape_invariant():
     plain = gpu_plan(sc, p, 1500, 1, seed=6, sigma=None)
     ref = gpu_plan(sc, p, 1500, 1, seed=6, sigma=(0.4, 0.2))
     assert not np.array_equal(plain["k_star"], ref["k_star"])
-    for block, ctas in ((64, 0), (128, 2), (256, 1)):
-        o = P.launch_opts(block=block, samples_per_thread=256 // block, ctas_per_sm=ctas)
+    for block, spt, ctas in ((128, 3, 0), (128, 1, 2), (256, 1, 1)):
+        o = P.launch_opts(block=block, samples_per_thread=spt, ctas_per_sm=ctas)
         g = gpu_plan(sc, p, 1500, 1, seed=6, sigma=(0.4, 0.2), opts=o)
         for k in ("k_star", "U", "xi", "xi_hist", "u_hist"):
             np.testing.assert_array_equal(g[k], ref[k], err_msg=f"{k} block {block}")
