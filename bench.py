@@ -48,49 +48,68 @@ def parse():
 
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """SM clock and clock-event reasons of one GPU, polled through NVML
+    (libnvidia-ml, loaded with ctypes) by a background thread every 2 ms
+    between start and stop, so that even a short timed region carries
+    samples.  Read-only: changes no setting of the GPU."""
 
-    def __init__(self, gpu_index: int):
-        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-        self.p = None
+    # NVML clock-event reason bits and the clock domain of the SM
+    REASONS = (("sw_power_cap", 0x4), ("hw_slowdown", 0x8), ("sw_thermal_slowdown", 0x20),
+               ("hw_thermal_slowdown", 0x40))
+    CLOCK_SM = 1
+
+    def __init__(self, gpu_index: int, period_s: float = 0.002):
+        import ctypes
+        import threading
+        self.samples, self.reasons, self.err = [], set(), None
+        self.stop_ev = threading.Event()
+        self.t = None
         try:
-            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                       "-lms", "200", "-i", str(gpu_index)], stdout=self.f,
-                                      stderr=subprocess.DEVNULL)
-        except Exception:
-            self.p = None
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                raise RuntimeError("nvmlInit_v2 failed")
+            h = ctypes.c_void_p()
+            if nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(gpu_index), ctypes.byref(h)) != 0:
+                raise RuntimeError("no NVML handle")
+            mx = ctypes.c_uint()
+            nv.nvmlDeviceGetMaxClockInfo(h, self.CLOCK_SM, ctypes.byref(mx))
+            self.max_mhz = float(mx.value)
+            get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        except Exception as e:          # no NVML: report it, measure without clocks
+            self.err = f"NVML unavailable: {e}"
+            return
+
+        def run():
+            clk, bits = ctypes.c_uint(), ctypes.c_ulonglong()
+            while not self.stop_ev.is_set():
+                if nv.nvmlDeviceGetClockInfo(h, self.CLOCK_SM, ctypes.byref(clk)) == 0:
+                    self.samples.append(float(clk.value))
+                if get_reasons(h, ctypes.byref(bits)) == 0:
+                    for name, bit in self.REASONS:
+                        if bits.value & bit:
+                            self.reasons.add(name)
+                self.stop_ev.wait(period_s)
+
+        self.t = threading.Thread(target=run, daemon=True)
+        self.t.start()
 
     def stop(self):
-        if self.p is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.p.terminate()
-        try:
-            self.p.wait(timeout=5)
-        except Exception:
-            self.p.kill()
-        self.f.flush()
-        rows = [r.split(", ") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
-        os.unlink(self.f.name)
-        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
-        reasons = set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            if len(r) < 9:
-                continue
-            for n, v in zip(names, r[5:9]):
-                if v.strip() == "Active":
-                    reasons.add(n)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(rows)}
+        if self.t is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [self.err], "samples": 0}
+        self.stop_ev.set()
+        self.t.join()
+        return {"sm_mhz": statistics.median(self.samples) if self.samples else None, "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(self.reasons), "samples": len(self.samples),
+                "source": "NVML, polled every 2 ms during the timed region"}
 
 
 # ---------------------------------------------------------------- CPU oracle
-def oracle_rate(seconds: float, seed: int = 200):
-    """FP64 oracle on all host cores: round-0 best responses of the ten-car
-    workload at K = 256 samples each, repeated until `seconds` have passed."""
+def oracle_rate(seconds: float, seed: int = 200, ks: int = 256):
+    """FP64 oracle on all host cores: best responses of the ten-car workload
+    at K = ks samples each (vehicles in turn, round tags 0..L+1 in turn, the
+    game term on after round 0, opponents on their nominal rollouts),
+    repeated until `seconds` have passed."""
     import numpy as np
     import oracle as O
     from paper_2607_25388_b300 import scenario as S
@@ -100,23 +119,22 @@ def oracle_rate(seconds: float, seed: int = 200):
     lo = np.float32([p["a_min"], -p["delta_max"]]); hi = np.float32([p["a_max"], p["delta_max"]])
     nominal = np.stack([O.rollout(p, sc.X0[i], np.clip(sc.U0[i], lo, hi), T) for i in range(N_V)])
     cores = os.cpu_count() or 1
-    ks = 256
     steps = 0
     t0 = time.perf_counter()
     i = 0
     while True:
-        a = i % N_V
+        a, rnd = i % N_V, (i // N_V) % (L + 2)
         opp = np.stack([nominal[j] for j in range(N_V) if j != a])
-        O.best_response(p, ot, sc.X0[a], sc.U0[a], sc.vref_scale[a], opp, T, ks, seed=seed, agent=a, rnd=0,
-                        game_on=False, nthreads=cores)
+        O.best_response(p, ot, sc.X0[a], sc.U0[a], sc.vref_scale[a], opp, T, ks, seed=seed, agent=a, rnd=rnd,
+                        game_on=rnd > 0, nthreads=cores)
         steps += ks * T
         i += 1
         el = time.perf_counter() - t0
         if el >= seconds:
             break
     return {"value": steps / el, "unit": "rollout-steps/s", "cores": cores, "kind": "oracle",
-            "sample": f"{i} round-0 best responses of the ten-car workload at K={ks} (T={T}, 9 opponents, "
-                      f"N=2000 brute-force Frenet), {el:.1f} s on {cores} threads"}
+            "sample": f"{i} best responses of the ten-car workload at K={ks} (T={T}, 9 opponents, vehicles and "
+                      f"round tags 0..{L + 1} in turn, N=2000 brute-force Frenet), {el:.1f} s on {cores} threads"}
 
 
 def run_reference(args):
@@ -199,6 +217,10 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    peak, peak_form = R.measure_fma_peak()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     clocks = ClockSampler(local)
     n0 = _lib.lib().sgtp_launch_count()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -222,10 +244,11 @@ def run_ours(args):
     ms_per_step = total_ms / args.steps
     flops = R.flops_plan(N_V, K, T, L)
     achieved = flops / (statistics.mean(times) / 1e3) / 1e12
-    peak = R.fp32_peak_tflops()
-    # DRAM bytes per launch from the committed ncu summary, while it still
-    # describes the kernel that ran (same source digest)
-    rec = R.recorded_traffic(os.path.join(ROOT, "profiles", "plan_kernel_ten_car_full.md"))
+    # DRAM bytes per launch are not measurable inside this process: they are
+    # taken from the committed ncu summary of the same workload, and only
+    # while it describes the kernel that ran (same source digest)
+    prof = os.path.join(ROOT, "profiles", "plan_kernel_ten_car_full.md")
+    rec = R.recorded_traffic(prof)
     traffic = rec[0] if rec and rec[1] == R.kernel_source_digest() else None
 
     # ---- end to end through the public API with pinned host buffers
@@ -268,9 +291,14 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of "
+                                            "profiles/plan_kernel_ten_car_full.md (same source digest)")
+                         if traffic is not None else "no ncu summary of the current sources",
                          "kernel": "plan_kernel (persistent cooperative, 1 launch per plan)",
-                         "peak_basis": "148 SMs x 128 FP32 lanes x 2 x 2032 MHz (unit counts, max clock)",
-                         "flops_per_plan": flops},
+                         "peak_basis": f"measured in this run: sgtp_fma_probe ({peak_form}), best of 5 launches",
+                         "peak_nominal_max_clock": R.fp32_peak_tflops(),
+                         "flops_per_plan": flops, "flops_per_rollout_step": flops / steps_per_plan,
+                         "flop_count": "72 + 5 n_opp per rollout-step + 26 n_opp per candidate (roofline.py)"},
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = oracle_rate(args.cpu_seconds)

@@ -180,7 +180,12 @@ sgtp_status sgtp_best_response(const sgtp_track *trk, int32_t track_id, const sg
  *     race on it and give wrong results.  Issue them on one stream, or
  *     order them with events.
  *   - A problem whose workspace (sgtp_br_workspace_bytes) exceeds
- *     SGTP_NOALLOC_SCRATCH_BYTES is rejected with SGTP_E_INVALID. */
+ *     SGTP_NOALLOC_SCRATCH_BYTES is rejected with SGTP_E_INVALID (the
+ *     largest problem the ABI accepts fits, checked when the library is
+ *     compiled).
+ *   - The cached address lives as long as the process: after the device's
+ *     context is destroyed (cudaDeviceReset) it is stale, so do not call
+ *     this entry point on a device after resetting it. */
 sgtp_status sgtp_best_response_noalloc(const sgtp_track *trk, int32_t track_id, const sgtp_params *p,
                                        const float *x0, const float *u_nom, float vref_scale, const float *opp,
                                        int32_t n_opp, int32_t T, int32_t K, uint64_t seed, uint32_t race,
@@ -194,17 +199,23 @@ sgtp_status sgtp_best_response_noalloc(const sgtp_track *trk, int32_t track_id, 
 /* Launch shape of the persistent kernel.  Any zero field takes the
  * library's choice.  Every shape gives bit-identical results (each sample is
  * computed with the same code, and selection is an exact integer minimum).
- * Samples are processed in tiles of block x samples_per_thread consecutive k
- * (GA-IBR-MPPI: tiles of 256).  By default a plan whose Jacobi round fits in
- * one wave of 2 x 256 threads per SM runs one sample per thread with 128
- * registers; one that fits in one wave of two samples per thread on
- * 2 x 288 threads runs that; larger rounds run 3 x 256 threads per SM with
- * one sample per thread. */
+ * Two families of builds:
+ *   - 128-thread CTAs (3 per SM, 168 registers) rolling out one to three
+ *     samples per thread at once, interleaved; the count is
+ *     samples_per_thread, or, when 0, chosen per round as the fewest that
+ *     put the round's samples in one wave of the grid (at most 3);
+ *   - 256-thread CTAs with one sample per thread: 3 per SM with 80
+ *     registers, or (ctas_per_sm <= 2) 2 per SM with 128 registers.
+ * Samples are processed in tiles of block x samples_per_thread consecutive
+ * k (GA-IBR-MPPI: tiles of 256).  Defaults: a plain plan takes the
+ * 128-thread build unless its Jacobi round holds at most 256 x SMs samples
+ * (then 2 x 256 threads); a learned-proposal plan takes the 256-thread
+ * builds (2 per SM when its round has fewer 256-sample tiles than 3 x SMs);
+ * GA-IBR-MPPI takes the 256-thread builds only. */
 typedef struct sgtp_launch_opts {
-    int32_t block;                /* threads per CTA: 64, 128, 256 or 288 (288 only
-                                     with two samples per thread)                    */
-    int32_t samples_per_thread;   /* 0, 1 or 2: samples each thread rolls out at once
-                                     (2: interleaved, block 256 or 288)              */
+    int32_t block;                /* threads per CTA: 128 or 256 (0: default)        */
+    int32_t samples_per_thread;   /* 0 .. 3: samples each thread rolls out at once
+                                     (> 1 only with block 128 or 0)                  */
     int32_t ctas_per_sm;          /* resident CTAs per SM (capped at the occupancy
                                      limit; default the limit)                       */
     int32_t window;               /* track segments staged in shared memory per CTA
@@ -467,6 +478,39 @@ sgtp_status sgtp_graph_set_seed(sgtp_graph *g, uint64_t seed);
 /* Launch the graph on `stream` (results as from the captured call). */
 sgtp_status sgtp_graph_launch(sgtp_graph *g, void *stream);
 void sgtp_graph_destroy(sgtp_graph *g);
+
+/* ------------------------------------------------------------------ */
+/* Measurement and verification (no paper counterpart)                 */
+/* ------------------------------------------------------------------ */
+/* FP32 FMA throughput of the current device, the peak the best-response
+ * path's roofline is reported against: ctas_per_sm x SMs CTAs of 256
+ * threads, each thread running eight independent chains of `iters` x 8
+ * FMAs (packed != 0: the same count as fma.rn.f32x2 on four register
+ * pairs).  Enqueues one launch on `stream`; `sink` is a device float array
+ * of at least ctas_per_sm x SMs entries that is written only under a
+ * condition no chain meets.  *flops (host) receives the launch's FLOP count
+ * (2 per FMA); divide by its event-timed duration.  SGTP_E_INVALID for
+ * ctas_per_sm outside [1, 8] or iters outside [1, 2^24]. */
+sgtp_status sgtp_fma_probe(int32_t ctas_per_sm, int32_t iters, int32_t packed, float *sink, void *stream,
+                           double *flops);
+
+/* Raw Philox4x32-10 blocks of the noise (counter layout above), as the
+ * sample loop computes them: block i (0 <= i < n) of counter
+ * (k0 + i, c1, c2, c3) under key (seed lo32, seed hi32) into words[4 i ..
+ * 4 i + 3] (DEVICE, n x 4 uint32).  The device also evaluates each block
+ * with the key schedule computed round by round (the form the winner
+ * re-roll uses) and adds the count of blocks where the two differ to
+ * *mismatch (DEVICE int32, caller zeroes it).  One launch on `stream`. */
+sgtp_status sgtp_philox_words(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, int32_t n,
+                              uint32_t *words, int32_t *mismatch, void *stream);
+
+/* The standard normal pairs (z_a, z_delta) the sample loop draws for
+ * candidates k0 .. k0 + nk - 1 at steps 0 .. T-1 of best response (race,
+ * agent, round) on noise stream stream_bit (0 plain, 1 proposal), FP32
+ * Box-Muller on the words above: z[(i T + tau) 2 + {0, 1}] (DEVICE,
+ * nk x T x 2).  One launch on `stream`. */
+sgtp_status sgtp_noise_normals(uint64_t seed, uint32_t race, uint32_t agent, uint32_t round, uint32_t stream_bit,
+                               uint32_t k0, int32_t nk, int32_t T, float *z, void *stream);
 
 /* ------------------------------------------------------------------ */
 /* Misc                                                                 */

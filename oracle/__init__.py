@@ -121,6 +121,8 @@ def lib():
             C.c_int, C.c_uint64, C.c_uint32, C.c_double, C.c_double, dp, C.POINTER(C.c_int), dp, dp, C.c_int]
         L.orc_reference.argtypes = [C.POINTER(OrcParams), dp, dp, dp, C.c_int, dp, C.c_double, C.c_int, dp]
         L.orc_rollout.argtypes = [C.POINTER(OrcParams), dp, dp, C.c_int, dp]
+        L.orc_philox_batch.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int, C.c_uint32,
+                                       C.c_uint32, C.POINTER(C.c_uint32)]
         L.orc_std_normals_batch.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
                                             C.c_uint32, C.c_int, C.c_int, dp]
         _lib = L
@@ -176,6 +178,15 @@ def philox(ctr, key):
     o = (C.c_uint32 * 4)()
     lib().orc_philox4x32_10(c, k, o)
     return [int(x) for x in o]
+
+
+def philox_batch(c1, c2, c3, k0, n, seed):
+    """Philox4x32-10 blocks of counters (k0 + i, c1, c2, c3), i < n, key = seed
+    split into 32-bit halves: (n, 4) uint32."""
+    out = np.zeros((n, 4), dtype=np.uint32)
+    lib().orc_philox_batch(c1, c2, c3, k0, n, seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF,
+                           out.ctypes.data_as(C.POINTER(C.c_uint32)))
+    return out
 
 
 def std_normals(seed, race, agent, rnd, stream, k, tau):

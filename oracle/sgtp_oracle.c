@@ -932,3 +932,16 @@ void orc_std_normals_batch(uint64_t seed, uint32_t race, uint32_t agent, uint32_
             orc_std_normals(seed, race, agent, round, stream, k0 + (uint32_t)i, tau,
                             &out[((size_t)i * T + tau) * 2], &out[((size_t)i * T + tau) * 2 + 1]);
 }
+
+/* Raw Philox4x32-10 blocks of counters (k0 + i, c1, c2, c3), i = 0..n-1,
+ * under key (key lo, key hi): out[4 i .. 4 i + 3] (used by the parity tests
+ * of the device generator; the same function as orc_philox4x32_10). */
+void orc_philox_batch(uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, int n, uint32_t key_lo, uint32_t key_hi,
+                      uint32_t *out)
+{
+    const uint32_t key[2] = {key_lo, key_hi};
+    for (int i = 0; i < n; ++i) {
+        const uint32_t ctr[4] = {k0 + (uint32_t)i, c1, c2, c3};
+        orc_philox4x32_10(ctr, key, out + 4 * (size_t)i);
+    }
+}

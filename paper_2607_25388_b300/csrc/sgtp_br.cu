@@ -242,15 +242,14 @@ struct BRHeader {
 
 struct BRLayout {
     size_t ref, opp, osum, odbar, total;
-    BRLayout(int n_opp, int T)
+    static constexpr size_t up(size_t x) { return (x + 255) & ~(size_t)255; }
+    constexpr BRLayout(int n_opp, int T)
+        : ref(up(sizeof(BRHeader))),
+          opp(up(ref + sizeof(float4) * (T + 1))),
+          osum(up(opp + sizeof(float2) * (size_t)T * (n_opp > 0 ? n_opp : 1))),
+          odbar(up(osum + sizeof(float4) * (n_opp > 0 ? n_opp : 1))),
+          total(up(odbar + sizeof(float) * (n_opp > 0 ? n_opp : 1)))
     {
-        auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-        const int no = n_opp > 0 ? n_opp : 1;
-        ref = up(sizeof(BRHeader));
-        opp = up(ref + sizeof(float4) * (T + 1));
-        osum = up(opp + sizeof(float2) * (size_t)T * no);
-        odbar = up(osum + sizeof(float4) * no);
-        total = up(odbar + sizeof(float) * no);
     }
 };
 
@@ -708,6 +707,8 @@ extern "C" sgtp_status sgtp_best_response_mixed(const sgtp_track *trk, int32_t t
 // the call itself never allocates.  Its callers are control loops that must
 // not wait on an allocator and hosts without a device allocator.
 static __device__ __align__(256) unsigned char g_br_scratch[SGTP_NOALLOC_SCRATCH_BYTES];
+static_assert(BRLayout(SGTP_MAX_AGENTS - 1, SGTP_MAX_T).total <= SGTP_NOALLOC_SCRATCH_BYTES,
+              "the static scratch must hold the largest best response the ABI accepts");
 
 namespace {
 std::mutex g_scratch_mu;

@@ -1,32 +1,27 @@
 """Algorithmic work of the best-response path, counted from its definition.
 
-One rollout-step is one (candidate k, step tau) pair.  Its floating-point
-operations are counted from the method's definition (Sec. II sampling and
-dynamics, Eq. ctrack, Sec. III-B checks, Eq. Dmin), one per add, subtract,
-multiply, divide, min/max, compare, square root, logarithm or trigonometric
-function; an FMA counts as two.  The Frenet projection is counted as three
-point-to-segment evaluations (the nearest segment and the two neighbours that
-certify it as the local minimum) plus the signed offset and progress.
+One rollout-step is one (candidate k, step tau) pair.  The FP32 work of a
+step follows the method's definition (Sec. II sampling and dynamics,
+Eq. ctrack, Sec. III-B checks, Eq. Dmin) with the projection taken as the
+incremental nearest-segment search of about 2.5 segment evaluations per
+step: 72 FP32 operations for noise scaling, controls, control costs,
+dynamics, projection, tracking and boundary terms, plus 5 per opponent
+(two differences, the squared distance, its minimum).  The terminal game
+terms (Eqs. c_contest, c_long, c_block, c_safety) cost 25 FP32 operations
+and one square root per opponent and candidate.  An FMA counts as two
+operations.  The Philox integer work and the special-function evaluations
+(logarithm, square root, sine, cosine of the noise and the dynamics) are
+not counted as FP32 operations, so the fraction of the FP32 peak is a
+lower bound of the arithmetic the kernel issues.
 
-Per step (n = opponents):
-  noise        12   two uniforms (2 each), ln, x(-2), sqrt, 2*pi*u, cos, sin, 2 products
-  controls      8   two sigma*z, two additions to U-bar, two clips (min+max)
-  control cost  6   a^2, delta^2, two weights, two sums
-  smoothness    8   two differences, two squares, two weights... (tau >= 1)
-  dynamics     16   cos, sin, dt*v, two products, two sums, tan, product, /L, sum, dt*a, sum, clamp(2)
-  Frenet       61   3 x 16 per segment evaluation, sqrt, cross product (3), sign, s_j + t*len (2), unwrap (7)
-  tracking     17   four errors (heading wrap 4 extra), four squares, four weights, sums
-  boundary      8   two width interpolations (4), w+d, w-d, two minima
-  tail offset   0.3 one sum over the tail share (mu_tail = 0.3) of the steps
-  opponents    6n   per opponent: dx, dy, dx^2 + dy^2 (3), minimum
-Terminal work per candidate: 10 + 26 n (progress gap, indicators, alpha-
-weighted gain, blocking ratio, sqrt, safety square, sums, checks).
+Per rollout-step: 72 + 5 n_opp; per candidate: 26 n_opp.  Ten-car plan
+(n_opp = 9, T = 60): 117 + 234 / 60 = 120.9 per rollout-step.
 """
 from __future__ import annotations
 
-STEP_BASE = 12 + 8 + 6 + 8 + 16 + 61 + 17 + 8 + 0.3
-STEP_PER_OPP = 6.0
-TERM_BASE = 10.0
+STEP_BASE = 72.0
+STEP_PER_OPP = 5.0
+TERM_BASE = 0.0
 TERM_PER_OPP = 26.0
 
 SMS = 148
@@ -87,5 +82,39 @@ def recorded_traffic(profile_md: str):
 
 
 def fp32_peak_tflops(sm_mhz: float = MAX_SM_MHZ, sms: int = SMS) -> float:
-    """SMs x 128 FP32 lanes x 2 (FMA) x clock."""
+    """Nominal FP32 peak from unit counts: SMs x 128 FP32 lanes x 2 (FMA) x clock."""
     return sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def measure_fma_peak(reps: int = 5, iters: int = 20000):
+    """FP32 FMA throughput of the current device measured with the library's
+    own probe (sgtp_fma_probe: independent FMA chains, scalar and packed
+    f32x2, four 256-thread CTAs per SM), CUDA events on the launching
+    stream, best of `reps` launches of each form.  Returns (TFLOP/s, form)."""
+    import ctypes
+
+    import torch
+
+    from . import _lib
+    L = _lib.lib()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sink = torch.zeros(sms * 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    best = (0.0, "")
+    for packed in (0, 1):
+        for r in range(reps + 1):
+            fl = ctypes.c_double()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st = L.sgtp_fma_probe(4, iters, packed, ctypes.c_void_p(sink.data_ptr()),
+                                  ctypes.c_void_p(stream.cuda_stream), ctypes.byref(fl))
+            b.record(stream)
+            torch.cuda.synchronize()
+            if st != 0:
+                raise RuntimeError(f"sgtp_fma_probe failed: {L.sgtp_last_error().decode()}")
+            if r == 0:
+                continue                      # first launch warms the clocks
+            tf = fl.value / (a.elapsed_time(b) / 1e3) / 1e12
+            if tf > best[0]:
+                best = (tf, "fma.rn.f32x2" if packed else "fma.rn.f32")
+    return best
