@@ -27,3 +27,12 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+def pytest_terminal_summary(terminalreporter):
+    """Print the worst GPU-vs-oracle errors the parity checks measured."""
+    mod = sys.modules.get("tests.parity_util")
+    worst = getattr(mod, "WORST", None) if mod else None
+    if worst:
+        terminalreporter.write_line("parity worst errors: " +
+                                    ", ".join(f"{k} {v:.2e}" for k, v in sorted(worst.items())))

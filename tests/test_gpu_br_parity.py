@@ -62,9 +62,9 @@ def test_oval_single_response_all_candidates():
     p = S.params_fullscale()
     g, o, _ = run_both(sc.track, p, sc.X0[0], sc.U0[0], 1.0, sc.opp, sc.T, sc.K, rnd=1)
     assert_rel_close(g["states"], o["states"], STATE_RTOL, "states")
-    assert_frenet_close(g["frenet"], o["frenet"], o["states"])
+    assert_frenet_close(g["frenet"], o["frenet"], o["states"], sc.track.xr)
     assert_rel_close(g["controls"], o["controls"], STATE_RTOL, "controls")
-    nb = check_candidates(g, o, "oval", pos_scale=float(np.abs(sc.track.xr[:, :2]).max()))
+    nb = check_candidates(g, o, "oval")
     assert nb <= 0.01 * sc.K
     assert 0 < o["feasible"].sum() < sc.K        # the case exercises both branches
 
@@ -90,8 +90,8 @@ def test_fuzzed_small_problems(seed, n_opp, T, K):
     g, o, _ = run_both(td, p, x0, u_nom, float(np.float32(rng.uniform(0.8, 1.0))), opp, T, K, seed=seed,
                        agent=int(rng.integers(0, 9)), rnd=int(rng.integers(0, 6)), game_on=bool(seed % 2))
     assert_rel_close(g["states"], o["states"], STATE_RTOL, "states")
-    assert_frenet_close(g["frenet"], o["frenet"], o["states"])
-    check_candidates(g, o, f"fuzz{seed}", pos_scale=float(np.abs(td.xr[:, :2]).max()))
+    assert_frenet_close(g["frenet"], o["frenet"], o["states"], td.xr)
+    check_candidates(g, o, f"fuzz{seed}")
 
 
 def test_zero_noise_makes_every_sample_the_nominal():
@@ -164,7 +164,7 @@ def test_full_size_ten_car_response_on_sampled_candidates():
     kl = np.unique(np.concatenate([np.arange(0, 64), np.random.default_rng(0).integers(0, K, 128), [K - 1]]))
     g, o, _ = run_both(sc.track, p, sc.X0[0], sc.U0[0], 1.0, opp, T, K, k_list=kl, seed=11, agent=0, rnd=3)
     assert_rel_close(g["states"], o["states"], STATE_RTOL, "states")
-    check_candidates(g, o, "ten-car sample", pos_scale=float(np.abs(sc.track.xr[:, :2]).max()))
+    check_candidates(g, o, "ten-car sample")
 
 
 def test_vehicles_driving_against_the_track_direction():
@@ -185,5 +185,5 @@ def test_vehicles_driving_against_the_track_direction():
         opp.append(S.constant_velocity_prediction([ox, oy, op + np.pi, 50.0], T, p["dt"]))
     g, o, _ = run_both(td, p, x0, u_nom, 1.0, np.stack(opp), T, K, seed=11, rnd=2, game_on=True)
     assert_rel_close(g["states"], o["states"], STATE_RTOL, "states")
-    assert_frenet_close(g["frenet"], o["frenet"], o["states"])
-    check_candidates(g, o, "reversed", pos_scale=float(np.abs(td.xr[:, :2]).max()))
+    assert_frenet_close(g["frenet"], o["frenet"], o["states"], td.xr)
+    check_candidates(g, o, "reversed")
