@@ -380,6 +380,8 @@ __device__ bool br_stage(const BRArgs &a)
         const int j0 = h->j0;
         S.tv = a.tv;
         S.x0 = h->x0; S.s_t = h->s_t; S.d_t = h->d_t;
+        const float2 hs = heading_split(h->x0.z);
+        S.psi0 = hs.x; S.psi_off = hs.y;
         S.Wn = a.Wn;
         S.w0 = window_start(j0, a.back, a.tv.N);
         S.r0 = wrap_index(j0 - S.w0, a.tv.N);
@@ -504,12 +506,13 @@ __global__ void br_finalize_kernel(BRArgs a, int *k_star, float *u_star, float *
     __syncthreads();
     if (threadIdx.x == 0) {
         const float4 x0 = h->x0;
-        float x = x0.x, y = x0.y, psi = x0.z, v = x0.w;
+        const float2 hs = heading_split(x0.z);
+        float x = x0.x, y = x0.y, psi = hs.x, v = x0.w;
         ((float4 *)xi_star)[0] = x0;
         for (int tau = 0; tau < a.T; ++tau) {
             const float2 u = Tl::ctl()[tau];
             bicycle_step(a.p, x, y, psi, v, u.x, u.y);
-            ((float4 *)xi_star)[tau + 1] = make_float4(x, y, psi, v);
+            ((float4 *)xi_star)[tau + 1] = make_float4(x, y, psi + hs.y, v);
         }
     }
 }

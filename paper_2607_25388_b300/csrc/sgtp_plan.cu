@@ -787,6 +787,8 @@ __device__ __forceinline__ void plan_body(const PlanArgs &a)
                 if (threadIdx.x == 0) {
                     cta_key = ~0ull;
                     S.x0 = A.x0; S.s_t = A.s_t; S.d_t = A.d_t;
+                    const float2 hs = heading_split(A.x0.z);
+                    S.psi0 = hs.x; S.psi_off = hs.y;
                     S.pos0 = (float)S.r0 + A.t0;
                     S.ppred0 = S.pos0 + __fdiv_rn(__fmul_rn(a.p.dt, A.x0.w), __ldg(tv.B + A.j0).w) - 0.5f;
                     S.T = T; S.n_opp = n_opp; S.n_tail = R.n_tail;

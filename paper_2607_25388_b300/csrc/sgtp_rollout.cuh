@@ -28,6 +28,8 @@ struct BRScalars {
     TrackView tv;         // global track (out-of-window segments)
     float4 x0;
     float s_t, d_t;
+    float psi0, psi_off;  // x0's heading wrapped into (-pi, pi], and x0.z - psi0 (rollouts run from
+                          // psi0 and add psi_off back to every heading they output)
     float pos0;           // continuous segment position of x0 (window-local segment + parameter)
     float ppred0;         // first predicted position: pos0 + advance at v0 - 1/2
     int r0;               // window-local segment of x0
@@ -38,8 +40,18 @@ struct BRScalars {
     uint2 key;            // noise counter words
     unsigned ctr_agent_round, ctr_race, stream_bit;
     int K_prop;           // samples k < K_prop come from the proposal distribution
-    int pad[3];
+    int pad[1];
 };
+
+// A heading wrapped into (-pi, pi] and the offset that restores it: the
+// rollouts start from the wrapped heading, so that the sine and cosine
+// approximations of the dynamics stay in their accurate range without a
+// wrap at every step, and add the offset to every heading they output.
+__device__ __forceinline__ float2 heading_split(float psi)
+{
+    const float w = wrap_angle(psi);
+    return make_float2(w, psi - w);
+}
 
 // Shared-memory tile of one best response: fixed offsets for a given MAXO.
 // The track window holds the sample-loop projection records G0..G3 of
@@ -287,9 +299,25 @@ __device__ __forceinline__ float2 sample_control_d(const sgtp_params &p, float4 
 __device__ __forceinline__ unsigned stream_bit_of(unsigned k, int K_prop) { return k < (unsigned)K_prop ? 0x80000000u : 0u; }
 
 // One forward-Euler step of the kinematic bicycle (rear-axle reference,
-// steering input, speed clamp), every right-hand side at the old state.
+// steering input, speed clamp), every right-hand side at the old state.  The
+// heading is used as given (a rollout keeps it near (-pi, pi], see
+// heading_split); bicycle_step_wrap wraps it first.
 __device__ __forceinline__ void bicycle_step(const sgtp_params &p, float &x, float &y, float &psi, float &v, float a,
                                              float delta)
+{
+    const float sn = sin_ftz(psi), cs = cos_ftz(psi);
+    const float sd = sin_ftz(delta), cd = cos_ftz(delta);
+    const float dv = __fmul_rn(p.dt, v);
+    const float x1 = __fmaf_rn(dv, cs, x);
+    const float y1 = __fmaf_rn(dv, sn, y);
+    const float psi1 = psi + __fmul_rn(__fmul_rn(dv, sd), rcp_ftz(__fmul_rn(cd, p.wheelbase)));
+    const float v1 = fminf(fmaxf(__fmaf_rn(p.dt, a, v), p.v_min), p.v_max);
+    x = x1; y = y1; psi = psi1; v = v1;
+}
+
+// bicycle_step for a heading of any size (the closed-loop plant).
+__device__ __forceinline__ void bicycle_step_wrap(const sgtp_params &p, float &x, float &y, float &psi, float &v,
+                                                  float a, float delta)
 {
     const float pw = wrap_angle(psi);
     const float sn = sin_ftz(pw), cs = cos_ftz(pw);
@@ -309,8 +337,7 @@ __device__ __forceinline__ void bicycle_step(const sgtp_params &p, float &x, flo
 __device__ __forceinline__ void bicycle_step_pre(const sgtp_params &p, float &x, float &y, float &psi, float &v, float a,
                                                  float2 steer)
 {
-    const float pw = wrap_angle(psi);
-    const float sn = sin_ftz(pw), cs = cos_ftz(pw);
+    const float sn = sin_ftz(psi), cs = cos_ftz(psi);
     const float dv = __fmul_rn(p.dt, v);
     const float x1 = __fmaf_rn(dv, cs, x);
     const float y1 = __fmaf_rn(dv, sn, y);
@@ -356,7 +383,7 @@ struct SampleState {
 template <int MAXO>
 __device__ __forceinline__ void sample_init(SampleState<MAXO> &St, const BRScalars &S)
 {
-    St.x = S.x0.x; St.y = S.x0.y; St.psi = S.x0.z; St.v = S.x0.w;
+    St.x = S.x0.x; St.y = S.x0.y; St.psi = S.psi0; St.v = S.x0.w;
     St.a_prev = 0.f; St.d_prev = 0.f;
     St.s = S.s_t;
     St.pos = S.pos0; St.ppred = S.ppred0;
@@ -466,8 +493,8 @@ __device__ __forceinline__ void sample_steps(SampleState<MAXO> (&St)[NI], const 
         step_opponents<0, MAXO / 2, true, MAXO>(St[i].g2, St[i].x, St[i].y, T::opp() + tau * BRTile<MAXO>::NP);
         if (OUT) {
             if (st_out) {
-                st_out[4 * st + 0] = St[i].x; st_out[4 * st + 1] = St[i].y; st_out[4 * st + 2] = St[i].psi;
-                st_out[4 * st + 3] = St[i].v;
+                st_out[4 * st + 0] = St[i].x; st_out[4 * st + 1] = St[i].y;
+                st_out[4 * st + 2] = St[i].psi + S.psi_off; st_out[4 * st + 3] = St[i].v;
             }
             if (fr_out) { fr_out[2 * st] = St[i].s; fr_out[2 * st + 1] = f.d; }
         }
@@ -542,7 +569,7 @@ __device__ __forceinline__ void run_candidates(const BRScalars &S, const sgtp_pa
         dist[i] = T::dist() + (prop ? SGTP_MAX_T : 0);
     }
     if (OUT) {
-        if (st_out) { st_out[0] = St[0].x; st_out[1] = St[0].y; st_out[2] = St[0].psi; st_out[3] = St[0].v; }
+        if (st_out) { st_out[0] = S.x0.x; st_out[1] = S.x0.y; st_out[2] = S.x0.z; st_out[3] = S.x0.w; }
         if (fr_out) { fr_out[0] = S.s_t; fr_out[1] = S.d_t; }
     }
     const int Tn = S.T, tail0 = S.T - S.n_tail, wlim = S.Wn - 2;
@@ -623,12 +650,13 @@ __device__ void roll_cooperative(const sgtp_params &p, float4 x0, float s_t, int
         for (int q = threadIdx.x; q < T; q += 32) steer[q] = steer_terms(p, Tl::ctl()[q].y);
         __syncwarp();
         if (threadIdx.x == 0) {
-            float x = x0.x, y = x0.y, psi = x0.z, v = x0.w;
+            const float2 h = heading_split(x0.z);
+            float x = x0.x, y = x0.y, psi = h.x, v = x0.w;
             st[0] = x0;
 #pragma unroll 4
             for (int tau = 0; tau < T; ++tau) {
                 bicycle_step_pre(p, x, y, psi, v, Tl::ctl()[tau].x, steer[tau]);
-                st[tau + 1] = make_float4(x, y, psi, v);
+                st[tau + 1] = make_float4(x, y, psi + h.y, v);
             }
         }
     }

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(256) sim_step_kernel(SimArgs a)
                 S->u_prev[0] = u.x;
                 S->u_prev[1] = u.y;
             }
-            bicycle_step(a.p, x.x, x.y, x.z, x.w, u.x, u.y);
+            bicycle_step_wrap(a.p, x.x, x.y, x.z, x.w, u.x, u.y);
             xs[tid] = x;
             if (tid == ego) S->ego_speed_sum += x.w;
         }
