@@ -14,8 +14,11 @@
  * BF16 weights and activations, FP32 accumulation on the tensor cores, FP32
  * master weights for Adam.  Output row: [mu_a(T), mu_delta(T), logsig_a(T),
  * logsig_delta(T)] in units of the plain sampler's sigma per channel;
- * logsig is clamped to [-5, 2].  Parameters are laid out per layer l as
- * W_l [out][in] (row-major) followed by b_l [out].
+ * logsig is clamped to [-5, 2].  The proposal is a residual around the
+ * plain sampler's centre: per step, mean = U-bar + sigma_plain mu and
+ * sigma = sigma_plain exp(logsig), so mu = 0, logsig = 0 is the plain
+ * sampler.  Parameters are laid out per layer l as W_l [out][in]
+ * (row-major) followed by b_l [out].
  *
  * Features of vehicle i (all float32, computed on the device by the plan
  * kernel; sgtp_ibr_plan_learned can write them out):
@@ -63,15 +66,19 @@ sgtp_status sgtp_mlp_reserve(sgtp_mlp *m, int32_t batch);
 sgtp_status sgtp_mlp_forward(sgtp_mlp *m, const float *x, int32_t batch, float *out, void *stream);
 
 /* Forward pass followed by the proposal transform: prop [batch x T x 4]
- * DEVICE floats, per step (sigma_a mu_a, sigma_delta mu_delta,
- * sigma_a exp(logsig_a), sigma_delta exp(logsig_delta)), logsig clamped to
- * [-5, 2] -- the input of sgtp_best_response_mixed. */
-sgtp_status sgtp_mlp_proposal(sgtp_mlp *m, const float *x, int32_t batch, float sigma_a, float sigma_delta,
-                              float *prop, void *stream);
+ * DEVICE floats, per step (a_nom + sigma_a mu_a, delta_nom + sigma_delta
+ * mu_delta, sigma_a exp(logsig_a), sigma_delta exp(logsig_delta)), logsig
+ * clamped to [-5, 2] -- the input of sgtp_best_response_mixed.  u_nom
+ * [batch x T x 2] DEVICE: each row's nominal controls U-bar (NULL: zero). */
+sgtp_status sgtp_mlp_proposal(sgtp_mlp *m, const float *x, const float *u_nom, int32_t batch, float sigma_a,
+                              float sigma_delta, float *prop, void *stream);
 
 /* One training step on a DEVICE batch: forward, Gaussian NLL of target
- * [batch x 2T] = (U*_a / sigma_a, U*_delta / sigma_delta) per step, mean over
- * batch x 2T elements; backward; and, when apply != 0, one Adam step
+ * [batch x 2T] per step, mean over
+ * batch x 2T elements (the learned proposal trains on the residuals
+ * ((U*_a - a_nom) / sigma_a, (U*_delta - delta_nom) / sigma_delta) of the
+ * selected controls U* around the nominal); backward; and, when apply != 0,
+ * one Adam step
  * (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on the FP32 master
  * weights with a refreshed BF16 copy.  Optional DEVICE outputs: loss_out [1]
  * and grad_out [param_count] (the gradient before the update). */

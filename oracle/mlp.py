@@ -9,8 +9,9 @@ Output row: [mu_a (T), mu_delta (T), logsig_a (T), logsig_delta (T)], in
 units of the plain sampler's sigma per channel.  Parameters are one flat
 vector, per layer W [out][in] (row-major) followed by b [out].
 
-Loss: Gaussian negative log-likelihood of the target (the selected controls
-U* divided by sigma_a, sigma_delta) under N(mu, diag exp(2 logsig)), logsig
+Loss: Gaussian negative log-likelihood of the target (the residual of the
+selected controls U* around the nominal controls U-bar, divided by sigma_a,
+sigma_delta) under N(mu, diag exp(2 logsig)), logsig
 clamped to [-5, 2], constant term dropped, mean over batch x 2T elements.
 
 With ``bf16=True`` the arithmetic is FP64 on BF16-rounded tensors, rounded
@@ -136,12 +137,15 @@ def adam(w, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
     return w - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
-def proposal(out_row, T, sigma_a, sigma_delta):
+def proposal(out_row, T, sigma_a, sigma_delta, u_nom=None):
     """Per-step Gaussian (T x 4: mean a, mean delta, sigma a, sigma delta) of
-    one output row: means scale by the plain sigmas, sigmas are the plain
-    sigmas times exp(logsig) with logsig clamped to [-5, 2]."""
+    one output row around the nominal controls u_nom (T x 2; None: zero):
+    mean = u_nom + plain sigma x mu (a residual around the plain sampler's
+    centre), sigma = plain sigma x exp(logsig) with logsig clamped to
+    [-5, 2]."""
     o = np.asarray(out_row, dtype=np.float64)
+    un = np.zeros((T, 2)) if u_nom is None else np.asarray(u_nom, dtype=np.float64).reshape(T, 2)
     la = np.clip(o[2 * T:3 * T], -5.0, 2.0)
     ld = np.clip(o[3 * T:4 * T], -5.0, 2.0)
-    return np.stack([sigma_a * o[:T], sigma_delta * o[T:2 * T], sigma_a * np.exp(la), sigma_delta * np.exp(ld)],
-                    axis=1)
+    return np.stack([un[:, 0] + sigma_a * o[:T], un[:, 1] + sigma_delta * o[T:2 * T], sigma_a * np.exp(la),
+                     sigma_delta * np.exp(ld)], axis=1)

@@ -152,7 +152,7 @@ def lib():
             L.sgtp_mlp_destroy.restype = None
             L.sgtp_mlp_reserve.argtypes = [vp, i32]
             L.sgtp_mlp_forward.argtypes = [vp, vp, i32, vp, vp]
-            L.sgtp_mlp_proposal.argtypes = [vp, vp, i32, f32, f32, vp, vp]
+            L.sgtp_mlp_proposal.argtypes = [vp, vp, vp, i32, f32, f32, vp, vp]
             L.sgtp_mlp_train_step.argtypes = [vp, vp, vp, i32, f32, vp, vp, i32, vp]
             L.sgtp_mlp_get_params.argtypes = [vp, vp]
             L.sgtp_mlp_set_params.argtypes = [vp, vp]

@@ -262,14 +262,19 @@ __global__ void init_kernel(float *w, bf16 *wb, long long off, int out, int in, 
 
 // Per-step Gaussian of each output row: (sigma_a mu_a, sigma_delta mu_delta,
 // sigma_a exp(ls_a), sigma_delta exp(ls_delta)), ls clamped to [-5, 2].
-__global__ void proposal_kernel(const float *out, int Bsz, int T, float sa, float sd, float4 *prop)
+// Per-step Gaussian of each row: mean = nominal + sigma_plain mu (a residual
+// around the plain sampler's centre; nominal 0 when u_nom is NULL), sigma =
+// sigma_plain exp(clamp(logsig, -5, 2)).
+__global__ void proposal_kernel(const float *out, const float *u_nom, int Bsz, int T, float sa, float sd,
+                                float4 *prop)
 {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Bsz * T; e += gridDim.x * blockDim.x) {
         const int b = e / T, t = e - b * T;
         const float *o = out + (size_t)b * 4 * T;
         const float la = fminf(fmaxf(o[2 * T + t], -5.f), 2.f);
         const float ld = fminf(fmaxf(o[3 * T + t], -5.f), 2.f);
-        prop[e] = make_float4(sa * o[t], sd * o[T + t], sa * expf(la), sd * expf(ld));
+        const float na = u_nom ? u_nom[2 * (size_t)e] : 0.f, nd = u_nom ? u_nom[2 * (size_t)e + 1] : 0.f;
+        prop[e] = make_float4(__fmaf_rn(sa, o[t], na), __fmaf_rn(sd, o[T + t], nd), sa * expf(la), sd * expf(ld));
     }
 }
 
@@ -401,8 +406,8 @@ extern "C" sgtp_status sgtp_mlp_forward(sgtp_mlp *M, const float *x, int32_t bat
     return SGTP_OK;
 }
 
-extern "C" sgtp_status sgtp_mlp_proposal(sgtp_mlp *M, const float *x, int32_t batch, float sigma_a,
-                                         float sigma_delta, float *prop, void *stream)
+extern "C" sgtp_status sgtp_mlp_proposal(sgtp_mlp *M, const float *x, const float *u_nom, int32_t batch,
+                                         float sigma_a, float sigma_delta, float *prop, void *stream)
 {
     SGTP_CHECK(M && x && prop, "NULL argument");
     SGTP_CHECK(sigma_a > 0.f && sigma_delta > 0.f, "sigmas must be positive");
@@ -411,7 +416,8 @@ extern "C" sgtp_status sgtp_mlp_proposal(sgtp_mlp *M, const float *x, int32_t ba
     cudaStream_t s = (cudaStream_t)stream;
     forward_impl(M, x, batch, s);
     const int n = batch * M->T;
-    proposal_kernel<<<(n + 255) / 256, 256, 0, s>>>(M->outf, batch, M->T, sigma_a, sigma_delta, (float4 *)prop);
+    proposal_kernel<<<(n + 255) / 256, 256, 0, s>>>(M->outf, u_nom, batch, M->T, sigma_a, sigma_delta,
+                                                    (float4 *)prop);
     count_launch();
     SGTP_CUDA(cudaGetLastError());
     return SGTP_OK;

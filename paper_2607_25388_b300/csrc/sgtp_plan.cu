@@ -420,8 +420,9 @@ __device__ void mlp_layer(const __nv_bfloat16 *act, const uint2 *frag, const flo
 }
 
 // Proposal of vehicle i for its next best response: features, network, and
-// the per-step Gaussian (mean = sigma_plain * mu, sigma = sigma_plain *
-// exp(clamp(logsig, -5, 2))).  All threads of the CTA; shared scratch at buf.
+// the per-step Gaussian (mean = U-bar + sigma_plain * mu, a residual around
+// the plain sampler's centre, sigma = sigma_plain * exp(clamp(logsig, -5,
+// 2))).  All threads of the CTA; shared scratch at buf.
 __device__ void proposal_for(const PlanArgs &a, const RaceDev &R, int i, int bin, bool game_on, int round,
                              unsigned char *buf)
 {
@@ -453,11 +454,13 @@ __device__ void proposal_for(const PlanArgs &a, const RaceDev &R, int i, int bin
         const __nv_bfloat16 *t = cur; cur = nxt; nxt = (__nv_bfloat16 *)t;
     }
     float4 *dst = a.prop + (size_t)ag * a.maxT;
+    const float *U = a.U_io + R.u_off + (size_t)i * T * 2;
     for (int q = threadIdx.x; q < T; q += blockDim.x) {
         const float la = fminf(fmaxf(y[2 * T + q], -5.f), 2.f);
         const float ld = fminf(fmaxf(y[3 * T + q], -5.f), 2.f);
-        const float4 d = make_float4(a.p.sigma_a * y[q], a.p.sigma_delta * y[T + q], a.p.sigma_a * expf(la),
-                                     a.p.sigma_delta * expf(ld));
+        const float4 d = make_float4(__fmaf_rn(a.p.sigma_a, y[q], __ldcg(U + 2 * q)),
+                                     __fmaf_rn(a.p.sigma_delta, y[T + q], __ldcg(U + 2 * q + 1)),
+                                     a.p.sigma_a * expf(la), a.p.sigma_delta * expf(ld));
         dst[q] = d;
         if (a.prop_out) a.prop_out[((size_t)round * a.n_agents + ag) * a.maxT + q] = d;
     }

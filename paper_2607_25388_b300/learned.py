@@ -54,11 +54,16 @@ class Mlp:
         check(lib().sgtp_mlp_forward(self._h, x.data_ptr(), B, out.data_ptr(), stream_ptr(stream)), "sgtp_mlp_forward")
         return out
 
-    def proposal(self, x: torch.Tensor, sigma_a: float, sigma_delta: float, stream=None) -> torch.Tensor:
+    def proposal(self, x: torch.Tensor, sigma_a: float, sigma_delta: float, u_nom=None, stream=None) -> torch.Tensor:
+        """Per-step Gaussians (B, T, 4) around the rows' nominal controls
+        u_nom (B, T, 2) (None: zero)."""
         B = x.shape[0]
         prop = torch.empty((B, self.T, 4), dtype=torch.float32, device=x.device)
-        check(lib().sgtp_mlp_proposal(self._h, x.data_ptr(), B, float(sigma_a), float(sigma_delta), prop.data_ptr(),
-                                      stream_ptr(stream)), "sgtp_mlp_proposal")
+        if u_nom is not None:
+            assert u_nom.shape == (B, self.T, 2) and u_nom.is_contiguous() and u_nom.dtype == torch.float32
+        check(lib().sgtp_mlp_proposal(self._h, x.data_ptr(), None if u_nom is None else u_nom.data_ptr(), B,
+                                      float(sigma_a), float(sigma_delta), prop.data_ptr(), stream_ptr(stream)),
+              "sgtp_mlp_proposal")
         return prop
 
     def train_step(self, x, target, lr=1e-3, apply=True, want_grad=False, loss_out=None, stream=None):
@@ -136,17 +141,28 @@ class Race:
         self.U = U.contiguous()
 
 
-def _targets(u: torch.Tensor, params) -> torch.Tensor:
-    """(n, T, 2) controls -> (n, 2T) targets [a / sigma_a, delta / sigma_delta]."""
+def _targets(u: torch.Tensor, u_nom: torch.Tensor, params) -> torch.Tensor:
+    """(n, T, 2) selected controls and the nominal controls they were sampled
+    around -> (n, 2T) targets, the residuals in units of the plain sigmas:
+    [(a - a_nom) / sigma_a, (delta - delta_nom) / sigma_delta]."""
     sa, sd = float(np.float32(params["sigma_a"])), float(np.float32(params["sigma_delta"]))
-    return torch.cat([u[..., 0] / sa, u[..., 1] / sd], dim=-1)
+    r = u - u_nom
+    return torch.cat([r[..., 0] / sa, r[..., 1] / sd], dim=-1)
+
+
+def nominal_controls(u_start: torch.Tensor, u_hist: torch.Tensor, L: int) -> torch.Tensor:
+    """The nominal controls of every best response of a plan, (L+2, n_v, T, 2):
+    round 0 starts from the warm start, round r from round r-1's selection,
+    and the extra ego response from round L's."""
+    return torch.cat([u_start[None], u_hist[:L + 1]], dim=0)
 
 
 def generate_dataset(seeds, plans_per_race: int, advance: int = 10, K=16384, T=60, L=5, params=None, seed0=0,
                      device="cuda", log=None):
     """(features [N, 64], targets [N, 2T]) from plain plans of ten-car races:
     every best response of every plan contributes its features and the
-    controls it selected ((L+1) n_v + 1 per plan)."""
+    residual of the controls it selected around its nominal controls
+    ((L+1) n_v + 1 per plan)."""
     params = params or S.params_fullscale()
     xs, ys = [], []
     t0 = time.time()
@@ -154,13 +170,15 @@ def generate_dataset(seeds, plans_per_race: int, advance: int = 10, K=16384, T=6
         race = Race(S.ten_car_race(int(seed), K=K, T=T, L=L), device)
         ego = race.sc.ego
         for q in range(plans_per_race):
+            u_start = race.U.clone()
             out = ibr_plan(race.track, params, race.X, race.U, race.vs, T, K, L, ego=ego,
                            seed=seed0 + 7919 * int(seed) + q, want_hist=True, want_features=True)
             f, uh = out["features"], out["u_hist"]
+            un = nominal_controls(u_start, uh, L)
             xs.append(f[:L + 1].reshape(-1, IN))
-            ys.append(_targets(uh[:L + 1].reshape(-1, T, 2), params))
+            ys.append(_targets(uh[:L + 1].reshape(-1, T, 2), un[:L + 1].reshape(-1, T, 2), params))
             xs.append(f[L + 1, ego:ego + 1])
-            ys.append(_targets(uh[L + 1, ego:ego + 1], params))
+            ys.append(_targets(uh[L + 1, ego:ego + 1], un[L + 1, ego:ego + 1], params))
             race.advance(out["xi"], advance)
         if log and (n + 1) % 10 == 0:
             log(f"dataset: {n + 1}/{len(seeds)} races, {sum(x.shape[0] for x in xs)} examples, "
@@ -245,7 +263,8 @@ def compare(mlp: Mlp, seeds, states_per_race: int, advance=10, K=16384, K_eq=409
             xh, uh, feat, ks = out["xi_hist"], out["u_hist"], out["features"], out["k_star"].cpu().numpy()
             jobs = [(r, i) for r in range(1, L + 2) for i in range(n_v) if r <= L or i == ego]
             F = torch.stack([feat[r, i] for r, i in jobs]).contiguous()
-            P = mlp.proposal(F, sa, sd)
+            UN = torch.stack([uh[r - 1, i] for r, i in jobs]).contiguous()
+            P = mlp.proposal(F, sa, sd, UN)
             for n, (r, i) in enumerate(jobs):
                 others = [j for j in range(n_v) if j != i]
                 opp = xh[r - 1, others].contiguous()

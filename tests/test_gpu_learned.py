@@ -128,10 +128,14 @@ def test_proposal_matches_oracle(net):
     x = feature_batch(33, 9)
     p = S.params_fullscale()
     sa, sd = float(np.float32(p["sigma_a"])), float(np.float32(p["sigma_delta"]))
-    g = net.proposal(dev(x), sa, sd).cpu().numpy()
+    un = np.float32(np.random.default_rng(34).normal(0.0, [1.0, 0.05], (33, 60, 2)))
+    g = net.proposal(dev(x), sa, sd, dev(un)).cpu().numpy()
     out = OM.forward(net.get_params().astype(np.float64), x, OM.dims_for(60))[0]
-    o = np.stack([OM.proposal(r, 60, sa, sd) for r in out])
+    o = np.stack([OM.proposal(r, 60, sa, sd, u) for r, u in zip(out, un)])
     assert frob(g, o) <= NET_RTOL
+    # without nominal controls the means are sigma x mu alone
+    g0 = net.proposal(dev(x), sa, sd).cpu().numpy()
+    assert frob(g0, np.stack([OM.proposal(r, 60, sa, sd) for r in out])) <= NET_RTOL
 
 
 def test_save_load_round_trip(tmp_path, net):
@@ -283,11 +287,11 @@ def test_learned_plan_teacher_forced(net, case):
             _check_features(sc, p, g, Lr, i, rnd, prev_xi)
             # the in-kernel network on the kernel's own features
             out = OM.forward(w, g["features"][rnd, i][None], OM.dims_for(T))[0][0]
-            po = OM.proposal(out, T, sa, sd)
+            u_nom = sc.U0[i] if rnd == 0 else g["u_hist"][rnd - 1][i]
+            po = OM.proposal(out, T, sa, sd, u_nom)
             pg = g["prop"][rnd, i]
             assert frob(pg, po) <= NET_RTOL, f"proposal r{rnd} a{i}"
             # the response itself, teacher-forced on the kernel's proposal
-            u_nom = sc.U0[i] if rnd == 0 else g["u_hist"][rnd - 1][i]
             opp = np.stack([prev_xi[j] for j in range(n_v) if j != i]) if n_v > 1 else None
             slot = (Lr + 1) * n_v if rnd == Lr + 1 else rnd * n_v + i
             kg = int(g["k_star"][slot])

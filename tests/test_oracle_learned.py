@@ -116,6 +116,12 @@ def test_proposal_units():
     P = OM.proposal(row, T, 1.0, 0.05)
     assert np.allclose(P[:, 0], 2.0) and np.allclose(P[:, 1], -0.05)
     assert np.allclose(P[:, 2], 1.0) and np.allclose(P[:, 3], 0.05 * math.exp(-5.0))
+    # a residual around the nominal controls: mu = 0, logsig = 0 is the plain sampler N(U-bar, sigma^2)
+    un = np.stack([np.linspace(-1, 1, T), np.linspace(0.1, -0.1, T)], axis=1)
+    P = OM.proposal(np.zeros(4 * T), T, 1.0, 0.05, un)
+    assert np.allclose(P[:, :2], un) and np.allclose(P[:, 2], 1.0) and np.allclose(P[:, 3], 0.05)
+    P = OM.proposal(row, T, 1.0, 0.05, un)
+    assert np.allclose(P[:, 0], un[:, 0] + 2.0) and np.allclose(P[:, 1], un[:, 1] - 0.05)
 
 
 # ------------------------------------------------------------------ features
