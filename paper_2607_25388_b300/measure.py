@@ -11,14 +11,20 @@
    2048 proposal + 2048 plain samples (network weights do not change the work);
 5b. the same three samplers with 32 ten-car races per launch (per-plan time when the GPU is full);
 6. the GA-IBR-MPPI ablation (path-integral update, lambda = 1e4) of the ten-car plan next to SGTP at the
-   same K, direct launch.
+   same K, direct launch;
+oracle: the FP64 CPU oracle on the host's cores for configurations 1 (in full), 2 and 3 (plans at
+   reduced K, scaled linearly in K, and one full-K ten-car response for the record) and 4 (a subset of
+   the races at reduced K), with the core count and CPU model.
 
-Times are CUDA-event medians over `reps` calls after warm-up, inputs resident on the device.
+Times are CUDA-event medians over `reps` calls after warm-up, inputs resident on the device.  FP32
+fractions are against the FMA peak measured in the same run (roofline.measure_fma_peak).
 """
 from __future__ import annotations
 
 import argparse
 import json
+import os
+import time
 
 import numpy as np
 import torch
@@ -48,8 +54,19 @@ def _median_ms(fn, reps, warmup=5):
     return float(np.median(_times_ms(fn, reps, warmup)))
 
 
+_PEAK = {}
+
+
+def _peak():
+    if "tf" not in _PEAK:
+        _PEAK["tf"], _PEAK["form"] = R.measure_fma_peak()
+        print(json.dumps(dict(config="measured FP32 FMA peak", tflops=_PEAK["tf"], form=_PEAK["form"],
+                              nominal_max_clock=R.fp32_peak_tflops())), flush=True)
+    return _PEAK["tf"]
+
+
 def _line(config, ms, steps, flops, **extra):
-    peak = R.fp32_peak_tflops()
+    peak = _peak()
     d = dict(config=config, ms=ms, rollout_steps=steps, rollout_steps_per_s=steps / (ms / 1e3),
              tflops=flops / (ms / 1e3) / 1e12, fp32_frac=flops / (ms / 1e3) / 1e12 / peak)
     d.update(extra)
@@ -219,13 +236,75 @@ def config6(reps, lam=1.0e4):
     return res
 
 
+def _cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def _oracle_line(config, seconds, steps, **extra):
+    d = dict(config=config, oracle_s=seconds, rollout_steps=steps, oracle_rollout_steps_per_s=steps / seconds,
+             cores=os.cpu_count(), cpu=_cpu_model())
+    d.update(extra)
+    print(json.dumps(d), flush=True)
+    return d
+
+
+def oracle(reps):
+    """The FP64 oracle's rate on this host (all cores; the oracle's own
+    thread pool over samples)."""
+    import oracle as O
+    p = S.params_fullscale()
+    # 1: the oval best response in full
+    sc = S.single_br_oval()
+    ot = O.Track(sc.track.xr, sc.track.wl, sc.track.wr)
+    t0 = time.perf_counter()
+    O.best_response(p, ot, sc.X0[0], sc.U0[0], 1.0, sc.opp, sc.T, sc.K, seed=1, rnd=1)
+    _oracle_line("oracle 1: oval single best response, K=1024, T=40 (in full)", time.perf_counter() - t0,
+                 sc.K * sc.T)
+    # 2 and 3: whole plans at reduced K, scaled linearly to the configuration's K
+    for name, sc, k_red in (("2: two-car plan, K=8192, T=50, L=3", S.two_car_race(100), 1024),
+                            ("3: ten-car plan, K=16384, T=60, L=5", S.ten_car_race(200), 256)):
+        ot = O.Track(sc.track.xr, sc.track.wl, sc.track.wr)
+        n_v = sc.X0.shape[0]
+        t0 = time.perf_counter()
+        O.ibr_plan(p, ot, sc.X0, sc.U0, sc.vref_scale, sc.T, k_red, sc.L, sc.ego, seed=3)
+        dt = time.perf_counter() - t0
+        steps = R.rollout_steps_plan(n_v, k_red, sc.T, sc.L)
+        _oracle_line(f"oracle {name} at K={k_red}", dt, steps,
+                     plan_s_scaled_to_full_K=dt * sc.K / k_red)
+    # 3: one full-K ten-car response for the record (round 1 against the nominal predictions)
+    sc = S.ten_car_race(200)
+    ot = O.Track(sc.track.xr, sc.track.wl, sc.track.wr)
+    lo = np.float32([p["a_min"], -p["delta_max"]]); hi = np.float32([p["a_max"], p["delta_max"]])
+    nominal = np.stack([O.rollout(p, sc.X0[i], np.clip(sc.U0[i], lo, hi), sc.T) for i in range(10)])
+    t0 = time.perf_counter()
+    O.best_response(p, ot, sc.X0[0], sc.U0[0], sc.vref_scale[0], nominal[1:], sc.T, sc.K, seed=3, rnd=1)
+    _oracle_line("oracle 3: one ten-car best response, K=16384, T=60, 9 opponents (in full)",
+                 time.perf_counter() - t0, sc.K * sc.T)
+    # 4: a subset of the 256 batched races at reduced K
+    races = S.batched_races()[:4]
+    k_red = 256
+    t0 = time.perf_counter()
+    steps = 0
+    for r, sc in enumerate(races):
+        ot = O.Track(sc.track.xr, sc.track.wl, sc.track.wr)
+        O.ibr_plan(p, ot, sc.X0, sc.U0, sc.vref_scale, sc.T, k_red, sc.L, sc.ego, seed=5, race=r)
+        steps += R.rollout_steps_plan(sc.X0.shape[0], k_red, sc.T, sc.L)
+    _oracle_line(f"oracle 4: races 0-3 of the 256-race batch at K={k_red}", time.perf_counter() - t0, steps)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--reps", type=int, default=50)
-    ap.add_argument("--configs", type=str, default="1,2,3,4,5,5b,6")
+    ap.add_argument("--configs", type=str, default="1,2,3,4,5,5b,6,oracle")
     args = ap.parse_args(argv)
     fns = {"1": config1, "2": config2, "3": config3, "4": config4, "5": config5, "5b": config5_batched,
-           "6": config6}
+           "6": config6, "oracle": oracle}
     for c in args.configs.split(","):
         fns[c.strip()](args.reps)
 
