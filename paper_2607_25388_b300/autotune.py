@@ -9,9 +9,12 @@ across shapes; the tuner checks that on every candidate and refuses a shape
 that differs.
 
 Results are cached in a JSON file keyed by (horizon bucket, opponent bucket,
-K, L, SM count, device name); ``lookup`` returns the cached shape for a
-planning problem, ``tune`` measures and stores it.  The cache path is
-``$SGTP_AUTOTUNE_CACHE`` or ``~/.cache/sgtp/autotune.json``.
+K, L, SM count, device name) for single races and by (races, vehicles,
+longest horizon, largest race, K, L, SM count, device name) for batches;
+``lookup`` / ``lookup_batch`` return the cached shape (``ibr_plan`` and
+``Batch.plan`` use them with ``opts="auto"``), ``tune`` / ``tune_batch``
+measure and store it.  The cache path is ``$SGTP_AUTOTUNE_CACHE`` or
+``~/.cache/sgtp/autotune.json``; it is read once per path and process.
 """
 from __future__ import annotations
 
@@ -56,21 +59,45 @@ def key(n_v: int, T: int, K: int, L: int, info=None) -> str:
     return f"T{_t_bucket(T)}-o{_o_bucket(n_v - 1)}-K{K}-L{L}-sm{sms}-{name}"
 
 
-def _load(path):
+_CACHE = {}
+
+
+def _load(path, fresh=False):
+    if not fresh and path in _CACHE:
+        return _CACHE[path]
     try:
         with open(path) as f:
-            return json.load(f)
+            d = json.load(f)
     except (OSError, ValueError):
-        return {}
+        d = {}
+    _CACHE[path] = d
+    return d
 
 
 def lookup(n_v: int, T: int, K: int, L: int, path: str | None = None, info=None):
     """Cached launch options for this problem shape, or None."""
-    ent = _load(path or cache_path()).get(key(n_v, T, K, L, info))
+    return _opts(_load(path or cache_path()).get(key(n_v, T, K, L, info)))
+
+
+def _opts(ent):
     if not ent:
         return None
     return launch_opts(block=ent["block"], samples_per_thread=ent.get("samples_per_thread", 0),
                        ctas_per_sm=ent["ctas_per_sm"])
+
+
+def key_batch(batch, info=None) -> str:
+    """Cache key of a batch of races: its size and shape extremes."""
+    sms, name = info if info is not None else device_info()
+    T_max = max(int(r["T"]) for r in batch.races)
+    nv_max = max(int(r["n_v"]) for r in batch.races)
+    return (f"batch{len(batch.races)}-a{batch.agents}-T{_t_bucket(T_max)}-o{_o_bucket(nv_max - 1)}-K{batch.K}"
+            f"-L{batch.L}-sm{sms}-{name}")
+
+
+def lookup_batch(batch, path: str | None = None, info=None):
+    """Cached launch options for this batch's shape, or None."""
+    return _opts(_load(path or cache_path()).get(key_batch(batch, info)))
 
 
 def _time_plan(trk, params, sc, K, L, opts, reps, warmup):
@@ -103,14 +130,19 @@ def _time_plan(trk, params, sc, K, L, opts, reps, warmup):
 
 def store(n_v: int, T: int, K: int, L: int, entry: dict, path: str | None = None, info=None):
     """Write one cache entry (atomic replace of the JSON file)."""
+    _store(key(n_v, T, K, L, info), entry, path)
+
+
+def _store(k: str, entry: dict, path: str | None = None):
     p = path or cache_path()
-    os.makedirs(os.path.dirname(p), exist_ok=True)
-    cache = _load(p)
-    cache[key(n_v, T, K, L, info)] = entry
+    os.makedirs(os.path.dirname(p) or ".", exist_ok=True)
+    cache = dict(_load(p, fresh=True))
+    cache[k] = entry
     tmp = p + f".tmp{os.getpid()}"
     with open(tmp, "w") as f:
         json.dump(cache, f, indent=1, sort_keys=True)
     os.replace(tmp, p)
+    _CACHE[p] = cache
 
 
 def tune(n_v: int, T: int, K: int, L: int, params=None, reps=10, warmup=3, track_seed=777, path: str | None = None,
@@ -137,4 +169,53 @@ def tune(n_v: int, T: int, K: int, L: int, params=None, reps=10, warmup=3, track
     best["default_ms"] = base_ms
     best["tuned_at"] = time.strftime("%Y-%m-%dT%H:%M:%S")
     store(n_v, T, K, L, best, path)
+    return best
+
+
+def _time_batch(batch, params, X0, U0, vs, opts, reps, warmup):
+    U = U0.clone()
+    out = None
+    for w in range(warmup):
+        U.copy_(U0)
+        out = batch.plan(params, X0, U, vs, seed=w, opts=opts, out=out)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    ts = []
+    for r in range(reps):
+        U.copy_(U0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        batch.plan(params, X0, U, vs, seed=r, opts=opts, out=out)
+        b.record(s)
+        ts.append((a, b))
+    torch.cuda.synchronize()
+    U.copy_(U0)
+    res = batch.plan(params, X0, U, vs, seed=12345, opts=opts, want_hist=True)
+    torch.cuda.synchronize()
+    digest = tuple(v.cpu().numpy().tobytes() for k, v in sorted(res.items()) if k != "status") + (
+        U.cpu().numpy().tobytes(),)
+    return float(np.median([a.elapsed_time(b) for a, b in ts])), digest
+
+
+def tune_batch(batch, params, X0, U0, vs, reps=5, warmup=2, path: str | None = None, log=None):
+    """Time every candidate shape on this batch's own inputs (device tensors;
+    U0 is not modified), check bit-identical plans, store and return the
+    fastest as a dict {block, samples_per_thread, ctas_per_sm, ms,
+    default_ms}."""
+    base_ms, base_digest = _time_batch(batch, params, X0, U0, vs, launch_opts(), reps, warmup)
+    best = dict(block=0, samples_per_thread=0, ctas_per_sm=0, ms=base_ms)
+    for block, spt in SHAPES:
+        for ctas in CTAS:
+            opts = launch_opts(block=block, samples_per_thread=spt, ctas_per_sm=ctas)
+            ms, digest = _time_batch(batch, params, X0, U0, vs, opts, reps, warmup)
+            if digest != base_digest:
+                raise RuntimeError(f"launch shape block={block} samples/thread={spt} ctas_per_sm={ctas} changed "
+                                   "the batch's plans")
+            if log:
+                log(f"batch block {block:3d} samples/thread {spt} ctas/SM {ctas}: {ms:.4f} ms")
+            if ms < best["ms"]:
+                best = dict(block=block, samples_per_thread=spt, ctas_per_sm=ctas, ms=ms)
+    best["default_ms"] = base_ms
+    best["tuned_at"] = time.strftime("%Y-%m-%dT%H:%M:%S")
+    _store(key_batch(batch), best, path)
     return best

@@ -427,12 +427,18 @@ class Batch:
 
     def plan(self, params, X0, U_io, vref_scale, seed=0, want_hist=False, opts=None, workspace=None, out=None,
              stream=None, mlp=None, K_prop=0, mppi_lambda=None, pred_sigma=None):
-        """Plan every race in one launch; with ``mlp`` (a learned.Mlp) K_prop
+        """Plan every race in one launch (``opts="auto"``: the autotuner's
+        cached shape for this batch, if any); with ``mlp`` (a learned.Mlp) K_prop
         samples of every best response come from the network's proposal; with
         ``mppi_lambda`` every race runs the GA-IBR-MPPI ablation; with
         ``pred_sigma = (sigma_lon, sigma_lat)`` the opponent predictions are
         perturbed (sgtp_batch_plan_perturbed)."""
         dev = X0.device
+        if isinstance(opts, str):
+            if opts != "auto":
+                raise ValueError("opts must be launch options, None or 'auto'")
+            from . import autotune
+            opts = autotune.lookup_batch(self)
         _dev(X0, "X0", shape=(self.agents, 4))
         _dev(U_io, "U_io", shape=(self.u_elems,))
         _dev(vref_scale, "vref_scale", shape=(self.agents,))

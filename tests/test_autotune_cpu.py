@@ -21,3 +21,24 @@ def test_cache_round_trip(tmp_path):
     assert (o.block, o.samples_per_thread, o.ctas_per_sm) == (128, 2, 3)
     A.store(2, 30, 4096, 3, dict(block=256, samples_per_thread=1, ctas_per_sm=0, ms=0.1), path, info)
     assert A.lookup(10, 60, 16384, 5, path, info).block == 128
+
+
+class _FakeBatch:
+    def __init__(self, races, K=4096, L=3):
+        self.races = races
+        self.agents = sum(r["n_v"] for r in races)
+        self.K, self.L = K, L
+
+
+def test_batch_keys_and_round_trip(tmp_path):
+    info = (148, "B300")
+    a = _FakeBatch([dict(n_v=2, T=30), dict(n_v=10, T=80)])
+    b = _FakeBatch([dict(n_v=2, T=31), dict(n_v=10, T=79)])
+    c = _FakeBatch([dict(n_v=3, T=30), dict(n_v=10, T=80)])
+    assert A.key_batch(a, info) == A.key_batch(b, info)      # same size, vehicles and extremes
+    assert A.key_batch(a, info) != A.key_batch(c, info)      # one more vehicle
+    path = str(tmp_path / "tune.json")
+    assert A.lookup_batch(a, path, info) is None
+    A._store(A.key_batch(a, info), dict(block=128, samples_per_thread=3, ctas_per_sm=0, ms=1.0), path)
+    o = A.lookup_batch(b, path, info)
+    assert (o.block, o.samples_per_thread, o.ctas_per_sm) == (128, 3, 0)

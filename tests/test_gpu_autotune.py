@@ -29,3 +29,31 @@ def test_tune_store_lookup_and_invariance(tmp_path):
         res.append((out["xi"].cpu().numpy(), out["k_star"].cpu().numpy()))
     np.testing.assert_array_equal(res[0][0], res[1][0])
     np.testing.assert_array_equal(res[0][1], res[1][1])
+
+
+def test_tune_batch_and_auto_shape_plan_identically(tmp_path):
+    from paper_2607_25388_b300 import autotune as A, planner as P
+    p = S.params_fullscale()
+    races = S.batched_races(n_races=6, K=512, L=1, seed0=4000, n_points=600)
+    trk = P.Track.from_many([sc.track for sc in races])
+    b = P.Batch(trk, [dict(track_id=r, n_v=sc.X0.shape[0], T=sc.T, ego=sc.ego, race_tag=r)
+                      for r, sc in enumerate(races)], K=512, L=1)
+    X0 = torch.as_tensor(np.concatenate([sc.X0 for sc in races])).cuda()
+    U0 = torch.as_tensor(np.concatenate([sc.U0.reshape(-1) for sc in races])).cuda()
+    vs = torch.as_tensor(np.concatenate([sc.vref_scale for sc in races])).cuda()
+    path = str(tmp_path / "tune.json")
+    best = A.tune_batch(b, p, X0, U0, vs, reps=1, warmup=1, path=path)
+    assert best["ms"] > 0 and A.lookup_batch(b, path) is not None
+    import os
+    os.environ["SGTP_AUTOTUNE_CACHE"] = path
+    try:
+        res = []
+        for opts in (None, "auto"):
+            U = U0.clone()
+            out = b.plan(p, X0, U, vs, seed=3, opts=opts)
+            torch.cuda.synchronize()
+            res.append((out["xi"].cpu().numpy(), out["k_star"].cpu().numpy(), U.cpu().numpy()))
+    finally:
+        del os.environ["SGTP_AUTOTUNE_CACHE"]
+    for x, y in zip(*res):
+        np.testing.assert_array_equal(x, y)
