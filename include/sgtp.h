@@ -203,7 +203,9 @@ sgtp_status sgtp_best_response_noalloc(const sgtp_track *trk, int32_t track_id, 
  *   - 128-thread CTAs (3 per SM, 168 registers) rolling out one to three
  *     samples per thread at once, interleaved; the count is
  *     samples_per_thread, or, when 0, chosen per round as the fewest that
- *     put the round's samples in one wave of the grid (at most 3);
+ *     put the round's samples in one wave of the grid (at most 3) -- for a
+ *     round of several waves even at 3, 2 or 3, whichever pads K less to
+ *     whole tiles;
  *   - 256-thread CTAs with one sample per thread: 3 per SM with 80
  *     registers, or (ctas_per_sm <= 2) 2 per SM with 128 registers.
  * Samples are processed in tiles of block x samples_per_thread consecutive
@@ -222,15 +224,35 @@ typedef struct sgtp_launch_opts {
                                      (rounded to a multiple of 4, at most 512)       */
     int64_t wait_timeout_ns;      /* limit of each device-side wait (default 1 s)    */
     int32_t debug_flags;          /* SGTP_DEBUG_*; 0 in production                   */
+    int32_t schedule;             /* SGTP_SCHEDULE_*; 0: default                     */
     int64_t *trace_ns;            /* optional DEVICE buffer of 3*L+8 int64: %globaltimer
                                      stamps by CTA 0 at the start, after setup, and after
-                                     each round's proposal, sample and winner phases      */
+                                     each round's proposal, sample and winner phases (under
+                                     the queue schedule: when CTA 0 leaves each phase)    */
 } sgtp_launch_opts;
+
+/* How the rounds of a planning call are scheduled on the persistent grid.
+ * LOCKSTEP: every CTA takes a fixed share of each round's sample tiles, then
+ * of its winners, with a grid barrier after each phase (every race of a
+ * batch waits for the slowest).  QUEUE: after the setup, CTAs claim work
+ * items from one device queue (samples of round 0, winners of round 0,
+ * samples of round 1, ...); a sample tile waits (bounded by wait_timeout_ns)
+ * until its race's previous round is complete, a winner until its vehicle's
+ * tiles are in, so each race advances at its own pace.  Both give the same
+ * plans bit for bit.  DEFAULT: QUEUE for batches, LOCKSTEP for single races
+ * and for every call with the learned proposal (which takes LOCKSTEP only). */
+#define SGTP_SCHEDULE_DEFAULT 0
+#define SGTP_SCHEDULE_LOCKSTEP 1
+#define SGTP_SCHEDULE_QUEUE 2
 
 /* Fault injection for tests: CTA 0 never arrives at the grid barrier, so
  * every other CTA's wait runs out and the call reports SGTP_E_TIMEOUT in
  * status_dev.  No wait in the library is unbounded. */
 #define SGTP_DEBUG_SKIP_BARRIER_ARRIVAL 1
+/* Fault injection for tests, queue schedule: no winner item reports its
+ * completion, so the next round's sample tiles wait until their limit and
+ * the call reports SGTP_E_TIMEOUT. */
+#define SGTP_DEBUG_SKIP_WINNER_SIGNAL 2
 
 /* Description of one race of a batch (HOST array given to
  * sgtp_batch_create).  Arrays of a batch concatenate the races' agents:

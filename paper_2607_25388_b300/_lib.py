@@ -20,6 +20,7 @@ PARAM_FIELDS = [
 MAX_AGENTS = 16
 MAX_T = 128
 DEBUG_SKIP_BARRIER_ARRIVAL = 1
+DEBUG_SKIP_WINNER_SIGNAL = 2
 
 STATUS = {0: "SGTP_OK", 1: "SGTP_E_INVALID", 2: "SGTP_E_CUDA", 3: "SGTP_E_NOMEM", 4: "SGTP_E_TIMEOUT",
           5: "SGTP_E_DEVICE", 6: "SGTP_E_UNSUPPORTED"}
@@ -40,7 +41,7 @@ class Params(C.Structure):
 class LaunchOpts(C.Structure):
     _fields_ = [("block", C.c_int32), ("samples_per_thread", C.c_int32), ("ctas_per_sm", C.c_int32),
                 ("window", C.c_int32), ("wait_timeout_ns", C.c_int64), ("debug_flags", C.c_int32),
-                ("trace_ns", C.c_void_p)]
+                ("schedule", C.c_int32), ("trace_ns", C.c_void_p)]
 
 
 class Race(C.Structure):

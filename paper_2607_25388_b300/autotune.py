@@ -2,11 +2,16 @@
 
 The search space is the launch shape of ``sgtp_launch_opts``: the build
 (128-thread CTAs with one to three samples per thread at once, or the
-256-thread builds with one), samples per thread (0 = chosen per round) and
-resident CTAs per SM.  Every shape computes each sample with the same code
-and selects by an exact integer minimum, so the plan must be bit-identical
-across shapes; the tuner checks that on every candidate and refuses a shape
-that differs.
+256-thread builds with one), samples per thread (0 = chosen per round),
+resident CTAs per SM and the schedule (lock-step rounds or per-race
+progression from the device queue).  Block and samples per thread fix the
+tile, block x samples per thread consecutive samples, and with it the
+number of CTA work items per best response, ceil(K / tile); the entries
+record it.  Every shape computes each sample with the same code and selects
+by an exact integer minimum, so the plan must be bit-identical across
+shapes; the tuner checks that on every candidate and refuses a shape that
+differs.  (There is no 512-thread build: its one CTA per SM would hold the
+registers of three 128-thread CTAs with less latency hiding per thread.)
 
 Results are cached in a JSON file keyed by (horizon bucket, opponent bucket,
 K, L, SM count, device name) for single races and by (races, vehicles,
@@ -26,12 +31,13 @@ import numpy as np
 import torch
 
 from . import scenario as S
-from .planner import Track, ibr_plan, launch_opts
+from .planner import SCHEDULE_LOCKSTEP, SCHEDULE_QUEUE, Track, ibr_plan, launch_opts
 
 # (block, samples per thread): the 128-thread build with 0 (per round), 1, 2
 # or 3 samples per thread, the 256-thread builds with one
 SHAPES = ((128, 0), (128, 1), (128, 2), (128, 3), (256, 1))
 CTAS = (0, 1, 2, 3)              # 0 = the occupancy limit; larger values are capped by the library
+SCHEDULES = (SCHEDULE_LOCKSTEP, SCHEDULE_QUEUE)
 
 
 def cache_path() -> str:
@@ -83,7 +89,22 @@ def _opts(ent):
     if not ent:
         return None
     return launch_opts(block=ent["block"], samples_per_thread=ent.get("samples_per_thread", 0),
-                       ctas_per_sm=ent["ctas_per_sm"])
+                       ctas_per_sm=ent["ctas_per_sm"], schedule=ent.get("schedule", 0))
+
+
+def _tiles(K: int, block: int, spt: int):
+    """Work items (tiles) per best response of a fixed shape (None when the
+    library chooses samples per thread per round)."""
+    if block == 0 or (block == 128 and spt == 0):
+        return None
+    return -(-K // (block * max(spt, 1)))
+
+
+def _candidates():
+    for block, spt in SHAPES:
+        for ctas in CTAS:
+            for sched in SCHEDULES:
+                yield block, spt, ctas, sched
 
 
 def key_batch(batch, info=None) -> str:
@@ -149,23 +170,24 @@ def tune(n_v: int, T: int, K: int, L: int, params=None, reps=10, warmup=3, track
          log=None):
     """Time every candidate shape on a synthetic race of this shape (seeded
     Fourier track, two-wide grid), check bit-identical plans, store and
-    return the fastest as a dict {block, ctas_per_sm, ms, default_ms}."""
+    return the fastest as a dict {block, samples_per_thread, ctas_per_sm,
+    schedule, tiles_per_response, ms, default_ms}."""
     params = params or S.params_fullscale()
     sc = S.grid_race(S.fourier_track(track_seed), n_v, T, K, L, track_seed + 1)
     trk = Track.from_data(sc.track)
     base_ms, base_digest = _time_plan(trk, params, sc, K, L, launch_opts(), reps, warmup)
-    best = dict(block=0, samples_per_thread=0, ctas_per_sm=0, ms=base_ms)
-    for block, spt in SHAPES:
-        for ctas in CTAS:
-            opts = launch_opts(block=block, samples_per_thread=spt, ctas_per_sm=ctas)
-            ms, digest = _time_plan(trk, params, sc, K, L, opts, reps, warmup)
-            if digest != base_digest:
-                raise RuntimeError(f"launch shape block={block} samples/thread={spt} ctas_per_sm={ctas} changed "
-                                   "the plan")
-            if log:
-                log(f"block {block:3d} samples/thread {spt} ctas/SM {ctas}: {ms:.4f} ms")
-            if ms < best["ms"]:
-                best = dict(block=block, samples_per_thread=spt, ctas_per_sm=ctas, ms=ms)
+    best = dict(block=0, samples_per_thread=0, ctas_per_sm=0, schedule=0, ms=base_ms)
+    for block, spt, ctas, sched in _candidates():
+        opts = launch_opts(block=block, samples_per_thread=spt, ctas_per_sm=ctas, schedule=sched)
+        ms, digest = _time_plan(trk, params, sc, K, L, opts, reps, warmup)
+        if digest != base_digest:
+            raise RuntimeError(f"launch shape block={block} samples/thread={spt} ctas_per_sm={ctas} "
+                               f"schedule={sched} changed the plan")
+        if log:
+            log(f"block {block:3d} samples/thread {spt} ctas/SM {ctas} schedule {sched}: {ms:.4f} ms")
+        if ms < best["ms"]:
+            best = dict(block=block, samples_per_thread=spt, ctas_per_sm=ctas, schedule=sched, ms=ms)
+    best["tiles_per_response"] = _tiles(K, best["block"], best["samples_per_thread"])
     best["default_ms"] = base_ms
     best["tuned_at"] = time.strftime("%Y-%m-%dT%H:%M:%S")
     store(n_v, T, K, L, best, path)
@@ -200,21 +222,21 @@ def _time_batch(batch, params, X0, U0, vs, opts, reps, warmup):
 def tune_batch(batch, params, X0, U0, vs, reps=5, warmup=2, path: str | None = None, log=None):
     """Time every candidate shape on this batch's own inputs (device tensors;
     U0 is not modified), check bit-identical plans, store and return the
-    fastest as a dict {block, samples_per_thread, ctas_per_sm, ms,
-    default_ms}."""
+    fastest as a dict {block, samples_per_thread, ctas_per_sm, schedule,
+    tiles_per_response, ms, default_ms}."""
     base_ms, base_digest = _time_batch(batch, params, X0, U0, vs, launch_opts(), reps, warmup)
-    best = dict(block=0, samples_per_thread=0, ctas_per_sm=0, ms=base_ms)
-    for block, spt in SHAPES:
-        for ctas in CTAS:
-            opts = launch_opts(block=block, samples_per_thread=spt, ctas_per_sm=ctas)
-            ms, digest = _time_batch(batch, params, X0, U0, vs, opts, reps, warmup)
-            if digest != base_digest:
-                raise RuntimeError(f"launch shape block={block} samples/thread={spt} ctas_per_sm={ctas} changed "
-                                   "the batch's plans")
-            if log:
-                log(f"batch block {block:3d} samples/thread {spt} ctas/SM {ctas}: {ms:.4f} ms")
-            if ms < best["ms"]:
-                best = dict(block=block, samples_per_thread=spt, ctas_per_sm=ctas, ms=ms)
+    best = dict(block=0, samples_per_thread=0, ctas_per_sm=0, schedule=0, ms=base_ms)
+    for block, spt, ctas, sched in _candidates():
+        opts = launch_opts(block=block, samples_per_thread=spt, ctas_per_sm=ctas, schedule=sched)
+        ms, digest = _time_batch(batch, params, X0, U0, vs, opts, reps, warmup)
+        if digest != base_digest:
+            raise RuntimeError(f"launch shape block={block} samples/thread={spt} ctas_per_sm={ctas} "
+                               f"schedule={sched} changed the batch's plans")
+        if log:
+            log(f"batch block {block:3d} samples/thread {spt} ctas/SM {ctas} schedule {sched}: {ms:.4f} ms")
+        if ms < best["ms"]:
+            best = dict(block=block, samples_per_thread=spt, ctas_per_sm=ctas, schedule=sched, ms=ms)
+    best["tiles_per_response"] = _tiles(batch.K, best["block"], best["samples_per_thread"])
     best["default_ms"] = base_ms
     best["tuned_at"] = time.strftime("%Y-%m-%dT%H:%M:%S")
     _store(key_batch(batch), best, path)

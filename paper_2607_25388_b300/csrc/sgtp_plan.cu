@@ -90,6 +90,14 @@ struct PlanArgs {
     // perturbed opponent predictions (sig_lon or sig_lat > 0)
     float sig_lon, sig_lat;
     float2 *ptan[2];               // per vehicle: T+1 unit directions of the predictions' nearest segments
+    // per-race round progression (queue != 0): after the setup, work items
+    // are claimed from one queue in the order samples of round 0, winners of
+    // round 0, samples of round 1, ...; a race moves to its next round as
+    // soon as its own winners are in, never waiting for another race
+    int queue;
+    unsigned long long *qhead;     // next queue position to claim
+    unsigned *wdone;               // per race: winner items completed
+    unsigned *tdone;               // per vehicle: sample tiles completed (all rounds)
 };
 
 __device__ __forceinline__ void stamp(const PlanArgs &a, int i)
@@ -177,6 +185,60 @@ __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v)
     unsigned old;
     asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
     return old;
+}
+
+__device__ __forceinline__ void red_add_release(unsigned *p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Waits (thread 0, bounded by the launch's timeout) until the counter *p has
+// reached `target`; every thread returns false when the wait ran out
+// (SGTP_E_TIMEOUT recorded) or another CTA recorded a fatal status.  What the
+// counter's producers wrote before their release is visible to the whole CTA
+// afterwards (thread 0's acquire, then the CTA barrier).
+__device__ bool wait_count(const PlanArgs &a, const unsigned *p, unsigned target)
+{
+    __shared__ int wc_sh;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        if ((int)(ld_acquire(p) - target) < 0) {
+            const unsigned long long t0 = global_ns();
+            while ((int)(ld_acquire(p) - target) < 0) {
+                if (ld_status(a.status) & 0xff) { ok = 0; break; }
+                if (global_ns() - t0 > (unsigned long long)a.timeout_ns) {
+                    atomicOr(a.status, SGTP_E_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        wc_sh = ok;
+    }
+    __syncthreads();
+    return wc_sh != 0;
+}
+
+// Marks one item done: the CTA's writes for it, then a release increment.
+__device__ __forceinline__ void signal_done(unsigned *p)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        red_add_release(p, 1u);
+    }
+}
+
+// Claims the next queue position for this CTA into q_sh (all threads; the
+// position is CTA-uniform, so it lives in shared memory, not in registers
+// across the sample loop).
+__device__ __forceinline__ void claim_item(const PlanArgs &a, unsigned long long &q_sh)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) q_sh = atomicAdd(a.qhead, 1ull);
+    __syncthreads();
 }
 
 __shared__ unsigned g_bar_epoch;      // barriers this CTA has entered (thread 0's count)
@@ -731,9 +793,21 @@ __device__ __forceinline__ void plan_body(const PlanArgs &a)
         const int n_keys = last.ks_off + (a.L + 1) * last.n_v + 1;
         for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_keys; q += gridDim.x * blockDim.x)
             a.keys[q] = ~0ull;
+        if (a.queue) {
+            const int n_cnt = a.n_races + a.n_agents;
+            for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_cnt; q += gridDim.x * blockDim.x)
+                a.wdone[q] = 0u;      // wdone and tdone are contiguous
+            if (blockIdx.x == 0 && threadIdx.x == 0) *a.qhead = 0ull;
+        }
     }
     ok = grid_barrier(a, skip);
     stamp(a, 1);
+    // queue schedule: q_sh is this CTA's claimed position; round k's sample
+    // items start at k (items[0] + n_agents), its winner items items[kind]
+    // later (one per vehicle)
+    const bool queue = a.queue != 0;
+    __shared__ unsigned long long q_sh;
+    if (ok && queue) claim_item(a, q_sh);
 
     for (int round = 0; ok && round <= a.L + 1; ++round) {
         const bool extra = round == a.L + 1;
@@ -751,10 +825,13 @@ __device__ __forceinline__ void plan_body(const PlanArgs &a)
             if (!grid_barrier(a, skip)) break;
         }
         stamp(a, 2 + 3 * round);
-        // this CTA's share of the round: equal item counts for one race, equal
-        // work (items weighted by their race's horizon) for a batch
-        int i0, i1;
-        if (!a.races) {
+        // lock step: this CTA's share of the round, equal item counts for one
+        // race, equal work (items weighted by their race's horizon) for a
+        // batch; queue: the positions base .. base + items - 1 as claimed
+        int i0 = 0, i1 = 0;
+        const unsigned long long base = (unsigned long long)round * (unsigned long long)(a.items[0] + a.n_agents);
+        if (queue) {
+        } else if (!a.races) {
             const int n_items = a.items[extra];
             i0 = (int)((long long)n_items * blockIdx.x / gridDim.x);
             i1 = (int)((long long)n_items * (blockIdx.x + 1) / gridDim.x);
@@ -765,7 +842,13 @@ __device__ __forceinline__ void plan_body(const PlanArgs &a)
         }
         int cur = -1;                 // vehicle (global index) staged
         unsigned long long *cur_slot = nullptr;
-        for (int item = i0; item < i1; ++item) {
+        for (int item = i0;; ++item) {
+            if (queue) {
+                if (q_sh >= base + (unsigned long long)a.items[extra]) break;
+                item = (int)(q_sh - base);
+            } else if (item >= i1) {
+                break;
+            }
             // item = vehicle (all vehicles of all races in a Jacobi round, the
             // races' egos in the extra round) x tile of that vehicle's samples
             int ri, i;
@@ -779,10 +862,17 @@ __device__ __forceinline__ void plan_body(const PlanArgs &a)
             }
             const RaceDev R = get_race(a, ri);
             const int ag = R.agent_off + i;
+            // queue: the race's previous round must be complete (its n_v
+            // winners per round)
+            if (queue && round > 0 && !wait_count(a, a.wdone + ri, (unsigned)(round * R.n_v))) {
+                ok = false;
+                break;
+            }
             if (ag != cur) {
-                // flush the previous vehicle's key, then stage this one
+                // flush the previous vehicle's key (lock step; the queue
+                // flushes after every item), then stage this one
                 __syncthreads();
-                if (threadIdx.x == 0 && cur_slot) atomicMin(cur_slot, cta_key);
+                if (threadIdx.x == 0 && cur_slot && !queue) atomicMin(cur_slot, cta_key);
                 const TrackView tv = get_track(a, R.track_id);
                 const AgentDev A = load_agent(a.agents + ag);
                 const int T = R.T, n_opp = R.n_v - 1;
@@ -876,15 +966,30 @@ __device__ __forceinline__ void plan_body(const PlanArgs &a)
             best = warp_min_u64(best);
             if (lane == 0) atomicMin(&cta_key, best);
             if constexpr (MPPI) mppi_tile<MAXO>(a, t, ag, R.T);
+            if (queue) {
+                __syncthreads();
+                if (threadIdx.x == 0) atomicMin(cur_slot, cta_key);
+                signal_done(a.tdone + ag);
+                claim_item(a, q_sh);
+            }
         }
         if (!ok) break;
-        __syncthreads();
-        if (threadIdx.x == 0 && cur_slot) atomicMin(cur_slot, cta_key);
-        if (!grid_barrier(a, skip)) break;
+        if (!queue) {
+            __syncthreads();
+            if (threadIdx.x == 0 && cur_slot) atomicMin(cur_slot, cta_key);
+            if (!grid_barrier(a, skip)) break;
+        }
         stamp(a, 3 + 3 * round);
 
         // -------------------------------------------------------- winners (one CTA per vehicle)
-        for (int ag = blockIdx.x; ag < a.n_agents; ag += gridDim.x) {
+        const unsigned long long wbase = base + (unsigned long long)a.items[extra];
+        for (int ag = blockIdx.x;; ag += gridDim.x) {
+            if (queue) {
+                if (q_sh >= wbase + (unsigned long long)a.n_agents) break;
+                ag = (int)(q_sh - wbase);
+            } else if (ag >= a.n_agents) {
+                break;
+            }
             const AgentDev A = load_agent(a.agents + ag);
             const RaceDev R = get_race(a, A.race);
             const int i = ag - R.agent_off;
@@ -893,6 +998,17 @@ __device__ __forceinline__ void plan_body(const PlanArgs &a)
             const size_t xo = (size_t)R.xi_off + (size_t)i * (T + 1) * 4;
             const size_t uo = (size_t)R.u_off + (size_t)i * T * 2;
             __syncthreads();
+            if (queue) {
+                // an active winner needs all of its vehicle's tiles so far;
+                // the extra round's copies need the race's round-L winners
+                const unsigned need = !extra ? (unsigned)((round + 1) * a.tiles[0])
+                                     : active ? (unsigned)((a.L + 1) * a.tiles[0] + a.tiles[1])
+                                              : (unsigned)(round * R.n_v);
+                if (!wait_count(a, active ? a.tdone + ag : a.wdone + A.race, need)) {
+                    ok = false;
+                    break;
+                }
+            }
             if (!active) {
                 if (a.xi_hist)
                     for (int q = threadIdx.x; q < (T + 1) * 4; q += blockDim.x)
@@ -900,6 +1016,11 @@ __device__ __forceinline__ void plan_body(const PlanArgs &a)
                 if (a.u_hist)
                     for (int q = threadIdx.x; q < T * 2; q += blockDim.x)
                         a.u_hist[(size_t)round * a.u_total + uo + q] = __ldcg(a.U_io + uo + q);
+                if (queue) {
+                    // (fault injection for tests: the winners never report)
+                    if (!(a.debug_flags & SGTP_DEBUG_SKIP_WINNER_SIGNAL)) signal_done(a.wdone + A.race);
+                    claim_item(a, q_sh);
+                }
                 continue;
             }
             const int slot = extra ? (a.L + 1) * R.n_v : round * R.n_v + i;
@@ -941,8 +1062,14 @@ __device__ __forceinline__ void plan_body(const PlanArgs &a)
                                    extra ? nullptr : a.pos[bout] + R.pos_off + (size_t)i * (T + 1), xi_final, xi_h,
                                    extra ? nullptr : a.summ[bout] + ag, flag,
                                    (extra || !a.ptan[bout]) ? nullptr : a.ptan[bout] + R.pos_off + (size_t)i * (T + 1));
+            if (queue) {
+                // (fault injection for tests: the winners never report)
+                if (!(a.debug_flags & SGTP_DEBUG_SKIP_WINNER_SIGNAL)) signal_done(a.wdone + A.race);
+                claim_item(a, q_sh);
+            }
         }
-        if (round <= a.L) ok = grid_barrier(a, skip);
+        if (!ok) break;
+        if (!queue && round <= a.L) ok = grid_barrier(a, skip);
         stamp(a, 4 + 3 * round);
     }
     if (flag) atomicOr(a.status, SGTP_E_DEVICE << 8);
@@ -950,9 +1077,10 @@ __device__ __forceinline__ void plan_body(const PlanArgs &a)
 
 // ================================================================ host side
 struct Layout {
-    size_t bar, keys, agents, ref, pos0, pos1, summ0, summ1, prop, part, tan0, tan1, total;
+    size_t bar, keys, agents, ref, pos0, pos1, summ0, summ1, prop, part, tan0, tan1, cnt, total;
     // part_floats: GA-IBR-MPPI partial sums (0 for the SGTP calls)
-    Layout(long long n_keys, long long n_agents, long long n_pos, int maxT, long long part_floats = 0)
+    Layout(long long n_keys, long long n_agents, long long n_pos, int maxT, long long part_floats = 0,
+           long long n_races = 1)
     {
         auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
         bar = 0;
@@ -967,7 +1095,8 @@ struct Layout {
         part = up(prop + sizeof(float4) * n_agents * maxT);
         tan0 = up(part + sizeof(float) * part_floats);
         tan1 = up(tan0 + sizeof(float2) * n_pos);
-        total = up(tan1 + sizeof(float2) * n_pos);
+        cnt = up(tan1 + sizeof(float2) * n_pos);      // queue head, then wdone, tdone
+        total = up(cnt + sizeof(unsigned long long) + sizeof(unsigned) * (n_races + n_agents));
     }
 };
 
@@ -1027,13 +1156,18 @@ sgtp_status launch_plan_v(PlanArgs &a, int block, int ctas, int spt, cudaStream_
     const int grid = sms * per_sm;
     // tiles of each round kind: kIlp rolls out ni samples per thread at once,
     // the fewest that fit the round's samples in one wave of the grid (at
-    // most 3), unless the caller fixed it
+    // most 3); a round of several waves even at 3 takes 2 or 3, whichever
+    // pads K less to whole tiles (ties: 3); unless the caller fixed it
     const long long cand[2] = {(long long)a.n_agents * a.K, (long long)a.n_races * a.K};
     for (int e = 0; e < 2; ++e) {
         int ni = 1;
         if (MODE == kIlp) {
             const long long slots = (long long)grid * block;
             ni = spt > 0 ? spt : (int)std::min(3ll, std::max(1ll, (cand[e] + slots - 1) / slots));
+            if (spt == 0 && cand[e] > 3 * slots) {
+                auto padded = [&](int n) { return (long long)((a.K + block * n - 1) / (block * n)) * block * n; };
+                if (padded(2) < padded(3)) ni = 2;
+            }
         }
         a.ni[e] = ni;
         a.tile[e] = MPPI ? kTileSingle : block * ni;
@@ -1072,6 +1206,9 @@ sgtp_status launch_plan_t(PlanArgs &a, const sgtp_launch_opts *opts, cudaStream_
     SGTP_CHECK(!(mppi && (spt > 1 || block == 128)), "GA-IBR-MPPI takes 256-thread CTAs, one sample per thread");
     // a round of at most one 256-thread CTA's worth of samples per SM runs
     // the wide 128-register build by default (measured faster there)
+    const int sched = opts ? opts->schedule : SGTP_SCHEDULE_DEFAULT;
+    SGTP_CHECK(!(learned && sched == SGTP_SCHEDULE_QUEUE), "the learned proposal runs in lock step only");
+    a.queue = sched == SGTP_SCHEDULE_QUEUE || (sched == SGTP_SCHEDULE_DEFAULT && a.races != nullptr && !learned);
     const bool small = (long long)a.n_agents * a.K <= 256ll * sms;
     const bool ilp = !mppi && (block == 128 || spt > 1 || (block == 0 && !learned && !small));
     if (ilp) return launch_plan_v<MAXO, kIlp, false>(a, 128, ctas, spt, s);
@@ -1096,6 +1233,8 @@ sgtp_status launch_plan(PlanArgs &a, int max_opp, const sgtp_launch_opts *opts, 
                    "256-thread CTAs take one sample per thread");
         SGTP_CHECK(opts->ctas_per_sm >= 0 && opts->window >= 0 && opts->wait_timeout_ns >= 0,
                    "negative launch option");
+        SGTP_CHECK(opts->schedule >= SGTP_SCHEDULE_DEFAULT && opts->schedule <= SGTP_SCHEDULE_QUEUE,
+                   "schedule must be 0 .. 2 (got %d)", opts->schedule);
     }
     switch (maxo_bucket(max_opp)) {
         case 1: return launch_plan_t<1>(a, opts, s);
@@ -1143,6 +1282,9 @@ void attach_workspace(PlanArgs &a, const Layout &lay, void *ws)
         a.ptan[0] = (float2 *)(w + lay.tan0);
         a.ptan[1] = (float2 *)(w + lay.tan1);
     }
+    a.qhead = (unsigned long long *)(w + lay.cnt);
+    a.wdone = (unsigned *)(w + lay.cnt + sizeof(unsigned long long));
+    a.tdone = a.wdone + a.n_races;
 }
 
 long long mppi_part_floats(long long n_agents, int K, int maxT)
@@ -1360,7 +1502,7 @@ extern "C" sgtp_status sgtp_batch_sizes(const sgtp_batch *b, int64_t *agents, in
     if (u_elems) *u_elems = b->u_elems;
     if (xi_elems) *xi_elems = b->xi_elems;
     if (ks) *ks = b->ks;
-    if (workspace_bytes) *workspace_bytes = Layout(b->ks, b->agents, b->n_pos, b->maxT).total;
+    if (workspace_bytes) *workspace_bytes = Layout(b->ks, b->agents, b->n_pos, b->maxT, 0, b->n_races).total;
     return SGTP_OK;
 }
 
@@ -1395,7 +1537,8 @@ static sgtp_status batch_plan_impl(const sgtp_batch *b, const sgtp_params *p, co
     const float il = mppi ? mppi_inverse(mppi_lambda) : 0.f;
     SGTP_CHECK(!mppi || il > 0.f, "lambda must be finite and > 0");
     SGTP_CHECK(!(mppi && mlp), "GA-IBR-MPPI takes the plain sampler only");
-    const Layout lay(b->ks, b->agents, b->n_pos, b->maxT, mppi ? mppi_part_floats(b->agents, b->K, b->maxT) : 0);
+    const Layout lay(b->ks, b->agents, b->n_pos, b->maxT, mppi ? mppi_part_floats(b->agents, b->K, b->maxT) : 0,
+                     b->n_races);
     SGTP_CHECK(workspace && workspace_bytes >= lay.total, "workspace too small: need %zu bytes", lay.total);
     SGTP_CHECK(((uintptr_t)workspace & 255u) == 0, "workspace must be 256-byte aligned");
     st = refresh_tail_counts(b, p);
@@ -1459,7 +1602,8 @@ extern "C" sgtp_status sgtp_batch_plan_learned(const sgtp_batch *b, const sgtp_p
 extern "C" sgtp_status sgtp_batch_mppi_workspace_bytes(const sgtp_batch *b, size_t *workspace_bytes)
 {
     SGTP_CHECK(b != nullptr && workspace_bytes != nullptr, "NULL argument");
-    *workspace_bytes = Layout(b->ks, b->agents, b->n_pos, b->maxT, mppi_part_floats(b->agents, b->K, b->maxT)).total;
+    *workspace_bytes =
+        Layout(b->ks, b->agents, b->n_pos, b->maxT, mppi_part_floats(b->agents, b->K, b->maxT), b->n_races).total;
     return SGTP_OK;
 }
 

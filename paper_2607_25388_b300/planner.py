@@ -53,12 +53,18 @@ def _ws(nbytes: int, device) -> torch.Tensor:
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
 
 
+SCHEDULE_DEFAULT, SCHEDULE_LOCKSTEP, SCHEDULE_QUEUE = 0, 1, 2
+
+
 def launch_opts(block=0, samples_per_thread=0, ctas_per_sm=0, window=0, wait_timeout_ns=0, debug_flags=0,
-                trace=None):
+                trace=None, schedule=SCHEDULE_DEFAULT):
     """Launch shape of the persistent kernel (0 = library default).  trace:
-    optional int64 CUDA tensor of 3*L+8 entries for per-phase timestamps."""
+    optional int64 CUDA tensor of 3*L+8 entries for per-phase timestamps.
+    schedule: SCHEDULE_LOCKSTEP (grid barrier after every phase) or
+    SCHEDULE_QUEUE (per-race round progression from a device work queue);
+    the default takes the queue for batches."""
     return _lib.LaunchOpts(int(block), int(samples_per_thread), int(ctas_per_sm), int(window), int(wait_timeout_ns),
-                           int(debug_flags), None if trace is None else trace.data_ptr())
+                           int(debug_flags), int(schedule), None if trace is None else trace.data_ptr())
 
 
 class Track:

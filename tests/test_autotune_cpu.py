@@ -39,6 +39,14 @@ def test_batch_keys_and_round_trip(tmp_path):
     assert A.key_batch(a, info) != A.key_batch(c, info)      # one more vehicle
     path = str(tmp_path / "tune.json")
     assert A.lookup_batch(a, path, info) is None
-    A._store(A.key_batch(a, info), dict(block=128, samples_per_thread=3, ctas_per_sm=0, ms=1.0), path)
+    A._store(A.key_batch(a, info), dict(block=128, samples_per_thread=3, ctas_per_sm=0, schedule=2, ms=1.0), path)
     o = A.lookup_batch(b, path, info)
-    assert (o.block, o.samples_per_thread, o.ctas_per_sm) == (128, 3, 0)
+    assert (o.block, o.samples_per_thread, o.ctas_per_sm, o.schedule) == (128, 3, 0, 2)
+
+
+def test_search_space_and_tiles_per_response():
+    c = list(A._candidates())
+    assert len(c) == len(set(c)) == len(A.SHAPES) * len(A.CTAS) * len(A.SCHEDULES)
+    assert {s for *_, s in c} == {1, 2}
+    assert A._tiles(4096, 128, 3) == 11 and A._tiles(4096, 128, 2) == 16 and A._tiles(4096, 256, 1) == 16
+    assert A._tiles(1000, 128, 1) == 8 and A._tiles(4096, 128, 0) is None and A._tiles(4096, 0, 0) is None

@@ -1,6 +1,6 @@
-"""The autotuner on a small problem: it measures every launch shape, checks
-that each gives the identical plan, stores the fastest, and the stored shape
-plans exactly like the default."""
+"""The autotuner on a small problem: it measures every launch shape and
+schedule, checks that each gives the identical plan, stores the fastest,
+and the stored shape plans exactly like the default."""
 import numpy as np
 import pytest
 
@@ -16,7 +16,7 @@ def test_tune_store_lookup_and_invariance(tmp_path):
     best = A.tune(3, 24, 512, 1, reps=2, warmup=1, path=path)
     assert ((best["block"], best["samples_per_thread"]) in A.SHAPES or best["block"] == 0) and best["ms"] > 0
     o = A.lookup(3, 24, 512, 1, path)
-    assert o is not None and o.block == best["block"]
+    assert o is not None and o.block == best["block"] and o.schedule == best["schedule"]
     sc = S.grid_race(S.fourier_track(778), 3, 24, 512, 1, 779)
     p = S.params_fullscale()
     trk = P.Track.from_data(sc.track)

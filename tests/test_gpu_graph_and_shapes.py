@@ -1,7 +1,8 @@
-"""Launch shapes and CUDA graphs of the planning call: every block size gives
-bit-identical plans; a captured graph replays to exactly the plan of a
-direct call (for its own seed and after a seed change); a captured batch
-replays to exactly the batch plan."""
+"""Launch shapes, schedules and CUDA graphs of the planning call: every
+block size and both schedules (lock-step rounds, per-race progression from
+the device queue) give bit-identical plans; a captured graph replays to
+exactly the plan of a direct call (for its own seed and after a seed
+change); a captured batch replays to exactly the batch plan."""
 import numpy as np
 import pytest
 
@@ -36,10 +37,48 @@ def test_launch_shapes_give_identical_plans():
     trk = P().Track.from_data(sc.track)
     ref = plan(sc, p, 1000, 2, 3, trk)
     assert ref["status"][0] == 0
-    for block, spt, ctas in ((128, 1, 0), (128, 2, 0), (128, 3, 1), (256, 1, 0), (256, 1, 2)):
-        got = plan(sc, p, 1000, 2, 3, trk, P().launch_opts(block=block, samples_per_thread=spt, ctas_per_sm=ctas))
+    Q = P().SCHEDULE_QUEUE
+    for block, spt, ctas, sched in ((128, 1, 0, 0), (128, 2, 0, 0), (128, 3, 1, 0), (256, 1, 0, 0), (256, 1, 2, 0),
+                                    (0, 0, 0, Q), (128, 3, 1, Q), (256, 1, 2, Q)):
+        got = plan(sc, p, 1000, 2, 3, trk, P().launch_opts(block=block, samples_per_thread=spt, ctas_per_sm=ctas,
+                                                           schedule=sched))
         for k in ("xi", "k_star", "U", "xi_hist", "u_hist"):
-            np.testing.assert_array_equal(got[k], ref[k], err_msg=f"block {block} x {spt} ctas {ctas} {k}")
+            np.testing.assert_array_equal(got[k], ref[k], err_msg=f"block {block} x {spt} ctas {ctas} sched {sched} {k}")
+
+
+def _uneven_batch(Pm, K, L):
+    races = [S.grid_race(S.fourier_track(620 + r, n_points=600), n_v, T, K, L, 40 + r)
+             for r, (n_v, T) in enumerate([(2, 30), (10, 80), (5, 41), (2, 80), (9, 30)])]
+    trk = Pm.Track.from_many([sc.track for sc in races])
+    b = Pm.Batch(trk, [dict(track_id=r, n_v=sc.X0.shape[0], T=sc.T, ego=sc.ego, race_tag=r)
+                       for r, sc in enumerate(races)], K=K, L=L)
+    X0 = dev(np.concatenate([sc.X0 for sc in races]))
+    U0 = np.concatenate([sc.U0.reshape(-1) for sc in races])
+    vs = dev(np.concatenate([sc.vref_scale for sc in races]))
+    return b, X0, U0, vs
+
+
+def test_batch_schedules_give_identical_plans():
+    """Per-race round progression (the batch default) and lock-step rounds,
+    over several launch shapes, on races of uneven size and horizon."""
+    Pm = P()
+    p = S.params_fullscale()
+    b, X0, U0, vs = _uneven_batch(Pm, 777, 3)
+    runs = {}
+    for name, o in (("default", None), ("lockstep", Pm.launch_opts(schedule=Pm.SCHEDULE_LOCKSTEP)),
+                    ("queue", Pm.launch_opts(schedule=Pm.SCHEDULE_QUEUE)),
+                    ("queue-256x2", Pm.launch_opts(block=256, ctas_per_sm=2, schedule=Pm.SCHEDULE_QUEUE)),
+                    ("queue-128x1", Pm.launch_opts(block=128, samples_per_thread=1, ctas_per_sm=1)),
+                    ("lockstep-128x3", Pm.launch_opts(block=128, samples_per_thread=3,
+                                                      schedule=Pm.SCHEDULE_LOCKSTEP))):
+        U = dev(U0)
+        out = b.plan(p, X0, U, vs, seed=5, want_hist=True, opts=o)
+        torch.cuda.synchronize()
+        assert out["status"].item() == 0, name
+        runs[name] = {k: v.cpu().numpy() for k, v in out.items()} | {"U": U.cpu().numpy()}
+    for name, r in runs.items():
+        for k in ("xi", "k_star", "U", "xi_hist", "u_hist"):
+            np.testing.assert_array_equal(r[k], runs["lockstep"][k], err_msg=f"{name} {k}")
 
 
 def test_invalid_launch_shapes_are_rejected():
@@ -47,7 +86,7 @@ def test_invalid_launch_shapes_are_rejected():
     p = S.params_fullscale()
     trk = P().Track.from_data(sc.track)
     for o in (dict(block=96), dict(block=512), dict(block=64), dict(block=256, samples_per_thread=2),
-              dict(samples_per_thread=4), dict(ctas_per_sm=-1)):
+              dict(samples_per_thread=4), dict(ctas_per_sm=-1), dict(schedule=3), dict(schedule=-1)):
         with pytest.raises(RuntimeError, match="SGTP_E_INVALID"):
             plan(sc, p, 256, 1, 0, trk, P().launch_opts(**o))
 

@@ -177,8 +177,9 @@ def test_batch_equals_single_race_plans():
 
 def test_barrier_wait_times_out_instead_of_hanging():
     """Fault injection on the device: CTA 0 never arrives at the grid
-    barrier; every wait gives up after its 50 ms limit and the call reports
-    SGTP_E_TIMEOUT; the context stays usable."""
+    barrier (or, under the queue schedule, no winner reports its
+    completion); every wait gives up after its 50 ms limit and the call
+    reports SGTP_E_TIMEOUT; the context stays usable."""
     P = planner()
     sc = S.two_car_race(103, K=256, T=20, L=1)
     p = S.params_fullscale()
@@ -186,6 +187,13 @@ def test_barrier_wait_times_out_instead_of_hanging():
                  opts=P.launch_opts(wait_timeout_ns=50_000_000, debug_flags=P._lib.DEBUG_SKIP_BARRIER_ARRIVAL))
     assert g["status"][0] & 0xFF == 4
     ok = gpu_plan(sc, p, 256, 1, seed=1)
+    assert ok["status"][0] == 0
+    # the queue schedule's waits: no winner reports, the next round's tiles give up
+    g = gpu_plan(sc, p, 256, 1, seed=1,
+                 opts=P.launch_opts(wait_timeout_ns=50_000_000, debug_flags=P._lib.DEBUG_SKIP_WINNER_SIGNAL,
+                                    schedule=P.SCHEDULE_QUEUE))
+    assert g["status"][0] & 0xFF == 4
+    ok = gpu_plan(sc, p, 256, 1, seed=1, opts=P.launch_opts(schedule=P.SCHEDULE_QUEUE))
     assert ok["status"][0] == 0
     # the host-side status query reads the same word
     st = torch.tensor([4 | (5 << 8)], dtype=torch.int32, device="cuda")
