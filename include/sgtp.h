@@ -211,9 +211,10 @@ sgtp_status sgtp_best_response_noalloc(const sgtp_track *trk, int32_t track_id, 
  * Samples are processed in tiles of block x samples_per_thread consecutive
  * k (GA-IBR-MPPI: tiles of 256).  Defaults: a plain plan takes the
  * 128-thread build unless its Jacobi round holds at most 256 x SMs samples
- * (then 2 x 256 threads); a learned-proposal plan takes the 256-thread
- * builds (2 per SM when its round has fewer 256-sample tiles than 3 x SMs);
- * GA-IBR-MPPI takes the 256-thread builds only. */
+ * (then 2 x 256 threads); a single learned-proposal plan takes the
+ * 256-thread builds (2 per SM when its round has fewer 256-sample tiles than
+ * 3 x SMs), a learned batch the 128-thread build; GA-IBR-MPPI takes the
+ * 256-thread builds only. */
 typedef struct sgtp_launch_opts {
     int32_t block;                /* threads per CTA: 128 or 256 (0: default)        */
     int32_t samples_per_thread;   /* 0 .. 3: samples each thread rolls out at once
@@ -236,11 +237,13 @@ typedef struct sgtp_launch_opts {
  * of its winners, with a grid barrier after each phase (every race of a
  * batch waits for the slowest).  QUEUE: after the setup, CTAs claim work
  * items from one device queue (samples of round 0, winners of round 0,
- * samples of round 1, ...); a sample tile waits (bounded by wait_timeout_ns)
- * until its race's previous round is complete, a winner until its vehicle's
- * tiles are in, so each race advances at its own pace.  Both give the same
- * plans bit for bit.  DEFAULT: QUEUE for batches, LOCKSTEP for single races
- * and for every call with the learned proposal (which takes LOCKSTEP only). */
+ * samples of round 1, ...; with the learned proposal each round starts with
+ * one proposal item per vehicle); a proposal or sample tile waits (bounded
+ * by wait_timeout_ns) until its race's previous round is complete and, for
+ * a tile, its vehicle's proposal is in; a winner waits until its vehicle's
+ * tiles are in; so each race advances at its own pace.  Both give the same
+ * plans bit for bit.  DEFAULT: QUEUE for batches, LOCKSTEP for single
+ * races. */
 #define SGTP_SCHEDULE_DEFAULT 0
 #define SGTP_SCHEDULE_LOCKSTEP 1
 #define SGTP_SCHEDULE_QUEUE 2

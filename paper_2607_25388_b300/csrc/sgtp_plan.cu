@@ -98,6 +98,7 @@ struct PlanArgs {
     unsigned long long *qhead;     // next queue position to claim
     unsigned *wdone;               // per race: winner items completed
     unsigned *tdone;               // per vehicle: sample tiles completed (all rounds)
+    unsigned *pdone;               // per vehicle: proposal items completed (learned proposal)
 };
 
 __device__ __forceinline__ void stamp(const PlanArgs &a, int i)
@@ -794,42 +795,67 @@ __device__ __forceinline__ void plan_body(const PlanArgs &a)
         for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_keys; q += gridDim.x * blockDim.x)
             a.keys[q] = ~0ull;
         if (a.queue) {
-            const int n_cnt = a.n_races + a.n_agents;
+            const int n_cnt = a.n_races + 2 * a.n_agents;
             for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_cnt; q += gridDim.x * blockDim.x)
-                a.wdone[q] = 0u;      // wdone and tdone are contiguous
+                a.wdone[q] = 0u;      // wdone, tdone and pdone are contiguous
             if (blockIdx.x == 0 && threadIdx.x == 0) *a.qhead = 0ull;
         }
     }
     ok = grid_barrier(a, skip);
     stamp(a, 1);
-    // queue schedule: q_sh is this CTA's claimed position; round k's sample
-    // items start at k (items[0] + n_agents), its winner items items[kind]
-    // later (one per vehicle)
+    // queue schedule: q_sh is this CTA's claimed position; a round holds
+    // (with the learned proposal) one proposal item per vehicle, then
+    // items[kind] sample items, then one winner item per vehicle
     const bool queue = a.queue != 0;
+    const bool learned = a.mlp_wb || a.feat_out;
+    const unsigned long long round_items =
+        (unsigned long long)((learned ? a.n_agents : 0) + a.items[0] + a.n_agents);
     __shared__ unsigned long long q_sh;
     if (ok && queue) claim_item(a, q_sh);
 
     for (int round = 0; ok && round <= a.L + 1; ++round) {
         const bool extra = round == a.L + 1;
         const int bin = round & 1, bout = bin ^ 1;
-        if (a.mlp_wb || a.feat_out) {
+        unsigned long long base = (unsigned long long)round * round_items;
+        if (learned) {
             // -------------------------------------------------- proposals (one CTA per vehicle)
-            for (int ag = blockIdx.x; ag < a.n_agents; ag += gridDim.x) {
+            // queue: a proposal needs the race's previous round complete
+            for (int ag = blockIdx.x;; ag += gridDim.x) {
+                if (queue) {
+                    if (q_sh >= base + (unsigned long long)a.n_agents) break;
+                    ag = (int)(q_sh - base);
+                } else if (ag >= a.n_agents) {
+                    break;
+                }
                 const int ri = find_race(a, ag, [](const RaceDev &r) { return r.agent_off; });
                 const RaceDev R = get_race(a, ri);
                 const int i = ag - R.agent_off;
-                if (extra && i != R.ego) continue;
-                __syncthreads();
-                proposal_for(a, R, i, bin, round > 0, round, Tl::scratch());
+                const bool active = !extra || i == R.ego;
+                if (queue && active && round > 0 && !wait_count(a, a.wdone + ri, (unsigned)(round * R.n_v))) {
+                    ok = false;
+                    break;
+                }
+                if (active) {
+                    __syncthreads();
+                    proposal_for(a, R, i, bin, round > 0, round, Tl::scratch());
+                }
+                if (queue) {
+                    // only a proposal that ran counts: the extra round's
+                    // idle items (claimed as early as any) must not stand
+                    // in for a vehicle's proposal of an earlier round
+                    if (active) signal_done(a.pdone + ag);
+                    claim_item(a, q_sh);
+                }
             }
-            if (!grid_barrier(a, skip)) break;
+            if (!ok) break;
+            if (!queue && !grid_barrier(a, skip)) break;
+            base += (unsigned long long)a.n_agents;
         }
         stamp(a, 2 + 3 * round);
         // lock step: this CTA's share of the round, equal item counts for one
         // race, equal work (items weighted by their race's horizon) for a
         // batch; queue: the positions base .. base + items - 1 as claimed
         int i0 = 0, i1 = 0;
-        const unsigned long long base = (unsigned long long)round * (unsigned long long)(a.items[0] + a.n_agents);
         if (queue) {
         } else if (!a.races) {
             const int n_items = a.items[extra];
@@ -863,8 +889,11 @@ __device__ __forceinline__ void plan_body(const PlanArgs &a)
             const RaceDev R = get_race(a, ri);
             const int ag = R.agent_off + i;
             // queue: the race's previous round must be complete (its n_v
-            // winners per round)
-            if (queue && round > 0 && !wait_count(a, a.wdone + ri, (unsigned)(round * R.n_v))) {
+            // winners per round); with the learned proposal, the vehicle's
+            // proposal of this round, which waited for that itself
+            if (queue && (learned || round > 0) &&
+                !(learned ? wait_count(a, a.pdone + ag, (unsigned)(round + 1))
+                          : wait_count(a, a.wdone + ri, (unsigned)(round * R.n_v)))) {
                 ok = false;
                 break;
             }
@@ -1095,8 +1124,8 @@ struct Layout {
         part = up(prop + sizeof(float4) * n_agents * maxT);
         tan0 = up(part + sizeof(float) * part_floats);
         tan1 = up(tan0 + sizeof(float2) * n_pos);
-        cnt = up(tan1 + sizeof(float2) * n_pos);      // queue head, then wdone, tdone
-        total = up(cnt + sizeof(unsigned long long) + sizeof(unsigned) * (n_races + n_agents));
+        cnt = up(tan1 + sizeof(float2) * n_pos);      // queue head, then wdone, tdone, pdone
+        total = up(cnt + sizeof(unsigned long long) + sizeof(unsigned) * (n_races + 2 * n_agents));
     }
 };
 
@@ -1184,12 +1213,14 @@ sgtp_status launch_plan_v(PlanArgs &a, int block, int ctas, int spt, cudaStream_
 }
 
 // Register budget and shape of one launch.  By default a plain SGTP plan
-// runs kIlp (samples per thread chosen per round) unless its Jacobi round is
-// at most one 256-thread CTA of samples per SM; a plan with the learned
-// proposal runs 256-thread CTAs (the network's layers are split over eight
-// warps): kWide2 when a Jacobi round has fewer 256-sample tiles than three
-// CTAs per SM could take at once, else kWide3; GA-IBR-MPPI likewise (it
-// takes the wide builds only).  Options override: block 128 (or
+// or batch runs kIlp (samples per thread chosen per round) unless its
+// Jacobi round is at most one 256-thread CTA of samples per SM; a single
+// plan with the learned proposal runs 256-thread CTAs (the network's layers
+// are split over eight warps, which shortens its proposal phase): kWide2
+// when a Jacobi round has fewer 256-sample tiles than three CTAs per SM
+// could take at once, else kWide3; a learned batch runs kIlp (its proposal
+// items overlap other races' tiles under the queue schedule); GA-IBR-MPPI
+// takes the wide builds only.  Options override: block 128 (or
 // samples_per_thread > 1) selects kIlp, block 256 the wide builds
 // (ctas_per_sm <= 2: kWide2).
 template <int MAXO>
@@ -1207,10 +1238,9 @@ sgtp_status launch_plan_t(PlanArgs &a, const sgtp_launch_opts *opts, cudaStream_
     // a round of at most one 256-thread CTA's worth of samples per SM runs
     // the wide 128-register build by default (measured faster there)
     const int sched = opts ? opts->schedule : SGTP_SCHEDULE_DEFAULT;
-    SGTP_CHECK(!(learned && sched == SGTP_SCHEDULE_QUEUE), "the learned proposal runs in lock step only");
-    a.queue = sched == SGTP_SCHEDULE_QUEUE || (sched == SGTP_SCHEDULE_DEFAULT && a.races != nullptr && !learned);
+    a.queue = sched == SGTP_SCHEDULE_QUEUE || (sched == SGTP_SCHEDULE_DEFAULT && a.races != nullptr);
     const bool small = (long long)a.n_agents * a.K <= 256ll * sms;
-    const bool ilp = !mppi && (block == 128 || spt > 1 || (block == 0 && !learned && !small));
+    const bool ilp = !mppi && (block == 128 || spt > 1 || (block == 0 && !small && (!learned || a.races)));
     if (ilp) return launch_plan_v<MAXO, kIlp, false>(a, 128, ctas, spt, s);
     block = 256;
     const bool wide2 = ctas > 0 ? ctas <= 2 : (long long)((a.K + 255) / 256) * a.n_agents < 3ll * sms;
@@ -1285,6 +1315,7 @@ void attach_workspace(PlanArgs &a, const Layout &lay, void *ws)
     a.qhead = (unsigned long long *)(w + lay.cnt);
     a.wdone = (unsigned *)(w + lay.cnt + sizeof(unsigned long long));
     a.tdone = a.wdone + a.n_races;
+    a.pdone = a.tdone + a.n_agents;
 }
 
 long long mppi_part_floats(long long n_agents, int K, int maxT)

@@ -307,9 +307,11 @@ def test_learned_plan_teacher_forced(net, case):
             checked += 1
 
 
-def test_learned_batch_equals_learned_single_plans(net):
+@pytest.mark.parametrize("schedule", [0, 1, 2])
+def test_learned_batch_equals_learned_single_plans(net, schedule):
     """Two ten-car races planned in one learned batch launch give exactly the
-    learned single-race plans (proposal phase included)."""
+    learned single-race plans (proposal phase included), under the default,
+    lock-step and queue schedules."""
     p = S.params_fullscale()
     races = [S.ten_car_race(221 + r, K=512, T=60, L=1) for r in range(2)]
     trk = P().Track.from_many([sc.track for sc in races])
@@ -317,7 +319,7 @@ def test_learned_batch_equals_learned_single_plans(net):
     X0 = dev(np.concatenate([sc.X0 for sc in races]))
     U = dev(np.concatenate([sc.U0.reshape(-1) for sc in races]))
     vs = dev(np.concatenate([sc.vref_scale for sc in races]))
-    out = b.plan(p, X0, U, vs, seed=4, mlp=net, K_prop=200)
+    out = b.plan(p, X0, U, vs, seed=4, mlp=net, K_prop=200, opts=P().launch_opts(schedule=schedule))
     torch.cuda.synchronize()
     assert out["status"].item() == 0
     xi_all, ks_all = out["xi"].cpu().numpy(), out["k_star"].cpu().numpy()
@@ -331,10 +333,11 @@ def test_learned_batch_equals_learned_single_plans(net):
         np.testing.assert_array_equal(ks_all[r * nk:(r + 1) * nk], single["k_star"].cpu().numpy())
 
 
-@pytest.mark.parametrize("shape", [(128, 1, 0), (128, 2, 1), (256, 1, 2)])
+@pytest.mark.parametrize("shape", [(128, 1, 0, 0), (128, 2, 1, 0), (256, 1, 2, 0), (0, 0, 0, 2), (128, 3, 0, 2),
+                                   (256, 1, 2, 2)])
 def test_learned_plan_is_identical_for_every_block_size(net, shape):
     """Features (incl. the zeroed slots of absent opponents), proposals and
-    selections do not depend on the CTA size."""
+    selections do not depend on the CTA size or the schedule."""
     p = S.params_fullscale()
     sc = S.two_car_race(331, K=1024, T=60, L=2)
     trk = P().Track.from_data(sc.track)
@@ -347,7 +350,7 @@ def test_learned_plan_is_identical_for_every_block_size(net, shape):
         return {k: v.cpu().numpy() for k, v in out.items()}
 
     a = run(None)
-    b = run(P().launch_opts(block=shape[0], samples_per_thread=shape[1], ctas_per_sm=shape[2]))
+    b = run(P().launch_opts(block=shape[0], samples_per_thread=shape[1], ctas_per_sm=shape[2], schedule=shape[3]))
     assert np.all(a["features"][:, :, 14:62] == 0.0)       # one opponent: slots 1..8 are zero
     for k in ("features", "prop", "xi", "k_star", "u_hist"):
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
