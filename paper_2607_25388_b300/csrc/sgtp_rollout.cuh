@@ -267,15 +267,22 @@ __device__ __noinline__ SegPick frenet_relocate(const BRScalars &S, float px, fl
     return q;
 }
 
-// Frenet of the state from its segment, and the next prediction.
-__device__ __forceinline__ GeoPt frenet_finish(const SegPick &q, float px, float py, float &pos, float &ppred)
+// Frenet of the state from its segment, and its continuous segment
+// position np = m + t (the next prediction follows from it, frenet_advance).
+__device__ __forceinline__ GeoPt frenet_point(const SegPick &q, float px, float py, float &np)
 {
     const GeoPt f = frenet_eval(q.g1, q.g2, q.g3, q.len, px, py);
-    const float np = (float)q.m + f.tc;
-    ppred = __fmaf_rn(2.f, np, -(pos + 0.5f));
-    pos = np;
+    np = (float)q.m + f.tc;
     return f;
 }
+
+// The next step's predicted position from the new position np.
+__device__ __forceinline__ void frenet_advance(float np, float &pos, float &ppred)
+{
+    ppred = __fmaf_rn(2.f, np, -(pos + 0.5f));
+    pos = np;
+}
+
 
 // Clipped control from a nominal control and a normal pair z (Pi_U).
 __device__ __forceinline__ float2 sample_control(const sgtp_params &p, float2 ubar, float2 z)
@@ -467,28 +474,37 @@ __device__ __forceinline__ void sample_steps(SampleState<MAXO> (&St)[NI], const 
                                              float *st_out, float *fr_out)
 {
     using T = Tile<MAXO>;
-    SegPick q[NI];
+    // each state's Frenet point from its predicted segment right away; only
+    // the point (not the segment's records) waits for the rare relocation
+    GeoPt f[NI];
+    float np[NI];
+    bool ok[NI];
     bool miss = false;
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
         step_control_cost(St[i].c, St[i].a_prev, St[i].d_prev, u[i], tau);
         bicycle_step(p, St[i].x, St[i].y, St[i].psi, St[i].v, u[i].x, u[i].y);
-        q[i] = frenet_locate<MAXO>(wlim, St[i].x, St[i].y, St[i].ppred);
-        miss = miss || !q[i].ok;
+        const SegPick q = frenet_locate<MAXO>(wlim, St[i].x, St[i].y, St[i].ppred);
+        f[i] = frenet_point(q, St[i].x, St[i].y, np[i]);
+        ok[i] = q.ok;
+        miss = miss || !q.ok;
     }
     if (__any_sync(__activemask(), miss)) {
 #pragma unroll
         for (int i = 0; i < NI; ++i)
-            if (!q[i].ok) q[i] = frenet_relocate<MAXO>(S, St[i].x, St[i].y, St[i].pos, St[i].ppred, flag);
+            if (!ok[i]) {
+                const SegPick q = frenet_relocate<MAXO>(S, St[i].x, St[i].y, St[i].pos, St[i].ppred, flag);
+                f[i] = frenet_point(q, St[i].x, St[i].y, np[i]);
+            }
     }
     const int st = tau + 1;
     const float4 r = T::ref()[st];
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
-        const GeoPt f = frenet_finish(q[i], St[i].x, St[i].y, St[i].pos, St[i].ppred);
-        St[i].s = f.s;
-        St[i].rho_bd = fminf(St[i].rho_bd, f.rho);
-        if (st > tail0) St[i].d_tail = St[i].d_tail + f.d;
+        frenet_advance(np[i], St[i].pos, St[i].ppred);
+        St[i].s = f[i].s;
+        St[i].rho_bd = fminf(St[i].rho_bd, f[i].rho);
+        if (st > tail0) St[i].d_tail = St[i].d_tail + f[i].d;
         step_tracking_cost(St[i].c, St[i].x, St[i].y, St[i].psi, St[i].v, r);
         step_opponents<0, MAXO / 2, true, MAXO>(St[i].g2, St[i].x, St[i].y, T::opp() + tau * BRTile<MAXO>::NP);
         if (OUT) {
@@ -496,7 +512,7 @@ __device__ __forceinline__ void sample_steps(SampleState<MAXO> (&St)[NI], const 
                 st_out[4 * st + 0] = St[i].x; st_out[4 * st + 1] = St[i].y;
                 st_out[4 * st + 2] = St[i].psi + S.psi_off; st_out[4 * st + 3] = St[i].v;
             }
-            if (fr_out) { fr_out[2 * st] = St[i].s; fr_out[2 * st + 1] = f.d; }
+            if (fr_out) { fr_out[2 * st] = St[i].s; fr_out[2 * st + 1] = f[i].d; }
         }
     }
 }
