@@ -47,6 +47,25 @@ def params_fullscale() -> dict:
     )
 
 
+# The paper's sample budget, horizon and IBR rounds (Sec. IV-B): K, H, L_IBR.
+PAPER_SAMPLES = (128, 12, 2)
+
+
+def params_paper() -> dict:
+    """The paper's own 1/10-scale setup (Sec. IV-B): sampling spreads, cost
+    weights, game weights and thresholds as printed, dt = 1.2 s / 12 steps.
+    The vehicle limits (wheelbase, acceleration, steering and speed ranges)
+    are not printed; these are our choice for a 1/10-scale car (wheelbase
+    0.33 m, a in [-9.5, 9.5], |delta| <= 0.4189, v in [0, 7])."""
+    return dict(
+        dt=0.1, wheelbase=0.33, a_min=-9.5, a_max=9.5, delta_max=0.4189, v_min=0.0, v_max=7.0,
+        sigma_a=0.335, sigma_delta=0.025,
+        Q=[60.0, 60.0, 47.75, 39.48], R=[8.43, 20.0], S=[1.0, 19.26],
+        w_game=60.0, w_contest=1.0, w_long=2.0, w_block=10.0, w_safety=50.0,
+        s_contest=8.0, s_role=1.0, mu_tail=0.3, g_safe=1.0, eps_alpha=1e-3, m_bd=0.515, d_col=0.9,
+    )
+
+
 # --------------------------------------------------------------- tracks
 @dataclass
 class TrackData:
