@@ -51,15 +51,21 @@ __device__ __forceinline__ void mma_bf16(float c[4], const unsigned a[4], const 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+// Split K: CTA z of a grid with gridDim.z > 1 sums k in [z kchunk,
+// (z+1) kchunk) only and writes its FP32 partial product to Cv + z
+// part_stride (EPI_F32); splitk_reduce_kernel then adds the partials in z
+// order, so the result does not depend on scheduling.
 template <bool TA, bool TB, int EPI>
 __global__ void __launch_bounds__(128) gemm_kernel(const bf16 *__restrict__ A, const bf16 *__restrict__ B, void *Cv,
                                                    const float *__restrict__ bias, int M, int N, int K, int lda,
-                                                   int ldb, int ldc)
+                                                   int ldb, int ldc, int kchunk, long long part_stride)
 {
     constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
     __shared__ __align__(16) bf16 As[BM][BK + PAD];
     __shared__ __align__(16) bf16 Bs[BN][BK + PAD];
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    if (EPI == EPI_F32) Cv = (float *)Cv + blockIdx.z * part_stride;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
     const int g = lane >> 2, t = lane & 3;
@@ -71,13 +77,13 @@ __global__ void __launch_bounds__(128) gemm_kernel(const bf16 *__restrict__ A, c
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
     const bf16 zero = __float2bfloat16(0.f);
-    for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int k0 = kb; k0 < ke; k0 += BK) {
         for (int e = threadIdx.x; e < BM * BK; e += blockDim.x) {
             int m, k;
             if (TA) { m = e % BM; k = e / BM; } else { k = e % BK; m = e / BK; }
             const int gm = m0 + m, gk = k0 + k;
             bf16 v = zero;
-            if (gm < M && gk < K) v = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
+            if (gm < M && gk < ke) v = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
             As[m][k] = v;
         }
         for (int e = threadIdx.x; e < BN * BK; e += blockDim.x) {
@@ -85,7 +91,7 @@ __global__ void __launch_bounds__(128) gemm_kernel(const bf16 *__restrict__ A, c
             if (TB) { k = e % BK; n = e / BK; } else { n = e % BN; k = e / BN; }
             const int gn = n0 + n, gk = k0 + k;
             bf16 v = zero;
-            if (gn < N && gk < K) v = TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
+            if (gn < N && gk < ke) v = TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
             Bs[n][k] = v;
         }
         __syncthreads();
@@ -139,7 +145,48 @@ void gemm(const bf16 *A, const bf16 *B, void *C, const float *bias, int M, int N
           cudaStream_t s)
 {
     dim3 grid((N + 63) / 64, (M + 63) / 64);
-    gemm_kernel<TA, TB, EPI><<<grid, 128, 0, s>>>(A, B, C, bias, M, N, K, lda, ldb, ldc);
+    gemm_kernel<TA, TB, EPI><<<grid, 128, 0, s>>>(A, B, C, bias, M, N, K, lda, ldb, ldc, K, 0ll);
+    count_launch();
+}
+
+// C[i] = sum_z part[z][i], z in order.
+__global__ void splitk_reduce_kernel(const float *part, int splits, long long n, float *C)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float v = part[i];
+        for (int z = 1; z < splits; ++z) v += part[(size_t)z * n + i];
+        C[i] = v;
+    }
+}
+
+// Work items (output tiles x K chunks) a split-K product aims at, and the
+// FP32 partials it may need: splits x tiles <= kSplitTarget and
+// M N <= tiles x 64 x 64.
+constexpr int kSplitTarget = 256;
+constexpr size_t kSplitPartFloats = (size_t)kSplitTarget * 64 * 64;
+
+// FP32 C [M x N] (row-major, ldc = N) = A B with K split into chunks of a
+// multiple of 32 so that the tiles times the chunks reach about
+// kSplitTarget CTAs: the weight gradients have K = batch and few output
+// tiles.  The split depends on M, N and K only, so results are
+// reproducible run to run.
+template <bool TA, bool TB>
+void gemm_splitk(const bf16 *A, const bf16 *B, float *C, float *part, int M, int N, int K, int lda, int ldb,
+                 cudaStream_t s)
+{
+    const int tiles = ((N + 63) / 64) * ((M + 63) / 64);
+    int splits = std::max(1, std::min((K + 31) / 32, kSplitTarget / tiles));
+    const int kchunk = ((K + splits - 1) / splits + 31) / 32 * 32;
+    splits = (K + kchunk - 1) / kchunk;
+    if (splits <= 1) {
+        gemm<TA, TB, EPI_F32>(A, B, C, nullptr, M, N, K, lda, ldb, N, s);
+        return;
+    }
+    dim3 grid((N + 63) / 64, (M + 63) / 64, splits);
+    const long long n = (long long)M * N;
+    gemm_kernel<TA, TB, EPI_F32><<<grid, 128, 0, s>>>(A, B, part, nullptr, M, N, K, lda, ldb, N, kchunk, n);
+    count_launch();
+    splitk_reduce_kernel<<<(int)std::min<long long>(1024, (n + 255) / 256), 256, 0, s>>>(part, splits, n, C);
     count_launch();
 }
 
@@ -175,14 +222,25 @@ __global__ void nll_kernel(const float *out, const float *target, int Bsz, int T
     if ((threadIdx.x & 31) == 0) atomicAdd(loss, lsum * inv);
 }
 
-// db[n] = sum_b dZ[b][n] (FP32), one thread per column.
-__global__ void colsum_kernel(const float *dz, int Bsz, int N, float *db)
+// db[n] = sum_b dZ[b][n] (FP32) in a fixed order: a CTA takes 32 columns;
+// its thread (g, c) sums rows g, g + 32, ... of column c (the warp reads 32
+// consecutive columns of a row), then the 32 partial sums of a column are
+// added in g order.
+__global__ void __launch_bounds__(1024) colsum_kernel(const float *dz, int Bsz, int N, float *db)
 {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    float s = 0.f;
-    for (int b = 0; b < Bsz; ++b) s += dz[(size_t)b * N + n];
-    db[n] = s;
+    __shared__ float part[32][33];
+    const int c = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int n = blockIdx.x * 32 + c;
+    float acc = 0.f;
+    if (n < N)
+        for (int b = g; b < Bsz; b += 32) acc += dz[(size_t)b * N + n];
+    part[g][c] = acc;
+    __syncthreads();
+    if (g == 0 && n < N) {
+        float t = 0.f;
+        for (int q = 0; q < 32; ++q) t += part[q][c];
+        db[n] = t;
+    }
 }
 
 // dZ = dH * (H > 0) as BF16 (the ReLU mask from the BF16 activation), and
@@ -292,6 +350,7 @@ struct sgtp_mlp {
     int cap = 0;
     bf16 *xb = nullptr, *h[3] = {nullptr, nullptr, nullptr}, *dzb = nullptr, *dhb = nullptr;
     float *outf = nullptr, *dout = nullptr, *dh = nullptr, *dzf = nullptr, *loss = nullptr;
+    float *part = nullptr;        // split-K partial products (kSplitPartFloats)
 };
 
 static void refresh_fragments(sgtp_mlp *M, cudaStream_t s)
@@ -340,10 +399,10 @@ extern "C" sgtp_status sgtp_mlp_create(int32_t T, uint64_t seed, void *stream, s
 static void free_scratch(sgtp_mlp *M)
 {
     cudaFree(M->xb); cudaFree(M->h[0]); cudaFree(M->h[1]); cudaFree(M->h[2]); cudaFree(M->dzb); cudaFree(M->dhb);
-    cudaFree(M->outf); cudaFree(M->dout); cudaFree(M->dh); cudaFree(M->dzf);
+    cudaFree(M->outf); cudaFree(M->dout); cudaFree(M->dh); cudaFree(M->dzf); cudaFree(M->part);
     M->xb = M->dzb = M->dhb = nullptr;
     M->h[0] = M->h[1] = M->h[2] = nullptr;
-    M->outf = M->dout = M->dh = M->dzf = nullptr;
+    M->outf = M->dout = M->dh = M->dzf = M->part = nullptr;
     M->cap = 0;
 }
 
@@ -368,7 +427,8 @@ extern "C" sgtp_status sgtp_mlp_reserve(sgtp_mlp *M, int32_t batch)
         (e = cudaMalloc(&M->h[1], 2 * B * kHid)) || (e = cudaMalloc(&M->h[2], 2 * B * kHid)) ||
         (e = cudaMalloc(&M->dzb, 2 * B * W)) || (e = cudaMalloc(&M->dhb, 2 * B * W)) ||
         (e = cudaMalloc(&M->outf, 4 * B * M->out)) || (e = cudaMalloc(&M->dout, 4 * B * M->out)) ||
-        (e = cudaMalloc(&M->dh, 4 * B * W)) || (e = cudaMalloc(&M->dzf, 4 * B * W))) {
+        (e = cudaMalloc(&M->dh, 4 * B * W)) || (e = cudaMalloc(&M->dzf, 4 * B * W)) ||
+        (e = cudaMalloc(&M->part, 4 * kSplitPartFloats))) {
         free_scratch(M);
         return set_error(SGTP_E_NOMEM, "MLP scratch allocation failed: %s", cudaGetErrorString(e));
     }
@@ -444,9 +504,9 @@ extern "C" sgtp_status sgtp_mlp_train_step(sgtp_mlp *M, const float *x, const fl
         const long long o = layer_off(l, OUT);
         const int in = layer_in(l);
         const bf16 *act_in = l == 0 ? M->xb : M->h[l - 1];
-        // dW_l [N x in] = dZ^T [N x B] * act_in [B x in]
-        gemm<true, false, EPI_F32>(M->dzb, act_in, M->g + o, nullptr, N, in, B, N, in, in, s);
-        colsum_kernel<<<(N + 127) / 128, 128, 0, s>>>(dzf, B, N, M->g + o + (long long)N * in);
+        // dW_l [N x in] = dZ^T [N x B] * act_in [B x in] (K = B: split)
+        gemm_splitk<true, false>(M->dzb, act_in, M->g + o, M->part, N, in, B, N, in, s);
+        colsum_kernel<<<(N + 31) / 32, 1024, 0, s>>>(dzf, B, N, M->g + o + (long long)N * in);
         count_launch();
         if (l == 0) break;
         // dH_{l-1} [B x in] = dZ [B x N] * W_l [N x in]

@@ -49,13 +49,15 @@ def rollout_steps_plan(n_v: int, K: int, T: int, L: int) -> int:
 
 
 def kernel_source_digest() -> str:
-    """SHA-256 over the CUDA sources and ABI headers, so that a DRAM traffic
-    figure taken by ncu can be tied to the exact kernel it measured."""
+    """SHA-256 over the sources the plan kernel is compiled from (its
+    translation unit sgtp_plan.cu, every CUDA header and the ABI headers),
+    so that a DRAM traffic figure taken by ncu can be tied to the exact
+    kernel it measured."""
     import hashlib
     import os
     here = os.path.dirname(os.path.abspath(__file__))
-    files = []
-    for d, exts in ((os.path.join(here, "csrc"), (".cu", ".cuh", ".hpp")),
+    files = [os.path.join(here, "csrc", "sgtp_plan.cu")]
+    for d, exts in ((os.path.join(here, "csrc"), (".cuh", ".hpp")),
                     (os.path.join(os.path.dirname(here), "include"), (".h",))):
         files += sorted(os.path.join(d, f) for f in os.listdir(d) if f.endswith(exts))
     h = hashlib.sha256()
