@@ -647,7 +647,7 @@ int orc_best_response_mixed(const orc_params *p, const double *xr, const double 
 }
 
 /* Perturbed prediction of opponent jv as seen by vehicle `observer` in
- * round `round` (robustness study of Sec. IV, Table II; the paper's
+ * round `round` (robustness study of Sec. IV-F, Table II; the paper's
  * perturbation model is a cited one that is not available, so this is plain
  * Gaussian noise in Frenet coordinates, first order): every predicted
  * position p_tau, tau = 1..T, moves by sigma_lon z_1 along the unit direction

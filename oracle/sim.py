@@ -1,5 +1,5 @@
 """FP64 oracle of one closed-loop trial step (the receding-horizon
-evaluation setting of Sec. IV-A and its Evaluation Metrics subsection).
+racing scenarios of Sec. IV-B and the Evaluation Metrics of Sec. IV-C).
 
 TEST INFRASTRUCTURE ONLY: imported by the test-suite alone.  It shares no
 code with the CUDA path; the dynamics and the Frenet projection are the

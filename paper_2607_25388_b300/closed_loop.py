@@ -1,5 +1,5 @@
 """Closed-loop trials of SGTP and its two ablations on synthetic tracks
-(the evaluation of Sec. IV-A: Wins, CFW, FPR, CSD, D, mean ego speed, MCS,
+(the evaluation of Sec. IV-B and IV-C: Wins, CFW, FPR, CSD, D, mean ego speed, MCS,
 CT), one JSON line per planner.
 
     python -m paper_2607_25388_b300.closed_loop [--tracks 7 --starts 6 --seconds 50]

@@ -35,11 +35,8 @@ __host__ __device__ inline long long layer_off(int l, int out)
 }
 
 // ---------------------------------------------------------------- tensor-core GEMM
-// C[M x N] = A[M x K] * B[K x N] with BF16 operands and FP32 accumulation on
-// mma.sync.m16n8k16.  A is stored [M][K] (TA = false) or [K][M] (TA = true);
-// B is stored [N][K] (TB = true) or [K][N] (TB = false).  CTA tile 64 x 64,
-// K step 32, 4 warps of 32 x 32.  Epilogues: FP32 out (optionally + bias),
-// or BF16 out of ReLU(acc + bias).
+// C[M x N] = A[M x K] * B[K x N] with BF16 operands and FP32 accumulation
+// (gemm_kernel below).
 enum { EPI_F32 = 0, EPI_BIAS_RELU_BF16 = 1, EPI_BIAS_F32 = 2 };
 
 __device__ __forceinline__ void mma_bf16(float c[4], const unsigned a[4], const unsigned b[2])
@@ -51,6 +48,69 @@ __device__ __forceinline__ void mma_bf16(float c[4], const unsigned a[4], const 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void ldsm_x4(unsigned r[4], const bf16 *p)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x4_t(unsigned r[4], const bf16 *p)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+// One operand tile of a pipeline stage, copied in the global layout: ROWS
+// rows of COLS contiguous elements (row pitch PITCH in shared memory).
+// Element (r, c) is global (row0 + r, col0 + c), present when row0 + r <
+// row_lim and col0 + c < col_lim, else zero.  Whole 16-byte chunks are
+// asynchronous copies (zero-filled outside the matrix); a chunk cut by
+// col_lim, or any chunk when the rows are not 16-byte aligned, is copied
+// element by element.
+template <int ROWS, int COLS, int PITCH>
+__device__ __forceinline__ void load_tile(bf16 *dst, const bf16 *g, int ld, int row0, int row_lim, int col0,
+                                          int col_lim, bool vec_ok)
+{
+    constexpr int CPR = COLS / 8;
+    for (int q = threadIdx.x; q < ROWS * CPR; q += blockDim.x) {
+        const int r = q / CPR, c = (q - r * CPR) * 8;
+        bf16 *d = dst + r * PITCH + c;
+        const int gr = row0 + r, gc = col0 + c;
+        if (gr >= row_lim || gc >= col_lim) {
+            cp_async16(d, g, 0);
+        } else {
+            const bf16 *src = g + (size_t)gr * ld + gc;
+            if (vec_ok && gc + 8 <= col_lim) {
+                cp_async16(d, src, 16);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) d[e] = gc + e < col_lim ? src[e] : __float2bfloat16(0.f);
+            }
+        }
+    }
+}
+
+// C = A B on the tensor cores (mma.sync m16n8k16, BF16 in, FP32 accumulate).
+// A is stored [M][K] (TA = false) or [K][M] (TA = true); B is stored [N][K]
+// (TB = true) or [K][N] (TB = false).  CTA tile 64 x 64, K step 32, 4 warps
+// of 32 x 32; three pipeline stages of 16-byte asynchronous copies keep the
+// operands in their global layout in shared memory, and ldmatrix (.trans for
+// the M- or N-major operands) builds the mma fragments.  Epilogues: FP32 out
+// (optionally + bias), or BF16 out of ReLU(acc + bias).
 // Split K: CTA z of a grid with gridDim.z > 1 sums k in [z kchunk,
 // (z+1) kchunk) only and writes its FP32 partial product to Cv + z
 // part_stride (EPI_F32); splitk_reduce_kernel then adds the partials in z
@@ -60,15 +120,26 @@ __global__ void __launch_bounds__(128) gemm_kernel(const bf16 *__restrict__ A, c
                                                    const float *__restrict__ bias, int M, int N, int K, int lda,
                                                    int ldb, int ldc, int kchunk, long long part_stride)
 {
-    constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
-    __shared__ __align__(16) bf16 As[BM][BK + PAD];
-    __shared__ __align__(16) bf16 Bs[BN][BK + PAD];
+    constexpr int BM = 64, BN = 64, BK = 32, STAGES = 3;
+    constexpr int PA = TA ? BM + 8 : BK + 8;          // row pitch of the A tile (elements)
+    constexpr int PB = TB ? BK + 8 : BN + 8;          // row pitch of the B tile
+    constexpr int SA = TA ? BK * PA : BM * PA, SB = TB ? BN * PB : BK * PB;
+    __shared__ __align__(16) bf16 As[STAGES][SA];
+    __shared__ __align__(16) bf16 Bs[STAGES][SB];
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
     if (EPI == EPI_F32) Cv = (float *)Cv + blockIdx.z * part_stride;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
     const int g = lane >> 2, t = lane & 3;
+    const bool va = (lda & 7) == 0 && ((uintptr_t)A & 15) == 0;
+    const bool vb = (ldb & 7) == 0 && ((uintptr_t)B & 15) == 0;
+    auto load_stage = [&](int st, int k0) {
+        if (TA) load_tile<BK, BM, PA>(As[st], A, lda, k0, ke, m0, M, va);
+        else load_tile<BM, BK, PA>(As[st], A, lda, m0, M, k0, ke, va);
+        if (TB) load_tile<BN, BK, PB>(Bs[st], B, ldb, n0, N, k0, ke, vb);
+        else load_tile<BK, BN, PB>(Bs[st], B, ldb, k0, ke, n0, N, vb);
+    };
     float acc[2][4][4];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -76,49 +147,48 @@ __global__ void __launch_bounds__(128) gemm_kernel(const bf16 *__restrict__ A, c
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-    const bf16 zero = __float2bfloat16(0.f);
-    for (int k0 = kb; k0 < ke; k0 += BK) {
-        for (int e = threadIdx.x; e < BM * BK; e += blockDim.x) {
-            int m, k;
-            if (TA) { m = e % BM; k = e / BM; } else { k = e % BK; m = e / BK; }
-            const int gm = m0 + m, gk = k0 + k;
-            bf16 v = zero;
-            if (gm < M && gk < ke) v = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
-            As[m][k] = v;
-        }
-        for (int e = threadIdx.x; e < BN * BK; e += blockDim.x) {
-            int n, k;
-            if (TB) { k = e % BK; n = e / BK; } else { n = e % BN; k = e / BN; }
-            const int gn = n0 + n, gk = k0 + k;
-            bf16 v = zero;
-            if (gn < N && gk < ke) v = TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
-            Bs[n][k] = v;
-        }
+    const int nk = ke > kb ? (ke - kb + BK - 1) / BK : 0;
+#pragma unroll
+    for (int st = 0; st < STAGES - 1; ++st) {
+        if (st < nk) load_stage(st, kb + st * BK);
+        cp_async_commit();
+    }
+    for (int kt = 0; kt < nk; ++kt) {
+        cp_async_wait<STAGES - 2>();
         __syncthreads();
+        {
+            const int nt = kt + STAGES - 1;
+            if (nt < nk) load_stage(nt % STAGES, kb + nt * BK);
+            cp_async_commit();
+        }
+        const bf16 *as = As[kt % STAGES], *bs = Bs[kt % STAGES];
 #pragma unroll
         for (int kk = 0; kk < BK; kk += 16) {
             unsigned af[2][4], bfr[4][2];
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
-                const int r = wm + 16 * i + g;
-                af[i][0] = *(const unsigned *)&As[r][kk + 2 * t];
-                af[i][1] = *(const unsigned *)&As[r + 8][kk + 2 * t];
-                af[i][2] = *(const unsigned *)&As[r][kk + 8 + 2 * t];
-                af[i][3] = *(const unsigned *)&As[r + 8][kk + 8 + 2 * t];
+                if (TA)
+                    ldsm_x4_t(af[i], as + (kk + (lane & 7) + ((lane >> 4) << 3)) * PA + wm + 16 * i +
+                                         ((lane >> 3) & 1) * 8);
+                else
+                    ldsm_x4(af[i], as + (wm + 16 * i + (lane & 15)) * PA + kk + (lane >> 4) * 8);
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int c = wn + 8 * j + g;
-                bfr[j][0] = *(const unsigned *)&Bs[c][kk + 2 * t];
-                bfr[j][1] = *(const unsigned *)&Bs[c][kk + 8 + 2 * t];
+            for (int jp = 0; jp < 2; ++jp) {
+                const int nb = wn + 16 * jp;
+                unsigned r[4];
+                if (TB) ldsm_x4(r, bs + (nb + (lane & 7) + ((lane >> 4) << 3)) * PB + kk + ((lane >> 3) & 1) * 8);
+                else ldsm_x4_t(r, bs + (kk + (lane & 15)) * PB + nb + (lane >> 4) * 8);
+                bfr[2 * jp][0] = r[0]; bfr[2 * jp][1] = r[1];
+                bfr[2 * jp + 1][0] = r[2]; bfr[2 * jp + 1][1] = r[3];
             }
 #pragma unroll
             for (int i = 0; i < 2; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j]);
         }
-        __syncthreads();
     }
+    cp_async_wait<0>();
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll

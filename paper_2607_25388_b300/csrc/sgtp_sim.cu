@@ -4,7 +4,7 @@
 // each vehicle's plan (its controls, or pure pursuit on its trajectory),
 // steps every vehicle with the planner's kinematic bicycle, projects each one
 // on the globally nearest raceline segment (Sec. II), checks the ego's
-// contacts and keeps the sums behind the trial metrics of Sec. IV-A
+// contacts and keeps the sums behind the trial metrics of Sec. IV-C
 // (progress gains for Wins and FPR, duration, close-interaction segments for
 // CSD, ego speed, control smoothness for MCS).
 //

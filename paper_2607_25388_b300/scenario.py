@@ -244,7 +244,7 @@ def grid_race(track: TrackData, n_v: int, T: int, K: int, L: int, seed: int, s0=
 
 def trial_race(track: TrackData, n_v: int, T: int, K: int, L: int, seed: int, s0: float, gap_lo=8.0, gap_hi=20.0,
                v_lo=40.0, v_hi=55.0) -> Scenario:
-    """One closed-loop trial (Sec. IV-A): the ego (vehicle 0) starts behind
+    """One closed-loop trial (Sec. IV-B): the ego (vehicle 0) starts behind
     every opponent; opponent j starts gap_lo..gap_hi m ahead of the previous
     car, d ~ U(-3, 3) m; speeds U(v_lo, v_hi); headings along the raceline;
     reference speed scale 1 for the ego and 0.9 for the opponents."""

@@ -1,5 +1,5 @@
 """Closed-loop race trials on the GPU (receding horizon) and their metrics
-(Sec. IV-A, Evaluation Metrics).
+(Sec. IV-C, Evaluation Metrics).
 
 Every trial is one race of an ``sgtp_batch``.  Each control period runs one
 batched planning call (SGTP, SGTP without the game-aware cost, or the

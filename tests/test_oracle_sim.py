@@ -1,5 +1,5 @@
 """Pins of the closed-loop trial oracle (oracle/sim.py) against closed forms
-and hand-counted cases (the evaluation setting of Sec. IV-A)."""
+and hand-counted cases (the racing scenarios of Sec. IV-B, the metrics of Sec. IV-C)."""
 import math
 
 import numpy as np

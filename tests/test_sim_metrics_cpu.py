@@ -1,5 +1,5 @@
 """The trial metrics of the library (sim.trial_metrics, host logic) against
-the paper's definitions worked by hand (Sec. IV-A, Evaluation Metrics):
+the paper's definitions worked by hand (Sec. IV-C, Evaluation Metrics):
 Wins, CFW among the wins, FPR from the final unwrapped progress, durations,
 CSD, mean ego speed and MCS."""
 import numpy as np
