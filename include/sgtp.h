@@ -223,7 +223,8 @@ typedef struct sgtp_launch_opts {
                                      limit; default the limit)                       */
     int32_t window;               /* track segments staged in shared memory per CTA
                                      (rounded to a multiple of 4, at most 512)       */
-    int64_t wait_timeout_ns;      /* limit of each device-side wait (default 1 s)    */
+    int64_t wait_timeout_ns;      /* limit of each device-side wait (default: 20 x the
+                                     launch's work at 5e10 rollout-steps/s, >= 100 ms) */
     int32_t debug_flags;          /* SGTP_DEBUG_*; 0 in production                   */
     int32_t schedule;             /* SGTP_SCHEDULE_*; 0: default                     */
     int64_t *trace_ns;            /* optional DEVICE buffer of 3*L+8 int64: %globaltimer
@@ -551,6 +552,13 @@ const char *sgtp_version(void);
 /* Number of kernel launches this library has enqueued since load (all
  * entry points); used to count launches inside a timed region. */
 int64_t sgtp_launch_count(void);
+
+/* Fault injection for tests (host side): the n-th device allocation the
+ * library makes from now on (track, batch table, network, training scratch)
+ * fails as if the device were out of memory, so that the entry point under
+ * test returns SGTP_E_NOMEM after releasing what it had allocated; n <= 0
+ * disarms.  Process-wide; no device work is involved. */
+void sgtp_debug_fail_alloc(int32_t n);
 
 #ifdef __cplusplus
 }

@@ -107,6 +107,8 @@ def lib():
             L.sgtp_last_error.restype = C.c_char_p
             L.sgtp_version.restype = C.c_char_p
             L.sgtp_launch_count.restype = C.c_int64
+            L.sgtp_debug_fail_alloc.argtypes = [i32]
+            L.sgtp_debug_fail_alloc.restype = None
             L.sgtp_fma_probe.argtypes = [i32, i32, i32, vp, vp, C.POINTER(C.c_double)]
             L.sgtp_philox_words.argtypes = [u64, u32, u32, u32, u32, i32, vp, vp, vp]
             L.sgtp_noise_normals.argtypes = [u64, u32, u32, u32, u32, u32, i32, i32, vp, vp]
@@ -191,7 +193,7 @@ EXPORTS = [
     "sgtp_best_response_mixed", "sgtp_ibr_plan_learned", "sgtp_batch_plan_learned",
     "sgtp_plan_mppi_workspace_bytes", "sgtp_ibr_plan_mppi", "sgtp_batch_mppi_workspace_bytes",
     "sgtp_batch_plan_mppi", "sgtp_sim_reset", "sgtp_sim_step", "sgtp_ibr_plan_perturbed", "sgtp_batch_plan_perturbed",
-    "sgtp_fma_probe", "sgtp_philox_words", "sgtp_noise_normals",
+    "sgtp_fma_probe", "sgtp_philox_words", "sgtp_noise_normals", "sgtp_debug_fail_alloc",
 ]
 
 

@@ -56,6 +56,8 @@ extern "C" const char *sgtp_last_error(void) { return g_error.c_str(); }
 extern "C" const char *sgtp_version(void) { return "sgtp-b300 0.1 (sm_103a)"; }
 extern "C" int64_t sgtp_launch_count(void) { return (int64_t)g_launches.load(); }
 
+extern "C" void sgtp_debug_fail_alloc(int32_t n) { sgtp::fail_alloc_countdown().store(n > 0 ? n : 0); }
+
 // ================================================================ track prep
 // One CTA per track: per waypoint the sum of the unit chords meeting there
 // (bisector direction), per segment the chord, its inverse squared length,
@@ -159,14 +161,14 @@ static sgtp_status track_create_impl(const float *xr, const float *wl, const flo
         cudaFree(d_xr); cudaFree(d_wl); cudaFree(d_wr); cudaFree(d_off);
     };
     cudaError_t e = cudaSuccess;
-    if ((e = cudaMalloc(&T->A, sizeof(float4) * total)) || (e = cudaMalloc(&T->B, sizeof(float4) * total)) ||
-        (e = cudaMalloc(&T->W, sizeof(float4) * total)) || (e = cudaMalloc(&T->C, sizeof(float4) * total)) ||
-        (e = cudaMalloc(&T->S, sizeof(float) * total)) || (e = cudaMalloc(&T->G0, sizeof(float4) * total)) ||
-        (e = cudaMalloc(&T->G1, sizeof(float4) * total)) || (e = cudaMalloc(&T->G2, sizeof(float4) * total)) ||
-        (e = cudaMalloc(&T->G3, sizeof(float2) * total)) ||
-        (e = cudaMalloc(&T->desc_dev, sizeof(TrackDesc) * n_tracks)) ||
-        (e = cudaMalloc(&d_xr, sizeof(float) * 4 * total_src)) || (e = cudaMalloc(&d_wl, sizeof(float) * total_src)) ||
-        (e = cudaMalloc(&d_wr, sizeof(float) * total_src)) || (e = cudaMalloc(&d_off, sizeof(int) * n_tracks))) {
+    if ((e = dev_malloc(&T->A, sizeof(float4) * total)) || (e = dev_malloc(&T->B, sizeof(float4) * total)) ||
+        (e = dev_malloc(&T->W, sizeof(float4) * total)) || (e = dev_malloc(&T->C, sizeof(float4) * total)) ||
+        (e = dev_malloc(&T->S, sizeof(float) * total)) || (e = dev_malloc(&T->G0, sizeof(float4) * total)) ||
+        (e = dev_malloc(&T->G1, sizeof(float4) * total)) || (e = dev_malloc(&T->G2, sizeof(float4) * total)) ||
+        (e = dev_malloc(&T->G3, sizeof(float2) * total)) ||
+        (e = dev_malloc(&T->desc_dev, sizeof(TrackDesc) * n_tracks)) ||
+        (e = dev_malloc(&d_xr, sizeof(float) * 4 * total_src)) || (e = dev_malloc(&d_wl, sizeof(float) * total_src)) ||
+        (e = dev_malloc(&d_wr, sizeof(float) * total_src)) || (e = dev_malloc(&d_off, sizeof(int) * n_tracks))) {
         cleanup();
         sgtp_track_destroy(T);
         return set_error(SGTP_E_NOMEM, "track allocation failed: %s", cudaGetErrorString(e));
@@ -580,7 +582,7 @@ static sgtp_status br_common(const sgtp_track *trk, int32_t track_id, const sgtp
     a.agent_round = agent | (round << 16);
     a.race = race;
     a.game_on = game_on;
-    a.timeout_ns = 1000000000ll;
+    a.timeout_ns = default_wait_ns((double)K * T);
     maxo = maxo_bucket(n_opp);
     return SGTP_OK;
 }

@@ -121,4 +121,36 @@ sgtp_status once_per_device(PerDeviceFlag &flag, F step)
     return st;
 }
 
+// Default limit of each device-side wait of a launch that rolls out
+// `rollout_steps` candidate-steps: 20 times its duration at a pessimistic
+// 5e10 rollout-steps/s, at least 100 ms (the measured rate is about 1e11).
+inline long long default_wait_ns(double rollout_steps)
+{
+    const double est_ns = rollout_steps / 5e10 * 1e9;
+    const double lim = 20.0 * est_ns;
+    return lim > 1e8 ? (long long)lim : 100000000ll;
+}
+
+// Every device allocation of the library goes through dev_malloc, so that
+// a test can make the n-th next one fail as if the device were out of
+// memory (sgtp_debug_fail_alloc; 0 = never, the default).
+inline std::atomic<int> &fail_alloc_countdown()
+{
+    static std::atomic<int> c{0};
+    return c;
+}
+
+template <typename T>
+cudaError_t dev_malloc(T **p, size_t bytes)
+{
+    int c = fail_alloc_countdown().load();
+    while (c > 0 && !fail_alloc_countdown().compare_exchange_weak(c, c - 1)) {
+    }
+    if (c == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc((void **)p, bytes);
+}
+
 }  // namespace sgtp

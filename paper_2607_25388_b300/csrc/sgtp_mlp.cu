@@ -445,10 +445,10 @@ extern "C" sgtp_status sgtp_mlp_create(int32_t T, uint64_t seed, void *stream, s
     M->out = 4 * T;
     M->n_params = layer_off(4, M->out);
     cudaError_t e;
-    if ((e = cudaMalloc(&M->w, 4 * M->n_params)) || (e = cudaMalloc(&M->m, 4 * M->n_params)) ||
-        (e = cudaMalloc(&M->v, 4 * M->n_params)) || (e = cudaMalloc(&M->g, 4 * M->n_params)) ||
-        (e = cudaMalloc(&M->wb, 2 * M->n_params)) || (e = cudaMalloc(&M->loss, 4)) ||
-        (e = cudaMalloc(&M->wfrag, 2 * frag_off(4, M->out)))) {
+    if ((e = dev_malloc(&M->w, 4 * M->n_params)) || (e = dev_malloc(&M->m, 4 * M->n_params)) ||
+        (e = dev_malloc(&M->v, 4 * M->n_params)) || (e = dev_malloc(&M->g, 4 * M->n_params)) ||
+        (e = dev_malloc(&M->wb, 2 * M->n_params)) || (e = dev_malloc(&M->loss, 4)) ||
+        (e = dev_malloc(&M->wfrag, 2 * frag_off(4, M->out)))) {
         sgtp_mlp_destroy(M);
         return set_error(SGTP_E_NOMEM, "MLP allocation failed: %s", cudaGetErrorString(e));
     }
@@ -493,12 +493,12 @@ extern "C" sgtp_status sgtp_mlp_reserve(sgtp_mlp *M, int32_t batch)
     free_scratch(M);
     const size_t B = (size_t)batch, W = (size_t)(M->out > kHid ? M->out : kHid);
     cudaError_t e;
-    if ((e = cudaMalloc(&M->xb, 2 * B * kIn)) || (e = cudaMalloc(&M->h[0], 2 * B * kHid)) ||
-        (e = cudaMalloc(&M->h[1], 2 * B * kHid)) || (e = cudaMalloc(&M->h[2], 2 * B * kHid)) ||
-        (e = cudaMalloc(&M->dzb, 2 * B * W)) || (e = cudaMalloc(&M->dhb, 2 * B * W)) ||
-        (e = cudaMalloc(&M->outf, 4 * B * M->out)) || (e = cudaMalloc(&M->dout, 4 * B * M->out)) ||
-        (e = cudaMalloc(&M->dh, 4 * B * W)) || (e = cudaMalloc(&M->dzf, 4 * B * W)) ||
-        (e = cudaMalloc(&M->part, 4 * kSplitPartFloats))) {
+    if ((e = dev_malloc(&M->xb, 2 * B * kIn)) || (e = dev_malloc(&M->h[0], 2 * B * kHid)) ||
+        (e = dev_malloc(&M->h[1], 2 * B * kHid)) || (e = dev_malloc(&M->h[2], 2 * B * kHid)) ||
+        (e = dev_malloc(&M->dzb, 2 * B * W)) || (e = dev_malloc(&M->dhb, 2 * B * W)) ||
+        (e = dev_malloc(&M->outf, 4 * B * M->out)) || (e = dev_malloc(&M->dout, 4 * B * M->out)) ||
+        (e = dev_malloc(&M->dh, 4 * B * W)) || (e = dev_malloc(&M->dzf, 4 * B * W)) ||
+        (e = dev_malloc(&M->part, 4 * kSplitPartFloats))) {
         free_scratch(M);
         return set_error(SGTP_E_NOMEM, "MLP scratch allocation failed: %s", cudaGetErrorString(e));
     }

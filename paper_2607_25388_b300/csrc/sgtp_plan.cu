@@ -1204,6 +1204,11 @@ sgtp_status launch_plan_v(PlanArgs &a, int block, int ctas, int spt, cudaStream_
         a.items[e] = (e ? a.n_races : a.n_agents) * a.tiles[e];
         a.w[e] = (e ? a.w_units_ego : a.w_units_all) * a.tiles[e];
     }
+    if (a.timeout_ns <= 0) {
+        const double units = a.races ? (double)(a.L + 1) * a.w_units_all + (double)a.w_units_ego
+                                     : ((double)(a.L + 1) * a.n_agents + 1.0) * a.maxT;
+        a.timeout_ns = default_wait_ns(units * a.K);
+    }
     void *args[] = {&a};
     SGTP_CUDA(cudaMemsetAsync(a.bar, 0, 256, s));
     SGTP_CUDA(cudaMemsetAsync(a.status, 0, sizeof(int), s));
@@ -1290,7 +1295,7 @@ void fill_common(PlanArgs &a, const sgtp_track *trk, const sgtp_params *p, int K
     a.status = status;
     a.Wn = window_len(kWinTile, opts ? opts->window : 0);
     a.back = 48;
-    a.timeout_ns = (opts && opts->wait_timeout_ns > 0) ? opts->wait_timeout_ns : 1000000000ll;
+    a.timeout_ns = (opts && opts->wait_timeout_ns > 0) ? opts->wait_timeout_ns : 0;   // 0: derived at launch
     a.debug_flags = opts ? opts->debug_flags : 0;
     a.trace = opts ? (long long *)opts->trace_ns : nullptr;
 }
@@ -1501,7 +1506,7 @@ extern "C" sgtp_status sgtp_batch_create(const sgtp_track *trk, const sgtp_race 
         return set_error(SGTP_E_INVALID, "batch too large for 32-bit offsets");
     }
     b->agents = ag; b->u_elems = u; b->xi_elems = xi; b->ks = ks; b->n_pos = pos;
-    cudaError_t e = cudaMalloc(&b->races_dev, sizeof(RaceDev) * n_races);
+    cudaError_t e = dev_malloc(&b->races_dev, sizeof(RaceDev) * n_races);
     if (e != cudaSuccess) {
         delete b;
         return set_error(SGTP_E_NOMEM, "batch table allocation failed: %s", cudaGetErrorString(e));
