@@ -214,7 +214,8 @@ sgtp_status sgtp_best_response_noalloc(const sgtp_track *trk, int32_t track_id, 
  * (then 2 x 256 threads); a single learned-proposal plan takes the
  * 256-thread builds (2 per SM when its round has fewer 256-sample tiles than
  * 3 x SMs), a learned batch the 128-thread build; GA-IBR-MPPI takes the
- * 256-thread builds only. */
+ * 128-thread build with two samples per thread (a tile is then its 256
+ * samples) unless its round is small, or the 256-thread builds with one. */
 typedef struct sgtp_launch_opts {
     int32_t block;                /* threads per CTA: 128 or 256 (0: default)        */
     int32_t samples_per_thread;   /* 0 .. 3: samples each thread rolls out at once

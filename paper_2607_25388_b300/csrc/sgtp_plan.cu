@@ -693,7 +693,8 @@ __device__ void mppi_update(const PlanArgs &a, int ag, int T, size_t uo, int rou
 //           each other's latency, and 168 registers hold three of them.
 // Every mode computes every sample with the same code.  MPPI selects the
 // GA-IBR-MPPI update (a build of its own, so that the SGTP builds carry none
-// of its code; kWide3 and kWide2 only).
+// of its code); its kIlp build rolls two samples per thread, so that a tile
+// is the 256 samples of its path-integral partial sums in every build.
 constexpr int kWide3 = 0, kWide2 = 1, kIlp = 2;
 
 template <int MAXO, int MODE, bool MPPI>
@@ -705,15 +706,17 @@ __global__ void __launch_bounds__(256, MINB) plan_kernel(PlanArgs a)
     plan_body<MAXO, MINB == 3 ? kWide3 : kWide2, MPPI>(a);
 }
 
-template <int MAXO>
+template <int MAXO, bool MPPI>
 __global__ void __launch_bounds__(128, 3) plan_kernel_ilp(PlanArgs a)
 {
-    plan_body<MAXO, kIlp, false>(a);
+    plan_body<MAXO, kIlp, MPPI>(a);
 }
 
 // Selection key of the NI candidates k0 + i blockDim of this thread (all
-// threads of the tile call it; candidates k >= K key as ~0).
-template <int MAXO, int NI>
+// threads of the tile call it; candidates k >= K key as ~0).  GA-IBR-MPPI
+// keys every sample as feasible and keeps each sample's cost (+inf when not
+// finite or k >= K) at its place in the tile for the partial sums.
+template <int MAXO, int NI, bool MPPI = false>
 __device__ __forceinline__ unsigned long long tile_keys(const BRScalars &S, const PlanArgs &a, unsigned k0, int round,
                                                         int &flag)
 {
@@ -725,8 +728,12 @@ __device__ __forceinline__ unsigned long long tile_keys(const BRScalars &S, cons
     unsigned long long best = ~0ull;
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
-        const unsigned long long key = make_key(r[i].feasible, r[i].cost, r[i].viol, kk[i]);
+        const unsigned long long key = make_key(r[i].feasible || MPPI, r[i].cost, r[i].viol, kk[i]);
         if (kk[i] < (unsigned)a.K && key < best) best = key;
+        if constexpr (MPPI) {
+            const bool fin = kk[i] < (unsigned)a.K && fabsf(r[i].cost) <= 3.402823466e38f;
+            ((float *)Tile<MAXO>::st())[threadIdx.x + i * blockDim.x] = fin ? r[i].cost : __int_as_float(0x7f800000);
+        }
     }
     return best;
 }
@@ -972,7 +979,9 @@ __device__ __forceinline__ void plan_body(const PlanArgs &a)
             // cost) and keeps the tile's costs for its partial sums
             constexpr bool mppi = MPPI;
             unsigned long long best = ~0ull;
-            if constexpr (MODE == kIlp) {
+            if constexpr (MODE == kIlp && MPPI) {
+                best = tile_keys<MAXO, 2, true>(S, a, (unsigned)t * a.tile[extra] + threadIdx.x, round, flag);
+            } else if constexpr (MODE == kIlp) {
                 const unsigned k0 = (unsigned)t * a.tile[extra] + threadIdx.x;
                 const int ni = a.ni[extra];
                 if (ni == 3) best = tile_keys<MAXO, 3>(S, a, k0, round, flag);
@@ -1134,7 +1143,7 @@ int maxo_bucket(int n) { return n <= 1 ? 1 : n <= 3 ? 3 : n <= 9 ? 9 : 15; }
 template <int MAXO, int MODE, bool MPPI>
 const void *plan_kernel_of()
 {
-    if constexpr (MODE == kIlp) return (const void *)plan_kernel_ilp<MAXO>;
+    if constexpr (MODE == kIlp) return (const void *)plan_kernel_ilp<MAXO, MPPI>;
     else return (const void *)plan_kernel<MAXO, MODE == kWide3 ? 3 : 2, MPPI>;
 }
 
@@ -1156,7 +1165,7 @@ sgtp_status configure_plan_maxo()
     sgtp_status st;
     if ((st = configure_plan_t<MAXO, kWide3, false>()) || (st = configure_plan_t<MAXO, kWide2, false>()) ||
         (st = configure_plan_t<MAXO, kIlp, false>()) || (st = configure_plan_t<MAXO, kWide3, true>()) ||
-        (st = configure_plan_t<MAXO, kWide2, true>()))
+        (st = configure_plan_t<MAXO, kWide2, true>()) || (st = configure_plan_t<MAXO, kIlp, true>()))
         return st;
     return SGTP_OK;
 }
@@ -1190,7 +1199,9 @@ sgtp_status launch_plan_v(PlanArgs &a, int block, int ctas, int spt, cudaStream_
     const long long cand[2] = {(long long)a.n_agents * a.K, (long long)a.n_races * a.K};
     for (int e = 0; e < 2; ++e) {
         int ni = 1;
-        if (MODE == kIlp) {
+        if (MODE == kIlp && MPPI) {
+            ni = 2;                       // a tile is the 256 samples of the partial sums
+        } else if (MODE == kIlp) {
             const long long slots = (long long)grid * block;
             ni = spt > 0 ? spt : (int)std::min(3ll, std::max(1ll, (cand[e] + slots - 1) / slots));
             if (spt == 0 && cand[e] > 3 * slots) {
@@ -1225,7 +1236,7 @@ sgtp_status launch_plan_v(PlanArgs &a, int block, int ctas, int spt, cudaStream_
 // when a Jacobi round has fewer 256-sample tiles than three CTAs per SM
 // could take at once, else kWide3; a learned batch runs kIlp (its proposal
 // items overlap other races' tiles under the queue schedule); GA-IBR-MPPI
-// takes the wide builds only.  Options override: block 128 (or
+// runs kIlp with two samples per thread unless its round is small.  Options override: block 128 (or
 // samples_per_thread > 1) selects kIlp, block 256 the wide builds
 // (ctas_per_sm <= 2: kWide2).
 template <int MAXO>
@@ -1239,13 +1250,16 @@ sgtp_status launch_plan_t(PlanArgs &a, const sgtp_launch_opts *opts, cudaStream_
     SGTP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const bool mppi = a.mppi_il > 0.f;
     const bool learned = a.mlp_wb != nullptr || a.feat_out != nullptr;
-    SGTP_CHECK(!(mppi && (spt > 1 || block == 128)), "GA-IBR-MPPI takes 256-thread CTAs, one sample per thread");
+    SGTP_CHECK(!(mppi && (spt == 3 || (block == 128 && spt == 1))),
+               "GA-IBR-MPPI rolls two samples per thread with 128-thread CTAs, one with 256");
     // a round of at most one 256-thread CTA's worth of samples per SM runs
     // the wide 128-register build by default (measured faster there)
     const int sched = opts ? opts->schedule : SGTP_SCHEDULE_DEFAULT;
     a.queue = sched == SGTP_SCHEDULE_QUEUE || (sched == SGTP_SCHEDULE_DEFAULT && a.races != nullptr);
     const bool small = (long long)a.n_agents * a.K <= 256ll * sms;
-    const bool ilp = !mppi && (block == 128 || spt > 1 || (block == 0 && !small && (!learned || a.races)));
+    const bool ilp = mppi ? (block == 128 || spt == 2 || (block == 0 && spt == 0 && !small))
+                          : (block == 128 || spt > 1 || (block == 0 && !small && (!learned || a.races)));
+    if (ilp && mppi) return launch_plan_v<MAXO, kIlp, true>(a, 128, ctas, 2, s);
     if (ilp) return launch_plan_v<MAXO, kIlp, false>(a, 128, ctas, spt, s);
     block = 256;
     const bool wide2 = ctas > 0 ? ctas <= 2 : (long long)((a.K + 255) / 256) * a.n_agents < 3ll * sms;

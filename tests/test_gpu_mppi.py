@@ -134,11 +134,14 @@ def test_launch_shape_invariance():
     sc = S.ten_car_race(204, K=1500, T=40, L=1)
     p = S.params_fullscale()
     ref = gpu_plan(sc, p, 1500, 1, seed=2, lam=5e4)
-    for block, ctas in ((256, 3), (256, 1), (256, 2)):
-        o = P.launch_opts(block=block, samples_per_thread=1, ctas_per_sm=ctas)
+    for block, spt, ctas in ((256, 1, 3), (256, 1, 1), (256, 1, 2), (128, 2, 0), (128, 0, 1), (0, 2, 0)):
+        o = P.launch_opts(block=block, samples_per_thread=spt, ctas_per_sm=ctas)
         g = gpu_plan(sc, p, 1500, 1, seed=2, lam=5e4, opts=o)
         for k in ("k_star", "U", "xi", "xi_hist", "u_hist"):
-            np.testing.assert_array_equal(g[k], ref[k], err_msg=f"{k} block {block} ctas {ctas}")
+            np.testing.assert_array_equal(g[k], ref[k], err_msg=f"{k} block {block} x {spt} ctas {ctas}")
+    for bad in (dict(block=128, samples_per_thread=1), dict(samples_per_thread=3)):
+        with pytest.raises(RuntimeError, match="SGTP_E_INVALID"):
+            gpu_plan(sc, p, 1500, 1, seed=2, lam=5e4, opts=P.launch_opts(**bad))
 
 
 def test_batch_equals_single_race_plans():
