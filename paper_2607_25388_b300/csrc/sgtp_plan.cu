@@ -364,7 +364,7 @@ __device__ void compute_features(const PlanArgs &a, const RaceDev &R, int i, int
     }
     if (tid == 0) {
         const float4 c0 = __ldg(tv.C + A.j0);
-        const float e = wrap_angle(A.x0.z - (c0.x + A.t0 * c0.y));
+        const float e = wrap_angle(__fsub_rn(A.x0.z, __fmaf_rn(A.t0, c0.y, c0.x)));
         float sn, cs;
         sincosf(e, &sn, &cs);
         f[0] = A.d_t / 5.f;
@@ -381,7 +381,7 @@ __device__ void compute_features(const PlanArgs &a, const RaceDev &R, int i, int
         const int N = tv.N;
         auto sj = [&](int j) {
             const int lap = j >= 0 ? j / N : -((-j + N - 1) / N);
-            return __ldg(tv.S + (j - lap * N)) + (float)lap * tv.L;
+            return __fmaf_rn((float)lap, tv.L, __ldg(tv.S + (j - lap * N)));
         };
         int j = A.j0 + (int)(ahead / __ldg(tv.B + A.j0).w);
         for (int it = 0; it < 4 * N && sj(j) > tgt; ++it) --j;
@@ -400,14 +400,14 @@ __device__ void compute_features(const PlanArgs &a, const RaceDev &R, int i, int
         }
         if (rank < 9) {
             const float prog = __ldcg(a.summ[bin] + R.agent_off + jo).x;
-            const float horizon_gain = A.x0.w * (float)R.T * a.p.dt;
+            const float horizon_gain = __fmul_rn(__fmul_rn(A.x0.w, (float)R.T), a.p.dt);
             float *o = f + 8 + 6 * rank;
             o[0] = 1.f;
             o[1] = ds / 40.f;
             o[2] = B.d_t / 5.f;
             o[3] = (B.x0.w - A.x0.w) / 10.f;
             o[4] = wrap_angle(B.x0.z - A.x0.z);
-            o[5] = (prog - horizon_gain) / 40.f;
+            o[5] = __fdiv_rn(__fsub_rn(prog, horizon_gain), 40.f);
         }
     }
     for (int q = tid; q < 9 * 6; q += blockDim.x)
@@ -545,8 +545,10 @@ __device__ __forceinline__ float2 perturb_point(const PlanArgs &a, float2 p, flo
                                                 unsigned ar, unsigned race)
 {
     const float2 z = pred_noise(a.key, jv, tau, ar, race);
-    const float ds = a.sig_lon * z.x, dd = a.sig_lat * z.y;
-    return make_float2(p.x + ds * t.x - dd * t.y, p.y + ds * t.y + dd * t.x);
+    // explicitly rounded operations: every build gives the same bits
+    const float ds = __fmul_rn(a.sig_lon, z.x), dd = __fmul_rn(a.sig_lat, z.y);
+    return make_float2(__fsub_rn(__fmaf_rn(ds, t.x, p.x), __fmul_rn(dd, t.y)),
+                       __fmaf_rn(dd, t.x, __fmaf_rn(ds, t.y, p.y)));
 }
 
 // ---------------------------------------------------------------- GA-IBR-MPPI
@@ -952,11 +954,11 @@ __device__ __forceinline__ void plan_body(const PlanArgs &a)
                     float2 sm = __ldcg(a.summ[bin] + R.agent_off + jv);
                     if (tin) {
                         // the perturbed prediction's progress gain and tail-mean offset
-                        sm.x += a.sig_lon * pred_noise(a.key, (unsigned)jv, T, ar, R.race_tag).x;
+                        sm.x = __fmaf_rn(a.sig_lon, pred_noise(a.key, (unsigned)jv, T, ar, R.race_tag).x, sm.x);
                         float dsum = 0.f;
                         for (int tau = T - R.n_tail + 1; tau <= T; ++tau)
-                            dsum += a.sig_lat * pred_noise(a.key, (unsigned)jv, tau, ar, R.race_tag).y;
-                        sm.y += dsum / (float)R.n_tail;
+                            dsum = __fmaf_rn(a.sig_lat, pred_noise(a.key, (unsigned)jv, tau, ar, R.race_tag).y, dsum);
+                        sm.y = __fadd_rn(sm.y, __fdiv_rn(dsum, (float)R.n_tail));
                     }
                     const float ds_t = wrap_len(A.s_t - B.s_t, tv.L, 1.0f / tv.L);
                     const float alpha = 1.0f / (1.0f + fabsf(ds_t) / (a.p.s_contest + a.p.eps_alpha));

@@ -529,22 +529,25 @@ __device__ __forceinline__ SampleResult finish_terms(float c_track, float s, flo
                                                      const BRScalars &S, const sgtp_params &p, bool game_on)
 {
     using T = Tile<MAXO>;
-    const float dbar_i = d_tail / (float)S.n_tail;
-    const float prog_i = s - S.s_t;
+    const float dbar_i = __fdiv_rn(d_tail, (float)S.n_tail);
+    const float prog_i = __fsub_rn(s, S.s_t);
     float c_game = 0.f;
     float rho_obs = __int_as_float(0x7f800000);
 #pragma unroll
     for (int o = 0; o < MAXO; ++o) {
         if (o < S.n_opp) {
+            // every operation explicitly rounded (no fused contraction left
+            // to the compiler), so that all builds give the same bits
             const float4 os = T::osum()[o];          // ds_t, alpha, gamma, prog_j
-            const float ds_H = os.x + (prog_i - os.w);
+            const float ds_H = __fadd_rn(os.x, __fsub_rn(prog_i, os.w));
             const float c_contest = fabsf(ds_H) < p.s_contest ? -p.w_contest : 0.f;
-            const float c_long = -p.w_long * os.y * ds_H;
-            const float c_block = os.z != 0.f ? -os.z / (1.f + fabsf(dbar_i - T::odbar()[o])) : 0.f;
+            const float c_long = __fmul_rn(__fmul_rn(-p.w_long, os.y), ds_H);
+            const float c_block =
+                os.z != 0.f ? __fdiv_rn(-os.z, __fadd_rn(1.f, fabsf(__fsub_rn(dbar_i, T::odbar()[o])))) : 0.f;
             const float g = sqrtf(g2[o]);
-            const float sh = fmaxf(0.f, p.g_safe - g);
-            const float c_safety = p.w_safety * sh * sh;
-            c_game = c_game + (c_contest + c_long + c_block + c_safety);
+            const float sh = fmaxf(0.f, __fsub_rn(p.g_safe, g));
+            const float c_safety = __fmul_rn(__fmul_rn(p.w_safety, sh), sh);
+            c_game = __fadd_rn(c_game, __fadd_rn(__fadd_rn(__fadd_rn(c_contest, c_long), c_block), c_safety));
             rho_obs = fminf(rho_obs, g);
         }
     }
@@ -553,7 +556,7 @@ __device__ __forceinline__ SampleResult finish_terms(float c_track, float s, flo
     const bool b = rho_bd >= p.m_bd;
     const bool ob = rho_obs >= p.d_col;
     r.feasible = b && ob;
-    r.viol = fmaxf(0.f, p.m_bd - rho_bd) + fmaxf(0.f, p.d_col - rho_obs);
+    r.viol = __fadd_rn(fmaxf(0.f, __fsub_rn(p.m_bd, rho_bd)), fmaxf(0.f, __fsub_rn(p.d_col, rho_obs)));
     return r;
 }
 
