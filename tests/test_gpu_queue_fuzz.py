@@ -99,3 +99,31 @@ def test_learned_batches_are_identical_across_schedules_and_builds(seed):
     for r in runs[1:]:
         for k in ("xi", "k_star", "U", "xi_hist", "u_hist"):
             np.testing.assert_array_equal(r[k], runs[0][k], err_msg=f"seed {seed} {k}")
+
+
+def test_repeated_queue_launches_are_identical():
+    """Under the queue schedule the CTA that runs an item changes from launch
+    to launch; five launches of one batch (plain and GA-IBR-MPPI) must still
+    give the same bits, so no reduction or hand-off depends on timing."""
+    Pm = P()
+    races, K, L = _batch(11)
+    trk = Pm.Track.from_many([sc.track for sc in races])
+    b = Pm.Batch(trk, [dict(track_id=r, n_v=sc.X0.shape[0], T=sc.T, ego=sc.ego, race_tag=r)
+                       for r, sc in enumerate(races)], K=K, L=L)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a)).cuda()
+    X0 = dev(np.concatenate([sc.X0 for sc in races]))
+    U0 = np.concatenate([sc.U0.reshape(-1) for sc in races])
+    vs = dev(np.concatenate([sc.vref_scale for sc in races]))
+    for kw in (dict(), dict(mppi_lambda=5e3)):
+        ref = None
+        for _ in range(5):
+            U = dev(U0)
+            out = b.plan(S.params_fullscale(), X0, U, vs, seed=3, want_hist=True,
+                         opts=Pm.launch_opts(schedule=Pm.SCHEDULE_QUEUE), **kw)
+            torch.cuda.synchronize()
+            got = {k: v.cpu().numpy() for k, v in out.items()} | {"U": U.cpu().numpy()}
+            assert got["status"][0] == 0
+            if ref is None:
+                ref = got
+            for k in ("xi", "k_star", "U", "xi_hist", "u_hist"):
+                np.testing.assert_array_equal(got[k], ref[k], err_msg=f"{kw} {k}")
