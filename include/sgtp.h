@@ -205,7 +205,7 @@ sgtp_status sgtp_best_response_noalloc(const sgtp_track *trk, int32_t track_id, 
  *     samples_per_thread, or, when 0, chosen per round as the fewest that
  *     put the round's samples in one wave of the grid (at most 3) -- for a
  *     round of several waves even at 3, 2 or 3, whichever pads K less to
- *     whole tiles;
+ *     whole tiles, except a plain batch under the queue schedule (3);
  *   - 256-thread CTAs with one sample per thread: 3 per SM with 80
  *     registers, or (ctas_per_sm <= 2) 2 per SM with 128 registers.
  * Samples are processed in tiles of block x samples_per_thread consecutive

@@ -1197,7 +1197,11 @@ sgtp_status launch_plan_v(PlanArgs &a, int block, int ctas, int spt, cudaStream_
     // tiles of each round kind: kIlp rolls out ni samples per thread at once,
     // the fewest that fit the round's samples in one wave of the grid (at
     // most 3); a round of several waves even at 3 takes 2 or 3, whichever
-    // pads K less to whole tiles (ties: 3); unless the caller fixed it
+    // pads K less to whole tiles (ties: 3) -- except a plain batch under the
+    // queue schedule, which keeps 3 (measured: the dynamic balance and the
+    // third interleaved sample repay up to 3 % of padding, while a learned
+    // batch's proposal items overlap better with the finer tiles); unless
+    // the caller fixed it
     const long long cand[2] = {(long long)a.n_agents * a.K, (long long)a.n_races * a.K};
     for (int e = 0; e < 2; ++e) {
         int ni = 1;
@@ -1206,7 +1210,8 @@ sgtp_status launch_plan_v(PlanArgs &a, int block, int ctas, int spt, cudaStream_
         } else if (MODE == kIlp) {
             const long long slots = (long long)grid * block;
             ni = spt > 0 ? spt : (int)std::min(3ll, std::max(1ll, (cand[e] + slots - 1) / slots));
-            if (spt == 0 && cand[e] > 3 * slots) {
+            const bool keep3 = a.queue && !(a.mlp_wb || a.feat_out);
+            if (spt == 0 && cand[e] > 3 * slots && !keep3) {
                 auto padded = [&](int n) { return (long long)((a.K + block * n - 1) / (block * n)) * block * n; };
                 if (padded(2) < padded(3)) ni = 2;
             }
