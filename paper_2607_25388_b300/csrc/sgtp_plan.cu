@@ -1,17 +1,23 @@
 // sgtp_plan.cu -- the SGTP planning call (Alg. 1) as one persistent
 // cooperative kernel, for one race or a batch of independent races.
 //
-// Phases of the kernel (grid barriers in between):
+// Phases of the kernel:
 //   setup   : per vehicle, Frenet of x_{i,t} (global search), reference
 //             trajectory (Sec. III-A), nominal rollout of the current U-bar
-//             = the opponents' predictions for round 0;
+//             = the opponents' predictions for round 0 (then a grid
+//             barrier);
+//   proposal: with the learned proposal, per vehicle, features, network and
+//             the per-step Gaussian of its next best response;
 //   round r : every (race, vehicle, sample tile) item evaluates its samples
 //             and folds their selection keys into the best response's key;
 //   winner r: per vehicle, re-roll of the selected sample k*, warm start
 //             U-bar <- U^(k*) (Alg. 1, update step), and the new prediction
 //             (positions, progress gain, tail offset) for the next round.
 // Rounds 0..L are Jacobi rounds over all vehicles (round 0 without the game
-// term); round L+1 is the extra ego response.
+// term); round L+1 is the extra ego response.  Under the lock-step schedule
+// a grid barrier separates the phases; under the queue schedule the items
+// are claimed from one device counter and wait only for their own race's
+// (or vehicle's) earlier items (see wait_count / signal_done).
 #include <cmath>
 #include <cstring>
 
