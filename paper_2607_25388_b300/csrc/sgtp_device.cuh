@@ -255,18 +255,43 @@ __device__ __forceinline__ int chord_guess(float dx, float dy, float4 b, int cap
     return __fmaf_rn(dx, b.x, dy * b.y) < 0.0f ? -n : n;
 }
 
+// Segments of one brute-force pass that a thread loads before it evaluates
+// them: the pass over a cold track then waits for a few memory round trips
+// instead of one per segment.
+constexpr int kScanBatch = 8;
+
+// This thread's minimum key (squared distance bits, segment) over segments
+// j0, j0 + step, ... < N; out-of-range slots of the last batch load segment
+// N - 1 and are ignored.
+__device__ __forceinline__ unsigned long long nearest_scan(const TrackView &tv, float px, float py, int j0, int step)
+{
+    unsigned long long best = ~0ull;
+    for (int jb = j0; jb < tv.N; jb += kScanBatch * step) {
+        float4 va[kScanBatch], vb[kScanBatch];
+#pragma unroll
+        for (int u = 0; u < kScanBatch; ++u) {
+            const int j = min(jb + u * step, tv.N - 1);
+            va[u] = __ldg(tv.A + j);
+            vb[u] = __ldg(tv.B + j);
+        }
+#pragma unroll
+        for (int u = 0; u < kScanBatch; ++u) {
+            const int j = jb + u * step;
+            float t, cr;
+            const float d2 = seg_dist2(va[u], vb[u], px, py, t, cr);
+            const unsigned long long key = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)j;
+            if (j < tv.N && key < best) best = key;
+        }
+    }
+    return best;
+}
+
 // Global nearest segment by brute force over all N segments, cooperatively by
 // one warp (lowest index on ties).  Used once per vehicle state x_{i,t}.
 __device__ __forceinline__ int nearest_segment_warp(const TrackView &tv, float px, float py)
 {
     const int lane = threadIdx.x & 31;
-    unsigned long long best = ~0ull;
-    for (int j = lane; j < tv.N; j += 32) {
-        float t, cr;
-        const float d2 = seg_dist2(__ldg(tv.A + j), __ldg(tv.B + j), px, py, t, cr);
-        const unsigned long long key = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)j;
-        best = key < best ? key : best;
-    }
+    unsigned long long best = nearest_scan(tv, px, py, lane, 32);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
@@ -281,13 +306,7 @@ __device__ __forceinline__ int nearest_segment_cta(const TrackView &tv, float px
 {
     if (threadIdx.x == 0) *key_sh = ~0ull;
     __syncthreads();
-    unsigned long long best = ~0ull;
-    for (int j = threadIdx.x; j < tv.N; j += blockDim.x) {
-        float t, cr;
-        const float d2 = seg_dist2(__ldg(tv.A + j), __ldg(tv.B + j), px, py, t, cr);
-        const unsigned long long key = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)j;
-        best = key < best ? key : best;
-    }
+    unsigned long long best = nearest_scan(tv, px, py, threadIdx.x, blockDim.x);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);

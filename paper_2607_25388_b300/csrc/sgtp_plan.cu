@@ -281,6 +281,38 @@ __device__ bool grid_barrier(const PlanArgs &a, bool skip_arrival)
 __shared__ const float4 *g_win_track;
 __shared__ int g_win_w0, g_win_lap0, g_win_fix;
 
+// Segments of track from a vehicle's own segment that the setup stages for
+// its reference recursion (vertex, chord, arc length and the heading/speed
+// coefficients; 52 bytes each, in the tile's scratch area).  A 60-step
+// reference at up to 3 m per step spans about 100 segments of 1.8 m, and the
+// recursion's block of 32 lanes reaches up to 31 segments past its progress;
+// whatever lies beyond the staged stretch is read from global memory.
+constexpr int kRefSegs = 152;
+
+// Stage the reference stretch of track from segment j0 (all threads; the
+// caller synchronises before the window is read).  Copies the same values
+// that the recursion would read from global memory, so the reference is
+// unchanged bit for bit.
+template <int MAXO>
+__device__ __forceinline__ SegWindow stage_ref_window(const TrackView &tv, int j0, const float4 *&Cw)
+{
+    static_assert(kRefSegs * 52 <= (int)BRTile<MAXO>::kScrBytes, "reference stretch exceeds the scratch area");
+    float4 *A = (float4 *)Tile<MAXO>::scratch();
+    float4 *B = A + kRefSegs;
+    float4 *C = B + kRefSegs;
+    float *Sv = (float *)(C + kRefSegs);
+    const int Wn = min(kRefSegs, tv.N);
+    for (int r = threadIdx.x; r < Wn; r += blockDim.x) {
+        const int g = wrap_index(j0 + r, tv.N);
+        A[r] = __ldg(tv.A + g);
+        B[r] = __ldg(tv.B + g);
+        C[r] = __ldg(tv.C + g);
+        Sv[r] = __ldg(tv.S + g);
+    }
+    Cw = C;
+    return SegWindow{A, B, nullptr, Sv, j0, Wn};
+}
+
 // Stage the sample window of a vehicle whose state lies on segment j0
 // (thread 0 issues the bulk copies and returns true; every thread then
 // calls window_ready) and fill the tile scalars' window fields.  The window
@@ -776,27 +808,31 @@ __device__ __forceinline__ void plan_body(const PlanArgs &a)
         const TrackView tv = get_track(a, R.track_id);
         const float4 x0 = make_float4(a.X0[4 * ag], a.X0[4 * ag + 1], a.X0[4 * ag + 2], a.X0[4 * ag + 3]);
         __syncthreads();
-        {
-            const int j = nearest_segment_cta(tv, x0.x, x0.y, &cta_key);
-            if (threadIdx.x == 0) j0_sh = j;
-        }
         for (int q = threadIdx.x; q < R.T; q += blockDim.x) {
             // nominal controls, clipped: the zero-noise sample
             const float *U = a.U_io + R.u_off + (size_t)i * R.T * 2;
             Tl::ctl()[q] = sample_control(a.p, make_float2(U[2 * q], U[2 * q + 1]), make_float2(0.f, 0.f));
         }
+        {
+            const int j = nearest_segment_cta(tv, x0.x, x0.y, &cta_key);
+            if (threadIdx.x == 0) j0_sh = j;
+        }
         __syncthreads();
         const int j0 = j0_sh;
-        window_ready<MAXO>(a, stage_vehicle_window<MAXO>(a, tv, j0), phase);
+        // the window copy, the reference stretch and x0's projection are
+        // all in flight before the CTA waits for the copy
+        const bool issued = stage_vehicle_window<MAXO>(a, tv, j0);
+        const float4 *ref_c;
+        const SegWindow ref_w = stage_ref_window<MAXO>(tv, j0, ref_c);
         const FrenetPt f = frenet_at(tv, j0, x0.x, x0.y);
+        window_ready<MAXO>(a, issued, phase);
         AgentDev A;
         A.x0 = x0; A.s_t = f.s; A.d_t = f.d; A.j0 = j0; A.race = ri; A.t0 = f.t;
         if ((threadIdx.x >> 5) == 1) {
-            // reference recursion (warp 1, track from global memory) alongside
-            // the nominal rollout's dynamics (warp 0)
+            // reference recursion (warp 1, the staged stretch of track)
+            // alongside the nominal rollout's dynamics (warp 0)
             if (threadIdx.x == 32) a.agents[ag] = A;
-            const SegWindow none{nullptr, nullptr, nullptr, nullptr, 0, 0};
-            reference_traj(tv, none, nullptr, j0, f.s, a.p.dt, a.vref[ag], R.T,
+            reference_traj(tv, ref_w, ref_c, j0, f.s, a.p.dt, a.vref[ag], R.T,
                            a.ref + (size_t)R.pos_off + (size_t)i * (R.T + 1));
         }
         roll_cooperative<MAXO>(a.p, x0, f.s, j0, R.T, R.n_tail, a.pos[0] + R.pos_off + (size_t)i * (R.T + 1), nullptr,
