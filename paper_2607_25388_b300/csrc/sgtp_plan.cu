@@ -787,7 +787,7 @@ __device__ __forceinline__ void plan_body(const PlanArgs &a)
     __shared__ unsigned ks_sh;
     BRScalars &S = Tl::sc();
 
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const bool skip = (a.debug_flags & SGTP_DEBUG_SKIP_BARRIER_ARRIVAL) && blockIdx.x == 0;
     int flag = 0;
     unsigned phase = 0;
