@@ -209,7 +209,11 @@ sgtp_status sgtp_best_response_noalloc(const sgtp_track *trk, int32_t track_id, 
  *   - 256-thread CTAs with one sample per thread: 3 per SM with 80
  *     registers, or (ctas_per_sm <= 2) 2 per SM with 128 registers.
  * Samples are processed in tiles of block x samples_per_thread consecutive
- * k (GA-IBR-MPPI: tiles of 256).  Defaults: a plain plan takes the
+ * k (GA-IBR-MPPI: tiles of 256); a round whose samples fit the grid twice
+ * over at one per thread takes half tiles, one sample for each thread of a
+ * CTA's first half (the 128-thread build when samples_per_thread is 0, the
+ * 256-thread builds always), so that its lone-sample chains spread over
+ * twice the CTAs.  Defaults: a plain plan takes the
  * 128-thread build unless its Jacobi round holds at most 256 x SMs samples
  * (then 2 x 256 threads); a single learned-proposal plan takes the
  * 256-thread builds (2 per SM when its round has fewer 256-sample tiles than

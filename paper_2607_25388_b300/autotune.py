@@ -94,7 +94,7 @@ def _opts(ent):
 
 def _tiles(K: int, block: int, spt: int):
     """Work items (tiles) per best response of a fixed shape (None when the
-    library chooses samples per thread per round)."""
+    library chooses samples per thread, and with it the tile, per round)."""
     if block == 0 or (block == 128 and spt == 0):
         return None
     return -(-K // (block * max(spt, 1)))

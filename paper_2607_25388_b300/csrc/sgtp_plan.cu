@@ -731,6 +731,9 @@ __device__ void mppi_update(const PlanArgs &a, int ag, int T, size_t uo, int rou
 //           once (chosen per round, so that a round fits in one wave where
 //           it can): independent rollouts interleaved in one thread hide
 //           each other's latency, and 168 registers hold three of them.
+// In every SGTP build a round that fits the grid twice over at one sample
+// per thread takes half tiles (the CTA's first half of threads), so that
+// its lone-sample chains spread over twice the CTAs.
 // Every mode computes every sample with the same code.  MPPI selects the
 // GA-IBR-MPPI update (a build of its own, so that the SGTP builds carry none
 // of its code); its kIlp build rolls two samples per thread, so that a tile
@@ -1030,7 +1033,7 @@ __device__ __forceinline__ void plan_body(const PlanArgs &a)
                 const int ni = a.ni[extra];
                 if (ni == 3) best = tile_keys<MAXO, 3>(S, a, k0, round, flag);
                 else if (ni == 2) best = tile_keys<MAXO, 2>(S, a, k0, round, flag);
-                else best = tile_keys<MAXO, 1>(S, a, k0, round, flag);
+                else if (threadIdx.x < (unsigned)a.tile[extra]) best = tile_keys<MAXO, 1>(S, a, k0, round, flag);
             } else {
                 for (unsigned j = threadIdx.x; j < (unsigned)a.tile[extra]; j += blockDim.x) {
                     const unsigned k = (unsigned)t * a.tile[extra] + j;
@@ -1260,6 +1263,11 @@ sgtp_status launch_plan_v(PlanArgs &a, int block, int ctas, int spt, cudaStream_
         }
         a.ni[e] = ni;
         a.tile[e] = MPPI ? kTileSingle : block * ni;
+        // a round that fits twice over in one wave at one sample per thread
+        // takes half tiles (one sample for each thread of the CTA's first
+        // half): its lone-sample chains then spread over twice the CTAs
+        if (!MPPI && ni <= 1 && spt <= 1 && (MODE != kIlp || spt == 0) && 2 * cand[e] <= (long long)grid * block)
+            a.tile[e] = block / 2;
         a.tiles[e] = (a.K + a.tile[e] - 1) / a.tile[e];
         a.items[e] = (e ? a.n_races : a.n_agents) * a.tiles[e];
         a.w[e] = (e ? a.w_units_ego : a.w_units_all) * a.tiles[e];

@@ -38,8 +38,10 @@ def test_launch_shapes_give_identical_plans():
     ref = plan(sc, p, 1000, 2, 3, trk)
     assert ref["status"][0] == 0
     Q = P().SCHEDULE_QUEUE
+    # (128, 0, ...): the 128-thread build choosing per round; these rounds fit
+    # the grid twice over, so they run half tiles of 64 samples
     for block, spt, ctas, sched in ((128, 1, 0, 0), (128, 2, 0, 0), (128, 3, 1, 0), (256, 1, 0, 0), (256, 1, 2, 0),
-                                    (0, 0, 0, Q), (128, 3, 1, Q), (256, 1, 2, Q)):
+                                    (0, 0, 0, Q), (128, 3, 1, Q), (256, 1, 2, Q), (128, 0, 0, 0), (128, 0, 0, Q)):
         got = plan(sc, p, 1000, 2, 3, trk, P().launch_opts(block=block, samples_per_thread=spt, ctas_per_sm=ctas,
                                                            schedule=sched))
         for k in ("xi", "k_star", "U", "xi_hist", "u_hist"):
