@@ -12,6 +12,8 @@
 5b. the same three samplers with 32 ten-car races per launch (per-plan time when the GPU is full);
 6. the GA-IBR-MPPI ablation (path-integral update, lambda = 1e4) of the ten-car plan next to SGTP at the
    same K, direct launch;
+7. planning time against the number of vehicles (n_v = 2..10 on one track), at the full-scale sampling
+   and at the paper's sample counts (K = 128, H = 12, L = 2);
 oracle: the FP64 CPU oracle on the host's cores for configurations 1 (in full), 2 and 3 (plans at
    reduced K, scaled linearly in K, and one full-K ten-car response for the record) and 4 (a subset of
    the races at reduced K), with the core count and CPU model.
@@ -254,6 +256,31 @@ def _oracle_line(config, seconds, steps, **extra):
     return d
 
 
+def config7(reps):
+    """Planning time against the number of vehicles (the scalability study of
+    Sec. IV-G): grid starts of n_v = 2..10 cars on one Fourier track, at the
+    full-scale sampling (K = 16384, T = 60, L = 5) and at the paper's sample
+    counts (K = 128, H = 12, L = 2; the full-scale tracks and parameters)."""
+    p = S.params_fullscale()
+    track = S.fourier_track(200)
+    trk = Track.from_data(track)
+    Kp, Tp, Lp = S.PAPER_SAMPLES
+    for K, T, L in ((16384, 60, 5), (Kp, Tp, Lp)):
+        for n_v in (2, 3, 4, 6, 8, 10):
+            sc = S.grid_race(track, n_v, T, K, L, 211)
+            X0, vs = torch.as_tensor(sc.X0).cuda(), torch.as_tensor(sc.vref_scale).cuda()
+            U0 = torch.as_tensor(sc.U0).cuda()
+            U = U0.clone()
+            holder = {}
+
+            def direct():
+                U.copy_(U0)
+                holder["o"] = ibr_plan(trk, p, X0, U, vs, T, K, L, ego=sc.ego, seed=3, out=holder.get("o"))
+
+            _line(f"7: planning time vs vehicles, n_v={n_v}, K={K}, T={T}, L={L}", _median_ms(direct, reps),
+                  R.rollout_steps_plan(n_v, K, T, L), R.flops_plan(n_v, K, T, L), n_v=n_v)
+
+
 def oracle(reps):
     """The FP64 oracle's rate on this host (all cores; the oracle's own
     thread pool over samples)."""
@@ -301,10 +328,10 @@ def oracle(reps):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--reps", type=int, default=50)
-    ap.add_argument("--configs", type=str, default="1,2,3,4,5,5b,6,oracle")
+    ap.add_argument("--configs", type=str, default="1,2,3,4,5,5b,6,7,oracle")
     args = ap.parse_args(argv)
     fns = {"1": config1, "2": config2, "3": config3, "4": config4, "5": config5, "5b": config5_batched,
-           "6": config6, "oracle": oracle}
+           "6": config6, "7": config7, "oracle": oracle}
     for c in args.configs.split(","):
         fns[c.strip()](args.reps)
 
