@@ -524,7 +524,7 @@ template <int MAXO>
 static size_t br_smem(const BRArgs &) { return BRTile<MAXO>::kBytes; }
 
 template <int MAXO>
-static sgtp_status launch_rollout(const BRArgs &a, bool key_mode, cudaStream_t s, int grid)
+static sgtp_status launch_rollout(const BRArgs &a, bool key_mode, cudaStream_t s, int grid, int block)
 {
     // the shared-memory opt-in applies to the current device only
     static PerDeviceFlag configured;
@@ -539,9 +539,9 @@ static sgtp_status launch_rollout(const BRArgs &a, bool key_mode, cudaStream_t s
     });
     if (cst) return cst;
     if (key_mode)
-        br_rollout_kernel<MAXO, true><<<grid, 256, br_smem<MAXO>(a), s>>>(a);
+        br_rollout_kernel<MAXO, true><<<grid, block, br_smem<MAXO>(a), s>>>(a);
     else
-        br_rollout_kernel<MAXO, false><<<grid, 256, br_smem<MAXO>(a), s>>>(a);
+        br_rollout_kernel<MAXO, false><<<grid, block, br_smem<MAXO>(a), s>>>(a);
     return SGTP_OK;
 }
 
@@ -590,7 +590,14 @@ static sgtp_status br_common(const sgtp_track *trk, int32_t track_id, const sgtp
 static sgtp_status br_launch(const BRArgs &a, int maxo, bool key_mode, const float *x0, const float *opp,
                              float vref_scale, cudaStream_t s)
 {
-    const int grid = (a.K + 255) / 256;
+    // a response of at most 128 samples per SM runs 128-thread CTAs: its
+    // lone-sample chains then spread over twice the SMs (every sample is
+    // computed the same way in either shape)
+    int dev = 0, sms = 0;
+    SGTP_CUDA(cudaGetDevice(&dev));
+    SGTP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int block = (long long)a.K <= 128ll * sms ? 128 : 256;
+    const int grid = (a.K + block - 1) / block;
     static PerDeviceFlag prep_configured;
     const sgtp_status cst = once_per_device(prep_configured, []() -> sgtp_status {
         SGTP_CUDA(cudaFuncSetAttribute(br_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
@@ -602,10 +609,10 @@ static sgtp_status br_launch(const BRArgs &a, int maxo, bool key_mode, const flo
                                              (unsigned char *)a.ws, a.off_ref, a.off_opp, a.off_osum, a.off_odbar);
     sgtp_status st;
     switch (maxo) {
-        case 1: st = launch_rollout<1>(a, key_mode, s, grid); break;
-        case 3: st = launch_rollout<3>(a, key_mode, s, grid); break;
-        case 9: st = launch_rollout<9>(a, key_mode, s, grid); break;
-        default: st = launch_rollout<15>(a, key_mode, s, grid); break;
+        case 1: st = launch_rollout<1>(a, key_mode, s, grid, block); break;
+        case 3: st = launch_rollout<3>(a, key_mode, s, grid, block); break;
+        case 9: st = launch_rollout<9>(a, key_mode, s, grid, block); break;
+        default: st = launch_rollout<15>(a, key_mode, s, grid, block); break;
     }
     if (st) return st;
     count_launch(2);

@@ -428,6 +428,38 @@ __device__ __forceinline__ void reference_traj(const TrackView &tv, const SegWin
     }
 }
 
+// Segments of track from a vehicle's own segment that a setup stages in
+// shared memory for its reference recursion (vertex, chord, arc length and
+// the heading/speed coefficients; 52 bytes each).  A 60-step reference at
+// up to 3 m per step spans about 100 segments of 1.8 m, and the recursion's
+// block of 32 lanes reaches up to 31 segments past its progress; whatever
+// lies beyond the staged stretch is read from global memory.
+constexpr int kRefSegs = 152;
+constexpr unsigned kRefStretchBytes = 52u * kRefSegs;
+
+// Stage the stretch from segment j0 into dst (16-byte aligned, all threads
+// of the CTA; the caller synchronises before the recursion reads it).  The
+// copies are the values the recursion would read from global memory, so the
+// reference is the same bit for bit.  Returns the window for reference_traj
+// and its coefficient array in Cw.
+__device__ __forceinline__ SegWindow stage_ref_stretch(const TrackView &tv, int j0, void *dst, const float4 *&Cw)
+{
+    float4 *A = (float4 *)dst;
+    float4 *B = A + kRefSegs;
+    float4 *C = B + kRefSegs;
+    float *Sv = (float *)(C + kRefSegs);
+    const int Wn = min(kRefSegs, tv.N);
+    for (int r = threadIdx.x; r < Wn; r += blockDim.x) {
+        const int g = wrap_index(j0 + r, tv.N);
+        A[r] = __ldg(tv.A + g);
+        B[r] = __ldg(tv.B + g);
+        C[r] = __ldg(tv.C + g);
+        Sv[r] = __ldg(tv.S + g);
+    }
+    Cw = C;
+    return SegWindow{A, B, nullptr, Sv, j0, Wn};
+}
+
 // ---------------------------------------------------------------- Philox4x32-10
 // Salmon et al., SC'11: ten rounds of two 32x32->64 multiplies with a Weyl
 // key schedule.

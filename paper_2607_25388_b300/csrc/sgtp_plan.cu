@@ -281,36 +281,12 @@ __device__ bool grid_barrier(const PlanArgs &a, bool skip_arrival)
 __shared__ const float4 *g_win_track;
 __shared__ int g_win_w0, g_win_lap0, g_win_fix;
 
-// Segments of track from a vehicle's own segment that the setup stages for
-// its reference recursion (vertex, chord, arc length and the heading/speed
-// coefficients; 52 bytes each, in the tile's scratch area).  A 60-step
-// reference at up to 3 m per step spans about 100 segments of 1.8 m, and the
-// recursion's block of 32 lanes reaches up to 31 segments past its progress;
-// whatever lies beyond the staged stretch is read from global memory.
-constexpr int kRefSegs = 152;
-
-// Stage the reference stretch of track from segment j0 (all threads; the
-// caller synchronises before the window is read).  Copies the same values
-// that the recursion would read from global memory, so the reference is
-// unchanged bit for bit.
+// The reference recursion's stretch of track in the tile's scratch area.
 template <int MAXO>
 __device__ __forceinline__ SegWindow stage_ref_window(const TrackView &tv, int j0, const float4 *&Cw)
 {
-    static_assert(kRefSegs * 52 <= (int)BRTile<MAXO>::kScrBytes, "reference stretch exceeds the scratch area");
-    float4 *A = (float4 *)Tile<MAXO>::scratch();
-    float4 *B = A + kRefSegs;
-    float4 *C = B + kRefSegs;
-    float *Sv = (float *)(C + kRefSegs);
-    const int Wn = min(kRefSegs, tv.N);
-    for (int r = threadIdx.x; r < Wn; r += blockDim.x) {
-        const int g = wrap_index(j0 + r, tv.N);
-        A[r] = __ldg(tv.A + g);
-        B[r] = __ldg(tv.B + g);
-        C[r] = __ldg(tv.C + g);
-        Sv[r] = __ldg(tv.S + g);
-    }
-    Cw = C;
-    return SegWindow{A, B, nullptr, Sv, j0, Wn};
+    static_assert(kRefStretchBytes <= BRTile<MAXO>::kScrBytes, "reference stretch exceeds the scratch area");
+    return stage_ref_stretch(tv, j0, Tile<MAXO>::scratch(), Cw);
 }
 
 // Stage the sample window of a vehicle whose state lies on segment j0

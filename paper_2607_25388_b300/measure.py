@@ -33,7 +33,7 @@ import torch
 
 from . import roofline as R
 from . import scenario as S
-from .planner import Batch, PlanGraph, Track, best_response, ibr_plan, launch_opts
+from .planner import Batch, PlanGraph, Track, best_response, br_workspace_bytes, ibr_plan, launch_opts
 
 
 def _times_ms(fn, reps, warmup=5):
@@ -83,8 +83,24 @@ def config1(reps):
     x0, u = torch.as_tensor(sc.X0[0]).cuda(), torch.as_tensor(sc.U0[0]).cuda()
     opp = torch.as_tensor(sc.opp).cuda()
     ms = _median_ms(lambda: best_response(trk, p, x0, u, 1.0, opp, sc.T, sc.K, seed=1), reps)
-    return _line("1: oval single best response, K=1024, T=40, 1 opponent", ms, sc.K * sc.T,
-                 R.flops_best_response(sc.K, sc.T, 1), launches_per_call=3)
+    res = _line("1: oval single best response, K=1024, T=40, 1 opponent", ms, sc.K * sc.T,
+                R.flops_best_response(sc.K, sc.T, 1), launches_per_call=3)
+    # the same three launches captured once in a CUDA graph (workspace and
+    # outputs reused): the response's device time without launch gaps
+    ws = torch.empty(br_workspace_bytes(1, sc.T), dtype=torch.uint8, device="cuda")
+    out = best_response(trk, p, x0, u, 1.0, opp, sc.T, sc.K, seed=1, workspace=ws)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        best_response(trk, p, x0, u, 1.0, opp, sc.T, sc.K, seed=1, workspace=ws, out=out)
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        best_response(trk, p, x0, u, 1.0, opp, sc.T, sc.K, seed=1, workspace=ws, out=out)
+    ms_g = _median_ms(g.replay, reps)
+    _line("1: oval single best response, K=1024, T=40, 1 opponent (CUDA graph replay)", ms_g, sc.K * sc.T,
+          R.flops_best_response(sc.K, sc.T, 1), launches_per_call=3)
+    return res
 
 
 def _plan_lines(name, sc, reps, graph=True, min_graph_reps=0):
