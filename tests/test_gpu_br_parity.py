@@ -187,3 +187,26 @@ def test_vehicles_driving_against_the_track_direction():
     assert_rel_close(g["states"], o["states"], STATE_RTOL, "states")
     assert_frenet_close(g["frenet"], o["frenet"], o["states"], td.xr)
     check_candidates(g, o, "reversed")
+
+
+@pytest.mark.parametrize("K", [1024, 20480])
+def test_best_response_launch_shapes_select_the_oracle_argmin(K):
+    """The standalone response runs its rollouts in 128-thread CTAs while
+    K <= 128 x SMs and in 256-thread CTAs above (20480 > 128 x 148): in both
+    shapes the selection equals the oracle's argmin over all K candidates
+    (Eq. selection) and its sampled candidates match element by element."""
+    P = planner()
+    sc = S.single_br_oval(K=K)
+    p = S.params_fullscale()
+    trk = P.Track.from_data(sc.track)
+    br = P.best_response(trk, p, dev(sc.X0[0]), dev(sc.U0[0]), 1.0, dev(sc.opp), sc.T, K, seed=5, rnd=1)
+    torch.cuda.synchronize()
+    ot = O.Track(sc.track.xr, sc.track.wl, sc.track.wr)
+    o = O.rollout_costs(p, ot, sc.X0[0], sc.U0[0], 1.0, sc.opp, sc.T, K=K, seed=5, rnd=1)
+    ko, _ = O.select(o["cost"], o["feasible"], o["violation"])
+    assert selection_ok(br["k_star"].item(), ko, o["cost"], o["feasible"], o["violation"], o["margins"])
+    assert br["any_feasible"].item() == int(o["feasible"].any())
+    kl = np.unique(np.concatenate([np.arange(0, 32), np.random.default_rng(K).integers(0, K, 96), [K - 1]]))
+    g, oo, _ = run_both(sc.track, p, sc.X0[0], sc.U0[0], 1.0, sc.opp, sc.T, K, k_list=kl, seed=5, rnd=1,
+                        want_states=False)
+    check_candidates(g, oo, f"oval K={K}")
